@@ -1,0 +1,236 @@
+"""FP64 CPU oracle for the passing-point search (ZJUNlict 2019, Sec. 4.1-4.4).
+
+TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only code allowed to import this
+package.  It shares no code with the CUDA path: it takes plain float64
+arrays, defines its own grid rule and loads its own C library
+(``pps_oracle.c``, compiled with gcc, no fast-math).
+
+Every function here is a thin ctypes marshaller; the arithmetic is in
+``pps_oracle.c``, whose header comment lists the readings of the paper.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pps_oracle.c")
+_HDR = os.path.join(_HERE, "pps_oracle.h")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+
+# Scalar record and parameter layouts (pps_oracle.h).
+SCALARS = ("ball_x", "ball_y", "ball_decel", "vmax", "amax",
+           "field_len", "field_wid", "goal_width")
+PARAMS = ("w_angle", "w_dist", "w_margin", "margin_cap", "tau_safe",
+          "robot_radius", "reach_radius", "min_pass_dist")
+
+
+def build(force: bool = False, src: str = _SRC, out: str = _LIB) -> str:
+    """Compile the oracle library (gcc -O2 -fopenmp, no fast-math)."""
+    hdr_dir = os.path.dirname(os.path.abspath(src))
+    stale = (not os.path.exists(out)
+             or os.path.getmtime(out) < max(os.path.getmtime(src),
+                                            os.path.getmtime(_HDR)))
+    if force or stale:
+        tmp = out + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp",
+               "-Wall", "-Wextra", "-I", _HERE, "-I", hdr_dir, "-o", tmp, src,
+               "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, out)
+    return out
+
+
+def _bind(lib):
+    d, i, p = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+    lib.pps_oracle_ball_time.restype = d
+    lib.pps_oracle_ball_time.argtypes = [d, d, d]
+    lib.pps_oracle_intercept_time.restype = d
+    lib.pps_oracle_intercept_time.argtypes = [d] * 9
+    lib.pps_oracle_min_intercept.restype = d
+    lib.pps_oracle_min_intercept.argtypes = [p, d, d, d]
+    lib.pps_oracle_margin.restype = d
+    lib.pps_oracle_margin.argtypes = [p, d, d, d, d, p, p]
+    lib.pps_oracle_shot_angle.restype = d
+    lib.pps_oracle_shot_angle.argtypes = [p, d, d, d]
+    lib.pps_oracle_score.restype = d
+    lib.pps_oracle_score.argtypes = [p, p, d, d, d]
+    lib.pps_oracle_grid.restype = None
+    lib.pps_oracle_grid.argtypes = [d, d, d, p, p, p, p]
+    lib.pps_oracle_search.restype = i
+    lib.pps_oracle_search.argtypes = (
+        [i, p, p, p, i, p, d, i, i, d, d, p, i, p] + [p] * 8 + [i, i])
+    lib.pps_oracle_max_threads.restype = i
+    lib.pps_oracle_max_threads.argtypes = []
+    return lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+class _State(ctypes.Structure):
+    _fields_ = [("sc", ctypes.c_void_p), ("n_opp", ctypes.c_int),
+                ("opp", ctypes.c_void_p), ("K", ctypes.c_int)]
+
+
+class State:
+    """One state in the oracle's own layout (all float64).
+
+    ``scalars``: dict with the keys of ``SCALARS``; ``opp``: (n, 4) array of
+    x, y, vx, vy; ``K``: samples per pass line.
+    """
+
+    def __init__(self, scalars: dict, opp, K: int):
+        self.sc = np.array([float(scalars[k]) for k in SCALARS], np.float64)
+        self.opp = np.ascontiguousarray(
+            np.asarray(opp, np.float64).reshape(-1, 4))
+        self.K = int(K)
+        self._c = _State(_ptr(self.sc), self.opp.shape[0], _ptr(self.opp),
+                         self.K)
+
+    @property
+    def ref(self):
+        return ctypes.byref(self._c)
+
+
+class Oracle:
+    """The oracle's entry points over one loaded copy of the C library.
+
+    ``Oracle()`` uses ``pps_oracle.c``; ``Oracle(path)`` loads another build
+    of it (the tests load deliberately broken copies to show that the pins
+    catch them)."""
+
+    def __init__(self, lib_path: str | None = None):
+        self.lib = _bind(ctypes.CDLL(lib_path or build()))
+
+    def grid(self, L, W, g):
+        """Grid rule of the oracle: (nx, ny, x0, y0)."""
+        nx, ny = ctypes.c_int(), ctypes.c_int()
+        x0, y0 = ctypes.c_double(), ctypes.c_double()
+        self.lib.pps_oracle_grid(float(L), float(W), float(g),
+                                 ctypes.byref(nx), ctypes.byref(ny),
+                                 ctypes.byref(x0), ctypes.byref(y0))
+        return nx.value, ny.value, x0.value, y0.value
+
+    def ball_time(self, s, v, a):
+        return self.lib.pps_oracle_ball_time(float(s), float(v), float(a))
+
+    def intercept_time(self, o, u, p, vmax, amax, reach=0.0):
+        return self.lib.pps_oracle_intercept_time(
+            float(o[0]), float(o[1]), float(u[0]), float(u[1]), float(p[0]),
+            float(p[1]), float(vmax), float(amax), float(reach))
+
+    def min_intercept(self, state: State, p, reach=0.0):
+        return self.lib.pps_oracle_min_intercept(state.ref, float(p[0]),
+                                                 float(p[1]), float(reach))
+
+    def margin(self, state: State, c, v, reach=0.0):
+        """(margin, reachable, T[K]) of the pass to point c at speed v."""
+        T = np.empty(state.K, np.float64)
+        r = ctypes.c_int()
+        m = self.lib.pps_oracle_margin(state.ref, float(c[0]), float(c[1]),
+                                       float(v), float(reach), _ptr(T),
+                                       ctypes.byref(r))
+        return m, bool(r.value), T
+
+    def shot_angle(self, state: State, c, r):
+        return self.lib.pps_oracle_shot_angle(state.ref, float(c[0]),
+                                              float(c[1]), float(r))
+
+    def score(self, state: State, params: dict, c, m):
+        prm = np.array([float(params[k]) for k in PARAMS], np.float64)
+        return self.lib.pps_oracle_score(state.ref, _ptr(prm), float(c[0]),
+                                         float(c[1]), float(m))
+
+    def search(self, batch: dict, grid_spec, speeds, params: dict, *,
+               dense=False, want_T=False, n_threads=0):
+        """Run the oracle over a batch.
+
+        ``batch``: arrays of a seeded input batch (promoted to float64):
+        ball (S,2), n_opp (S,), opp_pos (S,J,2), opp_vel (S,J,2), ball_decel,
+        vmax, amax, field_len, field_wid, goal_width (S,), K (S,).
+        ``grid_spec``: (g, nx, ny, x0, y0).  Returns a dict of numpy arrays.
+        """
+        ball = np.asarray(batch["ball"], np.float64)
+        S = ball.shape[0]
+        sc = np.stack([ball[:, 0], ball[:, 1]]
+                      + [np.asarray(batch[k], np.float64)
+                         for k in SCALARS[2:]], axis=1)
+        sc = np.ascontiguousarray(sc)
+        opp_pos = np.asarray(batch["opp_pos"], np.float64)
+        opp_vel = np.asarray(batch["opp_vel"], np.float64)
+        J = opp_pos.shape[1]
+        opp = np.ascontiguousarray(np.concatenate([opp_pos, opp_vel], axis=2))
+        n_opp = np.ascontiguousarray(np.asarray(batch["n_opp"], np.int32))
+        K = np.ascontiguousarray(np.asarray(batch["K"], np.int32))
+        g, nx, ny, x0, y0 = grid_spec
+        P = int(nx) * int(ny)
+        sp = np.ascontiguousarray(np.asarray(speeds, np.float64))
+        V = sp.shape[0]
+        prm = np.array([float(params[k]) for k in PARAMS], np.float64)
+        out = {
+            "best_idx": np.empty(S, np.int64),
+            "best_score": np.empty(S, np.float64),
+            "best_margin": np.empty(S, np.float64),
+            "n_feasible": np.empty(S, np.int64),
+        }
+        kstride = int(K.max()) if S else 1
+        if dense:
+            out["feasible"] = np.empty((S, V, P), np.uint8)
+            out["margin"] = np.empty((S, V, P), np.float64)
+            out["score"] = np.empty((S, V, P), np.float64)
+        if want_T:
+            out["T"] = np.empty((S, P, kstride), np.float64)
+        rc = self.lib.pps_oracle_search(
+            S, _ptr(sc), _ptr(n_opp), _ptr(K), J, _ptr(opp), float(g),
+            int(nx), int(ny), float(x0), float(y0), _ptr(sp), V, _ptr(prm),
+            _ptr(out["best_idx"]), _ptr(out["best_score"]),
+            _ptr(out["best_margin"]), _ptr(out["n_feasible"]),
+            _ptr(out.get("feasible")), _ptr(out.get("margin")),
+            _ptr(out.get("score")), _ptr(out.get("T")), kstride,
+            int(n_threads))
+        if rc != 0:
+            raise ValueError("oracle rejected the batch")
+        return out
+
+    def max_threads(self) -> int:
+        return self.lib.pps_oracle_max_threads()
+
+
+def state_of(batch: dict, s: int) -> State:
+    """State ``s`` of a batch, in the oracle's layout."""
+    n = int(batch["n_opp"][s])
+    opp = np.concatenate([np.asarray(batch["opp_pos"][s, :n], np.float64),
+                          np.asarray(batch["opp_vel"][s, :n], np.float64)],
+                         axis=1)
+    sc = {"ball_x": batch["ball"][s][0], "ball_y": batch["ball"][s][1]}
+    for k in SCALARS[2:]:
+        sc[k] = batch[k][s]
+    return State(sc, opp, int(batch["K"][s]))
+
+
+def default() -> Oracle:
+    """The oracle built from ``pps_oracle.c`` (loaded once)."""
+    global _default
+    with _lock:
+        if _default is None:
+            _default = Oracle()
+        return _default
+
+
+_default = None
+
+
+def __getattr__(name):
+    # Module-level shortcuts: oracle.ball_time(...) == default().ball_time(...)
+    if name in ("grid", "ball_time", "intercept_time", "min_intercept",
+                "margin", "shot_angle", "score", "search", "max_threads"):
+        return getattr(default(), name)
+    raise AttributeError(name)

@@ -1,0 +1,310 @@
+/*
+ * pps_oracle.c -- plain FP64 CPU oracle for the passing-point search of the
+ * ZJUNlict 2019 team description paper.
+ *
+ * TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's
+ * CPU-baseline leg are its only callers.  It shares nothing with the CUDA
+ * path.  It is written to be read against the paper, not to be fast: every
+ * candidate pass recomputes every intercept time, loops run in the order of
+ * the definitions, and nothing is blocked, fused or reordered.
+ *
+ * What the paper fixes and what this file reads into it:
+ *
+ *  Sec. 4.1  The ball is kicked, slides briefly, then rolls with a small
+ *            constant deceleration; the sliding phase is neglected, and
+ *            Eq. 1 relates distance d, time t, speed and the rolling
+ *            deceleration a.  Eq. 1 is garbled in print; read as
+ *            d = v t - a t^2 / 2.  READING: the kick speed is the speed at
+ *            which rolling starts (no 5/7 slide factor on this path).
+ *  Sec. 4.2  A pass is feasible when no opponent can intercept the ball
+ *            (SBIP, cited but not defined).  READING: the ball is sampled
+ *            at K points spaced uniformly in distance along the pass line,
+ *            k = 1..K (the kick point excluded, the receiver included); an
+ *            opponent intercepts at sample k when it can be there no later
+ *            than the ball.  The opponent's minimum time is that of a 1-D
+ *            bang-bang motion along the line to the sample: full
+ *            acceleration amax toward it, speed capped at vmax, starting
+ *            from the component of its velocity toward the sample (the
+ *            perpendicular component dropped), arriving at any speed.
+ *  Sec. 4.3  Score = sum_i w_i x_i (Eq. 3); lengths and angles divided by
+ *            their upper bound, times unchanged.  Features used here: shot
+ *            angle at the receiver (angle / pi), distance from the receiver
+ *            to the opponent goal (/ field diagonal, counted negatively:
+ *            shorter is better) and the intercept-time margin (capped).
+ *  Sec. 4.4  Shot angle: the valid angle to the goal given the opponents'
+ *            positions.  READING: the largest contiguous part of the goal
+ *            mouth's angular interval not covered by any opponent disc.
+ *  Sec. 1 / Sec. 4.3  The best pass is the highest score; READING: ties go
+ *            to the smallest candidate index.
+ */
+#include "pps_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---- C1: the candidate grid (Sec. 5.1 rasterises at a fixed spacing) ---- */
+void pps_oracle_grid(double L, double W, double g, int* nx, int* ny,
+                     double* x0, double* y0)
+{
+    /* Field corners are included: 12 m at 0.1 m gives 121 columns. */
+    *nx = (int)lround(L / g) + 1;
+    *ny = (int)lround(W / g) + 1;
+    *x0 = -0.5 * L;
+    *y0 = -0.5 * W;
+}
+
+/* ---- C2: ball arrival time (Sec. 4.1, Eq. 1) ---- */
+double pps_oracle_ball_time(double s, double v, double a)
+{
+    /* Rolling from speed v with deceleration a: s(t) = v t - a t^2 / 2.
+     * The first time s is reached is the smaller root of a t^2/2 - v t + s,
+     * t = (v - sqrt(v^2 - 2 a s)) / a, written here in the algebraically
+     * equal form 2 s / (v + sqrt(v^2 - 2 a s)), which also covers a = 0.
+     * Past the stopping distance v^2 / (2a) the ball never arrives. */
+    double disc = v * v - 2.0 * a * s;
+    if (disc < 0.0) return INFINITY;
+    return 2.0 * s / (v + sqrt(disc));
+}
+
+/* ---- C3: opponent minimum intercept time (Sec. 4.2, SBIP) ---- */
+double pps_oracle_intercept_time(double ox, double oy, double ux, double uy,
+                                 double px, double py, double vmax,
+                                 double amax, double reach)
+{
+    double dx = px - ox, dy = py - oy;
+    double d = sqrt(dx * dx + dy * dy);
+    if (d <= reach) return 0.0; /* already within reach */
+
+    /* Velocity component along the line toward the sample point. */
+    double w = (ux * dx + uy * dy) / d;
+    if (w > vmax) w = vmax;
+    if (w < -vmax) w = -vmax;
+
+    /* Distance the centre must cover to come within reach. */
+    double dist = d - reach;
+
+    /* Accelerate at amax toward the point until the speed reaches vmax:
+     * that takes (vmax - w)/amax and covers (vmax^2 - w^2)/(2 amax). */
+    double t_top = (vmax - w) / amax;
+    double d_top = (vmax * vmax - w * w) / (2.0 * amax);
+    if (dist <= d_top) {
+        /* Arrives while still accelerating: w t + amax t^2 / 2 = dist. */
+        return (-w + sqrt(w * w + 2.0 * amax * dist)) / amax;
+    }
+    /* Otherwise cruise the rest at vmax. */
+    return t_top + (dist - d_top) / vmax;
+}
+
+double pps_oracle_min_intercept(const pps_oracle_state* st, double px,
+                                double py, double reach)
+{
+    double vmax = st->sc[PPS_ORACLE_VMAX], amax = st->sc[PPS_ORACLE_AMAX];
+    double T = INFINITY;
+    for (int j = 0; j < st->n_opp; ++j) {
+        const double* o = st->opp + 4 * j;
+        double t = pps_oracle_intercept_time(o[0], o[1], o[2], o[3], px, py,
+                                             vmax, amax, reach);
+        if (t < T) T = t;
+    }
+    return T;
+}
+
+/* ---- C4: margin and reachability of one candidate pass ---- */
+double pps_oracle_margin(const pps_oracle_state* st, double cx, double cy,
+                         double v, double reach, double* T_out,
+                         int* reachable)
+{
+    double bx = st->sc[PPS_ORACLE_BALL_X], by = st->sc[PPS_ORACLE_BALL_Y];
+    double a = st->sc[PPS_ORACLE_BALL_DECEL];
+    double D = sqrt((cx - bx) * (cx - bx) + (cy - by) * (cy - by));
+    int reach_ok = (v * v - 2.0 * a * D >= 0.0);
+    if (reachable) *reachable = reach_ok;
+
+    double m = INFINITY;
+    int K = st->K;
+    for (int k = 1; k <= K; ++k) {
+        double f = (double)k / (double)K;
+        /* Sample k on the pass line and the distance the ball rolls to it. */
+        double px = bx + f * (cx - bx);
+        double py = by + f * (cy - by);
+        double s = f * D;
+        double T = pps_oracle_min_intercept(st, px, py, reach);
+        if (T_out) T_out[k - 1] = T;
+        if (reach_ok) {
+            double tb = pps_oracle_ball_time(s, v, a);
+            double diff = T - tb;
+            if (diff < m) m = diff;
+        }
+    }
+    /* A ball that stops short arrives at time +inf: margin -inf. */
+    return reach_ok ? m : -INFINITY;
+}
+
+/* ---- C6: shot angle (Sec. 4.3 feature, Sec. 4.4 "valid angle") ---- */
+double pps_oracle_shot_angle(const pps_oracle_state* st, double cx,
+                             double cy, double r)
+{
+    double gx = 0.5 * st->sc[PPS_ORACLE_FIELD_LEN];
+    double hw = 0.5 * st->sc[PPS_ORACLE_GOAL_WIDTH];
+    /* READING: no shot from on or behind the goal line. */
+    if (cx >= gx) return 0.0;
+
+    /* The mouth spans directions lo..hi (both in (-pi/2, pi/2)). */
+    double lo = atan2(-hw - cy, gx - cx);
+    double hi = atan2(hw - cy, gx - cx);
+
+    /* Each opponent disc blocks the directions within asin(r/d) of the
+     * direction to its centre; a disc containing the receiver blocks all. */
+    double s[64], e[64];
+    int n = 0;
+    for (int j = 0; j < st->n_opp && n < 64; ++j) {
+        const double* o = st->opp + 4 * j;
+        double dx = o[0] - cx, dy = o[1] - cy;
+        double d = sqrt(dx * dx + dy * dy);
+        if (d <= r) return 0.0;
+        double phi = atan2(dy, dx);
+        double half = asin(r / d);
+        double a0 = phi - half, a1 = phi + half;
+        if (a1 <= lo || a0 >= hi) continue; /* misses the mouth */
+        s[n] = a0 < lo ? lo : a0;
+        e[n] = a1 > hi ? hi : a1;
+        ++n;
+    }
+    /* Sort the blocked intervals by start (insertion sort), then sweep. */
+    for (int i = 1; i < n; ++i) {
+        double si = s[i], ei = e[i];
+        int k = i - 1;
+        while (k >= 0 && s[k] > si) {
+            s[k + 1] = s[k];
+            e[k + 1] = e[k];
+            --k;
+        }
+        s[k + 1] = si;
+        e[k + 1] = ei;
+    }
+    double best = 0.0, cur = lo;
+    for (int i = 0; i < n; ++i) {
+        if (s[i] > cur && s[i] - cur > best) best = s[i] - cur;
+        if (e[i] > cur) cur = e[i];
+    }
+    if (hi - cur > best) best = hi - cur;
+    return best;
+}
+
+/* ---- C5: value function (Sec. 4.3, Eq. 3) ---- */
+double pps_oracle_score(const pps_oracle_state* st, const double* prm,
+                        double cx, double cy, double margin)
+{
+    const double pi = 3.14159265358979323846;
+    double L = st->sc[PPS_ORACLE_FIELD_LEN], W = st->sc[PPS_ORACLE_FIELD_WID];
+    double theta = pps_oracle_shot_angle(st, cx, cy,
+                                         prm[PPS_ORACLE_ROBOT_RADIUS]);
+    double gdx = 0.5 * L - cx, gdy = 0.0 - cy;
+    double dist_goal = sqrt(gdx * gdx + gdy * gdy);
+    double diag = sqrt(L * L + W * W);
+    double mcap = margin < prm[PPS_ORACLE_MARGIN_CAP]
+                      ? margin
+                      : prm[PPS_ORACLE_MARGIN_CAP];
+    return prm[PPS_ORACLE_W_ANGLE] * theta / pi
+         - prm[PPS_ORACLE_W_DIST] * dist_goal / diag
+         + prm[PPS_ORACLE_W_MARGIN] * mcap;
+}
+
+/* ---- C1..C7 for one state ---- */
+static void search_one(const pps_oracle_state* st, double g, int nx, int ny,
+                       double x0, double y0, const double* speeds, int V,
+                       const double* prm, int64_t* best_idx,
+                       double* best_score, double* best_margin,
+                       int64_t* n_feasible, uint8_t* feas, double* marg,
+                       double* score, double* T, int kstride)
+{
+    int64_t P = (int64_t)nx * ny;
+    double bx = st->sc[PPS_ORACLE_BALL_X], by = st->sc[PPS_ORACLE_BALL_Y];
+    double reach = prm[PPS_ORACLE_REACH_RADIUS];
+    int64_t bi = -1;
+    double bs = -INFINITY, bm = -INFINITY;
+    int64_t nf = 0;
+
+    for (int v = 0; v < V; ++v) {
+        for (int iy = 0; iy < ny; ++iy) {
+            for (int ix = 0; ix < nx; ++ix) {
+                int64_t p = (int64_t)iy * nx + ix;
+                int64_t idx = (int64_t)v * P + p;
+                double cx = x0 + ix * g, cy = y0 + iy * g;
+                double D = sqrt((cx - bx) * (cx - bx) + (cy - by) * (cy - by));
+                int reachable = 0;
+                double* Tk = (T && v == 0) ? T + p * kstride : NULL;
+                double m = pps_oracle_margin(st, cx, cy, speeds[v], reach, Tk,
+                                             &reachable);
+                int ok = reachable && D >= prm[PPS_ORACLE_MIN_PASS_DIST]
+                         && m > prm[PPS_ORACLE_TAU_SAFE];
+                double sc = ok ? pps_oracle_score(st, prm, cx, cy, m)
+                               : -INFINITY;
+                if (feas) feas[idx] = (uint8_t)ok;
+                if (marg) marg[idx] = m;
+                if (score) score[idx] = sc;
+                if (ok) {
+                    ++nf;
+                    /* Highest score; equal scores go to the smaller idx. */
+                    if (bi < 0 || sc > bs || (sc == bs && idx < bi)) {
+                        bi = idx;
+                        bs = sc;
+                        bm = m;
+                    }
+                }
+            }
+        }
+    }
+    *best_idx = bi;
+    *best_score = bs;
+    *best_margin = bm;
+    *n_feasible = nf;
+}
+
+int pps_oracle_search(int S, const double* sc, const int* n_opp,
+                      const int* K, int jstride, const double* opp,
+                      double g, int nx, int ny, double x0, double y0,
+                      const double* speeds, int V, const double* prm,
+                      int64_t* best_idx, double* best_score,
+                      double* best_margin, int64_t* n_feasible,
+                      uint8_t* feasible, double* margin, double* score,
+                      double* T, int kstride, int n_threads)
+{
+    if (S < 0 || V < 1 || nx < 1 || ny < 1 || !(g > 0.0)) return -1;
+    for (int s = 0; s < S; ++s)
+        if (n_opp[s] < 0 || n_opp[s] > jstride || K[s] < 1
+            || (T && K[s] > kstride))
+            return -1;
+    int64_t P = (int64_t)nx * ny;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int s = 0; s < S; ++s) {
+        pps_oracle_state st;
+        st.sc = sc + (int64_t)s * PPS_ORACLE_NSCALAR;
+        st.n_opp = n_opp[s];
+        st.opp = opp + (int64_t)s * jstride * 4;
+        st.K = K[s];
+        search_one(&st, g, nx, ny, x0, y0, speeds, V, prm, best_idx + s,
+                   best_score + s, best_margin + s, n_feasible + s,
+                   feasible ? feasible + (int64_t)s * V * P : NULL,
+                   margin ? margin + (int64_t)s * V * P : NULL,
+                   score ? score + (int64_t)s * V * P : NULL,
+                   T ? T + (int64_t)s * P * kstride : NULL, kstride);
+    }
+    (void)n_threads;
+    return 0;
+}
+
+int pps_oracle_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,157 @@
+"""Seeded synthetic game states shaped like RoboCup SSL play.
+
+This module only draws inputs; it holds none of the search's arithmetic, so
+both the CUDA path and the CPU oracle can be fed from it.  All arrays are
+float32 (int32 for counts), the precision the search takes its inputs in.
+
+Recipe (the paper's match logs are not available; uniform states stand in):
+  * ball and every robot: position uniform over the field rectangle
+    [-L/2, L/2] x [-W/2, W/2];
+  * robot velocity: speed uniform in [0, vmax], heading uniform in [0, 2 pi);
+  * optional "marked" layout: each opponent placed U[0.3, 1.0] m from a
+    random teammate in a uniform direction (clipped to the field), the
+    crowded regime the paper describes for surrounded receivers;
+  * generator: numpy PCG64 with a fixed seed per workload, draws in a fixed
+    order, so a (seed, sizes) pair always gives the same batch.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field as dc_field
+
+import numpy as np
+
+# Value-function and feasibility parameters.  The paper states that the
+# weights are tuned by hand and gives no values; these are the defaults of
+# the build (weights 1, margin capped at 1 s, no safety threshold).  Robot
+# radius 0.09 m and goal widths are SSL rule values.
+DEFAULT_PARAMS = {
+    "w_angle": 1.0,
+    "w_dist": 1.0,
+    "w_margin": 1.0,
+    "margin_cap": 1.0,
+    "tau_safe": 0.0,
+    "robot_radius": 0.09,
+    "reach_radius": 0.0,
+    "min_pass_dist": 0.0,
+}
+
+GOAL_WIDTH = {(12.0, 9.0): 1.8, (9.0, 6.0): 1.0}
+
+
+def ssl_states(seed: int, n_states: int, *, field_len: float = 12.0,
+               field_wid: float = 9.0, goal_width: float | None = None,
+               n_opp: int = 8, j_stride: int | None = None, n_team: int = 8,
+               K: int = 64, ball_decel: float = 0.5, vmax: float = 3.25,
+               amax: float = 3.0, marked: bool = False) -> dict:
+    """A batch of ``n_states`` states with identical shape parameters."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return _draw(rng, n_states, field_len, field_wid, goal_width, n_opp,
+                 j_stride or n_opp, n_team, K, ball_decel, vmax, amax, marked)
+
+
+def _draw(rng, S, L, W, gw, J, jstride, nteam, K, decel, vmax, amax, marked):
+    if gw is None:
+        gw = GOAL_WIDTH.get((float(L), float(W)), 1.8)
+    lo = np.array([-L / 2, -W / 2])
+    hi = np.array([L / 2, W / 2])
+    ball = rng.uniform(lo, hi, size=(S, 2))
+    team = rng.uniform(lo, hi, size=(S, nteam, 2))
+    tspeed = rng.uniform(0.0, vmax, size=(S, nteam))
+    thead = rng.uniform(0.0, 2 * math.pi, size=(S, nteam))
+    opp = rng.uniform(lo, hi, size=(S, J, 2))
+    ospeed = rng.uniform(0.0, vmax, size=(S, J))
+    ohead = rng.uniform(0.0, 2 * math.pi, size=(S, J))
+    if marked and nteam > 0:
+        mate = rng.integers(0, nteam, size=(S, J))
+        dist = rng.uniform(0.3, 1.0, size=(S, J))
+        ang = rng.uniform(0.0, 2 * math.pi, size=(S, J))
+        base = np.take_along_axis(team, mate[..., None], axis=1)
+        off = np.stack([dist * np.cos(ang), dist * np.sin(ang)], axis=-1)
+        opp = np.clip(base + off, lo, hi)
+    opp_pos = np.zeros((S, jstride, 2), np.float32)
+    opp_vel = np.zeros((S, jstride, 2), np.float32)
+    opp_pos[:, :J] = opp
+    opp_vel[:, :J, 0] = ospeed * np.cos(ohead)
+    opp_vel[:, :J, 1] = ospeed * np.sin(ohead)
+    team_vel = np.stack([tspeed * np.cos(thead), tspeed * np.sin(thead)], -1)
+    full = lambda x, dt=np.float32: np.full(S, x, dt)  # noqa: E731
+    return {
+        "ball": ball.astype(np.float32),
+        "n_opp": full(J, np.int32),
+        "opp_pos": opp_pos,
+        "opp_vel": opp_vel,
+        "team_pos": team.astype(np.float32),
+        "team_vel": team_vel.astype(np.float32),
+        "ball_decel": full(decel),
+        "vmax": full(vmax),
+        "amax": full(amax),
+        "field_len": full(L),
+        "field_wid": full(W),
+        "goal_width": full(gw),
+        "K": full(K, np.int32),
+    }
+
+
+def concat(batches: list[dict]) -> dict:
+    """Concatenate batches along the state axis (padding opponent slots)."""
+    J = max(b["opp_pos"].shape[1] for b in batches)
+    out = {}
+    for k in batches[0]:
+        parts = []
+        for b in batches:
+            x = b[k]
+            if k in ("opp_pos", "opp_vel") and x.shape[1] < J:
+                pad = np.zeros((x.shape[0], J - x.shape[1], 2), x.dtype)
+                x = np.concatenate([x, pad], axis=1)
+            parts.append(x)
+        if k in ("team_pos", "team_vel"):
+            T = max(p.shape[1] for p in parts)
+            parts = [np.concatenate([p, np.zeros((p.shape[0], T - p.shape[1], 2),
+                                                 p.dtype)], axis=1)
+                     if p.shape[1] < T else p for p in parts]
+        out[k] = np.concatenate(parts, axis=0)
+    return out
+
+
+def take(batch: dict, idx) -> dict:
+    """Sub-batch of the states ``idx``."""
+    return {k: np.ascontiguousarray(v[idx]) for k, v in batch.items()}
+
+
+@dataclass
+class Workload:
+    """A named workload: states plus the shared grid spacing and speeds."""
+    name: str
+    seed: int
+    n_states: int
+    spacing: float
+    speeds: list
+    K: int
+    field: tuple = (12.0, 9.0)
+    n_opp: int = 8
+    ball_decel: float = 0.5
+    vmax: float = 3.25
+    amax: float = 3.0
+    params: dict = dc_field(default_factory=lambda: dict(DEFAULT_PARAMS))
+
+    def states(self, n_states: int | None = None, marked=False) -> dict:
+        return ssl_states(self.seed, self.n_states if n_states is None
+                          else n_states, field_len=self.field[0],
+                          field_wid=self.field[1], n_opp=self.n_opp, K=self.K,
+                          ball_decel=self.ball_decel, vmax=self.vmax,
+                          amax=self.amax, marked=marked)
+
+    def speeds_f32(self):
+        return np.asarray(self.speeds, np.float32)
+
+
+# Plain exact search of one state: 12x9 m, 0.1 m grid (121x91), one kick
+# speed 4 m/s, K = 32, decel 0.5, 8 v 8, vmax 3.25, amax 3.
+SINGLE = Workload("single_12x9_g0.1_v1_K32_J8", seed=0, n_states=1,
+                  spacing=0.1, speeds=[4.0], K=32)
+
+# Batched exact search: 4096 states, 12x9 m, 0.05 m grid (241x181), speeds
+# {2, 3.5, 5, 6.5} m/s, K = 64, 8 v 8.
+BATCHED = Workload("batched_4096x241x181_v4_K64_J8", seed=1, n_states=4096,
+                   spacing=0.05, speeds=[2.0, 3.5, 5.0, 6.5], K=64)

@@ -1,0 +1,106 @@
+"""The oracle's pins catch plausible slips.
+
+Each case copies ``oracle/pps_oracle.c`` to a temporary directory, plants
+one mistake of the kind a careful reader could still make (a dropped
+factor, a flipped sign, a transposed operand, an off-by-one index, a wrong
+comparison), builds that copy with gcc and runs the pin checks of
+test_oracle_pins.py against it.  At least one pin must fail for every
+mutant.  Nothing here touches the real oracle or any GPU.
+"""
+from __future__ import annotations
+
+import os
+import shutil
+
+import pytest
+
+import oracle
+from tests import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "pps_oracle.c")
+
+# (name, original text, planted mistake)
+MUTANTS = [
+    ("ball: dropped factor 2", "double disc = v * v - 2.0 * a * s;",
+     "double disc = v * v - a * s;"),
+    ("ball: wrong root", "return 2.0 * s / (v + sqrt(disc));",
+     "return (v + sqrt(disc)) / a;"),
+    ("intercept: sign in projection", "double w = (ux * dx + uy * dy) / d;",
+     "double w = (ux * dx - uy * dy) / d;"),
+    ("intercept: projection onto o - p", "double w = (ux * dx + uy * dy) / d;",
+     "double w = -(ux * dx + uy * dy) / d;"),
+    ("intercept: clamp dropped", "if (w > vmax) w = vmax;", ";"),
+    ("intercept: d_top missing 2",
+     "double d_top = (vmax * vmax - w * w) / (2.0 * amax);",
+     "double d_top = (vmax * vmax - w * w) / amax;"),
+    ("intercept: cruise term dropped",
+     "return t_top + (dist - d_top) / vmax;", "return t_top + dist / vmax;"),
+    ("intercept: reach ignored in distance", "double dist = d - reach;",
+     "double dist = d;"),
+    ("intercept: accel root sign",
+     "return (-w + sqrt(w * w + 2.0 * amax * dist)) / amax;",
+     "return (w + sqrt(w * w + 2.0 * amax * dist)) / amax;"),
+    ("min over opponents flipped", "if (t < T) T = t;", "if (t > T) T = t;"),
+    ("sample: transposed operand", "double px = bx + f * (cx - bx);",
+     "double px = bx + f * (cy - by);"),
+    ("sample: off-by-one index", "double f = (double)k / (double)K;",
+     "double f = (double)(k - 1) / (double)K;"),
+    ("sample: ball distance not scaled", "double s = f * D;",
+     "double s = D;"),
+    ("margin: operands swapped", "double diff = T - tb;",
+     "double diff = tb - T;"),
+    ("reachability: dropped factor 2",
+     "int reach_ok = (v * v - 2.0 * a * D >= 0.0);",
+     "int reach_ok = (v * v - a * D >= 0.0);"),
+    ("shot: atan for asin", "double half = asin(r / d);",
+     "double half = atan(r / d);"),
+    ("shot: sweep forgets nesting", "if (e[i] > cur) cur = e[i];",
+     "cur = e[i];"),
+    ("shot: lower post sign", "double lo = atan2(-hw - cy, gx - cx);",
+     "double lo = atan2(-hw + cy, gx - cx);"),
+    ("shot: goal at the far edge", "double gx = 0.5 * st->sc[PPS_ORACLE_FIELD_LEN];",
+     "double gx = st->sc[PPS_ORACLE_FIELD_LEN];"),
+    ("score: distance sign", "- prm[PPS_ORACLE_W_DIST] * dist_goal / diag",
+     "+ prm[PPS_ORACLE_W_DIST] * dist_goal / diag"),
+    ("score: goal point", "double gdx = 0.5 * L - cx, gdy = 0.0 - cy;",
+     "double gdx = L - cx, gdy = 0.0 - cy;"),
+    ("score: cap ignored", "? margin\n                      : prm[PPS_ORACLE_MARGIN_CAP];",
+     "? margin\n                      : margin;"),
+    ("argmax: ties to the larger index", "(sc == bs && idx < bi)",
+     "(sc == bs && idx > bi)"),
+    ("grid: edge excluded", "*nx = (int)lround(L / g) + 1;",
+     "*nx = (int)lround(L / g);"),
+]
+
+CHECKS = [pins.check_hand_ball, pins.check_hand_intercept,
+          pins.check_hand_shot, pins.check_hand_score, pins.check_hand_grid,
+          pins.check_invariants, pins.check_shot_closed_form,
+          pins.check_score_closed_form, pins.check_search_tie_rule,
+          pins.check_search_reachability, pins.check_search_consistency,
+          pins.check_ball_vs_sim, pins.check_intercept_vs_sim,
+          pins.check_margin_vs_sim, pins.check_shot_vs_rays,
+          pins.check_intercept_monotone]
+
+
+def _caught(orc):
+    for chk in CHECKS:
+        try:
+            chk(orc)
+        except (AssertionError, ValueError, ZeroDivisionError, OverflowError):
+            return chk.__name__
+    return None
+
+
+@pytest.mark.parametrize("name,orig,mut", MUTANTS,
+                         ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(tmp_path, name, orig, mut):
+    text = open(SRC).read()
+    assert text.count(orig) >= 1, f"mutation site missing: {orig!r}"
+    bad = os.path.join(tmp_path, "pps_oracle.c")
+    with open(bad, "w") as f:
+        f.write(text.replace(orig, mut, 1))
+    shutil.copy(os.path.join(os.path.dirname(SRC), "pps_oracle.h"), tmp_path)
+    lib = oracle.build(force=True, src=bad,
+                       out=os.path.join(tmp_path, "libmutant.so"))
+    caught = _caught(oracle.Oracle(lib))
+    assert caught is not None, f"no pin caught mutant: {name}"
