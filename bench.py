@@ -1,0 +1,409 @@
+#!/usr/bin/env python3
+"""Benchmark of the exact passing-point search on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pps|reference]
+
+One step = one pass of the whole search (state staging, intercept times,
+ball times, margins, shot angles, scores, mask, argmax) over one batch of
+the batched workload: 4096 seeded SSL-shaped states, 12 x 9 m field, 0.05 m
+grid (241 x 181 receive points), kick speeds {2, 3.5, 5, 6.5} m/s, K = 64
+samples per pass, 8 opponents.  Metric: pass-candidate evaluations per
+second, states x points x speeds x opponents / time.
+
+Under torchrun each rank searches its own 4096 states (weak scaling, no
+data-path collective); the barrier and the max over ranks of the timed
+region are the only cross-rank traffic.  Rank 0 prints one JSON line.
+
+--impl reference times the FP64 CPU oracle on the host cores instead,
+each step a bounded sample (16 states) of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pass-candidate evals/s (state×pt×speed×opp)"
+UNIT = "evals/s"
+L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
+CPU_SAMPLE_STATES = 32       # oracle sample for the cpu_baseline key
+REF_SAMPLE_STATES = 16       # oracle sample per step of --impl reference
+
+# Algorithmic work of the formulation the kernel evaluates (FP32 lane-ops,
+# an FMA counted once; MUFU ops counted separately):
+#   per opponent interaction (state, point, sample, opponent): 15 FP32 + 2 MUFU
+#   per ball evaluation (state, point, sample, speed):          3 FP32 + 1 MUFU
+OPS_INTERACTION, MUFU_INTERACTION = 15, 2
+OPS_BALL, MUFU_BALL = 3, 1
+FP32_LANES_PER_SM = 128
+MUFU_LANES_PER_SM = 32   # ncu: XU pipe peak ~1 warp-instr/clk/SM on GB300
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _kernel_src_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1909_07717_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic(digest):
+    """DRAM bytes per launch of the search kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "search_kernel_batched.txt")
+    try:
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_digest") == digest:
+            return float(kv["dram_bytes_per_launch_full"])
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,"
+         "clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.rows = []
+        if self.proc is None:
+            return False
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 8:
+                self.rows.append(parts)
+        return False
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [],
+                    "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[4 + i].lower() == "active"})
+        busy = [s for s in sm if s > 0.5 * max(sm)] if sm else []
+        return {"sm_mhz": statistics.median(busy) if busy else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def _cpu_oracle_rate(w, batch, grid_spec, n_states):
+    """Oracle evals/s on the first n_states states, all host cores."""
+    import oracle
+    from paper_1909_07717_gb300 import synth
+    sub = synth.take(batch, list(range(n_states)))
+    cores = oracle.max_threads()
+    t0 = time.perf_counter()
+    oracle.search(sub, grid_spec, w.speeds, w.params, n_threads=cores)
+    dt = time.perf_counter() - t0
+    P = grid_spec[1] * grid_spec[2]
+    evals = n_states * P * len(w.speeds) * w.n_opp
+    return evals / dt, dt, cores
+
+
+def _workload():
+    from paper_1909_07717_gb300 import synth
+    return synth.BATCHED
+
+
+def _config(w, grid_nx, grid_ny, world, extra=None):
+    cfg = {"workload": w.name, "states_per_gpu": w.n_states,
+           "grid": [grid_nx, grid_ny], "spacing_m": w.spacing,
+           "field_m": list(w.field), "speeds_mps": list(w.speeds),
+           "K": w.K, "opponents": w.n_opp, "ball_decel": w.ball_decel,
+           "vmax": w.vmax, "amax": w.amax, "seed": w.seed,
+           "parallelism": f"state-sharded x{world} (replicas)",
+           "l2": "flushed between timed steps (256 MiB write)"}
+    cfg.update(extra or {})
+    return cfg
+
+
+def run_reference(args):
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    if rank != 0:
+        return 0
+    import oracle
+    w = _workload()
+    batch = w.states()
+    nx, ny, x0, y0 = oracle.grid(w.field[0], w.field[1], np.float32(w.spacing))
+    gs = (float(np.float32(w.spacing)), nx, ny, x0, y0)
+    for _ in range(args.warmup):
+        _cpu_oracle_rate(w, batch, gs, REF_SAMPLE_STATES)
+    rates, times = [], []
+    cores = 1
+    for _ in range(args.steps):
+        r, dt, cores = _cpu_oracle_rate(w, batch, gs, REF_SAMPLE_STATES)
+        rates.append(r)
+        times.append(dt)
+    value = (REF_SAMPLE_STATES * nx * ny * len(w.speeds) * w.n_opp
+             * len(times)) / sum(times)
+    sample = (f"first {REF_SAMPLE_STATES} states of the batched workload "
+              f"(seed {w.seed}) per step, full grid, all speeds")
+    line = {"impl": "reference", "metric": METRIC, "value": value,
+            "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(w, nx, ny, 1, {"states_per_step":
+                                            REF_SAMPLE_STATES}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_pps(args):
+    import torch
+
+    from paper_1909_07717_gb300 import build as pbuild
+    from paper_1909_07717_gb300 import pps, synth
+
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    if world != args.gpus and world == 1 and args.gpus > 1:
+        print("use torchrun for --gpus > 1", file=sys.stderr)
+        return 2
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        pbuild.build()
+
+    if dist is not None:
+        dist.barrier()
+    w = _workload()
+    if args.states:
+        w.n_states = args.states
+    # Rank r searches its own states: the workload's seed for rank 0, a
+    # rank-derived seed for the others (weak scaling, no shared data).
+    seed = w.seed if rank == 0 else 1000 + rank
+    batch = synth.ssl_states(seed, w.n_states, field_len=w.field[0],
+                             field_wid=w.field[1], n_opp=w.n_opp, K=w.K,
+                             ball_decel=w.ball_decel, vmax=w.vmax,
+                             amax=w.amax)
+    grid = pps.pps_grid_from_field(w.field[0], w.field[1], w.spacing)
+    S, V, P, J = w.n_states, len(w.speeds), grid.nx * grid.ny, w.n_opp
+    stream = torch.cuda.current_stream(dev)
+    searcher = pps.Searcher(max_states=S, max_opp=J, device=local,
+                            stream=stream)
+    states_dev = searcher.states_to_device(batch)
+    out = searcher.alloc_outputs(S, grid, V, mask=True)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    prm = pps.params_from_dict(w.params)
+
+    def step():
+        searcher.search(states_dev, S, grid, w.speeds, prm, out=out)
+
+    for _ in range(max(3, args.warmup)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    evals_per_step = S * P * V * J
+    value = world * evals_per_step * args.steps / (total_ms / 1e3)
+
+    # correctness guard on the measured output (cheap, after timing)
+    best = pps.unpack_best(out["best"].cpu().numpy())
+    if not np.all(best["status"] == 0):
+        print("search reported inconsistent states", file=sys.stderr)
+        return 3
+
+    # ---- end to end through the C ABI with host (pinned) buffers
+    rec = pps.pack_states(batch)
+    h_states = torch.from_numpy(rec.view(np.uint8).copy()).pin_memory()
+    h_best = torch.empty(S * 32, dtype=torch.uint8).pin_memory()
+    words = pps.pps_mask_words(grid, V)
+    h_mask = torch.empty(S * words, dtype=torch.int32).pin_memory()
+    sp = np.asarray(w.speeds, np.float32)
+
+    def step_host():
+        pps.pps_search(searcher.ctx, h_states.data_ptr(), S, grid,
+                       sp.ctypes.data, V, prm, h_best.data_ptr(),
+                       h_mask.data_ptr(), None, 0)
+
+    for _ in range(2):
+        step_host()
+    torch.cuda.synchronize()
+    ev2 = [(torch.cuda.Event(enable_timing=True),
+            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        ev2[i][0].record(stream)
+        step_host()
+        ev2[i][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in ev2)
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * evals_per_step * args.steps / (e2e_ms / 1e3)
+    host_best = pps.unpack_best(h_best.numpy())
+    if host_best.tobytes() != best.tobytes():
+        print("host-buffer path disagrees with device path", file=sys.stderr)
+        return 3
+
+    line = None
+    if rank == 0:
+        props = torch.cuda.get_device_properties(dev)
+        peaks = _peaks()
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        nsm = props.multi_processor_count
+        interactions = S * P * w.K * J
+        ball_evals = S * P * w.K * V
+        ops = OPS_INTERACTION * interactions + OPS_BALL * ball_evals
+        mufu = MUFU_INTERACTION * interactions + MUFU_BALL * ball_evals
+        t_launch = (total_ms / args.steps) / 1e3
+        peak_ops = nsm * FP32_LANES_PER_SM * sm_max * 1e6
+        peak_mufu = nsm * MUFU_LANES_PER_SM * sm_max * 1e6
+        digest = _kernel_src_digest()
+        roof = {"bound": "alu", "achieved": ops / t_launch / 1e12,
+                "peak": peak_ops / 1e12, "unit": "Tops/s (FP32 lane-ops)",
+                "frac": ops / t_launch / peak_ops,
+                "traffic": _profiled_traffic(digest),
+                "peak_basis": (f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                               f"{sm_max:.0f} MHz (max SM clock)"),
+                "ops_per_launch": ops,
+                "xu": {"achieved": mufu / t_launch / 1e12,
+                       "peak": peak_mufu / 1e12, "unit": "T MUFU ops/s",
+                       "frac": mufu / t_launch / peak_mufu},
+                "kernel_source_digest": digest}
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            gs = (float(np.float32(grid.spacing)), grid.nx, grid.ny,
+                  float(grid.x0), float(grid.y0))
+            r, dt, cores = _cpu_oracle_rate(w, batch, gs, CPU_SAMPLE_STATES)
+            cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": (f"first {CPU_SAMPLE_STATES} states of the "
+                              f"batched workload (seed {w.seed}), full grid, "
+                              f"all speeds; {dt:.1f} s wall")}
+        line = {"metric": METRIC, "value": value, "unit": UNIT,
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": _config(w, grid.nx, grid.ny, world),
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT,
+                        "h2d_bytes_per_step": int(S * 296),
+                        "d2h_bytes_per_step": int(S * 32 + S * words * 4),
+                        "ms_per_step": e2e_ms / args.steps},
+                "clocks": clk.summary(),
+                "gpu_launches": 2 * args.steps,
+                "states_per_s": world * S * args.steps / (total_ms / 1e3)}
+        print(json.dumps(line), flush=True)
+    searcher.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["pps", "reference"], default="pps")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--states", type=int, default=0,
+                    help="states per GPU (default: the workload's 4096); "
+                         "smaller only for profiling captures")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_pps(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

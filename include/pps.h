@@ -1,0 +1,243 @@
+/*
+ * pps.h -- C ABI of libpps, the GB300 (sm_103a) passing-point search.
+ *
+ * libpps computes the data-parallel core of the SBIP-based dynamic
+ * passing-point search (DPPS) of the ZJUNlict 2019 team description paper:
+ * for every game state, every candidate receive point of a field grid and
+ * every kick speed it decides whether any opponent can intercept the pass
+ * (Sec. 4.2), scores the feasible passes with the weighted-sum value
+ * function (Sec. 4.3, Eq. 3) and returns the best pass per state.
+ *
+ * Model (the paper's prose, and the readings this library takes where the
+ * paper is silent):
+ *   ball     (Sec. 4.1, Eq. 1 read as d = v t - a t^2/2): rolls from the
+ *            kick speed v with constant deceleration a (the short sliding
+ *            phase neglected); it stops after v^2/(2a).
+ *   samples  (Sec. 4.2): the ball is checked at K points spaced uniformly
+ *            in distance along the pass line, k = 1..K, the receiver point
+ *            being sample K.
+ *   opponent (Sec. 4.2, SBIP): minimum time to bring its centre within
+ *            reach_radius of a sample under a 1-D bang-bang motion along the
+ *            line to it -- acceleration amax, speed cap vmax, starting from
+ *            its velocity component toward the sample.
+ *   feasible (Sec. 4.2): the ball reaches the receiver, the pass is at least
+ *            min_pass_dist long, and margin > tau_safe, where
+ *            margin = min_k (min_j t_opp_j(sample k) - t_ball(sample k)).
+ *   score    (Sec. 4.3, Eq. 3; Sec. 4.4 shot angle):
+ *            w_angle * theta / pi - w_dist * |receiver - goal| / diag
+ *            + w_margin * min(margin, margin_cap), theta the largest
+ *            opponent-free angular gap of the goal mouth (x = +L/2) seen from
+ *            the receiver, opponents as discs of robot_radius; theta = 0 on
+ *            or behind the goal line.
+ *   best     (Sec. 1 item 1, Sec. 4.3): highest score; ties go to the
+ *            smallest candidate index idx = v * P + iy * nx + ix.
+ *
+ * Conventions.  All functions return a pps_status and never abort or exit.
+ * Floats are IEEE binary32, integers are int32 unless stated.  The caller
+ * owns every input and output buffer and must keep them alive until the
+ * work is complete (pps_sync, or a sync of the context's stream); the
+ * library keeps no caller pointer past that point.  A context is used by
+ * one host thread at a time.
+ */
+#ifndef PPS_H
+#define PPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PPS_ABI_VERSION 1
+
+#define PPS_MAX_OPP 16   /* opponents per state (the paper: up to 16 a side) */
+#define PPS_MAX_SPEEDS 8 /* kick speeds per call */
+#define PPS_MAX_K 4096   /* samples per pass line */
+
+typedef int pps_status;
+#define PPS_OK 0
+#define PPS_EINVAL 1   /* an argument or an input value is out of range */
+#define PPS_ENOMEM 2   /* device memory or the context's budget ran out */
+#define PPS_ECUDA 3    /* a CUDA call failed; the context needs pps_reset */
+#define PPS_ETIMEOUT 4 /* a bounded device wait gave up */
+#define PPS_ENOTIMPL 5 /* not available in this build */
+
+/* pps_search flag: every buffer argument is device memory (e.g. a torch
+ * CUDA tensor's data pointer).  Without it they are host memory; the
+ * library then stages them through its own device buffers and copies the
+ * results back asynchronously on the context's stream (pinned host memory
+ * makes those copies truly asynchronous). */
+#define PPS_DEVICE_PTRS 1u
+
+/* pps_best.status bits (per state). */
+#define PPS_STATE_OK 0
+#define PPS_STATE_INVALID 1      /* the state failed validation: no result */
+#define PPS_STATE_INCONSISTENT 2 /* self-check: the best score could not be
+                                    reproduced when re-evaluated (a library
+                                    bug; please report) */
+
+/* One game state.  296 bytes, 4-byte aligned, no padding.  Coordinates in
+ * metres with the field centred on the origin, x toward the opponent goal,
+ * velocities in m/s.  Opponent slots n_opp..PPS_MAX_OPP-1 are ignored. */
+typedef struct pps_state {
+    float ball[2];                  /* kick point (the passer's ball) */
+    int32_t n_opp;                  /* 0..PPS_MAX_OPP opponents */
+    float opp_pos[PPS_MAX_OPP][2];  /* opponent centres */
+    float opp_vel[PPS_MAX_OPP][2];  /* opponent velocities */
+    float ball_decel;               /* rolling deceleration a > 0, m/s^2 */
+    float vmax;                     /* opponent speed limit > 0 */
+    float amax;                     /* opponent acceleration limit > 0 */
+    float field_len;                /* L > 0 (goal line at x = +L/2) */
+    float field_wid;                /* W > 0 */
+    float goal_width;               /* goal mouth width >= 0 */
+    int32_t K;                      /* samples per pass line, 1..PPS_MAX_K */
+} pps_state;
+
+/* Candidate receive points: (x0 + ix * spacing, y0 + iy * spacing),
+ * 0 <= ix < nx, 0 <= iy < ny; point index p = iy * nx + ix, P = nx * ny. */
+typedef struct pps_grid {
+    float spacing;
+    int32_t nx, ny;
+    float x0, y0;
+} pps_grid;
+
+/* Value-function weights and thresholds (Sec. 4.3: "adjustable"; the
+ * paper gives no values -- pps_default_params gives the library's). */
+typedef struct pps_params {
+    float w_angle;       /* weight of theta / pi */
+    float w_dist;        /* weight of -(receiver-to-goal distance) / diag */
+    float w_margin;      /* weight of min(margin, margin_cap), in 1/s */
+    float margin_cap;    /* s */
+    float tau_safe;      /* feasibility threshold on the margin, s */
+    float robot_radius;  /* opponent disc radius for shot blocking, m */
+    float reach_radius;  /* opponent intercepts within this distance, m */
+    float min_pass_dist; /* shortest pass considered, m */
+} pps_params;
+
+/* Result per state.  idx = -1 when no pass is feasible (score and margin
+ * then -inf, ix = iy = speed_idx = -1); idx = -2 when the state was
+ * invalid (status has PPS_STATE_INVALID). */
+typedef struct pps_best {
+    int32_t idx;        /* speed_idx * P + iy * nx + ix */
+    int32_t ix, iy;
+    int32_t speed_idx;
+    float score;
+    float margin;       /* margin of the best pass, s */
+    int32_t n_feasible; /* feasible (point, speed) pairs of the state */
+    int32_t status;     /* PPS_STATE_* bits */
+} pps_best;
+
+/* Optional per-candidate outputs, for inspection and parity testing.  Any
+ * pointer may be NULL.  Same memory kind as the other buffers (flags).
+ *   margin[s][v][p]   margin (s); -inf if the ball stops short, +inf with
+ *                     no opponents
+ *   score[s][v][p]    score, -inf when infeasible
+ *   T[s][p][k]        min_j t_opp_j at sample k+1 (s), k < K_s; row stride
+ *                     T_stride >= max K of the batch; +inf with no
+ *                     opponents */
+typedef struct pps_debug_out {
+    float* margin;
+    float* score;
+    float* T;
+    int32_t T_stride;
+} pps_debug_out;
+
+/* Context creation parameters. */
+typedef struct pps_ctx_desc {
+    int32_t device;          /* CUDA device ordinal */
+    void* stream;            /* cudaStream_t to run on; NULL = the legacy
+                                default stream */
+    size_t mem_budget_bytes; /* cap on the library's own device memory;
+                                0 = no cap */
+    int32_t max_states;      /* largest n_states per call (> 0) */
+    int32_t max_points;      /* largest P per call; 0 = 1<<24 */
+    int32_t max_speeds;      /* 0 = PPS_MAX_SPEEDS */
+    int32_t max_K;           /* 0 = PPS_MAX_K */
+    int32_t max_opp;         /* most opponents any state will have; 1..16,
+                                0 = 16.  Sizes the kernel's opponent slots
+                                (<= 8 runs the faster 8-slot kernel); a
+                                state with more is invalid */
+} pps_ctx_desc;
+
+typedef struct pps_ctx pps_ctx;
+
+/* Library ABI version (PPS_ABI_VERSION of the build). */
+int pps_abi_version(void);
+
+/* Human-readable name of a status code (static storage). */
+const char* pps_status_string(pps_status s);
+
+/* Last error message of a context ("" if none); valid until the next call
+ * on the context.  ctx may be NULL (then: the last pps_create failure). */
+const char* pps_last_error(const pps_ctx* ctx);
+
+/* Library defaults: weights 1, margin_cap 1 s, tau_safe 0, robot_radius
+ * 0.09 m, reach_radius 0, min_pass_dist 0. */
+pps_status pps_default_params(pps_params* out);
+
+/* Grid covering an L x W field at the given spacing with both edges
+ * included: x0 = -L/2, y0 = -W/2, nx = round(L/spacing)+1,
+ * ny = round(W/spacing)+1 (the paper rasterises at 0.1 m, Sec. 5.1).
+ * EINVAL for non-finite or non-positive sizes or more than 2^24 points. */
+pps_status pps_grid_from_field(float L, float W, float spacing,
+                               pps_grid* out);
+
+/* 32-bit words of feasibility mask per state: n_speeds * ceil(P / 32).
+ * Mask layout: mask[s][v][w], bit b of word w is point p = 32 w + b
+ * (p = iy * nx + ix); bits at p >= P are zero.  0 on bad arguments. */
+size_t pps_mask_words(const pps_grid* grid, int n_speeds);
+
+/* Create a context on desc->device: selects the device, allocates the
+ * per-call scratch (max_states entries) and records the stream.
+ * EINVAL on a bad descriptor, ENOMEM past the budget or on allocation
+ * failure, ECUDA if the device cannot be used.  *out is NULL on error. */
+pps_status pps_create(pps_ctx** out, const pps_ctx_desc* desc);
+
+/* Free a context and everything it allocated.  NULL is accepted.  Waits
+ * for the context's stream first. */
+void pps_destroy(pps_ctx* ctx);
+
+/* The exact search (Sec. 4.2-4.3) over n_states states sharing one grid
+ * and one list of kick speeds.
+ *   states     [n_states] pps_state
+ *   grid       host pointer, always
+ *   speeds     host pointer, always: n_speeds kick speeds > 0 (m/s),
+ *              1 <= n_speeds <= min(PPS_MAX_SPEEDS, max_speeds)
+ *   params     host pointer, always; NULL = pps_default_params
+ *   out_best   [n_states] pps_best (required)
+ *   out_mask   [n_states * pps_mask_words(grid, n_speeds)] uint32, or NULL
+ *              to skip the mask
+ *   dbg        host pointer to a pps_debug_out, or NULL
+ *   flags      0 or PPS_DEVICE_PTRS
+ * Enqueues the work on the context's stream and returns without waiting.
+ * Host-memory states are validated before anything is enqueued (EINVAL on
+ * n_opp outside 0..max_opp, K outside 1..max_K, a non-finite value, or a
+ * non-positive decel, vmax, amax, L or W).  Device-memory states are
+ * validated on the device: an invalid one gets idx -2 and
+ * PPS_STATE_INVALID, the others are unaffected.  n_states == 0 is a no-op.
+ * EINVAL for bad scalar arguments, ENOMEM if staging buffers for host
+ * memory exceed the budget, ECUDA on a launch failure. */
+pps_status pps_search(pps_ctx* ctx, const pps_state* states, int n_states,
+                      const pps_grid* grid, const float* speeds,
+                      int n_speeds, const pps_params* params,
+                      pps_best* out_best, uint32_t* out_mask,
+                      const pps_debug_out* dbg, unsigned flags);
+
+/* Wait for the context's stream.  ECUDA if the device reported an error
+ * (the context is then failed until pps_reset). */
+pps_status pps_sync(pps_ctx* ctx);
+
+/* Clear a failed context's error state after the caller has dealt with
+ * the cause.  ECUDA if the device is still unusable. */
+pps_status pps_reset(pps_ctx* ctx);
+
+/* Number of SMs and the CTAs per SM the search kernel runs with (for
+ * benchmarks and the autotuner); EINVAL on NULL. */
+pps_status pps_launch_info(const pps_ctx* ctx, int* num_sms,
+                           int* ctas_per_sm);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PPS_H */

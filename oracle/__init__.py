@@ -55,6 +55,8 @@ def _bind(lib):
     lib.pps_oracle_intercept_time.argtypes = [d] * 9
     lib.pps_oracle_min_intercept.restype = d
     lib.pps_oracle_min_intercept.argtypes = [p, d, d, d]
+    lib.pps_oracle_min_intercept_many.restype = None
+    lib.pps_oracle_min_intercept_many.argtypes = [p, i, p, d, p]
     lib.pps_oracle_margin.restype = d
     lib.pps_oracle_margin.argtypes = [p, d, d, d, d, p, p]
     lib.pps_oracle_shot_angle.restype = d
@@ -130,6 +132,15 @@ class Oracle:
     def min_intercept(self, state: State, p, reach=0.0):
         return self.lib.pps_oracle_min_intercept(state.ref, float(p[0]),
                                                  float(p[1]), float(reach))
+
+    def min_intercept_many(self, state: State, pts, reach=0.0):
+        """min_intercept at each row of the (n, 2) array ``pts``."""
+        pts = np.ascontiguousarray(np.asarray(pts, np.float64).reshape(-1, 2))
+        out = np.empty(pts.shape[0], np.float64)
+        self.lib.pps_oracle_min_intercept_many(state.ref, pts.shape[0],
+                                               _ptr(pts), float(reach),
+                                               _ptr(out))
+        return out
 
     def margin(self, state: State, c, v, reach=0.0):
         """(margin, reachable, T[K]) of the pass to point c at speed v."""
@@ -231,6 +242,7 @@ _default = None
 def __getattr__(name):
     # Module-level shortcuts: oracle.ball_time(...) == default().ball_time(...)
     if name in ("grid", "ball_time", "intercept_time", "min_intercept",
+                "min_intercept_many",
                 "margin", "shot_angle", "score", "search", "max_threads"):
         return getattr(default(), name)
     raise AttributeError(name)

@@ -112,6 +112,15 @@ double pps_oracle_min_intercept(const pps_oracle_state* st, double px,
     return T;
 }
 
+void pps_oracle_min_intercept_many(const pps_oracle_state* st, int n,
+                                   const double* pxy, double reach,
+                                   double* out)
+{
+    for (int i = 0; i < n; ++i)
+        out[i] = pps_oracle_min_intercept(st, pxy[2 * i], pxy[2 * i + 1],
+                                          reach);
+}
+
 /* ---- C4: margin and reachability of one candidate pass ---- */
 double pps_oracle_margin(const pps_oracle_state* st, double cx, double cy,
                          double v, double reach, double* T_out,

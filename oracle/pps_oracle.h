@@ -79,6 +79,11 @@ double pps_oracle_intercept_time(double ox, double oy, double ux, double uy,
 double pps_oracle_min_intercept(const pps_oracle_state* st, double px,
                                 double py, double reach);
 
+/* pps_oracle_min_intercept at n points pxy[2i], pxy[2i+1] -> out[i]. */
+void pps_oracle_min_intercept_many(const pps_oracle_state* st, int n,
+                                   const double* pxy, double reach,
+                                   double* out);
+
 /* Safety margin of the pass to (cx, cy) at kick speed v:
  * min_k (T_k - t_ball(s_k)), k = 1..K.  Writes T_k to T_out[k-1] when
  * T_out is not NULL, and the reachability to *reachable.  -inf when the

@@ -1,0 +1,511 @@
+// pps_search.cuh -- device code of the exact passing-point search (sm_103a).
+//
+// One persistent kernel covers the whole hot path of the SBIP-based dynamic
+// passing-point search (ZJUNlict 2019, Sec. 4.1-4.4), fused:
+//   A1 state staging        the CTA copies its state into shared memory,
+//                           every thread derives the per-state constants
+//   A2 candidate geometry   one lane per grid point; samples are generated
+//                           on the fly, never stored
+//   A3 opponent intercept   T_k = min_j t_j(sample k), opponents held in
+//                           registers (warp-uniform, so every lane of a warp
+//                           reads the same opponent in the same cycle);
+//                           computed once per (point, k), shared by speeds
+//   A4 ball time + margin   per speed: min_k (T_k - t_ball(s_k))
+//   A5 shot angle, goal distance      once per point
+//   A6 feasibility, score, mask       warp ballot -> one mask word per warp
+//   A7 argmax               warp shuffle -> CTA -> 64-bit atomicMax per state
+// A second, tiny kernel turns the per-state keys into pps_best records.
+//
+// Arithmetic (FP32, inputs as given).  The opponent time is computed in a
+// scaled form: with sigma = sqrt(2 amax), w' = w / sigma, v' = vmax / sigma,
+// q'^2 = w'^2 + d and m' = max(v' - q', 0), the 1-D bang-bang time is
+//     t = ((v' - w')^2 + d - m'^2) / vmax,
+// which equals (-w + sqrt(w^2 + 2 amax d)) / amax while the robot is still
+// accelerating (q' <= v') and (vmax - w)/amax + (d - d_acc)/vmax once it
+// cruises; the numerator is the tangent-line identity of those two branches,
+// so no branch is needed.  The ball term uses
+//     a T_k + sqrt(v^2 - 2 a s_k),   margin = (min_k(...) - v) / a,
+// which is min_k (T_k - (v - sqrt(v^2 - 2 a s_k)) / a) rearranged.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+#include "pps.h"
+
+namespace pps {
+
+constexpr int kTPB = 128;          // threads per CTA = grid points per tile
+constexpr float kFar = 1.0e18f;    // offset of an unused opponent slot
+constexpr float kD2Floor = 1.0e-30f;  // keeps 1/d finite when d == 0
+
+struct SearchArgs {
+    const pps_state* states;
+    int n_states;
+    int nx, ny, P, words;  // words = ceil(P / 32): mask words per speed
+    float g, x0, y0;
+    int tiles;             // tiles (of kTPB points) per state
+    long long n_items;     // n_states * tiles
+    int V;
+    int kmax;              // largest K accepted
+    float speed[PPS_MAX_SPEEDS];
+    float speed2[PPS_MAX_SPEEDS];
+    pps_params prm;
+    pps_best* best;
+    uint32_t* mask;        // may be null
+    float* dbg_margin;     // may be null
+    float* dbg_score;      // may be null
+    float* dbg_T;          // may be null
+    int T_stride;
+    unsigned long long* keys;  // scratch: per-state packed (score, ~idx)
+    int* counts;               // scratch: per-state feasible count
+};
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ float rsqrt_fast(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float sqrt_fast(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Order-preserving map of a float onto uint32 (for the packed argmax key).
+__device__ __forceinline__ uint32_t order_bits(float f) {
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ float order_bits_inv(uint32_t k) {
+    uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+    return __uint_as_float(u);
+}
+
+__device__ __forceinline__ bool pos_finite(float x) {
+    return x > 0.f && x < CUDART_INF_F;  // false for NaN
+}
+
+__device__ __forceinline__ bool is_finite(float x) {
+    return fabsf(x) < CUDART_INF_F;
+}
+
+// Per-state constants (A1).  Computed identically by every thread.
+struct StateK {
+    float bx, by;
+    float vh;            // vmax / sigma
+    float inv_sigma;     // 1 / sqrt(2 amax)
+    float inv_vmax;
+    float ab;            // ball deceleration
+    float two_ab;
+    float ab_over_vmax;
+    float reach;
+    float Lh, hw;        // goal line x, half mouth width
+    float inv_diag;
+    float invK;
+    float fK;            // fraction of the last sample (K * invK)
+    int K, nopp;
+    bool general;        // needs the speed clamp or a reach radius
+    bool valid;
+};
+
+__device__ __forceinline__ StateK derive_state(const pps_state& st,
+                                               const pps_params& prm,
+                                               int jmax, int kmax) {
+    StateK d;
+    d.nopp = st.n_opp;
+    d.K = st.K;
+    bool ok = d.nopp >= 0 && d.nopp <= jmax && d.K >= 1 && d.K <= kmax &&
+              pos_finite(st.ball_decel) && pos_finite(st.vmax) &&
+              pos_finite(st.amax) && pos_finite(st.field_len) &&
+              pos_finite(st.field_wid) && is_finite(st.goal_width) &&
+              st.goal_width >= 0.f && is_finite(st.ball[0]) &&
+              is_finite(st.ball[1]);
+    if (!ok) d.nopp = 0;
+    bool fast_opp = false;
+    for (int j = 0; j < d.nopp; ++j) {
+        float ux = st.opp_vel[j][0], uy = st.opp_vel[j][1];
+        ok = ok && is_finite(st.opp_pos[j][0]) && is_finite(st.opp_pos[j][1]) &&
+             is_finite(ux) && is_finite(uy);
+        fast_opp |= __fmaf_rn(ux, ux, __fmul_rn(uy, uy)) >
+                    __fmul_rn(st.vmax, st.vmax);
+    }
+    d.valid = ok;
+    if (!ok) {
+        d.nopp = 0;
+        d.K = 1;
+    }
+    d.bx = st.ball[0];
+    d.by = st.ball[1];
+    const float sigma = __fsqrt_rn(__fmul_rn(2.f, st.amax));
+    d.inv_sigma = __frcp_rn(sigma);
+    d.vh = __fdiv_rn(st.vmax, sigma);
+    d.inv_vmax = __frcp_rn(st.vmax);
+    d.ab = st.ball_decel;
+    d.two_ab = __fmul_rn(2.f, st.ball_decel);
+    d.ab_over_vmax = __fdiv_rn(st.ball_decel, st.vmax);
+    d.reach = prm.reach_radius;
+    d.Lh = __fmul_rn(0.5f, st.field_len);
+    d.hw = __fmul_rn(0.5f, st.goal_width);
+    d.inv_diag = __frcp_rn(__fsqrt_rn(__fmaf_rn(
+        st.field_len, st.field_len, __fmul_rn(st.field_wid, st.field_wid))));
+    d.invK = __frcp_rn((float)d.K);
+    d.fK = __fmul_rn((float)d.K, d.invK);
+    d.general = fast_opp || prm.reach_radius > 0.f;
+    return d;
+}
+
+// Opponents in registers: (b - o) and u / sigma per slot; unused slots are
+// parked at kFar so they can never hold the minimum.
+template <int JMAX>
+struct OppRegs {
+    float bx[JMAX], by[JMAX], ux[JMAX], uy[JMAX];
+};
+
+template <int JMAX>
+__device__ __forceinline__ void load_opps(const pps_state& st,
+                                          const StateK& sk,
+                                          OppRegs<JMAX>& o) {
+#pragma unroll
+    for (int j = 0; j < JMAX; ++j) {
+        if (j < sk.nopp) {
+            o.bx[j] = __fsub_rn(sk.bx, st.opp_pos[j][0]);
+            o.by[j] = __fsub_rn(sk.by, st.opp_pos[j][1]);
+            o.ux[j] = __fmul_rn(st.opp_vel[j][0], sk.inv_sigma);
+            o.uy[j] = __fmul_rn(st.opp_vel[j][1], sk.inv_sigma);
+        } else {
+            o.bx[j] = kFar;
+            o.by[j] = kFar;
+            o.ux[j] = 0.f;
+            o.uy[j] = 0.f;
+        }
+    }
+}
+
+// A3: numerator of one opponent's intercept time at the sample
+// p = b + f (c - b); the time is num / vmax.  GEN adds the speed clamp and
+// the reach radius (num = 0 within reach).
+template <bool GEN>
+__device__ __forceinline__ float sbip_num(float f, float cbx, float cby,
+                                          float obx, float oby, float oux,
+                                          float ouy, float vh, float reach) {
+    const float rx = __fmaf_rn(f, cbx, obx);  // p - o
+    const float ry = __fmaf_rn(f, cby, oby);
+    const float d2 = __fmaf_rn(rx, rx, __fmaf_rn(ry, ry, kD2Floor));
+    const float ig = rsqrt_fast(d2);
+    const float d = __fmul_rn(d2, ig);
+    float w = __fmul_rn(__fmaf_rn(oux, rx, __fmul_rn(ouy, ry)), ig);
+    if (GEN) {
+        w = fminf(fmaxf(w, -vh), vh);
+        const float dl = __fsub_rn(d, reach);
+        const float dc = fmaxf(dl, 0.f);
+        const float q = sqrt_fast(__fmaf_rn(w, w, dc));
+        const float m = __fsub_rn(vh, fminf(q, vh));
+        const float e = __fsub_rn(vh, w);
+        const float num = __fmaf_rn(-m, m, __fmaf_rn(e, e, dc));
+        return dl > 0.f ? num : 0.f;
+    } else {
+        const float q = sqrt_fast(__fmaf_rn(w, w, d));
+        const float m = __fsub_rn(vh, fminf(q, vh));
+        const float e = __fsub_rn(vh, w);
+        return __fmaf_rn(-m, m, __fmaf_rn(e, e, d));
+    }
+}
+
+// A3 + A4 over the K samples of one point.  mv[v] accumulates
+// min_k (a T_k + sqrt(v^2 - 2 a s_k)); Trow (debug) receives T_k.
+template <int JMAX, int VMAX, bool GEN, bool TDBG>
+__device__ __forceinline__ void sample_loop(const StateK& sk,
+                                            const OppRegs<JMAX>& o,
+                                            float cbx, float cby,
+                                            float twoabD,
+                                            const float (&sp2)[VMAX],
+                                            float (&mv)[VMAX], float* Trow) {
+    for (int k = 1; k <= sk.K; ++k) {
+        const float f = __fmul_rn((float)k, sk.invK);
+        float n = CUDART_INF_F;
+#pragma unroll
+        for (int j = 0; j < JMAX; ++j)
+            n = fminf(n, sbip_num<GEN>(f, cbx, cby, o.bx[j], o.by[j], o.ux[j],
+                                       o.uy[j], sk.vh, sk.reach));
+        if (TDBG && Trow)
+            Trow[k - 1] = sk.nopp ? __fmul_rn(n, sk.inv_vmax) : CUDART_INF_F;
+        const float aT = __fmul_rn(n, sk.ab_over_vmax);
+        const float as = __fmul_rn(f, twoabD);
+#pragma unroll
+        for (int v = 0; v < VMAX; ++v)
+            mv[v] = fminf(mv[v],
+                          __fadd_rn(aT, sqrt_fast(__fsub_rn(sp2[v], as))));
+    }
+}
+
+// A5: largest opponent-free angular gap of the goal mouth seen from c.
+template <int JMAX>
+__device__ __forceinline__ float shot_angle(const pps_state& st,
+                                            const StateK& sk, bool front,
+                                            float cx, float cy, float gx,
+                                            float r) {
+    if (!front) return 0.f;
+    const float lo = atan2f(__fsub_rn(-sk.hw, cy), gx);
+    const float hi = atan2f(__fsub_rn(sk.hw, cy), gx);
+    float s[JMAX], e[JMAX];
+    bool all = false;
+    const float r2 = __fmul_rn(r, r);
+#pragma unroll
+    for (int j = 0; j < JMAX; ++j) {
+        s[j] = 1e30f;
+        e[j] = 1e30f;
+        if (j < sk.nopp) {
+            const float dx = __fsub_rn(st.opp_pos[j][0], cx);
+            const float dy = __fsub_rn(st.opp_pos[j][1], cy);
+            const float d2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
+            all |= d2 <= r2;
+            const float d = __fsqrt_rn(d2);
+            const float phi = atan2f(dy, dx);
+            const float half = asinf(fminf(__fdiv_rn(r, d), 1.f));
+            s[j] = __fsub_rn(phi, half);
+            e[j] = __fadd_rn(phi, half);
+        }
+    }
+    if (all) return 0.f;
+    float best = 0.f;
+    // Every maximal gap starts at lo or at the end of a blocked interval.
+#pragma unroll
+    for (int i = -1; i < JMAX; ++i) {
+        const float x = (i < 0) ? lo : e[i];
+        bool start = x >= lo && x < hi;
+        float end = hi;
+#pragma unroll
+        for (int j = 0; j < JMAX; ++j) {
+            start = start && !(s[j] < x && x < e[j]);
+            if (s[j] >= x) end = fminf(end, s[j]);
+        }
+        if (start) best = fmaxf(best, __fsub_rn(end, x));
+    }
+    return best;
+}
+
+// Everything per grid point (A2..A6): margins, feasibility and scores for
+// all VMAX speed slots.  Shared by the search and the finalize kernels so
+// that the finalize reproduces the search's numbers bit for bit.
+template <int JMAX, int VMAX>
+struct PointResult {
+    float margin[VMAX];
+    float score[VMAX];
+    bool feas[VMAX];
+};
+
+template <int JMAX, int VMAX, bool TDBG>
+__device__ __forceinline__ void eval_point(const SearchArgs& a,
+                                           const pps_state& st,
+                                           const StateK& sk,
+                                           const OppRegs<JMAX>& o, int ix,
+                                           int iy, float* Trow,
+                                           PointResult<JMAX, VMAX>& res) {
+    const float cx = __fmaf_rn((float)ix, a.g, a.x0);
+    const float cy = __fmaf_rn((float)iy, a.g, a.y0);
+    const float cbx = __fsub_rn(cx, sk.bx);
+    const float cby = __fsub_rn(cy, sk.by);
+    const float D = __fsqrt_rn(__fmaf_rn(cbx, cbx, __fmul_rn(cby, cby)));
+    const float twoabD = __fmul_rn(sk.two_ab, D);
+
+    float sp[VMAX], sp2[VMAX], mv[VMAX];
+#pragma unroll
+    for (int v = 0; v < VMAX; ++v) {
+        const int vv = v < a.V ? v : a.V - 1;  // unused slots repeat the last
+        sp[v] = a.speed[vv];
+        sp2[v] = a.speed2[vv];
+        mv[v] = CUDART_INF_F;
+    }
+    if (sk.general)
+        sample_loop<JMAX, VMAX, true, TDBG>(sk, o, cbx, cby, twoabD, sp2, mv,
+                                            Trow);
+    else
+        sample_loop<JMAX, VMAX, false, TDBG>(sk, o, cbx, cby, twoabD, sp2, mv,
+                                             Trow);
+
+    // A5: the receiver is in front of the goal line iff x0 + ix g < L/2,
+    // decided exactly (the FP64 product and sum are exact for these inputs).
+    const double cxd = fma((double)ix, (double)a.g, (double)a.x0);
+    const bool front = cxd < (double)sk.Lh;
+    const float gx = (float)((double)sk.Lh - cxd);
+    const float theta =
+        shot_angle<JMAX>(st, sk, front, cx, cy, gx, a.prm.robot_radius);
+    const float dg = __fsqrt_rn(__fmaf_rn(gx, gx, __fmul_rn(cy, cy)));
+    const float base =
+        __fsub_rn(__fmul_rn(a.prm.w_angle,
+                            __fmul_rn(theta, 0.318309886183790672f)),
+                  __fmul_rn(a.prm.w_dist, __fmul_rn(dg, sk.inv_diag)));
+    const float reach_lhs = __fmul_rn(sk.fK, twoabD);
+    const bool long_enough = D >= a.prm.min_pass_dist;
+#pragma unroll
+    for (int v = 0; v < VMAX; ++v) {
+        const bool reach = __fsub_rn(sp2[v], reach_lhs) >= 0.f;
+        float m;
+        if (!reach)
+            m = -CUDART_INF_F;
+        else if (sk.nopp == 0)
+            m = CUDART_INF_F;
+        else
+            m = __fdiv_rn(__fsub_rn(mv[v], sp[v]), sk.ab);
+        const bool ok = sk.valid && reach && long_enough && m > a.prm.tau_safe;
+        res.margin[v] = m;
+        res.feas[v] = ok;
+        res.score[v] =
+            ok ? __fadd_rn(base, __fmul_rn(a.prm.w_margin,
+                                           fminf(m, a.prm.margin_cap)))
+               : -CUDART_INF_F;
+    }
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(
+    unsigned long long x) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        unsigned long long y = __shfl_xor_sync(0xffffffffu, x, off);
+        x = y > x ? y : x;
+    }
+    return x;
+}
+
+// ------------------------------------------------------------ the kernels
+template <int JMAX, int VMAX>
+__global__ void __launch_bounds__(kTPB)
+    search_kernel(const SearchArgs a) {
+    __shared__ pps_state st;
+    __shared__ unsigned long long red_key[kTPB / 32];
+    __shared__ int red_cnt[kTPB / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kWords = sizeof(pps_state) / 4;
+    static_assert(sizeof(pps_state) % 4 == 0, "pps_state is word-sized");
+
+    for (long long item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+        const int s = (int)(item / a.tiles);
+        const int tile = (int)(item - (long long)s * a.tiles);
+        __syncthreads();  // the previous item is done with st / red_*
+        if (threadIdx.x < kWords)
+            reinterpret_cast<uint32_t*>(&st)[threadIdx.x] =
+                reinterpret_cast<const uint32_t*>(a.states + s)[threadIdx.x];
+        __syncthreads();
+
+        const StateK sk = derive_state(st, a.prm, JMAX, a.kmax);
+        OppRegs<JMAX> o;
+        load_opps<JMAX>(st, sk, o);
+
+        const int p = tile * kTPB + threadIdx.x;
+        const bool active = p < a.P;
+        const int pc = active ? p : a.P - 1;
+        const int iy = pc / a.nx, ix = pc - iy * a.nx;
+
+        PointResult<JMAX, VMAX> r;
+        float* Trow = nullptr;
+        if (a.dbg_T) {
+            Trow = a.dbg_T + ((long long)s * a.P + pc) * a.T_stride;
+            eval_point<JMAX, VMAX, true>(a, st, sk, o, ix, iy,
+                                         active ? Trow : nullptr, r);
+        } else {
+            eval_point<JMAX, VMAX, false>(a, st, sk, o, ix, iy, nullptr, r);
+        }
+
+        // A6: mask words, debug outputs, feasible count.
+        int cnt = 0;
+        unsigned long long key = 0ull;
+#pragma unroll
+        for (int v = 0; v < VMAX; ++v) {
+            const bool f = active && v < a.V && r.feas[v];
+            cnt += f;
+            if (f) {
+                // A7: packed (score, ~idx) -- larger is better, and on equal
+                // scores the smaller candidate index wins.
+                const uint32_t idx = (uint32_t)(v * a.P + p);
+                const unsigned long long k2 =
+                    ((unsigned long long)order_bits(r.score[v]) << 32) |
+                    (unsigned long long)(~idx);
+                key = k2 > key ? k2 : key;
+            }
+            if (v < a.V) {
+                const uint32_t word = __ballot_sync(0xffffffffu, f);
+                const int p0 = tile * kTPB + warp * 32;
+                if (a.mask && lane == 0 && p0 < a.P)
+                    a.mask[((long long)s * a.V + v) * a.words + (p0 >> 5)] =
+                        word;
+                if (active) {
+                    const long long o2 = ((long long)s * a.V + v) * a.P + p;
+                    if (a.dbg_margin) a.dbg_margin[o2] = r.margin[v];
+                    if (a.dbg_score) a.dbg_score[o2] = r.score[v];
+                }
+            }
+        }
+        key = warp_max_u64(key);
+        cnt = __reduce_add_sync(0xffffffffu, cnt);
+        if (lane == 0) {
+            red_key[warp] = key;
+            red_cnt[warp] = cnt;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long k = red_key[0];
+            int c = red_cnt[0];
+#pragma unroll
+            for (int w = 1; w < kTPB / 32; ++w) {
+                k = red_key[w] > k ? red_key[w] : k;
+                c += red_cnt[w];
+            }
+            if (k) atomicMax(a.keys + s, k);
+            if (c) atomicAdd(a.counts + s, c);
+        }
+    }
+}
+
+// Per state: decode the key, re-evaluate the winning point for its margin
+// and check that the score reproduces.
+template <int JMAX, int VMAX>
+__global__ void __launch_bounds__(128) finalize_kernel(const SearchArgs a) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.n_states) return;
+    const pps_state& st = a.states[s];
+    const StateK sk = derive_state(st, a.prm, JMAX, a.kmax);
+    pps_best b;
+    b.n_feasible = a.counts[s];
+    b.status = sk.valid ? PPS_STATE_OK : PPS_STATE_INVALID;
+    const unsigned long long key = a.keys[s];
+    if (!sk.valid || key == 0ull) {
+        b.idx = sk.valid ? -1 : -2;
+        b.ix = b.iy = b.speed_idx = -1;
+        b.score = -CUDART_INF_F;
+        b.margin = -CUDART_INF_F;
+        b.n_feasible = sk.valid ? b.n_feasible : 0;
+    } else {
+        const uint32_t idx = ~(uint32_t)(key & 0xffffffffull);
+        const int v = (int)(idx / (uint32_t)a.P);
+        const int p = (int)(idx - (uint32_t)v * (uint32_t)a.P);
+        b.idx = (int)idx;
+        b.speed_idx = v;
+        b.iy = p / a.nx;
+        b.ix = p - b.iy * a.nx;
+        b.score = order_bits_inv((uint32_t)(key >> 32));
+        OppRegs<JMAX> o;
+        load_opps<JMAX>(st, sk, o);
+        PointResult<JMAX, VMAX> r;
+        eval_point<JMAX, VMAX, false>(a, st, sk, o, b.ix, b.iy, nullptr, r);
+        float m = 0.f, sc = 0.f;
+        bool f = false;
+#pragma unroll
+        for (int w = 0; w < VMAX; ++w)
+            if (w == v) {
+                m = r.margin[w];
+                sc = r.score[w];
+                f = r.feas[w];
+            }
+        b.margin = m;
+        if (!f || __float_as_uint(sc) != __float_as_uint(b.score))
+            b.status |= PPS_STATE_INCONSISTENT;
+    }
+    a.best[s] = b;
+}
+
+}  // namespace pps

@@ -1,0 +1,349 @@
+"""ctypes binding of libpps (include/pps.h): same names, marshalling only.
+
+Every computation happens in the CUDA library; this module only converts
+Python values to the C structs, calls the C entry points and turns status
+codes into ``PpsError``.  PyTorch provides device memory and streams.  If
+libpps.so is missing the first call raises: there is no other code path.
+
+    from paper_1909_07717_gb300 import pps, synth
+    ctx = pps.pps_create(pps.pps_ctx_desc(max_states=4096, max_opp=8))
+    ...
+    pps.pps_destroy(ctx)
+
+``Searcher`` wraps a context and torch tensors for the common case.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libpps.so")
+
+PPS_ABI_VERSION = 1
+PPS_MAX_OPP = 16
+PPS_MAX_SPEEDS = 8
+PPS_MAX_K = 4096
+
+PPS_OK, PPS_EINVAL, PPS_ENOMEM, PPS_ECUDA, PPS_ETIMEOUT, PPS_ENOTIMPL = range(6)
+PPS_DEVICE_PTRS = 1
+PPS_STATE_OK, PPS_STATE_INVALID, PPS_STATE_INCONSISTENT = 0, 1, 2
+
+c_float, c_int32, c_size_t, c_void_p = (ctypes.c_float, ctypes.c_int32,
+                                        ctypes.c_size_t, ctypes.c_void_p)
+
+
+class pps_state(ctypes.Structure):
+    _fields_ = [("ball", c_float * 2), ("n_opp", c_int32),
+                ("opp_pos", (c_float * 2) * PPS_MAX_OPP),
+                ("opp_vel", (c_float * 2) * PPS_MAX_OPP),
+                ("ball_decel", c_float), ("vmax", c_float), ("amax", c_float),
+                ("field_len", c_float), ("field_wid", c_float),
+                ("goal_width", c_float), ("K", c_int32)]
+
+
+class pps_grid(ctypes.Structure):
+    _fields_ = [("spacing", c_float), ("nx", c_int32), ("ny", c_int32),
+                ("x0", c_float), ("y0", c_float)]
+
+
+class pps_params(ctypes.Structure):
+    _fields_ = [(n, c_float) for n in (
+        "w_angle", "w_dist", "w_margin", "margin_cap", "tau_safe",
+        "robot_radius", "reach_radius", "min_pass_dist")]
+
+
+class pps_best(ctypes.Structure):
+    _fields_ = [("idx", c_int32), ("ix", c_int32), ("iy", c_int32),
+                ("speed_idx", c_int32), ("score", c_float),
+                ("margin", c_float), ("n_feasible", c_int32),
+                ("status", c_int32)]
+
+
+class pps_debug_out(ctypes.Structure):
+    _fields_ = [("margin", c_void_p), ("score", c_void_p), ("T", c_void_p),
+                ("T_stride", c_int32)]
+
+
+class pps_ctx_desc(ctypes.Structure):
+    _fields_ = [("device", c_int32), ("stream", c_void_p),
+                ("mem_budget_bytes", c_size_t), ("max_states", c_int32),
+                ("max_points", c_int32), ("max_speeds", c_int32),
+                ("max_K", c_int32), ("max_opp", c_int32)]
+
+    def __init__(self, max_states=1, device=0, stream=None, mem_budget_bytes=0,
+                 max_points=0, max_speeds=0, max_K=0, max_opp=0):
+        super().__init__(device, stream, mem_budget_bytes, max_states,
+                         max_points, max_speeds, max_K, max_opp)
+
+
+# numpy mirrors of the record layouts (for packing batches).
+STATE_DTYPE = np.dtype([("ball", "<f4", (2,)), ("n_opp", "<i4"),
+                        ("opp_pos", "<f4", (PPS_MAX_OPP, 2)),
+                        ("opp_vel", "<f4", (PPS_MAX_OPP, 2)),
+                        ("ball_decel", "<f4"), ("vmax", "<f4"),
+                        ("amax", "<f4"), ("field_len", "<f4"),
+                        ("field_wid", "<f4"), ("goal_width", "<f4"),
+                        ("K", "<i4")])
+BEST_DTYPE = np.dtype([("idx", "<i4"), ("ix", "<i4"), ("iy", "<i4"),
+                       ("speed_idx", "<i4"), ("score", "<f4"),
+                       ("margin", "<f4"), ("n_feasible", "<i4"),
+                       ("status", "<i4")])
+assert STATE_DTYPE.itemsize == ctypes.sizeof(pps_state) == 296
+assert BEST_DTYPE.itemsize == ctypes.sizeof(pps_best) == 32
+
+EXPORTS = ("pps_abi_version", "pps_status_string", "pps_last_error",
+           "pps_default_params", "pps_grid_from_field", "pps_mask_words",
+           "pps_create", "pps_destroy", "pps_search", "pps_sync", "pps_reset",
+           "pps_launch_info")
+
+
+class PpsError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+
+
+_STATUS = {PPS_OK: "PPS_OK", PPS_EINVAL: "PPS_EINVAL", PPS_ENOMEM: "PPS_ENOMEM",
+           PPS_ECUDA: "PPS_ECUDA", PPS_ETIMEOUT: "PPS_ETIMEOUT",
+           PPS_ENOTIMPL: "PPS_ENOTIMPL"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libpps.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} is missing: build it with "
+                    "`python -m paper_1909_07717_gb300.build`")
+            L = ctypes.CDLL(LIB_PATH)
+            P = ctypes.POINTER
+            L.pps_abi_version.restype = ctypes.c_int
+            L.pps_status_string.restype = ctypes.c_char_p
+            L.pps_status_string.argtypes = [ctypes.c_int]
+            L.pps_last_error.restype = ctypes.c_char_p
+            L.pps_last_error.argtypes = [c_void_p]
+            L.pps_default_params.argtypes = [P(pps_params)]
+            L.pps_grid_from_field.argtypes = [c_float, c_float, c_float,
+                                              P(pps_grid)]
+            L.pps_mask_words.restype = c_size_t
+            L.pps_mask_words.argtypes = [P(pps_grid), ctypes.c_int]
+            L.pps_create.argtypes = [P(c_void_p), P(pps_ctx_desc)]
+            L.pps_destroy.restype = None
+            L.pps_destroy.argtypes = [c_void_p]
+            L.pps_search.argtypes = [c_void_p, c_void_p, ctypes.c_int,
+                                     P(pps_grid), c_void_p, ctypes.c_int,
+                                     P(pps_params), c_void_p, c_void_p,
+                                     P(pps_debug_out), ctypes.c_uint]
+            L.pps_sync.argtypes = [c_void_p]
+            L.pps_reset.argtypes = [c_void_p]
+            L.pps_launch_info.argtypes = [c_void_p, P(ctypes.c_int),
+                                          P(ctypes.c_int)]
+            if L.pps_abi_version() != PPS_ABI_VERSION:
+                raise RuntimeError("libpps ABI version mismatch")
+            _lib = L
+        return _lib
+
+
+def _check(status, ctx=None):
+    if status != PPS_OK:
+        raise PpsError(status, pps_last_error(ctx))
+    return status
+
+
+# ------------------------------------------------------------ entry points
+def pps_abi_version() -> int:
+    return lib().pps_abi_version()
+
+
+def pps_status_string(status: int) -> str:
+    return lib().pps_status_string(status).decode()
+
+
+def pps_last_error(ctx=None) -> str:
+    return lib().pps_last_error(ctx).decode()
+
+
+def pps_default_params() -> pps_params:
+    p = pps_params()
+    _check(lib().pps_default_params(ctypes.byref(p)))
+    return p
+
+
+def pps_grid_from_field(L: float, W: float, spacing: float) -> pps_grid:
+    g = pps_grid()
+    _check(lib().pps_grid_from_field(L, W, spacing, ctypes.byref(g)))
+    return g
+
+
+def pps_mask_words(grid: pps_grid, n_speeds: int) -> int:
+    return lib().pps_mask_words(ctypes.byref(grid), n_speeds)
+
+
+def pps_create(desc: pps_ctx_desc):
+    ctx = c_void_p()
+    _check(lib().pps_create(ctypes.byref(ctx), ctypes.byref(desc)))
+    return ctx
+
+
+def pps_destroy(ctx) -> None:
+    lib().pps_destroy(ctx)
+
+
+def pps_search(ctx, states, n_states, grid, speeds, n_speeds, params,
+               out_best, out_mask, dbg=None, flags=0) -> int:
+    """Buffers are raw addresses (int) or None; ``speeds`` is a host
+    address of n_speeds float32; ``params`` a pps_params or None."""
+    return _check(lib().pps_search(
+        ctx, states, n_states, ctypes.byref(grid), speeds, n_speeds,
+        ctypes.byref(params) if params is not None else None, out_best,
+        out_mask, ctypes.byref(dbg) if dbg is not None else None, flags), ctx)
+
+
+def pps_sync(ctx) -> int:
+    return _check(lib().pps_sync(ctx), ctx)
+
+
+def pps_reset(ctx) -> int:
+    return _check(lib().pps_reset(ctx), ctx)
+
+
+def pps_launch_info(ctx):
+    n, c = ctypes.c_int(), ctypes.c_int()
+    _check(lib().pps_launch_info(ctx, ctypes.byref(n), ctypes.byref(c)), ctx)
+    return n.value, c.value
+
+
+# ------------------------------------------------------------- marshalling
+def params_from_dict(d: dict | None) -> pps_params:
+    p = pps_default_params()
+    for k, v in (d or {}).items():
+        setattr(p, k, float(v))
+    return p
+
+
+def pack_states(batch: dict) -> np.ndarray:
+    """A synth batch -> structured array of pps_state records."""
+    S = batch["ball"].shape[0]
+    out = np.zeros(S, STATE_DTYPE)
+    out["ball"] = batch["ball"]
+    out["n_opp"] = batch["n_opp"]
+    J = batch["opp_pos"].shape[1]
+    if J > PPS_MAX_OPP:
+        raise ValueError("more opponent slots than PPS_MAX_OPP")
+    out["opp_pos"][:, :J] = batch["opp_pos"]
+    out["opp_vel"][:, :J] = batch["opp_vel"]
+    for k in ("ball_decel", "vmax", "amax", "field_len", "field_wid",
+              "goal_width", "K"):
+        out[k] = batch[k]
+    return out
+
+
+def unpack_best(raw: np.ndarray) -> np.ndarray:
+    """uint8 bytes of pps_best records -> structured array."""
+    return np.frombuffer(np.ascontiguousarray(raw).tobytes(), BEST_DTYPE)
+
+
+class Searcher:
+    """A libpps context plus torch buffers.
+
+    ``search`` takes device tensors (uint8 view of pps_state records, see
+    ``states_to_device``) and returns device tensors; ``search_host`` takes
+    and returns host numpy/pinned buffers through the library's own staging.
+    """
+
+    def __init__(self, max_states, max_opp=8, device=0, stream=None,
+                 mem_budget_bytes=0, max_K=0, max_points=0):
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else \
+            torch.cuda.current_stream(self.device)
+        desc = pps_ctx_desc(max_states=max_states, device=device,
+                            stream=self.stream.cuda_stream,
+                            mem_budget_bytes=mem_budget_bytes,
+                            max_opp=max_opp, max_K=max_K,
+                            max_points=max_points)
+        self.ctx = pps_create(desc)
+
+    def close(self):
+        if self.ctx is not None:
+            pps_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def states_to_device(self, batch: dict):
+        rec = pack_states(batch)
+        t = self.torch.from_numpy(rec.view(np.uint8).reshape(-1).copy())
+        return t.to(self.device)
+
+    def alloc_outputs(self, n_states, grid, n_speeds, mask=True, debug=False,
+                      T_stride=0):
+        torch = self.torch
+        out = {"best": torch.empty(n_states * 32, dtype=torch.uint8,
+                                   device=self.device)}
+        if mask:
+            out["mask"] = torch.empty(
+                n_states * pps_mask_words(grid, n_speeds), dtype=torch.int32,
+                device=self.device)
+        if debug:
+            P = grid.nx * grid.ny
+            out["margin"] = torch.empty((n_states, n_speeds, P),
+                                        dtype=torch.float32, device=self.device)
+            out["score"] = torch.empty_like(out["margin"])
+            if T_stride:
+                out["T"] = torch.empty((n_states, P, T_stride),
+                                       dtype=torch.float32, device=self.device)
+        return out
+
+    def search(self, states_dev, n_states, grid, speeds, params=None,
+               out=None, mask=True, debug=False, T_stride=0):
+        """Enqueue the search on the context's stream (device buffers)."""
+        sp = np.ascontiguousarray(np.asarray(speeds, np.float32))
+        if out is None:
+            out = self.alloc_outputs(n_states, grid, len(sp), mask, debug,
+                                     T_stride)
+        dbg = None
+        if "margin" in out or "T" in out:
+            dbg = pps_debug_out(
+                out["margin"].data_ptr() if "margin" in out else None,
+                out["score"].data_ptr() if "score" in out else None,
+                out["T"].data_ptr() if "T" in out else None,
+                out["T"].shape[2] if "T" in out else 0)
+        prm = params if isinstance(params, pps_params) else \
+            params_from_dict(params)
+        pps_search(self.ctx, states_dev.data_ptr(), n_states, grid,
+                   sp.ctypes.data, len(sp), prm, out["best"].data_ptr(),
+                   out["mask"].data_ptr() if "mask" in out else None, dbg,
+                   PPS_DEVICE_PTRS)
+        return out
+
+    def search_host(self, states_np, grid, speeds, params, best_np,
+                    mask_np=None):
+        """Host buffers (numpy; pinned for async copies): enqueue only."""
+        sp = np.ascontiguousarray(np.asarray(speeds, np.float32))
+        prm = params if isinstance(params, pps_params) else \
+            params_from_dict(params)
+        pps_search(self.ctx, states_np.ctypes.data, states_np.shape[0], grid,
+                   sp.ctypes.data, len(sp), prm, best_np.ctypes.data,
+                   None if mask_np is None else mask_np.ctypes.data, None, 0)
+
+    def sync(self):
+        pps_sync(self.ctx)
+
+    @staticmethod
+    def best_numpy(best_dev) -> np.ndarray:
+        return unpack_best(best_dev.cpu().numpy())
