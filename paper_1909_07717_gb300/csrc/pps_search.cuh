@@ -36,7 +36,13 @@
 
 namespace pps {
 
-constexpr int kTPB = 128;          // threads per CTA = grid points per tile
+#ifndef PPS_TPB
+#define PPS_TPB 128
+#endif
+#ifndef PPS_MIN_BLOCKS
+#define PPS_MIN_BLOCKS 1
+#endif
+constexpr int kTPB = PPS_TPB;      // threads per CTA = grid points per tile
 constexpr float kFar = 1.0e18f;    // offset of an unused opponent slot
 constexpr float kD2Floor = 1.0e-30f;  // keeps 1/d finite when d == 0
 
@@ -225,8 +231,12 @@ __device__ __forceinline__ void sample_loop(const StateK& sk,
                                             float twoabD,
                                             const float (&sp2)[VMAX],
                                             float (&mv)[VMAX], float* Trow) {
-    for (int k = 1; k <= sk.K; ++k) {
-        const float f = __fmul_rn((float)k, sk.invK);
+    // Float sample counter: exact for K <= 2^24, and keeps integer-to-float
+    // conversions out of the loop.
+    const float Kf = (float)sk.K;
+    for (float kf = 1.f; kf <= Kf; kf += 1.f) {
+        const float f = __fmul_rn(kf, sk.invK);
+        const int k = (int)kf;
         float n = CUDART_INF_F;
 #pragma unroll
         for (int j = 0; j < JMAX; ++j)
@@ -255,6 +265,10 @@ __device__ __forceinline__ float shot_angle(const pps_state& st,
     float s[JMAX], e[JMAX];
     bool all = false;
     const float r2 = __fmul_rn(r, r);
+    // Post directions from c: A to the lower post, B to the upper one.
+    const float ax = gx, ay = __fsub_rn(-sk.hw, cy), by = __fsub_rn(sk.hw, cy);
+    const float a2r2 = __fmul_rn(__fmaf_rn(ax, ax, __fmul_rn(ay, ay)), r2);
+    const float b2r2 = __fmul_rn(__fmaf_rn(ax, ax, __fmul_rn(by, by)), r2);
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
         s[j] = 1e30f;
@@ -264,6 +278,17 @@ __device__ __forceinline__ float shot_angle(const pps_state& st,
             const float dy = __fsub_rn(st.opp_pos[j][1], cy);
             const float d2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
             all |= d2 <= r2;
+            // A disc can block part of the mouth only if its centre lies in
+            // the wedge A..B or it reaches one of the two boundary rays;
+            // the others are skipped before any trigonometry.
+            const float ca = __fsub_rn(__fmul_rn(ax, dy), __fmul_rn(ay, dx));
+            const float cb = __fsub_rn(__fmul_rn(ax, dy), __fmul_rn(by, dx));
+            const bool inside = ca >= 0.f && cb <= 0.f;
+            const bool near_a = __fmaf_rn(ax, dx, __fmul_rn(ay, dy)) > 0.f &&
+                                __fmul_rn(ca, ca) <= a2r2;
+            const bool near_b = __fmaf_rn(ax, dx, __fmul_rn(by, dy)) > 0.f &&
+                                __fmul_rn(cb, cb) <= b2r2;
+            if (!(inside || near_a || near_b)) continue;
             const float d = __fsqrt_rn(d2);
             const float phi = atan2f(dy, dx);
             const float half = asinf(fminf(__fdiv_rn(r, d), 1.f));
@@ -333,15 +358,11 @@ __device__ __forceinline__ void eval_point(const SearchArgs& a,
     const double cxd = fma((double)ix, (double)a.g, (double)a.x0);
     const bool front = cxd < (double)sk.Lh;
     const float gx = (float)((double)sk.Lh - cxd);
-    const float theta =
-        shot_angle<JMAX>(st, sk, front, cx, cy, gx, a.prm.robot_radius);
-    const float dg = __fsqrt_rn(__fmaf_rn(gx, gx, __fmul_rn(cy, cy)));
-    const float base =
-        __fsub_rn(__fmul_rn(a.prm.w_angle,
-                            __fmul_rn(theta, 0.318309886183790672f)),
-                  __fmul_rn(a.prm.w_dist, __fmul_rn(dg, sk.inv_diag)));
+    // The shot angle only enters the score of a feasible pass: points with
+    // no feasible speed skip it (a warp runs it if any of its lanes needs it).
     const float reach_lhs = __fmul_rn(sk.fK, twoabD);
     const bool long_enough = D >= a.prm.min_pass_dist;
+    bool any_ok = false;
 #pragma unroll
     for (int v = 0; v < VMAX; ++v) {
         const bool reach = __fsub_rn(sp2[v], reach_lhs) >= 0.f;
@@ -355,11 +376,24 @@ __device__ __forceinline__ void eval_point(const SearchArgs& a,
         const bool ok = sk.valid && reach && long_enough && m > a.prm.tau_safe;
         res.margin[v] = m;
         res.feas[v] = ok;
-        res.score[v] =
-            ok ? __fadd_rn(base, __fmul_rn(a.prm.w_margin,
-                                           fminf(m, a.prm.margin_cap)))
-               : -CUDART_INF_F;
+        any_ok |= ok && v < a.V;
     }
+    float theta = 0.f;
+    if (any_ok)
+        theta = shot_angle<JMAX>(st, sk, front, cx, cy, gx, a.prm.robot_radius);
+    const float dg = __fsqrt_rn(__fmaf_rn(gx, gx, __fmul_rn(cy, cy)));
+    const float base =
+        __fsub_rn(__fmul_rn(a.prm.w_angle,
+                            __fmul_rn(theta, 0.318309886183790672f)),
+                  __fmul_rn(a.prm.w_dist, __fmul_rn(dg, sk.inv_diag)));
+#pragma unroll
+    for (int v = 0; v < VMAX; ++v)
+        res.score[v] =
+            res.feas[v]
+                ? __fadd_rn(base, __fmul_rn(a.prm.w_margin,
+                                            fminf(res.margin[v],
+                                                  a.prm.margin_cap)))
+                : -CUDART_INF_F;
 }
 
 __device__ __forceinline__ unsigned long long warp_max_u64(
@@ -374,7 +408,7 @@ __device__ __forceinline__ unsigned long long warp_max_u64(
 
 // ------------------------------------------------------------ the kernels
 template <int JMAX, int VMAX>
-__global__ void __launch_bounds__(kTPB)
+__global__ void __launch_bounds__(kTPB, PPS_MIN_BLOCKS)
     search_kernel(const SearchArgs a) {
     __shared__ pps_state st;
     __shared__ unsigned long long red_key[kTPB / 32];
@@ -387,9 +421,9 @@ __global__ void __launch_bounds__(kTPB)
         const int s = (int)(item / a.tiles);
         const int tile = (int)(item - (long long)s * a.tiles);
         __syncthreads();  // the previous item is done with st / red_*
-        if (threadIdx.x < kWords)
-            reinterpret_cast<uint32_t*>(&st)[threadIdx.x] =
-                reinterpret_cast<const uint32_t*>(a.states + s)[threadIdx.x];
+        for (int i = threadIdx.x; i < kWords; i += kTPB)
+            reinterpret_cast<uint32_t*>(&st)[i] =
+                reinterpret_cast<const uint32_t*>(a.states + s)[i];
         __syncthreads();
 
         const StateK sk = derive_state(st, a.prm, JMAX, a.kmax);
