@@ -169,7 +169,8 @@ int pps_abi_version(void);
 const char* pps_status_string(pps_status s);
 
 /* Last error message of a context ("" if none); valid until the next call
- * on the context.  ctx may be NULL (then: the last pps_create failure). */
+ * on the context.  ctx may be NULL (then: the calling thread's last
+ * pps_create or pps_search_noalloc failure). */
 const char* pps_last_error(const pps_ctx* ctx);
 
 /* Library defaults: weights 1, margin_cap 1 s, tau_safe 0, robot_radius
@@ -231,6 +232,47 @@ pps_status pps_sync(pps_ctx* ctx);
 /* Clear a failed context's error state after the caller has dealt with
  * the cause.  ECUDA if the device is still unusable. */
 pps_status pps_reset(pps_ctx* ctx);
+
+/* Largest n_states of one pps_search_noalloc call. */
+#define PPS_NOALLOC_MAX_STATES 16384
+
+/* The exact search without any device allocation.  The paper has no
+ * counterpart: this is a deployment variant of pps_search.
+ *
+ * Some callers cannot call cudaMalloc: a robot's real-time decision loop
+ * that forbids allocation once it is running (cudaMalloc can block and
+ * synchronise the device), or a host whose device memory is already handed
+ * out by another allocator.  They cannot create a context either, since
+ * pps_create allocates the per-call scratch.  This entry point needs no
+ * context: the scratch (an argmax key and a feasible count per state) is a
+ * fixed array compiled into the library, PPS_NOALLOC_MAX_STATES * 12 bytes
+ * (192 KiB), which every GPU that loads the library holds until the process
+ * exits.  The call itself allocates nothing: no cudaMalloc, no cudaFree, no
+ * allocating library routine.
+ *
+ *   device    CUDA device ordinal; made current by the call
+ *   stream    cudaStream_t to run on (NULL = the legacy default stream)
+ *   max_opp   1..16: <= 8 runs the 8-slot kernel; states with more
+ *             opponents than the kernel's slots are marked invalid
+ *   states, out_best, out_mask: DEVICE memory, as pps_search with
+ *             PPS_DEVICE_PTRS (out_mask may be NULL); results are identical
+ *             to pps_search's for the same inputs
+ *   grid, speeds, params: host memory, as pps_search
+ * Returns EINVAL for n_states > PPS_NOALLOC_MAX_STATES or any argument
+ * pps_search would reject (message in pps_last_error(NULL)), ECUDA on a
+ * device error.  Enqueues the work on `stream` and returns without waiting.
+ *
+ * The first call on each device resolves the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture.  Every call on a device shares the
+ * one array and clears the slots it uses before the search, so calls that
+ * overlap on the GPU (concurrent streams, or several host threads) race on
+ * it: order them on one stream or synchronise between them. */
+pps_status pps_search_noalloc(int device, void* stream, int max_opp,
+                              const pps_state* states, int n_states,
+                              const pps_grid* grid, const float* speeds,
+                              int n_speeds, const pps_params* params,
+                              pps_best* out_best, uint32_t* out_mask);
 
 /* Number of SMs and the CTAs per SM the search kernel runs with (for
  * benchmarks and the autotuner); EINVAL on NULL. */

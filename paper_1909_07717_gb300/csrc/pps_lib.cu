@@ -153,6 +153,10 @@ int occupancy_of() {
 
 }  // namespace
 
+// The calling thread's error buffer behind pps_last_error(NULL), shared with
+// the no-allocation entry point in pps_noalloc.cu.
+char* pps_thread_error_buffer() { return g_create_err; }
+
 extern "C" {
 
 int pps_abi_version(void) { return PPS_ABI_VERSION; }

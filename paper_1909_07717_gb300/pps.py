@@ -27,6 +27,7 @@ PPS_ABI_VERSION = 1
 PPS_MAX_OPP = 16
 PPS_MAX_SPEEDS = 8
 PPS_MAX_K = 4096
+PPS_NOALLOC_MAX_STATES = 16384
 
 PPS_OK, PPS_EINVAL, PPS_ENOMEM, PPS_ECUDA, PPS_ETIMEOUT, PPS_ENOTIMPL = range(6)
 PPS_DEVICE_PTRS = 1
@@ -98,7 +99,7 @@ assert BEST_DTYPE.itemsize == ctypes.sizeof(pps_best) == 32
 EXPORTS = ("pps_abi_version", "pps_status_string", "pps_last_error",
            "pps_default_params", "pps_grid_from_field", "pps_mask_words",
            "pps_create", "pps_destroy", "pps_search", "pps_sync", "pps_reset",
-           "pps_launch_info")
+           "pps_launch_info", "pps_search_noalloc")
 
 
 class PpsError(RuntimeError):
@@ -147,6 +148,10 @@ def lib():
             L.pps_reset.argtypes = [c_void_p]
             L.pps_launch_info.argtypes = [c_void_p, P(ctypes.c_int),
                                           P(ctypes.c_int)]
+            L.pps_search_noalloc.argtypes = [
+                ctypes.c_int, c_void_p, ctypes.c_int, c_void_p, ctypes.c_int,
+                P(pps_grid), c_void_p, ctypes.c_int, P(pps_params), c_void_p,
+                c_void_p]
             if L.pps_abi_version() != PPS_ABI_VERSION:
                 raise RuntimeError("libpps ABI version mismatch")
             _lib = L
@@ -206,6 +211,17 @@ def pps_search(ctx, states, n_states, grid, speeds, n_speeds, params,
         ctx, states, n_states, ctypes.byref(grid), speeds, n_speeds,
         ctypes.byref(params) if params is not None else None, out_best,
         out_mask, ctypes.byref(dbg) if dbg is not None else None, flags), ctx)
+
+
+def pps_search_noalloc(device, stream, max_opp, states, n_states, grid,
+                       speeds, n_speeds, params, out_best, out_mask) -> int:
+    """No-allocation search: ``states``, ``out_best``, ``out_mask`` are
+    device addresses (int); ``speeds`` a host address of n_speeds float32;
+    ``stream`` a cudaStream_t handle (int) or None."""
+    return _check(lib().pps_search_noalloc(
+        device, stream, max_opp, states, n_states, ctypes.byref(grid), speeds,
+        n_speeds, ctypes.byref(params) if params is not None else None,
+        out_best, out_mask))
 
 
 def pps_sync(ctx) -> int:
