@@ -222,7 +222,7 @@ def run_pps(args):
     import torch
 
     from paper_1909_07717_gb300 import build as pbuild
-    from paper_1909_07717_gb300 import pps, synth
+    from paper_1909_07717_gb300 import pps, shard, synth
 
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)
@@ -244,9 +244,8 @@ def run_pps(args):
     w = _workload()
     if args.states:
         w.n_states = args.states
-    # Rank r searches its own states: the workload's seed for rank 0, a
-    # rank-derived seed for the others (weak scaling, no shared data).
-    seed = w.seed if rank == 0 else 1000 + rank
+    # Rank r searches its own states (weak scaling, no shared data).
+    seed = shard.rank_seed(w.seed, rank)
     batch = synth.ssl_states(seed, w.n_states, field_len=w.field[0],
                              field_wid=w.field[1], n_opp=w.n_opp, K=w.K,
                              ball_decel=w.ball_decel, vmax=w.vmax,
@@ -284,13 +283,9 @@ def run_pps(args):
     if dist is not None:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = shard.max_over_ranks(sum(step_ms), dist, dev)
     evals_per_step = S * P * V * J
-    value = world * evals_per_step * args.steps / (total_ms / 1e3)
+    value = shard.job_rate(evals_per_step, world, args.steps, total_ms)
 
     # correctness guard on the measured output (cheap, after timing)
     best = pps.unpack_best(out["best"].cpu().numpy())
@@ -322,12 +317,9 @@ def run_pps(args):
         step_host()
         ev2[i][1].record(stream)
     torch.cuda.synchronize()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in ev2)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * evals_per_step * args.steps / (e2e_ms / 1e3)
+    e2e_ms = shard.max_over_ranks(sum(a.elapsed_time(b) for a, b in ev2),
+                                  dist, dev)
+    e2e_value = shard.job_rate(evals_per_step, world, args.steps, e2e_ms)
     host_best = pps.unpack_best(h_best.numpy())
     if host_best.tobytes() != best.tobytes():
         print("host-buffer path disagrees with device path", file=sys.stderr)
