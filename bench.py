@@ -41,9 +41,9 @@ REF_SAMPLE_STATES = 16       # oracle sample per step of --impl reference
 
 # Algorithmic work of the formulation the kernel evaluates (FP32 lane-ops,
 # an FMA counted once; MUFU ops counted separately):
-#   per opponent interaction (state, point, sample, opponent): 15 FP32 + 2 MUFU
+#   per opponent interaction (state, point, sample, opponent): 14 FP32 + 2 MUFU
 #   per ball evaluation (state, point, sample, speed):          3 FP32 + 1 MUFU
-OPS_INTERACTION, MUFU_INTERACTION = 15, 2
+OPS_INTERACTION, MUFU_INTERACTION = 14, 2
 OPS_BALL, MUFU_BALL = 3, 1
 FP32_LANES_PER_SM = 128
 MUFU_LANES_PER_SM = 32   # ncu: XU pipe peak ~1 warp-instr/clk/SM on GB300

@@ -128,8 +128,11 @@ cudaError_t launch(const pps::SearchArgs& a, int num_sms, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         if (occ < 1) occ = 1;
     }
+    // One warp per work item of 32 points; no more CTAs than items need.
+    const long long items = (long long)a.n_states * a.words;
     long long grid = (long long)num_sms * occ;
-    if (grid > a.n_items) grid = a.n_items;
+    const long long need = (items + pps::kTPB / 32 - 1) / (pps::kTPB / 32);
+    if (grid > need) grid = need;
     pps::search_kernel<J, V><<<(unsigned)grid, pps::kTPB, 0, st>>>(a);
     pps::finalize_kernel<J, V><<<(a.n_states + 127) / 128, 128, 0, st>>>(a);
     return cudaGetLastError();
@@ -400,16 +403,16 @@ pps_status pps_search(pps_ctx* ctx, const pps_state* states, int n_states,
     a.g = grid->spacing;
     a.x0 = grid->x0;
     a.y0 = grid->y0;
-    a.tiles = (int)((P + pps::kTPB - 1) / pps::kTPB);
-    a.n_items = (long long)n_states * a.tiles;
     a.V = n_speeds;
     a.kmax = on_dev && dbg && dbg->T ? (dbg->T_stride < ctx->max_K
                                             ? dbg->T_stride
                                             : ctx->max_K)
                                      : ctx->max_K;
-    for (int v = 0; v < n_speeds; ++v) {
-        a.speed[v] = speeds[v];
-        a.speed2[v] = speeds[v] * speeds[v];
+    // Unused speed slots repeat the last speed (their results are dropped).
+    for (int v = 0; v < PPS_MAX_SPEEDS; ++v) {
+        const float sv = speeds[v < n_speeds ? v : n_speeds - 1];
+        a.speed[v] = sv;
+        a.speed2[v] = sv * sv;
     }
     a.prm = prm;
     a.keys = ctx->keys;

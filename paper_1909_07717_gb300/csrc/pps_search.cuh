@@ -2,8 +2,8 @@
 //
 // One persistent kernel covers the whole hot path of the SBIP-based dynamic
 // passing-point search (ZJUNlict 2019, Sec. 4.1-4.4), fused:
-//   A1 state staging        the CTA copies its state into shared memory,
-//                           every thread derives the per-state constants
+//   A1 state staging        each warp reads its state record through the
+//                           read-only cache and derives the constants
 //   A2 candidate geometry   one lane per grid point; samples are generated
 //                           on the fly, never stored
 //   A3 opponent intercept   T_k = min_j t_j(sample k), opponents held in
@@ -14,16 +14,19 @@
 //   A5 shot angle, goal distance      once per point
 //   A6 feasibility, score, mask       warp ballot -> one mask word per warp
 //   A7 argmax               warp shuffle -> CTA -> 64-bit atomicMax per state
-// A second, tiny kernel turns the per-state keys into pps_best records.
+// Work is dealt per warp (a state and 32 consecutive grid points), so warps
+// never wait for one another.  A second, tiny kernel turns the per-state
+// keys into pps_best records.
 //
 // Arithmetic (FP32, inputs as given).  The opponent time is computed in a
-// scaled form: with sigma = sqrt(2 amax), w' = w / sigma, v' = vmax / sigma,
-// q'^2 = w'^2 + d and m' = max(v' - q', 0), the 1-D bang-bang time is
-//     t = ((v' - w')^2 + d - m'^2) / vmax,
+// scaled form: speeds in units of vmax (w' = w / vmax), lengths multiplied
+// by kappa = 2 amax / vmax^2 (d' = kappa d), q' = sqrt(w'^2 + d') and
+// m' = max(1 - q', 0); the 1-D bang-bang time is
+//     t = ((1 - w')^2 + d' - m'^2) * vmax / (2 amax),
 // which equals (-w + sqrt(w^2 + 2 amax d)) / amax while the robot is still
-// accelerating (q' <= v') and (vmax - w)/amax + (d - d_acc)/vmax once it
+// accelerating (q' <= 1) and (vmax - w)/amax + (d - d_acc)/vmax once it
 // cruises; the numerator is the tangent-line identity of those two branches,
-// so no branch is needed.  The ball term uses
+// so no branch is needed, and m' is a single saturating add.  The ball term uses
 //     a T_k + sqrt(v^2 - 2 a s_k),   margin = (min_k(...) - v) / a,
 // which is min_k (T_k - (v - sqrt(v^2 - 2 a s_k)) / a) rearranged.
 #pragma once
@@ -37,12 +40,16 @@
 namespace pps {
 
 #ifndef PPS_TPB
-#define PPS_TPB 128
+#define PPS_TPB 512  // measured best of 32..512 on the batched workload
 #endif
 #ifndef PPS_MIN_BLOCKS
 #define PPS_MIN_BLOCKS 1
 #endif
-constexpr int kTPB = PPS_TPB;      // threads per CTA = grid points per tile
+#ifndef PPS_KUNROLL
+#define PPS_KUNROLL 2
+#endif
+constexpr int kKUnroll = PPS_KUNROLL;  // unroll of the sample loop
+constexpr int kTPB = PPS_TPB;      // threads per CTA (16 independent warps)
 constexpr float kFar = 1.0e18f;    // offset of an unused opponent slot
 constexpr float kD2Floor = 1.0e-30f;  // keeps 1/d finite when d == 0
 
@@ -51,8 +58,6 @@ struct SearchArgs {
     int n_states;
     int nx, ny, P, words;  // words = ceil(P / 32): mask words per speed
     float g, x0, y0;
-    int tiles;             // tiles (of kTPB points) per state
-    long long n_items;     // n_states * tiles
     int V;
     int kmax;              // largest K accepted
     float speed[PPS_MAX_SPEEDS];
@@ -81,6 +86,10 @@ __device__ __forceinline__ float sqrt_fast(float x) {
     return y;
 }
 
+// Square roots of the intercept formula and the ball term: one MUFU each.
+__device__ __forceinline__ float sqrt_pos(float x) { return sqrt_fast(x); }
+__device__ __forceinline__ float sqrt_ball(float x) { return sqrt_fast(x); }
+
 // Order-preserving map of a float onto uint32 (for the packed argmax key).
 __device__ __forceinline__ uint32_t order_bits(float f) {
     uint32_t u = __float_as_uint(f);
@@ -103,13 +112,13 @@ __device__ __forceinline__ bool is_finite(float x) {
 // Per-state constants (A1).  Computed identically by every thread.
 struct StateK {
     float bx, by;
-    float vh;            // vmax / sigma
-    float inv_sigma;     // 1 / sqrt(2 amax)
-    float inv_vmax;
+    float kappa;         // 2 amax / vmax^2: length unit of the scaled form
+    float inv_vmax;      // velocity unit of the scaled form
+    float t_scale;       // vmax / (2 amax): scaled numerator -> seconds
     float ab;            // ball deceleration
     float two_ab;
-    float ab_over_vmax;
-    float reach;
+    float at_scale;      // ab * t_scale: scaled numerator -> a * T
+    float reach;         // reach radius in scaled units
     float Lh, hw;        // goal line x, half mouth width
     float inv_diag;
     float invK;
@@ -147,14 +156,14 @@ __device__ __forceinline__ StateK derive_state(const pps_state& st,
     }
     d.bx = st.ball[0];
     d.by = st.ball[1];
-    const float sigma = __fsqrt_rn(__fmul_rn(2.f, st.amax));
-    d.inv_sigma = __frcp_rn(sigma);
-    d.vh = __fdiv_rn(st.vmax, sigma);
+    const float two_amax = __fmul_rn(2.f, st.amax);
+    d.kappa = __fdiv_rn(two_amax, __fmul_rn(st.vmax, st.vmax));
     d.inv_vmax = __frcp_rn(st.vmax);
+    d.t_scale = __fdiv_rn(st.vmax, two_amax);
     d.ab = st.ball_decel;
     d.two_ab = __fmul_rn(2.f, st.ball_decel);
-    d.ab_over_vmax = __fdiv_rn(st.ball_decel, st.vmax);
-    d.reach = prm.reach_radius;
+    d.at_scale = __fmul_rn(st.ball_decel, d.t_scale);
+    d.reach = __fmul_rn(d.kappa, prm.reach_radius);
     d.Lh = __fmul_rn(0.5f, st.field_len);
     d.hw = __fmul_rn(0.5f, st.goal_width);
     d.inv_diag = __frcp_rn(__fsqrt_rn(__fmaf_rn(
@@ -165,8 +174,19 @@ __device__ __forceinline__ StateK derive_state(const pps_state& st,
     return d;
 }
 
-// Opponents in registers: (b - o) and u / sigma per slot; unused slots are
-// parked at kFar so they can never hold the minimum.
+// kappa (x - y) with one rounding: x - y is split exactly into hi + lo.
+__device__ __forceinline__ float scaled_diff(float x, float y, float kappa) {
+    const float hi = __fsub_rn(x, y);
+    const float t = __fsub_rn(hi, x);
+    const float lo = __fadd_rn(__fsub_rn(x, __fsub_rn(hi, t)),
+                               __fsub_rn(-y, t));
+    return __fmaf_rn(kappa, hi, __fmul_rn(kappa, lo));
+}
+
+// Opponents in registers, in scaled units: kappa (b - o) and u / vmax per
+// slot; unused slots are parked at kFar so they can never hold the minimum.
+// kappa (b - o) is formed from the exact difference (an error-free two-sum)
+// so it carries a single rounding.
 template <int JMAX>
 struct OppRegs {
     float bx[JMAX], by[JMAX], ux[JMAX], uy[JMAX];
@@ -179,10 +199,10 @@ __device__ __forceinline__ void load_opps(const pps_state& st,
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
         if (j < sk.nopp) {
-            o.bx[j] = __fsub_rn(sk.bx, st.opp_pos[j][0]);
-            o.by[j] = __fsub_rn(sk.by, st.opp_pos[j][1]);
-            o.ux[j] = __fmul_rn(st.opp_vel[j][0], sk.inv_sigma);
-            o.uy[j] = __fmul_rn(st.opp_vel[j][1], sk.inv_sigma);
+            o.bx[j] = scaled_diff(sk.bx, st.opp_pos[j][0], sk.kappa);
+            o.by[j] = scaled_diff(sk.by, st.opp_pos[j][1], sk.kappa);
+            o.ux[j] = __fmul_rn(st.opp_vel[j][0], sk.inv_vmax);
+            o.uy[j] = __fmul_rn(st.opp_vel[j][1], sk.inv_vmax);
         } else {
             o.bx[j] = kFar;
             o.by[j] = kFar;
@@ -192,32 +212,40 @@ __device__ __forceinline__ void load_opps(const pps_state& st,
     }
 }
 
-// A3: numerator of one opponent's intercept time at the sample
-// p = b + f (c - b); the time is num / vmax.  GEN adds the speed clamp and
-// the reach radius (num = 0 within reach).
+// A3: one opponent's intercept time at the sample p = b + f (c - b), as the
+// scaled numerator n (time = n * vmax / (2 amax)).  In units where vmax = 1
+// and lengths are multiplied by kappa = 2 amax / vmax^2, the along-line speed
+// w' = w / vmax, distance d' = kappa d and q' = sqrt(w'^2 + d') give
+//     n = (1 - w')^2 + d' - max(1 - q', 0)^2,
+// and max(1 - q', 0) is one saturating add because 1 - q' <= 1.  GEN adds
+// the clamp of w' to [-1, 1] and the reach radius (n = 0 within reach).
+__device__ __forceinline__ float one_minus_sat(float x) {
+    float y;  // saturate(1 - x) = clamp(1 - x, 0, 1)
+    asm("add.rn.sat.f32 %0, %1, %2;" : "=f"(y) : "f"(1.f), "f"(-x));
+    return y;
+}
+
 template <bool GEN>
 __device__ __forceinline__ float sbip_num(float f, float cbx, float cby,
                                           float obx, float oby, float oux,
-                                          float ouy, float vh, float reach) {
-    const float rx = __fmaf_rn(f, cbx, obx);  // p - o
+                                          float ouy, float reach) {
+    const float rx = __fmaf_rn(f, cbx, obx);  // kappa (p - o)
     const float ry = __fmaf_rn(f, cby, oby);
     const float d2 = __fmaf_rn(rx, rx, __fmaf_rn(ry, ry, kD2Floor));
     const float ig = rsqrt_fast(d2);
     const float d = __fmul_rn(d2, ig);
     float w = __fmul_rn(__fmaf_rn(oux, rx, __fmul_rn(ouy, ry)), ig);
     if (GEN) {
-        w = fminf(fmaxf(w, -vh), vh);
+        w = fminf(fmaxf(w, -1.f), 1.f);
         const float dl = __fsub_rn(d, reach);
         const float dc = fmaxf(dl, 0.f);
-        const float q = sqrt_fast(__fmaf_rn(w, w, dc));
-        const float m = __fsub_rn(vh, fminf(q, vh));
-        const float e = __fsub_rn(vh, w);
+        const float m = one_minus_sat(sqrt_pos(__fmaf_rn(w, w, dc)));
+        const float e = __fsub_rn(1.f, w);
         const float num = __fmaf_rn(-m, m, __fmaf_rn(e, e, dc));
         return dl > 0.f ? num : 0.f;
     } else {
-        const float q = sqrt_fast(__fmaf_rn(w, w, d));
-        const float m = __fsub_rn(vh, fminf(q, vh));
-        const float e = __fsub_rn(vh, w);
+        const float m = one_minus_sat(sqrt_pos(__fmaf_rn(w, w, d)));
+        const float e = __fsub_rn(1.f, w);
         return __fmaf_rn(-m, m, __fmaf_rn(e, e, d));
     }
 }
@@ -229,27 +257,35 @@ __device__ __forceinline__ void sample_loop(const StateK& sk,
                                             const OppRegs<JMAX>& o,
                                             float cbx, float cby,
                                             float twoabD,
-                                            const float (&sp2)[VMAX],
+                                            const float (&sp2)[PPS_MAX_SPEEDS],
                                             float (&mv)[VMAX], float* Trow) {
     // Float sample counter: exact for K <= 2^24, and keeps integer-to-float
     // conversions out of the loop.
     const float Kf = (float)sk.K;
+#pragma unroll kKUnroll
     for (float kf = 1.f; kf <= Kf; kf += 1.f) {
         const float f = __fmul_rn(kf, sk.invK);
         const int k = (int)kf;
-        float n = CUDART_INF_F;
+        // The JMAX interactions are independent; their minimum is taken as
+        // a balanced tree so the sample's critical path stays short.
+        float t[JMAX];
 #pragma unroll
         for (int j = 0; j < JMAX; ++j)
-            n = fminf(n, sbip_num<GEN>(f, cbx, cby, o.bx[j], o.by[j], o.ux[j],
-                                       o.uy[j], sk.vh, sk.reach));
+            t[j] = sbip_num<GEN>(f, cbx, cby, o.bx[j], o.by[j], o.ux[j],
+                                 o.uy[j], sk.reach);
+#pragma unroll
+        for (int w = 1; w < JMAX; w *= 2)
+#pragma unroll
+            for (int j = 0; j + w < JMAX; j += 2 * w) t[j] = fminf(t[j], t[j + w]);
+        const float n = t[0];
         if (TDBG && Trow)
-            Trow[k - 1] = sk.nopp ? __fmul_rn(n, sk.inv_vmax) : CUDART_INF_F;
-        const float aT = __fmul_rn(n, sk.ab_over_vmax);
-        const float as = __fmul_rn(f, twoabD);
+            Trow[k - 1] = sk.nopp ? __fmul_rn(n, sk.t_scale) : CUDART_INF_F;
+        const float aT = __fmul_rn(n, sk.at_scale);
+        const float nf = -f;
 #pragma unroll
         for (int v = 0; v < VMAX; ++v)
-            mv[v] = fminf(mv[v],
-                          __fadd_rn(aT, sqrt_fast(__fsub_rn(sp2[v], as))));
+            mv[v] = fminf(mv[v], __fadd_rn(aT, sqrt_ball(__fmaf_rn(
+                                                 nf, twoabD, sp2[v]))));
     }
 }
 
@@ -331,21 +367,26 @@ __device__ __forceinline__ void eval_point(const SearchArgs& a,
                                            const OppRegs<JMAX>& o, int ix,
                                            int iy, float* Trow,
                                            PointResult<JMAX, VMAX>& res) {
-    const float cx = __fmaf_rn((float)ix, a.g, a.x0);
-    const float cy = __fmaf_rn((float)iy, a.g, a.y0);
-    const float cbx = __fsub_rn(cx, sk.bx);
-    const float cby = __fsub_rn(cy, sk.by);
-    const float D = __fsqrt_rn(__fmaf_rn(cbx, cbx, __fmul_rn(cby, cby)));
+    // A2: the grid point and c - b are exact in FP64 (x0 + ix g and its
+    // difference with the FP32 ball fit in 53 bits); the pass vector enters
+    // the sample loop in scaled units, kappa (c - b), with one rounding.
+    const double cxd = fma((double)ix, (double)a.g, (double)a.x0);
+    const double cyd = fma((double)iy, (double)a.g, (double)a.y0);
+    const double dxd = cxd - (double)sk.bx, dyd = cyd - (double)sk.by;
+    const float cx = (float)cxd, cy = (float)cyd;
+    const float cbx = (float)((double)sk.kappa * dxd);
+    const float cby = (float)((double)sk.kappa * dyd);
+    const float dxm = (float)dxd, dym = (float)dyd;
+    const float D = __fsqrt_rn(__fmaf_rn(dxm, dxm, __fmul_rn(dym, dym)));
     const float twoabD = __fmul_rn(sk.two_ab, D);
 
-    float sp[VMAX], sp2[VMAX], mv[VMAX];
+    // Speeds come straight from the kernel parameters (the host repeats the
+    // last speed in unused slots), so they need no registers of their own.
+    const float(&sp)[PPS_MAX_SPEEDS] = a.speed;
+    const float(&sp2)[PPS_MAX_SPEEDS] = a.speed2;
+    float mv[VMAX];
 #pragma unroll
-    for (int v = 0; v < VMAX; ++v) {
-        const int vv = v < a.V ? v : a.V - 1;  // unused slots repeat the last
-        sp[v] = a.speed[vv];
-        sp2[v] = a.speed2[vv];
-        mv[v] = CUDART_INF_F;
-    }
+    for (int v = 0; v < VMAX; ++v) mv[v] = CUDART_INF_F;
     if (sk.general)
         sample_loop<JMAX, VMAX, true, TDBG>(sk, o, cbx, cby, twoabD, sp2, mv,
                                             Trow);
@@ -354,18 +395,16 @@ __device__ __forceinline__ void eval_point(const SearchArgs& a,
                                              Trow);
 
     // A5: the receiver is in front of the goal line iff x0 + ix g < L/2,
-    // decided exactly (the FP64 product and sum are exact for these inputs).
-    const double cxd = fma((double)ix, (double)a.g, (double)a.x0);
+    // decided exactly on the FP64 grid coordinate.
     const bool front = cxd < (double)sk.Lh;
     const float gx = (float)((double)sk.Lh - cxd);
     // The shot angle only enters the score of a feasible pass: points with
     // no feasible speed skip it (a warp runs it if any of its lanes needs it).
-    const float reach_lhs = __fmul_rn(sk.fK, twoabD);
     const bool long_enough = D >= a.prm.min_pass_dist;
     bool any_ok = false;
 #pragma unroll
     for (int v = 0; v < VMAX; ++v) {
-        const bool reach = __fsub_rn(sp2[v], reach_lhs) >= 0.f;
+        const bool reach = __fmaf_rn(-sk.fK, twoabD, sp2[v]) >= 0.f;
         float m;
         if (!reach)
             m = -CUDART_INF_F;
@@ -407,38 +446,37 @@ __device__ __forceinline__ unsigned long long warp_max_u64(
 }
 
 // ------------------------------------------------------------ the kernels
+// Every warp is an independent persistent worker: a work item is (state,
+// 32 consecutive grid points), items are dealt round-robin over all warps
+// of the grid, and nothing is shared between the warps of a CTA -- no
+// shared memory, no barriers, so a warp that finishes early (for example
+// because none of its points needed a shot angle) starts its next item at
+// once.  The state record is read through the read-only cache (all lanes
+// read the same address, one transaction per warp).
 template <int JMAX, int VMAX>
 __global__ void __launch_bounds__(kTPB, PPS_MIN_BLOCKS)
     search_kernel(const SearchArgs a) {
-    __shared__ pps_state st;
-    __shared__ unsigned long long red_key[kTPB / 32];
-    __shared__ int red_cnt[kTPB / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int kWords = sizeof(pps_state) / 4;
-    static_assert(sizeof(pps_state) % 4 == 0, "pps_state is word-sized");
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (kTPB / 32);
+    const long long gw = (long long)blockIdx.x * (kTPB / 32) + (threadIdx.x >> 5);
+    const long long n_items = (long long)a.n_states * a.words;
 
-    for (long long item = blockIdx.x; item < a.n_items; item += gridDim.x) {
-        const int s = (int)(item / a.tiles);
-        const int tile = (int)(item - (long long)s * a.tiles);
-        __syncthreads();  // the previous item is done with st / red_*
-        for (int i = threadIdx.x; i < kWords; i += kTPB)
-            reinterpret_cast<uint32_t*>(&st)[i] =
-                reinterpret_cast<const uint32_t*>(a.states + s)[i];
-        __syncthreads();
-
+    for (long long item = gw; item < n_items; item += warps) {
+        const int s = (int)(item / a.words);
+        const int chunk = (int)(item - (long long)s * a.words);
+        const pps_state& st = a.states[s];
         const StateK sk = derive_state(st, a.prm, JMAX, a.kmax);
         OppRegs<JMAX> o;
         load_opps<JMAX>(st, sk, o);
 
-        const int p = tile * kTPB + threadIdx.x;
+        const int p = chunk * 32 + lane;
         const bool active = p < a.P;
         const int pc = active ? p : a.P - 1;
         const int iy = pc / a.nx, ix = pc - iy * a.nx;
 
         PointResult<JMAX, VMAX> r;
-        float* Trow = nullptr;
         if (a.dbg_T) {
-            Trow = a.dbg_T + ((long long)s * a.P + pc) * a.T_stride;
+            float* Trow = a.dbg_T + ((long long)s * a.P + pc) * a.T_stride;
             eval_point<JMAX, VMAX, true>(a, st, sk, o, ix, iy,
                                          active ? Trow : nullptr, r);
         } else {
@@ -463,10 +501,8 @@ __global__ void __launch_bounds__(kTPB, PPS_MIN_BLOCKS)
             }
             if (v < a.V) {
                 const uint32_t word = __ballot_sync(0xffffffffu, f);
-                const int p0 = tile * kTPB + warp * 32;
-                if (a.mask && lane == 0 && p0 < a.P)
-                    a.mask[((long long)s * a.V + v) * a.words + (p0 >> 5)] =
-                        word;
+                if (a.mask && lane == 0)
+                    a.mask[((long long)s * a.V + v) * a.words + chunk] = word;
                 if (active) {
                     const long long o2 = ((long long)s * a.V + v) * a.P + p;
                     if (a.dbg_margin) a.dbg_margin[o2] = r.margin[v];
@@ -477,20 +513,8 @@ __global__ void __launch_bounds__(kTPB, PPS_MIN_BLOCKS)
         key = warp_max_u64(key);
         cnt = __reduce_add_sync(0xffffffffu, cnt);
         if (lane == 0) {
-            red_key[warp] = key;
-            red_cnt[warp] = cnt;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long k = red_key[0];
-            int c = red_cnt[0];
-#pragma unroll
-            for (int w = 1; w < kTPB / 32; ++w) {
-                k = red_key[w] > k ? red_key[w] : k;
-                c += red_cnt[w];
-            }
-            if (k) atomicMax(a.keys + s, k);
-            if (c) atomicAdd(a.counts + s, c);
+            if (key) atomicMax(a.keys + s, key);
+            if (cnt) atomicAdd(a.counts + s, cnt);
         }
     }
 }
