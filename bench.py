@@ -373,12 +373,64 @@ def run_pps(args):
                 "clocks": clk.summary(),
                 "gpu_launches": 2 * args.steps,
                 "states_per_s": world * S * args.steps / (total_ms / 1e3)}
-        print(json.dumps(line), flush=True)
     searcher.close()
+    if rank == 0:
+        if world == 1 and not args.no_uneven:
+            line["uneven"] = _uneven(args, dev, stream)
+        print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def _uneven(args, dev, stream):
+    """The uneven batch through a batched plan (autotuned, graph-captured):
+    8192 states mixing 12x9 m / 11 v 11 and 9x6 m / 6 v 6, grids
+    0.025-0.1 m, 1-8 speeds, K 32-128, decel 0.3-0.7; timed like the main
+    step (L2 flushed between runs, CUDA events on the plan's stream)."""
+    import torch
+    from paper_1909_07717_gb300 import pps, synth
+    batch = synth.uneven_batch(synth.UNEVEN_SEED, synth.UNEVEN_STATES)
+    S = synth.UNEVEN_STATES
+    jobs = pps.jobs_from_batch(batch)
+    searcher = pps.Searcher(max_states=S, max_opp=16, device=dev.index,
+                            stream=stream)
+    plan = pps.Plan(searcher, jobs, S, synth.DEFAULT_PARAMS, autotune=True,
+                    graph=True)
+    st = searcher.states_to_device(batch)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    t0 = time.perf_counter()
+    plan.run(st)             # autotunes and captures the graph
+    torch.cuda.synchronize()
+    first_s = time.perf_counter() - t0
+    for _ in range(2):
+        plan.run(st)
+    steps = max(3, min(args.steps, 5))
+    ev = [(torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        plan.run(st)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    best = pps.unpack_best(plan.best.cpu().numpy())
+    evals = sum(jobs[i].grid.nx * jobs[i].grid.ny * jobs[i].n_speeds
+                * int(batch["n_opp"][i]) for i in range(S))
+    groups = [{"opp_slots": g.opp_slots, "speed_slots": g.speed_slots,
+               "states": g.n_states, "cta_threads": g.cta_threads,
+               "items": g.n_items} for g in plan.groups()]
+    out = {"workload": (f"uneven_{S}: 12x9/11v11 + 9x6/6v6, grids "
+                        "0.025-0.1 m, 1-8 speeds, K 32-128 (seed 2)"),
+           "value": evals / (ms / 1e3), "unit": UNIT, "ms_per_run": ms,
+           "states_per_s": S / (ms / 1e3), "first_run_s": first_s,
+           "graph": True, "autotuned": True, "groups": groups,
+           "ok": bool(np.all(best["status"] == 0))}
+    plan.close()
+    searcher.close()
+    return out
 
 
 def main():
@@ -388,6 +440,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["pps", "reference"], default="pps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-uneven", action="store_true",
+                    help="skip the uneven-batch plan measurement")
     ap.add_argument("--states", type=int, default=0,
                     help="states per GPU (default: the workload's 4096); "
                          "smaller only for profiling captures")

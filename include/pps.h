@@ -274,6 +274,78 @@ pps_status pps_search_noalloc(int device, void* stream, int max_opp,
                               int n_speeds, const pps_params* params,
                               pps_best* out_best, uint32_t* out_mask);
 
+/* ---- Batched plans: uneven batches, per-state grids and speeds ---------
+ *
+ * A plan searches n_states states that each have their own receive grid and
+ * kick speeds (a field of 12x9 m at 0.025 m next to one of 9x6 m at 0.1 m,
+ * one speed next to eight), with the same per-candidate definition as
+ * pps_search (Sec. 4.2-4.3).  It is built once from the states' shapes; each
+ * pps_plan_run then searches the current contents of a device buffer of
+ * states.  The plan groups its states by kernel instance (6/8/12/16 opponent
+ * slots, 1/2/4/8 speed slots) and runs each group as one persistent launch
+ * whose work items are (state, 32 grid points), so states of very different
+ * sizes balance across the GPU. */
+
+/* One state's search shape.  60 bytes, 4-byte aligned. */
+typedef struct pps_job {
+    pps_grid grid;                 /* this state's receive points */
+    int32_t n_speeds;              /* 1..PPS_MAX_SPEEDS */
+    float speeds[PPS_MAX_SPEEDS];  /* kick speeds > 0, m/s (first n_speeds) */
+    int32_t max_opp;               /* most opponents the state will have,
+                                      0..16; picks the 6-, 8-, 12- or
+                                      16-slot kernel */
+} pps_job;
+
+typedef struct pps_plan pps_plan;
+
+/* pps_plan_create flags. */
+#define PPS_PLAN_AUTOTUNE 1u /* time each group's candidate CTA sizes (128,
+                                256, 512 threads) on the first run and keep
+                                the fastest; choices are cached per device
+                                and kernel instance for later plans */
+#define PPS_PLAN_GRAPH 2u    /* capture the run's launches in a CUDA graph
+                                and replay it while the buffers stay the
+                                same (re-captured when they change) */
+
+/* One kernel-instance group of a plan (pps_plan_groups). */
+typedef struct pps_plan_group {
+    int32_t opp_slots;    /* 6, 8, 12 or 16 */
+    int32_t speed_slots;  /* 1, 2, 4 or 8 */
+    int32_t n_states;
+    int32_t cta_threads;  /* CTA size in use */
+    int64_t n_items;      /* (state, 32-point) work items */
+    float tuned_ms[3];    /* autotuner's time per candidate (128, 256, 512
+                             threads); 0 when not measured */
+} pps_plan_group;
+
+/* Build a plan on ctx for n_states (1..2^24) states shaped by jobs (host
+ * memory; copied).  Mask layout: state s owns words
+ * [offset[s], offset[s+1]) of out_mask (pps_plan_mask_offsets), speed-major
+ * as in pps_search.  EINVAL on a bad job (grid or speeds as pps_search
+ * requires, max_opp outside 0..16), ENOMEM past the context's budget. */
+pps_status pps_plan_create(pps_ctx* ctx, const pps_job* jobs, int n_states,
+                           const pps_params* params, unsigned flags,
+                           pps_plan** out);
+
+/* Free a plan (waits for the context's stream first).  NULL is accepted. */
+void pps_plan_destroy(pps_plan* plan);
+
+/* Mask word offsets: offsets[0..n_states] (host), offsets[n_states] is the
+ * total number of words. */
+pps_status pps_plan_mask_offsets(const pps_plan* plan, int64_t* offsets);
+
+/* Search the states in `states` (DEVICE memory, n_states records in job
+ * order; a state with more opponents than its job's max_opp is invalid, see
+ * pps_best.status).  out_best (n_states records) and out_mask (total words,
+ * or NULL) are DEVICE memory.  Enqueued on the context's stream; the first
+ * run of an autotuned plan also times the candidates (synchronously). */
+pps_status pps_plan_run(pps_plan* plan, const pps_state* states,
+                        pps_best* out_best, uint32_t* out_mask);
+
+/* The plan's groups: up to cap entries into out, the count into *n. */
+pps_status pps_plan_groups(const pps_plan* plan, pps_plan_group* out, int cap,
+                           int* n);
+
 /* Number of SMs and the CTAs per SM the search kernel runs with (for
  * benchmarks and the autotuner); EINVAL on NULL. */
 pps_status pps_launch_info(const pps_ctx* ctx, int* num_sms,

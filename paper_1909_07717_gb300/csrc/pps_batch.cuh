@@ -1,0 +1,189 @@
+// pps_batch.cuh -- device code of the batched plans (uneven batches).
+//
+// A plan searches states that each carry their own receive grid and kick
+// speeds (pps_job).  The host groups the states into buckets by kernel
+// instance (opponent slots JMAX, speed slots VMAX); within a bucket the work
+// items are (state, 32 consecutive grid points) as in the single-grid
+// search, numbered through a per-bucket prefix sum of each state's item
+// count, so states of very different grid sizes share one persistent launch.
+// Every warp walks the item range round-robin and finds its state by binary
+// search in the prefix sum.  The per-point arithmetic is eval_point, the same
+// device code the single-grid search runs.
+#pragma once
+
+#include "pps_search.cuh"
+
+namespace pps {
+
+struct BatchArgs {
+    const pps_state* states;      // every state of the plan
+    const pps_job* jobs;          // per-state grid, speeds, opponent slots
+    const int* bucket_states;     // state indices of this bucket
+    const long long* item_start;  // n_bucket + 1 prefix sums of items
+    const long long* mask_off;    // per state: its first mask word
+    int n_bucket;
+    long long n_items;
+    int kmax;
+    pps_params prm;
+    pps_best* best;
+    uint32_t* mask;               // may be null
+    unsigned long long* keys;     // per state of the plan
+    int* counts;                  // per state of the plan
+};
+
+// A job's grid in the form the kernels use; speeds padded with the last one.
+struct JobView {
+    ItemGrid gr;
+    int nx, P, words;
+    float sp[PPS_MAX_SPEEDS], sp2[PPS_MAX_SPEEDS];
+};
+
+__device__ __forceinline__ void load_job(const pps_job& j, JobView& v) {
+    v.gr.g = j.grid.spacing;
+    v.gr.x0 = j.grid.x0;
+    v.gr.y0 = j.grid.y0;
+    v.gr.V = j.n_speeds;
+    v.nx = j.grid.nx;
+    v.P = j.grid.nx * j.grid.ny;
+    v.words = (v.P + 31) >> 5;
+#pragma unroll
+    for (int s = 0; s < PPS_MAX_SPEEDS; ++s) {
+        const float x = j.speeds[s < j.n_speeds ? s : j.n_speeds - 1];
+        v.sp[s] = x;
+        v.sp2[s] = __fmul_rn(x, x);
+    }
+}
+
+// Largest b with item_start[b] <= item (item_start is non-decreasing).
+__device__ __forceinline__ int find_bucket_slot(const long long* start, int n,
+                                                long long item) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(start + mid) <= item)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int JMAX, int VMAX, int TPB>
+__global__ void __launch_bounds__(TPB) batch_search_kernel(const BatchArgs a) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (TPB / 32);
+    const long long gw = (long long)blockIdx.x * (TPB / 32) + (threadIdx.x >> 5);
+
+    for (long long item = gw; item < a.n_items; item += warps) {
+        const int b = find_bucket_slot(a.item_start, a.n_bucket, item);
+        const int s = __ldg(a.bucket_states + b);
+        const int chunk = (int)(item - __ldg(a.item_start + b));
+        JobView jv;
+        load_job(a.jobs[s], jv);
+        const pps_state& st = a.states[s];
+        const StateK sk = derive_state(st, a.prm, JMAX, a.kmax);
+        OppRegs<JMAX> o;
+        load_opps<JMAX>(st, sk, o);
+
+        const int p = chunk * 32 + lane;
+        const bool active = p < jv.P;
+        const int pc = active ? p : jv.P - 1;
+        const int iy = pc / jv.nx, ix = pc - iy * jv.nx;
+
+        PointResult<JMAX, VMAX> r;
+        eval_point<JMAX, VMAX, false>(a.prm, jv.gr, jv.sp, jv.sp2, st, sk, o,
+                                      ix, iy, nullptr, r);
+
+        int cnt = 0;
+        unsigned long long key = 0ull;
+        const long long mbase = __ldg(a.mask_off + s);
+#pragma unroll
+        for (int v = 0; v < VMAX; ++v) {
+            const bool f = active && v < jv.gr.V && r.feas[v];
+            cnt += f;
+            if (f) {
+                const uint32_t idx = (uint32_t)(v * jv.P + p);
+                const unsigned long long k2 =
+                    ((unsigned long long)order_bits(r.score[v]) << 32) |
+                    (unsigned long long)(~idx);
+                key = k2 > key ? k2 : key;
+            }
+            if (v < jv.gr.V) {
+                const uint32_t word = __ballot_sync(0xffffffffu, f);
+                if (a.mask && lane == 0)
+                    a.mask[mbase + (long long)v * jv.words + chunk] = word;
+            }
+        }
+        key = warp_max_u64(key);
+        cnt = __reduce_add_sync(0xffffffffu, cnt);
+        if (lane == 0) {
+            if (key) atomicMax(a.keys + s, key);
+            if (cnt) atomicAdd(a.counts + s, cnt);
+        }
+    }
+}
+
+// One thread per state of the bucket: decode the key, re-evaluate the
+// winning point for its margin and check that the score reproduces.
+template <int JMAX, int VMAX>
+__global__ void __launch_bounds__(128) batch_finalize_kernel(const BatchArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n_bucket) return;
+    const int s = a.bucket_states[i];
+    const pps_state& st = a.states[s];
+    const StateK sk = derive_state(st, a.prm, JMAX, a.kmax);
+    JobView jv;
+    load_job(a.jobs[s], jv);
+    pps_best b;
+    b.n_feasible = a.counts[s];
+    b.status = sk.valid ? PPS_STATE_OK : PPS_STATE_INVALID;
+    const unsigned long long key = a.keys[s];
+    if (!sk.valid || key == 0ull) {
+        b.idx = sk.valid ? -1 : -2;
+        b.ix = b.iy = b.speed_idx = -1;
+        b.score = -CUDART_INF_F;
+        b.margin = -CUDART_INF_F;
+        b.n_feasible = sk.valid ? b.n_feasible : 0;
+    } else {
+        const uint32_t idx = ~(uint32_t)(key & 0xffffffffull);
+        const int v = (int)(idx / (uint32_t)jv.P);
+        const int p = (int)(idx - (uint32_t)v * (uint32_t)jv.P);
+        b.idx = (int)idx;
+        b.speed_idx = v;
+        b.iy = p / jv.nx;
+        b.ix = p - b.iy * jv.nx;
+        b.score = order_bits_inv((uint32_t)(key >> 32));
+        OppRegs<JMAX> o;
+        load_opps<JMAX>(st, sk, o);
+        PointResult<JMAX, VMAX> r;
+        eval_point<JMAX, VMAX, false>(a.prm, jv.gr, jv.sp, jv.sp2, st, sk, o,
+                                      b.ix, b.iy, nullptr, r);
+        float m = 0.f, sc = 0.f;
+        bool f = false;
+#pragma unroll
+        for (int w = 0; w < VMAX; ++w)
+            if (w == v) {
+                m = r.margin[w];
+                sc = r.score[w];
+                f = r.feas[w];
+            }
+        b.margin = m;
+        if (!f || __float_as_uint(sc) != __float_as_uint(b.score))
+            b.status |= PPS_STATE_INCONSISTENT;
+    }
+    a.best[s] = b;
+}
+
+// Launch entry points, one translation unit per opponent-slot count
+// (6, 8, 12, 16: the plan picks the smallest that holds a job's opponents).
+#define PPS_BATCH_DECLARE(J)                                              \
+    cudaError_t batch_launch_j##J(const BatchArgs& a, int vmax, int tpb, \
+                                  int grid, cudaStream_t st);            \
+    int batch_occupancy_j##J(int vmax, int tpb);
+PPS_BATCH_DECLARE(6)
+PPS_BATCH_DECLARE(8)
+PPS_BATCH_DECLARE(12)
+PPS_BATCH_DECLARE(16)
+#undef PPS_BATCH_DECLARE
+
+}  // namespace pps

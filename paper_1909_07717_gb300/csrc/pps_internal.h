@@ -1,0 +1,23 @@
+// pps_internal.h -- library-internal access to a context (C++ linkage, not
+// exported through the C ABI): device, stream, SM count, limits, budgeted
+// device allocation and the context's error message.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "pps.h"
+
+int pps_ctx_device(const pps_ctx* ctx);
+cudaStream_t pps_ctx_stream(const pps_ctx* ctx);
+int pps_ctx_num_sms(const pps_ctx* ctx);
+int pps_ctx_max_K(const pps_ctx* ctx);
+bool pps_ctx_failed(const pps_ctx* ctx);
+// Allocate `bytes` of device memory against the context's budget.
+pps_status pps_ctx_alloc(pps_ctx* ctx, void** p, size_t bytes,
+                         const char* what);
+void pps_ctx_free(pps_ctx* ctx, void* p, size_t bytes);
+// printf-style message into the context's error buffer; returns `s`.
+pps_status pps_ctx_error(pps_ctx* ctx, pps_status s, const char* fmt, ...);
+// Record a CUDA failure on the context (marks it failed).
+pps_status pps_ctx_cuda_error(pps_ctx* ctx, cudaError_t e, const char* what);

@@ -13,6 +13,7 @@
 #include <new>
 
 #include "pps.h"
+#include "pps_internal.h"
 #include "pps_search.cuh"
 
 struct pps_ctx {
@@ -159,6 +160,33 @@ int occupancy_of() {
 // The calling thread's error buffer behind pps_last_error(NULL), shared with
 // the no-allocation entry point in pps_noalloc.cu.
 char* pps_thread_error_buffer() { return g_create_err; }
+
+int pps_ctx_device(const pps_ctx* ctx) { return ctx->device; }
+cudaStream_t pps_ctx_stream(const pps_ctx* ctx) { return ctx->stream; }
+int pps_ctx_num_sms(const pps_ctx* ctx) { return ctx->num_sms; }
+int pps_ctx_max_K(const pps_ctx* ctx) { return ctx->max_K; }
+bool pps_ctx_failed(const pps_ctx* ctx) { return ctx->failed; }
+
+pps_status pps_ctx_alloc(pps_ctx* ctx, void** p, size_t bytes,
+                         const char* what) {
+    return dev_alloc(ctx, p, bytes, what);
+}
+
+void pps_ctx_free(pps_ctx* ctx, void* p, size_t bytes) {
+    dev_free(ctx, p, bytes);
+}
+
+pps_status pps_ctx_error(pps_ctx* ctx, pps_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(ctx->err, sizeof ctx->err, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+pps_status pps_ctx_cuda_error(pps_ctx* ctx, cudaError_t e, const char* what) {
+    return cuda_fail(ctx, e, what);
+}
 
 extern "C" {
 

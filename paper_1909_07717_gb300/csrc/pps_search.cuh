@@ -360,8 +360,18 @@ struct PointResult {
     bool feas[VMAX];
 };
 
+// Grid and speed list of the point being evaluated (shared by the whole
+// batch in pps_search, per state in the batched plans).
+struct ItemGrid {
+    float g, x0, y0;
+    int V;
+};
+
 template <int JMAX, int VMAX, bool TDBG>
-__device__ __forceinline__ void eval_point(const SearchArgs& a,
+__device__ __forceinline__ void eval_point(const pps_params& prm,
+                                           const ItemGrid& gr,
+                                           const float (&sp)[PPS_MAX_SPEEDS],
+                                           const float (&sp2)[PPS_MAX_SPEEDS],
                                            const pps_state& st,
                                            const StateK& sk,
                                            const OppRegs<JMAX>& o, int ix,
@@ -370,8 +380,8 @@ __device__ __forceinline__ void eval_point(const SearchArgs& a,
     // A2: the grid point and c - b are exact in FP64 (x0 + ix g and its
     // difference with the FP32 ball fit in 53 bits); the pass vector enters
     // the sample loop in scaled units, kappa (c - b), with one rounding.
-    const double cxd = fma((double)ix, (double)a.g, (double)a.x0);
-    const double cyd = fma((double)iy, (double)a.g, (double)a.y0);
+    const double cxd = fma((double)ix, (double)gr.g, (double)gr.x0);
+    const double cyd = fma((double)iy, (double)gr.g, (double)gr.y0);
     const double dxd = cxd - (double)sk.bx, dyd = cyd - (double)sk.by;
     const float cx = (float)cxd, cy = (float)cyd;
     const float cbx = (float)((double)sk.kappa * dxd);
@@ -380,10 +390,7 @@ __device__ __forceinline__ void eval_point(const SearchArgs& a,
     const float D = __fsqrt_rn(__fmaf_rn(dxm, dxm, __fmul_rn(dym, dym)));
     const float twoabD = __fmul_rn(sk.two_ab, D);
 
-    // Speeds come straight from the kernel parameters (the host repeats the
-    // last speed in unused slots), so they need no registers of their own.
-    const float(&sp)[PPS_MAX_SPEEDS] = a.speed;
-    const float(&sp2)[PPS_MAX_SPEEDS] = a.speed2;
+    // Unused speed slots repeat the last speed; their results are dropped.
     float mv[VMAX];
 #pragma unroll
     for (int v = 0; v < VMAX; ++v) mv[v] = CUDART_INF_F;
@@ -400,7 +407,7 @@ __device__ __forceinline__ void eval_point(const SearchArgs& a,
     const float gx = (float)((double)sk.Lh - cxd);
     // The shot angle only enters the score of a feasible pass: points with
     // no feasible speed skip it (a warp runs it if any of its lanes needs it).
-    const bool long_enough = D >= a.prm.min_pass_dist;
+    const bool long_enough = D >= prm.min_pass_dist;
     bool any_ok = false;
 #pragma unroll
     for (int v = 0; v < VMAX; ++v) {
@@ -412,26 +419,26 @@ __device__ __forceinline__ void eval_point(const SearchArgs& a,
             m = CUDART_INF_F;
         else
             m = __fdiv_rn(__fsub_rn(mv[v], sp[v]), sk.ab);
-        const bool ok = sk.valid && reach && long_enough && m > a.prm.tau_safe;
+        const bool ok = sk.valid && reach && long_enough && m > prm.tau_safe;
         res.margin[v] = m;
         res.feas[v] = ok;
-        any_ok |= ok && v < a.V;
+        any_ok |= ok && v < gr.V;
     }
     float theta = 0.f;
     if (any_ok)
-        theta = shot_angle<JMAX>(st, sk, front, cx, cy, gx, a.prm.robot_radius);
+        theta = shot_angle<JMAX>(st, sk, front, cx, cy, gx, prm.robot_radius);
     const float dg = __fsqrt_rn(__fmaf_rn(gx, gx, __fmul_rn(cy, cy)));
     const float base =
-        __fsub_rn(__fmul_rn(a.prm.w_angle,
+        __fsub_rn(__fmul_rn(prm.w_angle,
                             __fmul_rn(theta, 0.318309886183790672f)),
-                  __fmul_rn(a.prm.w_dist, __fmul_rn(dg, sk.inv_diag)));
+                  __fmul_rn(prm.w_dist, __fmul_rn(dg, sk.inv_diag)));
 #pragma unroll
     for (int v = 0; v < VMAX; ++v)
         res.score[v] =
             res.feas[v]
-                ? __fadd_rn(base, __fmul_rn(a.prm.w_margin,
+                ? __fadd_rn(base, __fmul_rn(prm.w_margin,
                                             fminf(res.margin[v],
-                                                  a.prm.margin_cap)))
+                                                  prm.margin_cap)))
                 : -CUDART_INF_F;
 }
 
@@ -475,12 +482,14 @@ __global__ void __launch_bounds__(kTPB, PPS_MIN_BLOCKS)
         const int iy = pc / a.nx, ix = pc - iy * a.nx;
 
         PointResult<JMAX, VMAX> r;
+        const ItemGrid gr{a.g, a.x0, a.y0, a.V};
         if (a.dbg_T) {
             float* Trow = a.dbg_T + ((long long)s * a.P + pc) * a.T_stride;
-            eval_point<JMAX, VMAX, true>(a, st, sk, o, ix, iy,
-                                         active ? Trow : nullptr, r);
+            eval_point<JMAX, VMAX, true>(a.prm, gr, a.speed, a.speed2, st, sk,
+                                         o, ix, iy, active ? Trow : nullptr, r);
         } else {
-            eval_point<JMAX, VMAX, false>(a, st, sk, o, ix, iy, nullptr, r);
+            eval_point<JMAX, VMAX, false>(a.prm, gr, a.speed, a.speed2, st, sk,
+                                          o, ix, iy, nullptr, r);
         }
 
         // A6: mask words, debug outputs, feasible count.
@@ -549,7 +558,9 @@ __global__ void __launch_bounds__(128) finalize_kernel(const SearchArgs a) {
         OppRegs<JMAX> o;
         load_opps<JMAX>(st, sk, o);
         PointResult<JMAX, VMAX> r;
-        eval_point<JMAX, VMAX, false>(a, st, sk, o, b.ix, b.iy, nullptr, r);
+        const ItemGrid gr{a.g, a.x0, a.y0, a.V};
+        eval_point<JMAX, VMAX, false>(a.prm, gr, a.speed, a.speed2, st, sk, o,
+                                      b.ix, b.iy, nullptr, r);
         float m = 0.f, sc = 0.f;
         bool f = false;
 #pragma unroll

@@ -81,6 +81,21 @@ class pps_ctx_desc(ctypes.Structure):
                          max_points, max_speeds, max_K, max_opp)
 
 
+class pps_job(ctypes.Structure):
+    _fields_ = [("grid", pps_grid), ("n_speeds", c_int32),
+                ("speeds", c_float * PPS_MAX_SPEEDS), ("max_opp", c_int32)]
+
+
+class pps_plan_group(ctypes.Structure):
+    _fields_ = [("opp_slots", c_int32), ("speed_slots", c_int32),
+                ("n_states", c_int32), ("cta_threads", c_int32),
+                ("n_items", ctypes.c_int64), ("tuned_ms", c_float * 3)]
+
+
+PPS_PLAN_AUTOTUNE = 1
+PPS_PLAN_GRAPH = 2
+
+
 # numpy mirrors of the record layouts (for packing batches).
 STATE_DTYPE = np.dtype([("ball", "<f4", (2,)), ("n_opp", "<i4"),
                         ("opp_pos", "<f4", (PPS_MAX_OPP, 2)),
@@ -99,7 +114,9 @@ assert BEST_DTYPE.itemsize == ctypes.sizeof(pps_best) == 32
 EXPORTS = ("pps_abi_version", "pps_status_string", "pps_last_error",
            "pps_default_params", "pps_grid_from_field", "pps_mask_words",
            "pps_create", "pps_destroy", "pps_search", "pps_sync", "pps_reset",
-           "pps_launch_info", "pps_search_noalloc")
+           "pps_launch_info", "pps_search_noalloc", "pps_plan_create",
+           "pps_plan_destroy", "pps_plan_mask_offsets", "pps_plan_run",
+           "pps_plan_groups")
 
 
 class PpsError(RuntimeError):
@@ -152,6 +169,15 @@ def lib():
                 ctypes.c_int, c_void_p, ctypes.c_int, c_void_p, ctypes.c_int,
                 P(pps_grid), c_void_p, ctypes.c_int, P(pps_params), c_void_p,
                 c_void_p]
+            L.pps_plan_create.argtypes = [c_void_p, c_void_p, ctypes.c_int,
+                                          P(pps_params), ctypes.c_uint,
+                                          P(c_void_p)]
+            L.pps_plan_destroy.restype = None
+            L.pps_plan_destroy.argtypes = [c_void_p]
+            L.pps_plan_mask_offsets.argtypes = [c_void_p, c_void_p]
+            L.pps_plan_run.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+            L.pps_plan_groups.argtypes = [c_void_p, c_void_p, ctypes.c_int,
+                                          P(ctypes.c_int)]
             if L.pps_abi_version() != PPS_ABI_VERSION:
                 raise RuntimeError("libpps ABI version mismatch")
             _lib = L
@@ -222,6 +248,40 @@ def pps_search_noalloc(device, stream, max_opp, states, n_states, grid,
         device, stream, max_opp, states, n_states, ctypes.byref(grid), speeds,
         n_speeds, ctypes.byref(params) if params is not None else None,
         out_best, out_mask))
+
+
+def pps_plan_create(ctx, jobs, n_states, params=None, flags=0):
+    """``jobs``: a ctypes array of pps_job (host)."""
+    plan = c_void_p()
+    _check(lib().pps_plan_create(
+        ctx, ctypes.addressof(jobs), n_states,
+        ctypes.byref(params) if params is not None else None, flags,
+        ctypes.byref(plan)), ctx)
+    return plan
+
+
+def pps_plan_destroy(plan) -> None:
+    lib().pps_plan_destroy(plan)
+
+
+def pps_plan_mask_offsets(plan, n_states, ctx=None) -> np.ndarray:
+    off = np.zeros(n_states + 1, np.int64)
+    _check(lib().pps_plan_mask_offsets(plan, off.ctypes.data), ctx)
+    return off
+
+
+def pps_plan_run(plan, states, out_best, out_mask, ctx=None) -> int:
+    """Device addresses (int); out_mask may be None."""
+    return _check(lib().pps_plan_run(plan, states, out_best, out_mask), ctx)
+
+
+def pps_plan_groups(plan, ctx=None):
+    n = ctypes.c_int()
+    _check(lib().pps_plan_groups(plan, None, 0, ctypes.byref(n)), ctx)
+    arr = (pps_plan_group * max(1, n.value))()
+    _check(lib().pps_plan_groups(plan, ctypes.addressof(arr), n.value,
+                                 ctypes.byref(n)), ctx)
+    return [arr[i] for i in range(n.value)]
 
 
 def pps_sync(ctx) -> int:
@@ -363,3 +423,60 @@ class Searcher:
     @staticmethod
     def best_numpy(best_dev) -> np.ndarray:
         return unpack_best(best_dev.cpu().numpy())
+
+
+def jobs_from_batch(batch: dict):
+    """pps_job records of a batch with per-state shapes (see
+    synth.uneven_batch): the grid of each state's field at its spacing."""
+    S = batch["ball"].shape[0]
+    jobs = (pps_job * S)()
+    for i in range(S):
+        g = pps_grid_from_field(float(batch["field_len"][i]),
+                                float(batch["field_wid"][i]),
+                                float(batch["spacing"][i]))
+        jobs[i].grid = g
+        n = int(batch["n_speeds"][i])
+        jobs[i].n_speeds = n
+        for v in range(n):
+            jobs[i].speeds[v] = float(batch["speeds"][i][v])
+        jobs[i].max_opp = int(batch["n_opp"][i])
+    return jobs
+
+
+class Plan:
+    """A batched plan on a Searcher's context, with device output buffers."""
+
+    def __init__(self, searcher, jobs, n_states, params=None,
+                 autotune=True, graph=True):
+        self.s = searcher
+        self.n = n_states
+        self.jobs = jobs
+        flags = (PPS_PLAN_AUTOTUNE if autotune else 0) | \
+            (PPS_PLAN_GRAPH if graph else 0)
+        prm = params if isinstance(params, pps_params) else \
+            params_from_dict(params)
+        self.plan = pps_plan_create(searcher.ctx, jobs, n_states, prm, flags)
+        self.offsets = pps_plan_mask_offsets(self.plan, n_states, searcher.ctx)
+        torch = searcher.torch
+        self.best = torch.empty(n_states * 32, dtype=torch.uint8,
+                                device=searcher.device)
+        self.mask = torch.empty(max(1, int(self.offsets[-1])),
+                                dtype=torch.int32, device=searcher.device)
+
+    def run(self, states_dev, mask=True):
+        pps_plan_run(self.plan, states_dev.data_ptr(), self.best.data_ptr(),
+                     self.mask.data_ptr() if mask else None, self.s.ctx)
+
+    def groups(self):
+        return pps_plan_groups(self.plan, self.s.ctx)
+
+    def close(self):
+        if self.plan is not None:
+            pps_plan_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

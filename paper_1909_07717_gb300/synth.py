@@ -155,3 +155,63 @@ SINGLE = Workload("single_12x9_g0.1_v1_K32_J8", seed=0, n_states=1,
 # {2, 3.5, 5, 6.5} m/s, K = 64, 8 v 8.
 BATCHED = Workload("batched_4096x241x181_v4_K64_J8", seed=1, n_states=4096,
                    spacing=0.05, speeds=[2.0, 3.5, 5.0, 6.5], K=64)
+
+
+def uneven_batch(seed: int, n_states: int, *,
+                 spacings=(0.025, 0.05, 0.1), k_range=(32, 128),
+                 speed_range=(2.0, 6.5), decel_range=(0.3, 0.7),
+                 vmax: float = 3.25, amax: float = 3.0) -> dict:
+    """An uneven batch: half the states on a 12 x 9 m field with 11
+    opponents, half on 9 x 6 m with 6; per state a grid spacing drawn from
+    ``spacings``, 1-8 kick speeds uniform in ``speed_range`` (sorted), K
+    uniform in ``k_range`` and a ball deceleration uniform in
+    ``decel_range``.  Opponent slots are padded to 16.  Besides the state
+    arrays of ``ssl_states`` it holds ``spacing`` (S,), ``n_speeds`` (S,) and
+    ``speeds`` (S, 8; unused slots 0)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    S = n_states
+    big = rng.integers(0, 2, S) == 0
+    L = np.where(big, 12.0, 9.0)
+    W = np.where(big, 9.0, 6.0)
+    gw = np.where(big, 1.8, 1.0)
+    J = np.where(big, 11, 6).astype(np.int32)
+    spacing = rng.choice(np.asarray(spacings, np.float64), S)
+    n_speeds = rng.integers(1, 9, S).astype(np.int32)
+    sp = np.sort(rng.uniform(speed_range[0], speed_range[1], (S, 8)), axis=1)
+    speeds = np.where(np.arange(8)[None, :] < n_speeds[:, None], sp, 0.0)
+    K = rng.integers(k_range[0], k_range[1] + 1, S).astype(np.int32)
+    decel = rng.uniform(decel_range[0], decel_range[1], S)
+    half = np.stack([L / 2, W / 2], axis=1)
+    ball = rng.uniform(-1.0, 1.0, (S, 2)) * half
+    opp = rng.uniform(-1.0, 1.0, (S, 16, 2)) * half[:, None, :]
+    ospeed = rng.uniform(0.0, vmax, (S, 16))
+    ohead = rng.uniform(0.0, 2 * math.pi, (S, 16))
+    used = np.arange(16)[None, :] < J[:, None]
+    opp_pos = np.where(used[..., None], opp, 0.0)
+    opp_vel = np.where(used[..., None],
+                       np.stack([ospeed * np.cos(ohead),
+                                 ospeed * np.sin(ohead)], -1), 0.0)
+    f32 = np.float32
+    return {
+        "ball": ball.astype(f32),
+        "n_opp": J,
+        "opp_pos": opp_pos.astype(f32),
+        "opp_vel": opp_vel.astype(f32),
+        "ball_decel": decel.astype(f32),
+        "vmax": np.full(S, vmax, f32),
+        "amax": np.full(S, amax, f32),
+        "field_len": L.astype(f32),
+        "field_wid": W.astype(f32),
+        "goal_width": gw.astype(f32),
+        "K": K,
+        "spacing": spacing.astype(f32),
+        "n_speeds": n_speeds,
+        "speeds": speeds.astype(f32),
+    }
+
+
+# Uneven batch + autotuner: 8192 states mixing 12x9 m / 11 v 11 and
+# 9x6 m / 6 v 6, grids 0.025-0.1 m, 1-8 kick speeds in [2, 6.5] m/s,
+# K 32-128, ball deceleration U[0.3, 0.7] m/s^2.
+UNEVEN_SEED = 2
+UNEVEN_STATES = 8192

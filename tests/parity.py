@@ -213,3 +213,30 @@ def check_best(gpu, orc, s, nx, P, dense=True):
             f"the oracle, best {os_}")
     v, p = divmod(int(b["idx"]), P)
     assert v == b["speed_idx"] and p == b["iy"] * nx + b["ix"]
+
+
+def check_mask_one(bits, orc_feasible, orc_margin, state, gspec, speeds,
+                   params):
+    """Mask bits (V, P) of one state against the oracle outside the bands;
+    returns the number of in-band candidates."""
+    g, nx, ny, x0, y0 = gspec
+    ix, iy = np.meshgrid(np.arange(nx), np.arange(ny))
+    cx = (x0 + ix * g).reshape(-1)
+    cy = (y0 + iy * g).reshape(-1)
+    D = np.hypot(cx - state.sc[0], cy - state.sc[1])
+    sp = np.asarray(speeds, np.float64)
+    gap = np.abs(sp[:, None] ** 2 - 2 * state.sc[2] * D[None, :]) / \
+        sp[:, None] ** 2
+    band = ((np.abs(orc_margin - params["tau_safe"]) <= TOL_MASK)
+            | (gap <= TOL_REACH)
+            | (np.abs(D - params["min_pass_dist"]) <= 1e-5)[None, :])
+    diff = (bits != orc_feasible.astype(bool)) & ~band
+    assert not diff.any(), f"{diff.sum()} mask bits differ outside the bands"
+    return int(band.sum())
+
+
+def words_to_bits(words, V, P):
+    w = np.asarray(words).view(np.uint32).reshape(V, -1)
+    bits = np.unpackbits(w.view(np.uint8), axis=-1, bitorder="little")
+    assert not bits[:, P:].any(), "mask bits beyond P must be zero"
+    return bits[:, :P].astype(bool)
