@@ -377,6 +377,8 @@ def run_pps(args):
     if rank == 0:
         if world == 1 and not args.no_uneven:
             line["uneven"] = _uneven(args, dev, stream)
+        if world == 1 and not args.no_serving:
+            line["serving"] = _serving(dev)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
@@ -433,6 +435,39 @@ def _uneven(args, dev, stream):
     return out
 
 
+def _serving(dev, seconds=2.0):
+    """The serving loop: 512 simulated matches at 60 Hz (12x9 or 9x6 fields,
+    6-11 opponents, 0.05 m grid, 4 speeds, K = 32) replayed in real time
+    through a pps_server (4 streams, continuous batching, 128 MiB mask pool);
+    frame latency is arrival -> result on the host."""
+    from paper_1909_07717_gb300 import pps, synth
+    hz = 60.0
+    M, F = synth.SERVING_MATCHES, int(seconds * hz)
+    frames = synth.serving_matches(synth.SERVING_SEED, M, F)
+    rec = pps.pack_states(frames)
+    jobs = pps.match_jobs(frames)
+    desc = pps.pps_server_desc(dev.index, 4, 512, 65536, 128 << 20, 16, 50,
+                               pps.params_from_dict(synth.DEFAULT_PARAMS))
+    srv = pps.pps_server_create(desc)
+    try:
+        # warm-up: one match's frames back to back
+        pps.pps_server_replay(srv, rec[:F], jobs, 1, F, 1e4)
+        res = np.zeros(M * F, pps.RESULT_DTYPE)
+        st = pps.pps_server_replay(srv, rec, jobs, M, F, hz, res)
+    finally:
+        pps.pps_server_destroy(srv)
+    d = st.as_dict()
+    return {"workload": (f"serving_{M}x60Hz: 12x9/9x6, 6-11 opp, grid 0.05 m,"
+                         " 4 speeds, K 32 (seed 4)"),
+            "frames": int(d["completed"]), "p50_us": d["p50_us"],
+            "p99_us": d["p99_us"], "max_us": d["max_us"],
+            "mean_us": d["mean_us"], "states_per_s": d["states_per_s"],
+            "mean_batch": d["mean_batch"],
+            "queue_p50_us": float(np.percentile(res["queue_ns"], 50) / 1e3),
+            "queue_p99_us": float(np.percentile(res["queue_ns"], 99) / 1e3),
+            "ok": bool(np.all(res["status"] == 0))}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -442,6 +477,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-uneven", action="store_true",
                     help="skip the uneven-batch plan measurement")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the serving-loop replay")
     ap.add_argument("--states", type=int, default=0,
                     help="states per GPU (default: the workload's 4096); "
                          "smaller only for profiling captures")

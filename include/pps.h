@@ -346,6 +346,94 @@ pps_status pps_plan_run(pps_plan* plan, const pps_state* states,
 pps_status pps_plan_groups(const pps_plan* plan, pps_plan_group* out, int cap,
                            int* n);
 
+/* ---- Serving: continuous batching of per-frame searches ----------------
+ *
+ * A server takes single-state requests (one vision frame of one match each,
+ * any grid and speeds) from any thread and answers each with its pps_best
+ * (and optionally its mask).  A scheduler thread forms batches
+ * continuously: whenever one of the server's streams is free it launches
+ * every queued request that fits -- at most max_batch, and only while the
+ * device memory pool has room for the request's mask -- so requests that
+ * arrive while others are on the GPU join the next launch, and launches on
+ * different streams overlap on the device.  While a launch is in flight a
+ * new one waits up to max_wait_us to gather more requests (one launch per
+ * request would spend the host's time on launch overhead).  Results are those of pps_search
+ * for the same state and shape, alone or in any mix. */
+
+typedef struct pps_server pps_server;
+
+typedef struct pps_server_desc {
+    int32_t device;
+    int32_t n_streams;        /* batches in flight at once, 1..8 */
+    int32_t max_batch;        /* requests per launch, 1..4096 */
+    int32_t max_queue;        /* pending requests before submit refuses
+                                 (PPS_ENOMEM), >= max_batch */
+    size_t pool_bytes;        /* device memory for masks of in-flight
+                                 requests (admission budget); 0 = masks off */
+    int32_t max_opp;          /* most opponents of any request (<= 16) */
+    int32_t max_wait_us;      /* with a launch already in flight, gather
+                                 queued requests for up to this long before
+                                 launching them (0 = launch at once) */
+    pps_params params;        /* value-function parameters of every search */
+} pps_server_desc;
+
+/* Per-request completion record. */
+typedef struct pps_server_result {
+    pps_best best;
+    uint64_t ticket;
+    int64_t latency_ns;       /* submit -> result available on the host */
+    int64_t queue_ns;         /* submit -> its launch was enqueued */
+    int32_t batch_size;       /* requests in the launch that served it */
+    int32_t status;           /* PPS_OK, or why the request failed */
+} pps_server_result;
+
+/* Latency and throughput summary over the requests completed so far. */
+typedef struct pps_server_stats {
+    int64_t completed;
+    int64_t batches;
+    double mean_batch;
+    double p50_us, p99_us, max_us, mean_us;
+    double wall_s;            /* first submit -> last completion */
+    double states_per_s;
+} pps_server_stats;
+
+/* Start a server (allocates its pools and streams, starts the scheduler
+ * thread).  EINVAL on a bad descriptor, ENOMEM, ECUDA. */
+pps_status pps_server_create(const pps_server_desc* desc, pps_server** out);
+
+/* Stop the scheduler (after finishing in-flight work) and free everything.
+ * NULL is accepted. */
+void pps_server_destroy(pps_server* srv);
+
+/* Queue one request: state and job in host memory (copied).  *ticket gets
+ * its id.  EINVAL on a bad state or job, ENOMEM when max_queue requests are
+ * pending or the request's mask can never fit the pool. */
+pps_status pps_server_submit(pps_server* srv, const pps_state* state,
+                             const pps_job* job, uint64_t* ticket);
+
+/* Wait up to timeout_us (< 0: forever) for a ticket's result; ETIMEOUT if
+ * it is not done.  If mask is not NULL and masks are on, the request's mask
+ * words (job.n_speeds * ceil(P/32)) are copied there.  A result can be
+ * taken once. */
+pps_status pps_server_wait(pps_server* srv, uint64_t ticket,
+                           int64_t timeout_us, pps_server_result* out,
+                           uint32_t* mask);
+
+/* Replay n_matches simulated matches of frames_per_match frames each at
+ * `hz` frames per second per match (match m's frames at
+ * t0 + (m / n_matches + f) / hz): frames[m * frames_per_match + f] with
+ * jobs[m] (all host memory), submitted on schedule by one thread while the
+ * scheduler serves them.  Results (n_matches * frames_per_match records,
+ * host, may be NULL) and a summary of this replay. */
+pps_status pps_server_replay(pps_server* srv, const pps_state* frames,
+                             const pps_job* jobs, int n_matches,
+                             int frames_per_match, double hz,
+                             pps_server_result* results,
+                             pps_server_stats* stats);
+
+/* Summary over everything completed since the server started. */
+pps_status pps_server_get_stats(pps_server* srv, pps_server_stats* out);
+
 /* Number of SMs and the CTAs per SM the search kernel runs with (for
  * benchmarks and the autotuner); EINVAL on NULL. */
 pps_status pps_launch_info(const pps_ctx* ctx, int* num_sms,

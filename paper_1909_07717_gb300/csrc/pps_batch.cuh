@@ -172,6 +172,9 @@ __global__ void __launch_bounds__(128) batch_finalize_kernel(const BatchArgs a) 
             b.status |= PPS_STATE_INCONSISTENT;
     }
     a.best[s] = b;
+    // Leave the scratch cleared for the next launch that reuses it.
+    a.keys[s] = 0ull;
+    a.counts[s] = 0;
 }
 
 // Launch entry points, one translation unit per opponent-slot count

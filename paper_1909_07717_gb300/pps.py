@@ -92,6 +92,30 @@ class pps_plan_group(ctypes.Structure):
                 ("n_items", ctypes.c_int64), ("tuned_ms", c_float * 3)]
 
 
+class pps_server_desc(ctypes.Structure):
+    _fields_ = [("device", c_int32), ("n_streams", c_int32),
+                ("max_batch", c_int32), ("max_queue", c_int32),
+                ("pool_bytes", c_size_t), ("max_opp", c_int32),
+                ("max_wait_us", c_int32), ("params", pps_params)]
+
+
+class pps_server_result(ctypes.Structure):
+    _fields_ = [("best", pps_best), ("ticket", ctypes.c_uint64),
+                ("latency_ns", ctypes.c_int64), ("queue_ns", ctypes.c_int64),
+                ("batch_size", c_int32), ("status", c_int32)]
+
+
+class pps_server_stats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("mean_batch", ctypes.c_double), ("p50_us", ctypes.c_double),
+                ("p99_us", ctypes.c_double), ("max_us", ctypes.c_double),
+                ("mean_us", ctypes.c_double), ("wall_s", ctypes.c_double),
+                ("states_per_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 PPS_PLAN_AUTOTUNE = 1
 PPS_PLAN_GRAPH = 2
 
@@ -116,7 +140,9 @@ EXPORTS = ("pps_abi_version", "pps_status_string", "pps_last_error",
            "pps_create", "pps_destroy", "pps_search", "pps_sync", "pps_reset",
            "pps_launch_info", "pps_search_noalloc", "pps_plan_create",
            "pps_plan_destroy", "pps_plan_mask_offsets", "pps_plan_run",
-           "pps_plan_groups")
+           "pps_plan_groups", "pps_server_create", "pps_server_destroy",
+           "pps_server_submit", "pps_server_wait", "pps_server_replay",
+           "pps_server_get_stats")
 
 
 class PpsError(RuntimeError):
@@ -178,6 +204,19 @@ def lib():
             L.pps_plan_run.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
             L.pps_plan_groups.argtypes = [c_void_p, c_void_p, ctypes.c_int,
                                           P(ctypes.c_int)]
+            L.pps_server_create.argtypes = [P(pps_server_desc), P(c_void_p)]
+            L.pps_server_destroy.restype = None
+            L.pps_server_destroy.argtypes = [c_void_p]
+            L.pps_server_submit.argtypes = [c_void_p, c_void_p, c_void_p,
+                                            P(ctypes.c_uint64)]
+            L.pps_server_wait.argtypes = [c_void_p, ctypes.c_uint64,
+                                          ctypes.c_int64,
+                                          P(pps_server_result), c_void_p]
+            L.pps_server_replay.argtypes = [c_void_p, c_void_p, c_void_p,
+                                            ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_double, c_void_p,
+                                            P(pps_server_stats)]
+            L.pps_server_get_stats.argtypes = [c_void_p, P(pps_server_stats)]
             if L.pps_abi_version() != PPS_ABI_VERSION:
                 raise RuntimeError("libpps ABI version mismatch")
             _lib = L
@@ -282,6 +321,54 @@ def pps_plan_groups(plan, ctx=None):
     _check(lib().pps_plan_groups(plan, ctypes.addressof(arr), n.value,
                                  ctypes.byref(n)), ctx)
     return [arr[i] for i in range(n.value)]
+
+
+def pps_server_create(desc: pps_server_desc):
+    srv = c_void_p()
+    _check(lib().pps_server_create(ctypes.byref(desc), ctypes.byref(srv)))
+    return srv
+
+
+def pps_server_destroy(srv) -> None:
+    lib().pps_server_destroy(srv)
+
+
+def pps_server_submit(srv, state_addr, job_addr) -> int:
+    """Host addresses of one pps_state and one pps_job; returns the ticket."""
+    t = ctypes.c_uint64()
+    _check(lib().pps_server_submit(srv, state_addr, job_addr,
+                                   ctypes.byref(t)))
+    return t.value
+
+
+def pps_server_wait(srv, ticket, timeout_us=-1, mask=None):
+    r = pps_server_result()
+    _check(lib().pps_server_wait(srv, ticket, timeout_us, ctypes.byref(r),
+                                 None if mask is None else mask.ctypes.data))
+    return r
+
+
+def pps_server_replay(srv, frames, jobs, n_matches, frames_per_match, hz,
+                      results=None):
+    """frames: structured array of pps_state (match-major); jobs: ctypes
+    array of n_matches pps_job; results: structured array or None."""
+    st = pps_server_stats()
+    _check(lib().pps_server_replay(
+        srv, frames.ctypes.data, ctypes.addressof(jobs), n_matches,
+        frames_per_match, hz,
+        None if results is None else results.ctypes.data, ctypes.byref(st)))
+    return st
+
+
+def pps_server_get_stats(srv):
+    st = pps_server_stats()
+    _check(lib().pps_server_get_stats(srv, ctypes.byref(st)))
+    return st
+
+
+RESULT_DTYPE = np.dtype([("best", BEST_DTYPE), ("ticket", "<u8"),
+                         ("latency_ns", "<i8"), ("queue_ns", "<i8"),
+                         ("batch_size", "<i4"), ("status", "<i4")])
 
 
 def pps_sync(ctx) -> int:
@@ -480,3 +567,11 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def match_jobs(batch: dict):
+    """One pps_job per match of a synth.serving_matches batch."""
+    M, F = batch["n_matches"], batch["n_frames"]
+    first = {k: v[::F] for k, v in batch.items()
+             if isinstance(v, np.ndarray)}
+    return jobs_from_batch(first)

@@ -215,3 +215,74 @@ def uneven_batch(seed: int, n_states: int, *,
 # K 32-128, ball deceleration U[0.3, 0.7] m/s^2.
 UNEVEN_SEED = 2
 UNEVEN_STATES = 8192
+
+
+def serving_matches(seed: int, n_matches: int, n_frames: int, *,
+                    hz: float = 60.0, spacing: float = 0.05,
+                    speeds=(2.0, 3.5, 5.0, 6.5), K: int = 32,
+                    vmax: float = 3.25, amax: float = 3.0,
+                    ball_decel: float = 0.5) -> dict:
+    """Simulated matches for the serving loop.  Each match plays on a 12 x 9
+    or 9 x 6 m field with 6-11 opponents; its frames are 1/hz apart, robots
+    moving with a random acceleration of at most amax per axis, speed capped
+    at vmax, reflected at the field edges; the ball drifts the same way at
+    half the speed.  Returns state arrays of shape (n_matches * n_frames,
+    ...) in match-major order plus per-match ``field_len``, ``field_wid``,
+    ``n_opp_match`` and the shared ``spacing`` and ``speeds``."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    M, F = n_matches, n_frames
+    big = rng.integers(0, 2, M) == 0
+    L = np.where(big, 12.0, 9.0)
+    W = np.where(big, 9.0, 6.0)
+    J = rng.integers(6, 12, M).astype(np.int32)
+    half = np.stack([L / 2, W / 2], axis=1)            # (M, 2)
+    dt = 1.0 / hz
+    pos = rng.uniform(-1, 1, (M, 16, 2)) * half[:, None, :]
+    vel = rng.uniform(-1, 1, (M, 16, 2)) * vmax / math.sqrt(2)
+    ball = rng.uniform(-1, 1, (M, 2)) * half
+    bvel = rng.uniform(-1, 1, (M, 2)) * vmax / 2
+    out_pos = np.zeros((M, F, 16, 2))
+    out_vel = np.zeros((M, F, 16, 2))
+    out_ball = np.zeros((M, F, 2))
+    for f in range(F):
+        out_pos[:, f], out_vel[:, f], out_ball[:, f] = pos, vel, ball
+        vel = vel + rng.uniform(-amax, amax, vel.shape) * dt
+        sp = np.linalg.norm(vel, axis=-1, keepdims=True)
+        vel = np.where(sp > vmax, vel * (vmax / np.maximum(sp, 1e-9)), vel)
+        pos = pos + vel * dt
+        over = np.abs(pos) > half[:, None, :]
+        vel = np.where(over, -vel, vel)
+        pos = np.clip(pos, -half[:, None, :], half[:, None, :])
+        bvel = bvel + rng.uniform(-amax, amax, bvel.shape) * dt / 2
+        ball = np.clip(ball + bvel * dt, -half, half)
+    used = np.arange(16)[None, None, :] < J[:, None, None]
+    S = M * F
+    f32 = np.float32
+    rep = lambda a: np.repeat(a, F)  # noqa: E731  per-match -> per-frame
+    return {
+        "ball": out_ball.reshape(S, 2).astype(f32),
+        "n_opp": rep(J).astype(np.int32),
+        "opp_pos": np.where(used[..., None], out_pos, 0).reshape(S, 16, 2)
+        .astype(f32),
+        "opp_vel": np.where(used[..., None], out_vel, 0).reshape(S, 16, 2)
+        .astype(f32),
+        "ball_decel": np.full(S, ball_decel, f32),
+        "vmax": np.full(S, vmax, f32),
+        "amax": np.full(S, amax, f32),
+        "field_len": rep(L).astype(f32),
+        "field_wid": rep(W).astype(f32),
+        "goal_width": rep(np.where(big, 1.8, 1.0)).astype(f32),
+        "K": np.full(S, K, np.int32),
+        "spacing": np.full(S, spacing, f32),
+        "n_speeds": np.full(S, len(speeds), np.int32),
+        "speeds": np.tile(np.pad(np.asarray(speeds, f32),
+                                 (0, 8 - len(speeds))), (S, 1)),
+        "n_matches": M,
+        "n_frames": F,
+    }
+
+
+# Serving: 512 concurrent simulated matches at 60 Hz, 9x6 or 12x9 fields,
+# 6-11 opponents, grid 0.05 m, 4 kick speeds (K = 32 samples per pass).
+SERVING_SEED = 4
+SERVING_MATCHES = 512
