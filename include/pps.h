@@ -141,6 +141,8 @@ typedef struct pps_debug_out {
     float* score;
     float* T;
     int32_t T_stride;
+    float* point_best; /* [s][p]: best score over the speeds, -inf if no
+                          speed is feasible (device memory only) */
 } pps_debug_out;
 
 /* Context creation parameters. */
@@ -433,6 +435,81 @@ pps_status pps_server_replay(pps_server* srv, const pps_state* frames,
 
 /* Summary over everything completed since the server started. */
 pps_status pps_server_get_stats(pps_server* srv, pps_server_stats* out);
+
+/* ---- Learned proposal -------------------------------------------------
+ *
+ * Not in the paper: a small network ranks coarse cells of the field so that
+ * the exact search (Sec. 4.2-4.3) only has to run on the best of them.  The
+ * network reads a 46 x 61 map of a 12 x 9 m field (0.2 m pixels, pixel
+ * (y, x) at (-6 + 0.2 x, -4.5 + 0.2 y)) with 8 channels rasterised from the
+ * state (opponent density, its two velocity-weighted components, ball
+ * proximity, distance to the ball, distance to the nearest opponent, x and
+ * y) and predicts, per pixel, the best exact score among the fine grid
+ * points of that pixel's cell: 4 layers of 3x3 convolutions
+ * (8 -> 32 -> 32 -> 32 -> 1, ReLU between), bfloat16 weights and
+ * activations with float32 accumulation, all on the tensor cores, trained
+ * on the GPU with the library's own forward and backward kernels (Adam). */
+
+#define PPS_NET_H 46
+#define PPS_NET_W 61
+#define PPS_NET_PARAMS 21121 /* per layer W[3][3][cout][cin] then bias */
+
+typedef struct pps_net pps_net;
+
+/* A network on `device` for batches of up to max_batch states, with zero
+ * weights (load them with pps_net_set_weights). */
+pps_status pps_net_create(int device, void* stream, int max_batch,
+                          pps_net** out);
+void pps_net_destroy(pps_net* net);
+
+/* Weights as PPS_NET_PARAMS floats (host).  Setting them resets Adam. */
+pps_status pps_net_set_weights(pps_net* net, const float* w);
+pps_status pps_net_get_weights(pps_net* net, float* w);
+
+/* The input map: out[n][46][61][8] bfloat16 bit patterns (device). */
+pps_status pps_net_raster(pps_net* net, const pps_state* states, int n,
+                          uint16_t* out);
+
+/* Predicted cell scores, out[n][46][61] float (device).  States (device)
+ * must be 12 x 9 m; n <= max_batch. */
+pps_status pps_net_forward(pps_net* net, const pps_state* states, int n,
+                           float* out);
+
+/* Mean squared error of the prediction against labels[n][46][61] (device)
+ * and its gradient with respect to the weights (grads: PPS_NET_PARAMS floats,
+ * host, or NULL).  Waits for the result. */
+pps_status pps_net_grad(pps_net* net, const pps_state* states,
+                        const float* labels, int n, float* grads,
+                        float* loss);
+
+/* One Adam step (lr, beta 0.9/0.999) on a batch; *loss (host, may be NULL:
+ * then the call does not wait) gets the batch's loss before the step. */
+pps_status pps_net_train_step(pps_net* net, const pps_state* states,
+                              const float* labels, int n, float lr,
+                              float* loss);
+
+/* Training labels from an exact search on the fine grid of the map (12 x 9 m
+ * at 0.025 m: 481 x 361 points, 8 x 8 fine points per map pixel, centred on
+ * it): point_best[n][361 * 481] (device; pps_debug_out.point_best) ->
+ * labels[n][46][61] = max(cell maximum, floor). */
+pps_status pps_net_labels(pps_net* net, const float* point_best, int n,
+                          float floor_value, float* labels);
+
+/* pps_propose flags. */
+#define PPS_PROPOSE_FALLBACK 1u /* states whose top-k cells hold no feasible
+                                   pass are searched on the full grid */
+
+/* The proposal path: rasterise, predict, take each state's topk best map
+ * pixels, and run the exact search only on their cells' fine grid points
+ * (fine_grid must be the 481 x 361 grid of the 12 x 9 m field at 0.025 m).
+ * states, out_best and out_cells (n x topk pixel indices y * 61 + x, or
+ * NULL) are device memory; 1 <= topk <= 2806; n <= both the context's
+ * max_states and the network's max_batch.  out_best.n_feasible counts the
+ * refined points only.  Enqueued on the context's stream. */
+pps_status pps_propose(pps_ctx* ctx, pps_net* net, const pps_state* states,
+                       int n, const pps_grid* fine_grid, const float* speeds,
+                       int n_speeds, const pps_params* params, int topk,
+                       unsigned flags, pps_best* out_best, int32_t* out_cells);
 
 /* Number of SMs and the CTAs per SM the search kernel runs with (for
  * benchmarks and the autotuner); EINVAL on NULL. */

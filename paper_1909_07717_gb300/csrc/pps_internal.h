@@ -21,3 +21,15 @@ void pps_ctx_free(pps_ctx* ctx, void* p, size_t bytes);
 pps_status pps_ctx_error(pps_ctx* ctx, pps_status s, const char* fmt, ...);
 // Record a CUDA failure on the context (marks it failed).
 pps_status pps_ctx_cuda_error(pps_ctx* ctx, cudaError_t e, const char* what);
+
+// Context scratch and limits for the proposal path.
+void pps_ctx_scratch(pps_ctx* ctx, unsigned long long** keys, int** counts);
+int pps_ctx_max_states(const pps_ctx* ctx);
+int pps_ctx_jmax(const pps_ctx* ctx);
+
+// Network internals for the proposal path (pps_net.cu).
+cudaError_t pps_net_predict(pps_net* net, const pps_state* states, int n,
+                            cudaStream_t* st, float** scores, int** cells,
+                            int** skip);
+cudaError_t pps_net_topk(pps_net* net, int n, int k, int* cells);
+int pps_net_max_batch(const pps_net* net);

@@ -166,6 +166,12 @@ cudaStream_t pps_ctx_stream(const pps_ctx* ctx) { return ctx->stream; }
 int pps_ctx_num_sms(const pps_ctx* ctx) { return ctx->num_sms; }
 int pps_ctx_max_K(const pps_ctx* ctx) { return ctx->max_K; }
 bool pps_ctx_failed(const pps_ctx* ctx) { return ctx->failed; }
+void pps_ctx_scratch(pps_ctx* ctx, unsigned long long** keys, int** counts) {
+    *keys = ctx->keys;
+    *counts = ctx->counts;
+}
+int pps_ctx_max_states(const pps_ctx* ctx) { return ctx->max_states; }
+int pps_ctx_jmax(const pps_ctx* ctx) { return ctx->jmax; }
 
 pps_status pps_ctx_alloc(pps_ctx* ctx, void** p, size_t bytes,
                          const char* what) {
@@ -394,6 +400,10 @@ pps_status pps_search(pps_ctx* ctx, const pps_state* states, int n_states,
     }
     const bool on_dev = flags & PPS_DEVICE_PTRS;
     const long long P = (long long)grid->nx * grid->ny;
+    if (dbg && dbg->point_best && !on_dev) {
+        set_err(ctx, "dbg->point_best needs PPS_DEVICE_PTRS");
+        return PPS_EINVAL;
+    }
     if (dbg && dbg->T && dbg->T_stride < 1) {
         set_err(ctx, "dbg->T_stride must be >= 1");
         return PPS_EINVAL;
@@ -456,6 +466,7 @@ pps_status pps_search(pps_ctx* ctx, const pps_state* states, int n_states,
             a.dbg_margin = dbg->margin;
             a.dbg_score = dbg->score;
             a.dbg_T = dbg->T;
+            a.dbg_point = dbg->point_best;
         }
     } else {
         const size_t dbg_n = nS * n_speeds * (size_t)P;

@@ -1,0 +1,363 @@
+// pps_net.cu -- host side of the learned proposal network (include/pps.h,
+// "Learned proposal"): buffers, the weight layouts, forward, backward and
+// the Adam step, all enqueued on the network's stream.
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pps.h"
+#include "pps_internal.h"
+#include "pps_net.cuh"
+
+using namespace pps::net;
+char* pps_thread_error_buffer();
+
+struct pps_net {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int max_batch = 0;
+    int step = 0;
+    float *w = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    __nv_bfloat16 *Wf = nullptr, *WT = nullptr;
+    __nv_bfloat16 *a0 = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr;
+    __nv_bfloat16 *g1 = nullptr, *g2 = nullptr, *g3 = nullptr, *g4 = nullptr;
+    float* out = nullptr;
+    float* loss = nullptr;
+    int* cells = nullptr;  // proposal scratch: max_batch x NPIX
+    int* skip = nullptr;   // proposal scratch: max_batch
+};
+
+namespace {
+
+constexpr int kWeights = 9 * (C0 * CH + CH * CH + CH * CH + CH * CO);
+// real (unpadded) channel counts of the flat host layout
+constexpr int kRealIn[4] = {8, 32, 32, 32}, kRealOut[4] = {32, 32, 32, 1};
+
+int wf_off(int l) {
+    int o = 0;
+    for (int i = 0; i < l; ++i) o += 9 * lcout(i) * lcin(i);
+    return o;
+}
+int bias_off(int l) { return layer_off(l) + 9 * lcout(l) * lcin(l); }
+
+pps_status fail(pps_status s, const char* msg, cudaError_t e = cudaSuccess) {
+    std::snprintf(pps_thread_error_buffer(), 512, "%s%s%s", msg,
+                  e != cudaSuccess ? ": " : "",
+                  e != cudaSuccess ? cudaGetErrorString(e) : "");
+    return s;
+}
+
+unsigned blocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+cudaError_t cast_weights(pps_net* nt) {
+    cast_kernel<<<blocks(kWeights, 256), 256, 0, nt->stream>>>(nt->w, nt->Wf,
+                                                               nt->WT);
+    return cudaGetLastError();
+}
+
+cudaError_t forward(pps_net* nt, const pps_state* states, int n) {
+    const long long P = (long long)n * NPIX;
+    const unsigned g = blocks(P, 64);
+    cudaStream_t st = nt->stream;
+    raster_kernel<<<blocks(P, 256), 256, 0, st>>>(states, n, nt->a0);
+    conv_kernel<C0, CH, kHidden><<<g, 128, 0, st>>>(
+        nt->a0, nt->Wf + wf_off(0), nt->w + bias_off(0), P, nt->a1, nullptr);
+    conv_kernel<CH, CH, kHidden><<<g, 128, 0, st>>>(
+        nt->a1, nt->Wf + wf_off(1), nt->w + bias_off(1), P, nt->a2, nullptr);
+    conv_kernel<CH, CH, kHidden><<<g, 128, 0, st>>>(
+        nt->a2, nt->Wf + wf_off(2), nt->w + bias_off(2), P, nt->a3, nullptr);
+    conv_kernel<CH, CO, kOutput><<<g, 128, 0, st>>>(
+        nt->a3, nt->Wf + wf_off(3), nt->w + bias_off(3), P, nt->out, nullptr);
+    return cudaGetLastError();
+}
+
+// Gradients of the mean squared error into nt->grad (accumulated).
+cudaError_t backward(pps_net* nt, const float* labels, int n) {
+    const long long P = (long long)n * NPIX;
+    const unsigned g = blocks(P, 64);
+    const int chunk = 2048;
+    const unsigned gw = blocks(P, chunk);
+    cudaStream_t st = nt->stream;
+    cudaError_t e = cudaMemsetAsync(nt->loss, 0, sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    loss_kernel<<<blocks(P, 256), 256, 0, st>>>(nt->out, labels, P,
+                                                1.f / (float)P, nt->g4,
+                                                nt->loss);
+    // layer 4 (32 -> 1)
+    wgrad_kernel<CH, CO><<<gw, 288, 0, st>>>(nt->g4, nt->a3, P, chunk,
+                                              nt->grad + layer_off(3));
+    bias_grad_kernel<CO><<<256, 256, 0, st>>>(nt->g4, P, nt->grad + bias_off(3));
+    conv_kernel<CO, CH, kMaskedGrad><<<g, 128, 0, st>>>(
+        nt->g4, nt->WT + wf_off(3), nullptr, P, nt->g3, nt->a3);
+    // layer 3
+    wgrad_kernel<CH, CH><<<gw, 288, 0, st>>>(nt->g3, nt->a2, P, chunk,
+                                              nt->grad + layer_off(2));
+    bias_grad_kernel<CH><<<256, 256, 0, st>>>(nt->g3, P, nt->grad + bias_off(2));
+    conv_kernel<CH, CH, kMaskedGrad><<<g, 128, 0, st>>>(
+        nt->g3, nt->WT + wf_off(2), nullptr, P, nt->g2, nt->a2);
+    // layer 2
+    wgrad_kernel<CH, CH><<<gw, 288, 0, st>>>(nt->g2, nt->a1, P, chunk,
+                                              nt->grad + layer_off(1));
+    bias_grad_kernel<CH><<<256, 256, 0, st>>>(nt->g2, P, nt->grad + bias_off(1));
+    conv_kernel<CH, CH, kMaskedGrad><<<g, 128, 0, st>>>(
+        nt->g2, nt->WT + wf_off(1), nullptr, P, nt->g1, nt->a1);
+    // layer 1 (8 -> 32; the input needs no gradient)
+    wgrad_kernel<C0, CH><<<gw, 288, 0, st>>>(nt->g1, nt->a0, P, chunk,
+                                              nt->grad + layer_off(0));
+    bias_grad_kernel<CH><<<256, 256, 0, st>>>(nt->g1, P, nt->grad + bias_off(0));
+    return cudaGetLastError();
+}
+
+// flat host layout <-> padded device layout
+void to_padded(const float* flat, std::vector<float>& pad) {
+    pad.assign(kPadParams, 0.f);
+    int k = 0;
+    for (int l = 0; l < 4; ++l) {
+        const int ci_r = kRealIn[l], co_r = kRealOut[l];
+        const int cin = lcin(l), cout = lcout(l);
+        for (int tap = 0; tap < 9; ++tap)
+            for (int co = 0; co < co_r; ++co)
+                for (int ci = 0; ci < ci_r; ++ci)
+                    pad[layer_off(l) + (tap * cout + co) * cin + ci] = flat[k++];
+        for (int co = 0; co < co_r; ++co) pad[bias_off(l) + co] = flat[k++];
+    }
+}
+
+void from_padded(const std::vector<float>& pad, float* flat) {
+    int k = 0;
+    for (int l = 0; l < 4; ++l) {
+        const int ci_r = kRealIn[l], co_r = kRealOut[l];
+        const int cin = lcin(l), cout = lcout(l);
+        for (int tap = 0; tap < 9; ++tap)
+            for (int co = 0; co < co_r; ++co)
+                for (int ci = 0; ci < ci_r; ++ci)
+                    flat[k++] = pad[layer_off(l) + (tap * cout + co) * cin + ci];
+        for (int co = 0; co < co_r; ++co) flat[k++] = pad[bias_off(l) + co];
+    }
+}
+
+}  // namespace
+
+static_assert(PPS_NET_PARAMS == 21121, "flat layout");
+
+// Library-internal: predicted scores of n states (into the net's buffer),
+// and the proposal scratch.
+cudaError_t pps_net_predict(pps_net* nt, const pps_state* states, int n,
+                            cudaStream_t* st, float** scores, int** cells,
+                            int** skip) {
+    *st = nt->stream;
+    *scores = nt->out;
+    *cells = nt->cells;
+    *skip = nt->skip;
+    return forward(nt, states, n);
+}
+
+int pps_net_max_batch(const pps_net* nt) { return nt->max_batch; }
+
+cudaError_t pps_net_topk(pps_net* nt, int n, int k, int* cells) {
+    topk_kernel<<<n, 512, 0, nt->stream>>>(nt->out, k, cells);
+    return cudaGetLastError();
+}
+
+extern "C" pps_status pps_net_create(int device, void* stream, int max_batch,
+                                     pps_net** out) {
+    if (!out) return PPS_EINVAL;
+    *out = nullptr;
+    if (max_batch < 1 || max_batch > (1 << 16))
+        return fail(PPS_EINVAL, "pps_net_create: max_batch outside 1..65536");
+    pps_net* nt = new (std::nothrow) pps_net();
+    if (!nt) return PPS_ENOMEM;
+    nt->device = device;
+    nt->stream = (cudaStream_t)stream;
+    nt->max_batch = max_batch;
+    const size_t P = (size_t)max_batch * NPIX;
+    cudaError_t e = cudaSetDevice(device);
+    auto al = [&](auto** p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc((void**)p, bytes);
+        if (e == cudaSuccess) e = cudaMemset(*p, 0, bytes);
+    };
+    al(&nt->w, sizeof(float) * kPadParams);
+    al(&nt->grad, sizeof(float) * kPadParams);
+    al(&nt->m, sizeof(float) * kPadParams);
+    al(&nt->v, sizeof(float) * kPadParams);
+    al(&nt->Wf, sizeof(__nv_bfloat16) * kWeights);
+    al(&nt->WT, sizeof(__nv_bfloat16) * kWeights);
+    al(&nt->a0, sizeof(__nv_bfloat16) * P * C0);
+    al(&nt->a1, sizeof(__nv_bfloat16) * P * CH);
+    al(&nt->a2, sizeof(__nv_bfloat16) * P * CH);
+    al(&nt->a3, sizeof(__nv_bfloat16) * P * CH);
+    al(&nt->g1, sizeof(__nv_bfloat16) * P * CH);
+    al(&nt->g2, sizeof(__nv_bfloat16) * P * CH);
+    al(&nt->g3, sizeof(__nv_bfloat16) * P * CH);
+    al(&nt->g4, sizeof(__nv_bfloat16) * P * CO);
+    al(&nt->out, sizeof(float) * P);
+    al(&nt->loss, sizeof(float));
+    al(&nt->cells, sizeof(int) * P);
+    al(&nt->skip, sizeof(int) * (size_t)max_batch);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        pps_net_destroy(nt);
+        return fail(e == cudaErrorMemoryAllocation ? PPS_ENOMEM : PPS_ECUDA,
+                    "pps_net_create", e);
+    }
+    *out = nt;
+    return PPS_OK;
+}
+
+extern "C" void pps_net_destroy(pps_net* nt) {
+    if (!nt) return;
+    cudaSetDevice(nt->device);
+    cudaStreamSynchronize(nt->stream);
+    for (void* p : {(void*)nt->w, (void*)nt->grad, (void*)nt->m, (void*)nt->v,
+                    (void*)nt->Wf, (void*)nt->WT, (void*)nt->a0, (void*)nt->a1,
+                    (void*)nt->a2, (void*)nt->a3, (void*)nt->g1, (void*)nt->g2,
+                    (void*)nt->g3, (void*)nt->g4, (void*)nt->out,
+                    (void*)nt->loss, (void*)nt->cells, (void*)nt->skip})
+        if (p) cudaFree(p);
+    cudaGetLastError();
+    delete nt;
+}
+
+extern "C" pps_status pps_net_set_weights(pps_net* nt, const float* w) {
+    if (!nt || !w) return PPS_EINVAL;
+    for (int i = 0; i < PPS_NET_PARAMS; ++i)
+        if (!std::isfinite(w[i]))
+            return fail(PPS_EINVAL, "pps_net_set_weights: non-finite weight");
+    std::vector<float> pad;
+    to_padded(w, pad);
+    cudaSetDevice(nt->device);
+    cudaError_t e = cudaMemcpyAsync(nt->w, pad.data(), sizeof(float) * kPadParams,
+                                    cudaMemcpyHostToDevice, nt->stream);
+    for (float* p : {nt->grad, nt->m, nt->v})
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(p, 0, sizeof(float) * kPadParams, nt->stream);
+    if (e == cudaSuccess) e = cast_weights(nt);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nt->stream);
+    nt->step = 0;
+    return e == cudaSuccess ? PPS_OK : fail(PPS_ECUDA, "pps_net_set_weights", e);
+}
+
+extern "C" pps_status pps_net_get_weights(pps_net* nt, float* w) {
+    if (!nt || !w) return PPS_EINVAL;
+    std::vector<float> pad(kPadParams);
+    cudaSetDevice(nt->device);
+    cudaError_t e = cudaMemcpyAsync(pad.data(), nt->w, sizeof(float) * kPadParams,
+                                    cudaMemcpyDeviceToHost, nt->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nt->stream);
+    if (e != cudaSuccess) return fail(PPS_ECUDA, "pps_net_get_weights", e);
+    from_padded(pad, w);
+    return PPS_OK;
+}
+
+namespace {
+pps_status check_batch(const pps_net* nt, const void* states, int n) {
+    if (!nt) return PPS_EINVAL;
+    if (n < 1 || n > nt->max_batch)
+        return fail(PPS_EINVAL, "pps_net: n outside 1..max_batch");
+    if (!states) return fail(PPS_EINVAL, "pps_net: states is NULL");
+    return PPS_OK;
+}
+}  // namespace
+
+extern "C" pps_status pps_net_raster(pps_net* nt, const pps_state* states,
+                                     int n, uint16_t* out) {
+    pps_status s = check_batch(nt, states, n);
+    if (s != PPS_OK) return s;
+    if (!out) return PPS_EINVAL;
+    cudaSetDevice(nt->device);
+    const long long P = (long long)n * NPIX;
+    raster_kernel<<<blocks(P, 256), 256, 0, nt->stream>>>(states, n, nt->a0);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(out, 8 * sizeof(uint16_t), nt->a0,
+                              C0 * sizeof(uint16_t), 8 * sizeof(uint16_t), P,
+                              cudaMemcpyDeviceToDevice, nt->stream);
+    return e == cudaSuccess ? PPS_OK : fail(PPS_ECUDA, "pps_net_raster", e);
+}
+
+extern "C" pps_status pps_net_forward(pps_net* nt, const pps_state* states,
+                                      int n, float* out) {
+    pps_status s = check_batch(nt, states, n);
+    if (s != PPS_OK) return s;
+    if (!out) return PPS_EINVAL;
+    cudaSetDevice(nt->device);
+    cudaError_t e = forward(nt, states, n);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, nt->out, sizeof(float) * (size_t)n * NPIX,
+                            cudaMemcpyDeviceToDevice, nt->stream);
+    return e == cudaSuccess ? PPS_OK : fail(PPS_ECUDA, "pps_net_forward", e);
+}
+
+extern "C" pps_status pps_net_grad(pps_net* nt, const pps_state* states,
+                                   const float* labels, int n, float* grads,
+                                   float* loss) {
+    pps_status s = check_batch(nt, states, n);
+    if (s != PPS_OK) return s;
+    if (!labels) return PPS_EINVAL;
+    cudaSetDevice(nt->device);
+    cudaError_t e = cudaMemsetAsync(nt->grad, 0, sizeof(float) * kPadParams,
+                                    nt->stream);
+    if (e == cudaSuccess) e = forward(nt, states, n);
+    if (e == cudaSuccess) e = backward(nt, labels, n);
+    std::vector<float> pad(kPadParams);
+    float l = 0.f;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(pad.data(), nt->grad, sizeof(float) * kPadParams,
+                            cudaMemcpyDeviceToHost, nt->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&l, nt->loss, sizeof(float), cudaMemcpyDeviceToHost,
+                            nt->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nt->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(nt->grad, 0, sizeof(float) * kPadParams, nt->stream);
+    if (e != cudaSuccess) return fail(PPS_ECUDA, "pps_net_grad", e);
+    if (grads) from_padded(pad, grads);
+    if (loss) *loss = l;
+    return PPS_OK;
+}
+
+extern "C" pps_status pps_net_train_step(pps_net* nt, const pps_state* states,
+                                         const float* labels, int n, float lr,
+                                         float* loss) {
+    pps_status s = check_batch(nt, states, n);
+    if (s != PPS_OK) return s;
+    if (!labels || !(lr > 0.f) || !std::isfinite(lr))
+        return fail(PPS_EINVAL, "pps_net_train_step: labels and lr > 0");
+    cudaSetDevice(nt->device);
+    cudaError_t e = forward(nt, states, n);
+    if (e == cudaSuccess) e = backward(nt, labels, n);
+    ++nt->step;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f / (1.f - std::pow(b1, (float)nt->step));
+    const float c2 = 1.f / (1.f - std::pow(b2, (float)nt->step));
+    if (e == cudaSuccess) {
+        adam_kernel<<<blocks(kPadParams, 256), 256, 0, nt->stream>>>(
+            nt->w, nt->grad, nt->m, nt->v, kPadParams, lr, b1, b2, 1e-8f, c1,
+            c2);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cast_weights(nt);
+    if (e == cudaSuccess && loss) {
+        e = cudaMemcpyAsync(loss, nt->loss, sizeof(float),
+                            cudaMemcpyDeviceToHost, nt->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(nt->stream);
+    }
+    return e == cudaSuccess ? PPS_OK : fail(PPS_ECUDA, "pps_net_train_step", e);
+}
+
+extern "C" pps_status pps_net_labels(pps_net* nt, const float* point_best,
+                                     int n, float floor_value, float* labels) {
+    pps_status s = check_batch(nt, point_best, n);
+    if (s != PPS_OK) return s;
+    if (!labels || !std::isfinite(floor_value)) return PPS_EINVAL;
+    cudaSetDevice(nt->device);
+    cell_label_kernel<<<blocks((long long)n * NPIX, 256), 256, 0, nt->stream>>>(
+        point_best, n, 481, 361, floor_value, labels);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PPS_OK : fail(PPS_ECUDA, "pps_net_labels", e);
+}

@@ -1,0 +1,421 @@
+// pps_net.cuh -- device code of the learned proposal network.
+//
+// A 4-layer 3x3 convolutional network on the 46 x 61 map of a 12 x 9 m
+// field (0.2 m pixels): 8 input channels -> 32 -> 32 -> 32 -> 1, ReLU after
+// the hidden layers, bfloat16 weights and activations, float32
+// accumulation.  Every convolution -- forward, input gradient and weight
+// gradient -- is an implicit GEMM on the tensor cores (mma.sync m16n8k16,
+// bf16 x bf16 -> f32).  Activations are stored pixel-major (NHWC) with the
+// channel count padded to a multiple of 16 (the input map carries 8 zero
+// channels; the output layer 15 zero channels), so one 32-bit load fetches
+// the two consecutive channels an mma fragment register holds.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pps.h"
+
+namespace pps {
+namespace net {
+
+constexpr int H = 46, W = 61, NPIX = H * W;
+constexpr int C0 = 16;  // padded input channels (8 used)
+constexpr int CH = 32;  // hidden channels
+constexpr int CO = 16;  // padded output channels (1 used)
+constexpr float kSigOpp = 0.3f, kSigBall = 0.5f, kDiag = 15.f;
+
+// Padded parameter layout (float32 master copy): per layer W[9][cout][cin]
+// then bias[cout].
+__host__ __device__ constexpr int lcin(int l) { return l == 0 ? C0 : CH; }
+__host__ __device__ constexpr int lcout(int l) { return l == 3 ? CO : CH; }
+__host__ __device__ constexpr int layer_size(int l) {
+    return 9 * lcout(l) * lcin(l) + lcout(l);
+}
+__host__ __device__ constexpr int layer_off(int l) {
+    return l == 0 ? 0 : layer_off(l - 1) + layer_size(l - 1);
+}
+constexpr int kPadParams = layer_off(4);
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0,
+                                         uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0,
+                                         uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// ------------------------------------------------------------ rasteriser
+// One thread per (state, pixel): the 8 input channels, bf16, 16-channel rows.
+__global__ void raster_kernel(const pps_state* __restrict__ states, int n,
+                              __nv_bfloat16* __restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)n * NPIX) return;
+    const int s = (int)(i / NPIX), q = (int)(i - (long long)s * NPIX);
+    const int y = q / W, x = q - y * W;
+    const pps_state& st = states[s];
+    const float cx = -6.f + 0.2f * x, cy = -4.5f + 0.2f * y;
+    const float inv_v = 1.f / st.vmax;
+    float dens = 0.f, vx = 0.f, vy = 0.f, dmin2 = 3.0e38f;
+    const int nopp = st.n_opp < 0 ? 0 : (st.n_opp > PPS_MAX_OPP ? PPS_MAX_OPP : st.n_opp);
+    for (int j = 0; j < nopp; ++j) {
+        const float dx = cx - st.opp_pos[j][0], dy = cy - st.opp_pos[j][1];
+        const float r2 = dx * dx + dy * dy;
+        const float g = expf(-r2 / (2.f * kSigOpp * kSigOpp));
+        dens += g;
+        vx += st.opp_vel[j][0] * inv_v * g;
+        vy += st.opp_vel[j][1] * inv_v * g;
+        dmin2 = fminf(dmin2, r2);
+    }
+    const float bx = cx - st.ball[0], by = cy - st.ball[1];
+    const float rb2 = bx * bx + by * by;
+    float c[8];
+    c[0] = dens;
+    c[1] = vx;
+    c[2] = vy;
+    c[3] = expf(-rb2 / (2.f * kSigBall * kSigBall));
+    c[4] = sqrtf(rb2) / kDiag;
+    c[5] = nopp ? sqrtf(dmin2) / kDiag : 1.f;
+    c[6] = cx / (0.5f * st.field_len);
+    c[7] = cy / (0.5f * st.field_wid);
+    uint4 lo, hi;
+    lo.x = pack_bf16(c[0], c[1]);
+    lo.y = pack_bf16(c[2], c[3]);
+    lo.z = pack_bf16(c[4], c[5]);
+    lo.w = pack_bf16(c[6], c[7]);
+    hi.x = hi.y = hi.z = hi.w = 0u;
+    uint4* o = reinterpret_cast<uint4*>(out + i * C0);
+    o[0] = lo;
+    o[1] = hi;
+}
+
+// --------------------------------------------------------- convolution
+// Epilogues of the implicit-GEMM convolution.
+enum Epi {
+    kHidden = 0,  // + bias, ReLU, bf16 out (hidden layers)
+    kOutput = 1,  // + bias, channel 0 as float32 (output layer)
+    kMaskedGrad = 2  // input gradient: bf16(acc) where the layer's input > 0
+};
+
+// out[p][co] = sum over taps and ci of Wt[tap][co][ci] * in[p + off(tap)][ci]
+// for every pixel p of n images; a CTA of 4 warps owns 64 consecutive
+// pixels, each warp 16 of them across all COUT output channels.
+template <int CIN, int COUT, int EPI>
+__global__ void __launch_bounds__(128)
+    conv_kernel(const __nv_bfloat16* __restrict__ in,
+                const __nv_bfloat16* __restrict__ Wt,
+                const float* __restrict__ bias, long long n_pix,
+                void* __restrict__ out,
+                const __nv_bfloat16* __restrict__ mask_src) {
+    static_assert(CIN % 16 == 0 && COUT % 8 == 0, "padded channel counts");
+    __shared__ __align__(16) __nv_bfloat16 sw[9 * COUT * CIN];
+    for (int i = threadIdx.x; i < 9 * COUT * CIN / 8; i += blockDim.x)
+        reinterpret_cast<uint4*>(sw)[i] = reinterpret_cast<const uint4*>(Wt)[i];
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gid = lane >> 2, tig = lane & 3;
+    const long long p0 = (long long)blockIdx.x * 64 + warp * 16;
+    // the two pixel rows this thread's A fragments cover
+    long long pr[2];
+    int yy[2], xx[2];
+    for (int h = 0; h < 2; ++h) {
+        pr[h] = p0 + gid + 8 * h;
+        const long long q = pr[h] < n_pix ? pr[h] % NPIX : 0;
+        yy[h] = (int)(q / W);
+        xx[h] = (int)(q - (long long)yy[h] * W);
+    }
+    constexpr int NT = COUT / 8;
+    float acc[NT][4];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
+
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        const uint32_t* src[2];
+        bool ok[2];
+        for (int h = 0; h < 2; ++h) {
+            const int y2 = yy[h] + dy, x2 = xx[h] + dx;
+            ok[h] = pr[h] < n_pix && y2 >= 0 && y2 < H && x2 >= 0 && x2 < W;
+            const long long pn = pr[h] + dy * W + dx;
+            src[h] = reinterpret_cast<const uint32_t*>(in + (ok[h] ? pn : 0) * CIN);
+        }
+#pragma unroll
+        for (int kc = 0; kc < CIN / 16; ++kc) {
+            const int k0 = kc * 16 + tig * 2;
+            const uint32_t a0 = ok[0] ? __ldg(src[0] + k0 / 2) : 0u;
+            const uint32_t a1 = ok[1] ? __ldg(src[1] + k0 / 2) : 0u;
+            const uint32_t a2 = ok[0] ? __ldg(src[0] + k0 / 2 + 4) : 0u;
+            const uint32_t a3 = ok[1] ? __ldg(src[1] + k0 / 2 + 4) : 0u;
+#pragma unroll
+            for (int t = 0; t < NT; ++t) {
+                const __nv_bfloat16* wrow = sw + (tap * COUT + t * 8 + gid) * CIN + k0;
+                const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wrow);
+                const uint32_t b1 = *reinterpret_cast<const uint32_t*>(wrow + 8);
+                mma_bf16(acc[t], a0, a1, a2, a3, b0, b1);
+            }
+        }
+    }
+    // epilogue: thread holds (row gid, cols 2tig, 2tig+1) and (row gid+8, ..)
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        const int c = t * 8 + tig * 2;
+        for (int h = 0; h < 2; ++h) {
+            const long long p = pr[h];
+            if (p >= n_pix) continue;
+            float v0 = acc[t][2 * h], v1 = acc[t][2 * h + 1];
+            if (EPI == kHidden) {
+                v0 = fmaxf(v0 + bias[c], 0.f);
+                v1 = fmaxf(v1 + bias[c + 1], 0.f);
+                reinterpret_cast<uint32_t*>(out)[(p * COUT + c) / 2] = pack_bf16(v0, v1);
+            } else if (EPI == kOutput) {
+                if (t == 0 && tig == 0)
+                    reinterpret_cast<float*>(out)[p] = v0 + bias[0];
+            } else {
+                const __nv_bfloat162 m = reinterpret_cast<const __nv_bfloat162*>(
+                    mask_src)[(p * COUT + c) / 2];
+                v0 = __bfloat162float(m.x) > 0.f ? v0 : 0.f;
+                v1 = __bfloat162float(m.y) > 0.f ? v1 : 0.f;
+                reinterpret_cast<uint32_t*>(out)[(p * COUT + c) / 2] = pack_bf16(v0, v1);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ training
+// Mean squared error over n_pix pixels: the loss (accumulated) and its
+// gradient 2 (out - label) / n_pix into channel 0 of a CO-channel bf16 map.
+__global__ void loss_kernel(const float* __restrict__ out,
+                            const float* __restrict__ label, long long n_pix,
+                            float inv_n, __nv_bfloat16* __restrict__ g,
+                            float* __restrict__ loss_sum) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    float sq = 0.f;
+    if (i < n_pix) {
+        const float d = out[i] - label[i];
+        sq = d * d * inv_n;
+        uint4 lo = {pack_bf16(2.f * d * inv_n, 0.f), 0u, 0u, 0u};
+        uint4 z = {0u, 0u, 0u, 0u};
+        uint4* o = reinterpret_cast<uint4*>(g + i * CO);
+        o[0] = lo;
+        o[1] = z;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss_sum, sq);
+}
+
+__device__ __forceinline__ uint32_t pair16(const __nv_bfloat16* base,
+                                           long long i0, bool ok0,
+                                           long long i1, bool ok1) {
+    const unsigned short* b = reinterpret_cast<const unsigned short*>(base);
+    const uint32_t lo = ok0 ? __ldg(b + i0) : 0u;
+    const uint32_t hi = ok1 ? __ldg(b + i1) : 0u;
+    return lo | (hi << 16);
+}
+
+// dW[tap][co][ci] += sum over pixels p of g[p][co] * x[p + off(tap)][ci]
+// (x zero outside its image).  One warp per tap; the CTA owns `chunk`
+// consecutive pixels; the warp's 16-pixel steps are the K of the mma
+// (A = g transposed: co x pixels, B = shifted x: pixels x ci).
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(288)
+    wgrad_kernel(const __nv_bfloat16* __restrict__ g,
+                 const __nv_bfloat16* __restrict__ x, long long n_pix,
+                 int chunk, float* __restrict__ dW) {
+    static_assert(CIN % 8 == 0 && COUT % 16 == 0, "padded channel counts");
+    constexpr int MT = COUT / 16, NT = CIN / 8;
+    const int lane = threadIdx.x & 31, tap = threadIdx.x >> 5;
+    const int gid = lane >> 2, tig = lane & 3;
+    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    const long long pbeg = (long long)blockIdx.x * chunk;
+    const long long pend = pbeg + chunk < n_pix ? pbeg + chunk : n_pix;
+    float acc[MT][NT][4];
+#pragma unroll
+    for (int m = 0; m < MT; ++m)
+#pragma unroll
+        for (int t = 0; t < NT; ++t) acc[m][t][0] = acc[m][t][1] = acc[m][t][2] = acc[m][t][3] = 0.f;
+
+    for (long long pk = pbeg; pk < pend; pk += 16) {
+        // the four K positions (pixels) of this thread: 2tig, 2tig+1, +8, +9
+        long long pp[4], nb[4];
+        bool okg[4], okx[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            pp[e] = pk + 2 * tig + (e & 1) + 8 * (e >> 1);
+            okg[e] = pp[e] < pend;
+            const long long q = okg[e] ? pp[e] % NPIX : 0;
+            const int y = (int)(q / W), xx = (int)(q - (long long)y * W);
+            const int y2 = y + dy, x2 = xx + dx;
+            okx[e] = okg[e] && y2 >= 0 && y2 < H && x2 >= 0 && x2 < W;
+            nb[e] = okx[e] ? pp[e] + dy * W + dx : 0;
+        }
+#pragma unroll
+        for (int m = 0; m < MT; ++m) {
+            const int co = m * 16 + gid;
+            const uint32_t a0 = pair16(g, pp[0] * COUT + co, okg[0], pp[1] * COUT + co, okg[1]);
+            const uint32_t a1 = pair16(g, pp[0] * COUT + co + 8, okg[0], pp[1] * COUT + co + 8, okg[1]);
+            const uint32_t a2 = pair16(g, pp[2] * COUT + co, okg[2], pp[3] * COUT + co, okg[3]);
+            const uint32_t a3 = pair16(g, pp[2] * COUT + co + 8, okg[2], pp[3] * COUT + co + 8, okg[3]);
+#pragma unroll
+            for (int t = 0; t < NT; ++t) {
+                const int ci = t * 8 + gid;
+                const uint32_t b0 = pair16(x, nb[0] * CIN + ci, okx[0], nb[1] * CIN + ci, okx[1]);
+                const uint32_t b1 = pair16(x, nb[2] * CIN + ci, okx[2], nb[3] * CIN + ci, okx[3]);
+                mma_bf16(acc[m][t], a0, a1, a2, a3, b0, b1);
+            }
+        }
+    }
+    float* base = dW + (long long)tap * COUT * CIN;
+#pragma unroll
+    for (int m = 0; m < MT; ++m)
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const int r = m * 16 + gid, c = t * 8 + tig * 2;
+            atomicAdd(base + r * CIN + c, acc[m][t][0]);
+            atomicAdd(base + r * CIN + c + 1, acc[m][t][1]);
+            atomicAdd(base + (r + 8) * CIN + c, acc[m][t][2]);
+            atomicAdd(base + (r + 8) * CIN + c + 1, acc[m][t][3]);
+        }
+}
+
+// db[c] += sum over pixels of g[p][c].
+template <int C>
+__global__ void bias_grad_kernel(const __nv_bfloat16* __restrict__ g,
+                                 long long n_pix, float* __restrict__ db) {
+    float acc[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] = 0.f;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n_pix;
+         p += (long long)gridDim.x * blockDim.x) {
+        const __nv_bfloat162* row = reinterpret_cast<const __nv_bfloat162*>(g + p * C);
+#pragma unroll
+        for (int c = 0; c < C / 2; ++c) {
+            const float2 v = __bfloat1622float2(row[c]);
+            acc[2 * c] += v.x;
+            acc[2 * c + 1] += v.y;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        float v = acc[c];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if ((threadIdx.x & 31) == 0) atomicAdd(db + c, v);
+    }
+}
+
+// Adam on the padded float32 parameters; clears the gradient.
+__global__ void adam_kernel(float* __restrict__ w, float* __restrict__ grad,
+                            float* __restrict__ m, float* __restrict__ v,
+                            int n, float lr, float b1, float b2, float eps,
+                            float c1, float c2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float g = grad[i];
+    const float mi = b1 * m[i] + (1.f - b1) * g;
+    const float vi = b2 * v[i] + (1.f - b2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    grad[i] = 0.f;
+}
+
+// bf16 copies of the weights: Wf[l][tap][co][ci] for the forward pass and
+// WT[l][8 - tap][ci][co] (taps mirrored, channels swapped) for the input
+// gradient, which is the same convolution run backwards.
+__global__ void cast_kernel(const float* __restrict__ w,
+                            __nv_bfloat16* __restrict__ Wf,
+                            __nv_bfloat16* __restrict__ WT) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int l = 0, base = 0, wbase = 0;
+    int rem = i;
+    for (l = 0; l < 4; ++l) {
+        const int nw = 9 * lcout(l) * lcin(l);
+        if (rem < nw) break;
+        rem -= nw;
+        base += layer_size(l);
+        wbase += nw;
+    }
+    if (l == 4) return;
+    const int cin = lcin(l), cout = lcout(l);
+    const int tap = rem / (cout * cin);
+    const int co = (rem / cin) % cout, ci = rem % cin;
+    const __nv_bfloat16 b = __float2bfloat16_rn(w[base + rem]);
+    Wf[wbase + rem] = b;
+    WT[wbase + ((8 - tap) * cin + ci) * cout + co] = b;
+}
+
+// Labels: per map pixel, the best exact score of the fine grid points of
+// its cell (the 8 x 8 fine points nearest the pixel centre), floored.
+__global__ void cell_label_kernel(const float* __restrict__ point_best,
+                                  int n, int fnx, int fny, float floor_v,
+                                  float* __restrict__ labels) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)n * NPIX) return;
+    const int s = (int)(i / NPIX), q = (int)(i - (long long)s * NPIX);
+    const int cy = q / W, cx = q - cy * W;
+    const float* pb = point_best + (long long)s * fnx * fny;
+    float m = floor_v;
+    for (int dy = 0; dy < 8; ++dy) {
+        const int fy = 8 * cy - 4 + dy;
+        if (fy < 0 || fy >= fny) continue;
+        for (int dx = 0; dx < 8; ++dx) {
+            const int fx = 8 * cx - 4 + dx;
+            if (fx < 0 || fx >= fnx) continue;
+            m = fmaxf(m, pb[(long long)fy * fnx + fx]);
+        }
+    }
+    labels[i] = m;
+}
+
+// Top-k map pixels of every state (one CTA per state): bitonic sort of
+// (score, ~pixel) keys, best first; equal scores keep the smaller pixel.
+__global__ void __launch_bounds__(512)
+    topk_kernel(const float* __restrict__ scores, int k,
+                int* __restrict__ cells) {
+    __shared__ unsigned long long key[4096];
+    const int s = blockIdx.x;
+    const float* sc = scores + (long long)s * NPIX;
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x) {
+        unsigned long long v = 0ull;
+        if (i < NPIX) {
+            uint32_t u = __float_as_uint(sc[i]);
+            u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+            v = ((unsigned long long)u << 32) | (uint32_t)(~(uint32_t)i);
+        }
+        key[i] = v;
+    }
+    __syncthreads();
+    for (int size = 2; size <= 4096; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < 4096; i += blockDim.x) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const bool desc = (i & size) == 0;
+                    const unsigned long long a = key[i], b = key[j];
+                    if (desc ? a < b : a > b) {
+                        key[i] = b;
+                        key[j] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < k; i += blockDim.x)
+        cells[(long long)s * k + i] = (int)(~(uint32_t)(key[i] & 0xffffffffull));
+}
+
+}  // namespace net
+}  // namespace pps

@@ -71,6 +71,8 @@ struct SearchArgs {
     int T_stride;
     unsigned long long* keys;  // scratch: per-state packed (score, ~idx)
     int* counts;               // scratch: per-state feasible count
+    float* dbg_point;          // may be null: per (s, p) best score
+    const int* skip;           // may be null: states to leave untouched
 };
 
 // ---------------------------------------------------------------- helpers
@@ -471,6 +473,7 @@ __global__ void __launch_bounds__(kTPB, PPS_MIN_BLOCKS)
     for (long long item = gw; item < n_items; item += warps) {
         const int s = (int)(item / a.words);
         const int chunk = (int)(item - (long long)s * a.words);
+        if (a.skip && a.skip[s]) continue;
         const pps_state& st = a.states[s];
         const StateK sk = derive_state(st, a.prm, JMAX, a.kmax);
         OppRegs<JMAX> o;
@@ -519,6 +522,13 @@ __global__ void __launch_bounds__(kTPB, PPS_MIN_BLOCKS)
                 }
             }
         }
+        if (a.dbg_point && active) {
+            float bs = -CUDART_INF_F;
+#pragma unroll
+            for (int v = 0; v < VMAX; ++v)
+                if (v < a.V && r.feas[v]) bs = fmaxf(bs, r.score[v]);
+            a.dbg_point[(long long)s * a.P + p] = bs;
+        }
         key = warp_max_u64(key);
         cnt = __reduce_add_sync(0xffffffffu, cnt);
         if (lane == 0) {
@@ -534,6 +544,7 @@ template <int JMAX, int VMAX>
 __global__ void __launch_bounds__(128) finalize_kernel(const SearchArgs a) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= a.n_states) return;
+    if (a.skip && a.skip[s]) return;
     const pps_state& st = a.states[s];
     const StateK sk = derive_state(st, a.prm, JMAX, a.kmax);
     pps_best b;

@@ -28,6 +28,8 @@ PPS_MAX_OPP = 16
 PPS_MAX_SPEEDS = 8
 PPS_MAX_K = 4096
 PPS_NOALLOC_MAX_STATES = 16384
+PPS_NET_H, PPS_NET_W, PPS_NET_PARAMS = 46, 61, 21121
+PPS_PROPOSE_FALLBACK = 1
 
 PPS_OK, PPS_EINVAL, PPS_ENOMEM, PPS_ECUDA, PPS_ETIMEOUT, PPS_ENOTIMPL = range(6)
 PPS_DEVICE_PTRS = 1
@@ -66,7 +68,7 @@ class pps_best(ctypes.Structure):
 
 class pps_debug_out(ctypes.Structure):
     _fields_ = [("margin", c_void_p), ("score", c_void_p), ("T", c_void_p),
-                ("T_stride", c_int32)]
+                ("T_stride", c_int32), ("point_best", c_void_p)]
 
 
 class pps_ctx_desc(ctypes.Structure):
@@ -142,7 +144,10 @@ EXPORTS = ("pps_abi_version", "pps_status_string", "pps_last_error",
            "pps_plan_destroy", "pps_plan_mask_offsets", "pps_plan_run",
            "pps_plan_groups", "pps_server_create", "pps_server_destroy",
            "pps_server_submit", "pps_server_wait", "pps_server_replay",
-           "pps_server_get_stats")
+           "pps_server_get_stats", "pps_net_create", "pps_net_destroy",
+           "pps_net_set_weights", "pps_net_get_weights", "pps_net_raster",
+           "pps_net_forward", "pps_net_grad", "pps_net_train_step",
+           "pps_net_labels", "pps_propose")
 
 
 class PpsError(RuntimeError):
@@ -217,6 +222,29 @@ def lib():
                                             ctypes.c_double, c_void_p,
                                             P(pps_server_stats)]
             L.pps_server_get_stats.argtypes = [c_void_p, P(pps_server_stats)]
+            L.pps_net_create.argtypes = [ctypes.c_int, c_void_p, ctypes.c_int,
+                                         P(c_void_p)]
+            L.pps_net_destroy.restype = None
+            L.pps_net_destroy.argtypes = [c_void_p]
+            L.pps_net_set_weights.argtypes = [c_void_p, c_void_p]
+            L.pps_net_get_weights.argtypes = [c_void_p, c_void_p]
+            L.pps_net_raster.argtypes = [c_void_p, c_void_p, ctypes.c_int,
+                                         c_void_p]
+            L.pps_net_forward.argtypes = [c_void_p, c_void_p, ctypes.c_int,
+                                          c_void_p]
+            L.pps_net_grad.argtypes = [c_void_p, c_void_p, c_void_p,
+                                       ctypes.c_int, c_void_p,
+                                       P(ctypes.c_float)]
+            L.pps_net_train_step.argtypes = [c_void_p, c_void_p, c_void_p,
+                                             ctypes.c_int, ctypes.c_float,
+                                             P(ctypes.c_float)]
+            L.pps_net_labels.argtypes = [c_void_p, c_void_p, ctypes.c_int,
+                                         ctypes.c_float, c_void_p]
+            L.pps_propose.argtypes = [c_void_p, c_void_p, c_void_p,
+                                      ctypes.c_int, P(pps_grid), c_void_p,
+                                      ctypes.c_int, P(pps_params),
+                                      ctypes.c_int, ctypes.c_uint, c_void_p,
+                                      c_void_p]
             if L.pps_abi_version() != PPS_ABI_VERSION:
                 raise RuntimeError("libpps ABI version mismatch")
             _lib = L
@@ -369,6 +397,66 @@ def pps_server_get_stats(srv):
 RESULT_DTYPE = np.dtype([("best", BEST_DTYPE), ("ticket", "<u8"),
                          ("latency_ns", "<i8"), ("queue_ns", "<i8"),
                          ("batch_size", "<i4"), ("status", "<i4")])
+
+
+def pps_net_create(device=0, stream=None, max_batch=256):
+    net = c_void_p()
+    _check(lib().pps_net_create(device, stream, max_batch, ctypes.byref(net)))
+    return net
+
+
+def pps_net_destroy(net) -> None:
+    lib().pps_net_destroy(net)
+
+
+def pps_net_set_weights(net, w) -> int:
+    w = np.ascontiguousarray(np.asarray(w, np.float32))
+    assert w.size == PPS_NET_PARAMS
+    return _check(lib().pps_net_set_weights(net, w.ctypes.data))
+
+
+def pps_net_get_weights(net) -> np.ndarray:
+    w = np.zeros(PPS_NET_PARAMS, np.float32)
+    _check(lib().pps_net_get_weights(net, w.ctypes.data))
+    return w
+
+
+def pps_net_raster(net, states, n, out) -> int:
+    return _check(lib().pps_net_raster(net, states, n, out))
+
+
+def pps_net_forward(net, states, n, out) -> int:
+    return _check(lib().pps_net_forward(net, states, n, out))
+
+
+def pps_net_grad(net, states, labels, n):
+    g = np.zeros(PPS_NET_PARAMS, np.float32)
+    loss = ctypes.c_float()
+    _check(lib().pps_net_grad(net, states, labels, n, g.ctypes.data,
+                              ctypes.byref(loss)))
+    return loss.value, g
+
+
+def pps_net_train_step(net, states, labels, n, lr, want_loss=True):
+    loss = ctypes.c_float()
+    _check(lib().pps_net_train_step(net, states, labels, n, lr,
+                                    ctypes.byref(loss) if want_loss else None))
+    return loss.value if want_loss else None
+
+
+def pps_net_labels(net, point_best, n, floor_value, labels) -> int:
+    return _check(lib().pps_net_labels(net, point_best, n, floor_value,
+                                       labels))
+
+
+def pps_propose(ctx, net, states, n, fine_grid, speeds, params, topk, flags,
+                out_best, out_cells=None) -> int:
+    """Device addresses for states, out_best, out_cells; speeds host."""
+    sp = np.ascontiguousarray(np.asarray(speeds, np.float32))
+    return _check(lib().pps_propose(
+        ctx, net, states, n, ctypes.byref(fine_grid), sp.ctypes.data, len(sp),
+        ctypes.byref(params) if params is not None else None, topk, flags,
+        out_best, out_cells), ctx)
 
 
 def pps_sync(ctx) -> int:
@@ -575,3 +663,50 @@ def match_jobs(batch: dict):
     first = {k: v[::F] for k, v in batch.items()
              if isinstance(v, np.ndarray)}
     return jobs_from_batch(first)
+
+
+class Net:
+    """The proposal network (weights on the device) with torch buffers."""
+
+    def __init__(self, device=0, stream=None, max_batch=256, weights=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        st = stream if stream is not None else torch.cuda.current_stream(
+            self.device)
+        self.max_batch = max_batch
+        self.net = pps_net_create(device, st.cuda_stream, max_batch)
+        if weights is not None:
+            pps_net_set_weights(self.net, weights)
+
+    def forward(self, states_dev, n):
+        out = self.torch.empty((n, PPS_NET_H, PPS_NET_W),
+                               dtype=self.torch.float32, device=self.device)
+        pps_net_forward(self.net, states_dev.data_ptr(), n, out.data_ptr())
+        return out
+
+    def close(self):
+        if self.net is not None:
+            pps_net_destroy(self.net)
+            self.net = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fine_grid_12x9():
+    """The 0.025 m grid of the 12 x 9 m field the proposal refines on."""
+    return pps_grid_from_field(12.0, 9.0, 0.025)
+
+
+def init_weights(seed: int) -> np.ndarray:
+    """He-style random weights in the flat layout (biases zero)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for ci, co in [(8, 32), (32, 32), (32, 32), (32, 1)]:
+        out.append(rng.normal(0.0, np.sqrt(2.0 / (9 * ci)), 9 * co * ci))
+        out.append(np.zeros(co))
+    return np.concatenate(out).astype(np.float32)

@@ -1,0 +1,216 @@
+"""The proposal network's kernels and the proposal path on the GPU.
+
+Rasteriser, forward pass and weight gradients are compared with the FP64
+CPU reference oracle/net_ref.py (which rounds to bfloat16 where the GPU
+does); the labels, the top-k order and the refinement are compared with
+their definitions and with the full exact search.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import net_ref
+from paper_1909_07717_gb300 import pps, synth
+
+pytestmark = pytest.mark.gpu
+PARAMS = dict(synth.DEFAULT_PARAMS)
+SPEEDS = [2.0, 3.5, 5.0, 6.5]
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_07717_gb300 import build
+    build.build()
+    return t
+
+
+def _bits_to_float(bits):
+    return (np.asarray(bits).astype(np.uint32) << 16).view(np.float32)
+
+
+def _state_dict(batch, s):
+    return {k: batch[k][s] for k in ("ball", "n_opp", "opp_pos", "opp_vel",
+                                     "vmax", "field_len", "field_wid")}
+
+
+def _gpu_raster(torch, net, batch):
+    n = batch["ball"].shape[0]
+    rec = pps.pack_states(batch)
+    dev = torch.from_numpy(rec.view(np.uint8).copy()).cuda()
+    out = torch.empty((n, 46, 61, 8), dtype=torch.int16, device="cuda")
+    pps.pps_net_raster(net.net, dev.data_ptr(), n, out.data_ptr())
+    torch.cuda.synchronize()
+    return dev, _bits_to_float(out.cpu().numpy().view(np.uint16)).astype(
+        np.float64)
+
+
+def _layers_as_gpu(w):
+    """The reference network as the GPU runs it: bf16 weights, f32 biases."""
+    out = []
+    for Wl, bl in net_ref.unflatten(w):
+        out.append((net_ref.bf16(Wl), np.asarray(bl, np.float32)
+                    .astype(np.float64)))
+    return out
+
+
+def test_raster_matches_reference(torch):
+    batch = synth.ssl_states(501, 3, K=64)
+    batch["n_opp"][2] = 0
+    net = pps.Net(max_batch=4)
+    try:
+        _, x = _gpu_raster(torch, net, batch)
+    finally:
+        net.close()
+    for s in range(3):
+        ref = net_ref.raster(_state_dict(batch, s))
+        tol = 2.0 ** -7 * np.abs(ref) + 1e-6
+        assert np.all(np.abs(x[s] - ref) <= tol), s
+
+
+def test_forward_matches_reference(torch):
+    batch = synth.ssl_states(502, 2, K=64)
+    w = pps.init_weights(7)
+    net = pps.Net(max_batch=4, weights=w)
+    try:
+        dev, x = _gpu_raster(torch, net, batch)
+        y = net.forward(dev, 2).cpu().numpy().astype(np.float64)
+    finally:
+        net.close()
+    _, ref = net_ref.forward(x, _layers_as_gpu(w))
+    scale = np.mean(np.abs(ref)) + 1e-3
+    err = np.abs(y - ref)
+    assert np.max(err) <= 2e-2 * scale + 1e-2 * np.abs(ref).max()
+    assert np.mean(err) <= 2e-3 * scale
+
+
+def test_gradients_match_reference(torch):
+    batch = synth.ssl_states(503, 2, K=64)
+    rng = np.random.default_rng(8)
+    labels = rng.normal(0.5, 0.3, size=(2, 46, 61)).astype(np.float32)
+    w = pps.init_weights(9)
+    net = pps.Net(max_batch=4, weights=w)
+    try:
+        dev, x = _gpu_raster(torch, net, batch)
+        lab = torch.from_numpy(labels).cuda()
+        loss, g = pps.pps_net_grad(net.net, dev.data_ptr(), lab.data_ptr(), 2)
+    finally:
+        net.close()
+    ref_loss, ref_grads = net_ref.loss_and_grads(x, labels.astype(np.float64),
+                                                 _layers_as_gpu(w))
+    assert abs(loss - ref_loss) <= 1e-3 * abs(ref_loss)
+    ref = net_ref.flatten(ref_grads)
+    got = g.astype(np.float64)
+    for (Wl, bl), (Wr, br) in zip(net_ref.unflatten(got),
+                                   net_ref.unflatten(ref)):
+        for a, b in ((Wl, Wr), (bl, br)):
+            a, b = a.reshape(-1), b.reshape(-1)
+            if np.linalg.norm(b) == 0:
+                assert np.linalg.norm(a) == 0
+                continue
+            rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+            cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
+            assert rel <= 2e-2 and cos >= 0.9995, (rel, cos)
+
+
+def test_training_reduces_the_loss(torch):
+    """Adam steps on one batch: the network learns to reproduce a map
+    (the ball-proximity channel) it is given as input."""
+    batch = synth.ssl_states(504, 16, K=64)
+    net = pps.Net(max_batch=16, weights=pps.init_weights(10))
+    try:
+        dev, x = _gpu_raster(torch, net, batch)
+        lab = torch.from_numpy(x[..., 3].astype(np.float32)).cuda()
+        losses = [pps.pps_net_train_step(net.net, dev.data_ptr(),
+                                         lab.data_ptr(), 16, 3e-3)
+                  for _ in range(300)]
+    finally:
+        net.close()
+    assert losses[-1] < 0.1 * losses[0], (losses[0], losses[-1])
+
+
+def test_labels_are_cell_maxima(torch):
+    rng = np.random.default_rng(11)
+    pb = rng.normal(size=(2, 361, 481)).astype(np.float32)
+    pb[pb < -1] = -np.inf
+    net = pps.Net(max_batch=2)
+    try:
+        d = torch.from_numpy(pb).cuda()
+        lab = torch.empty((2, 46, 61), dtype=torch.float32, device="cuda")
+        pps.pps_net_labels(net.net, d.data_ptr(), 2, -1.2, lab.data_ptr())
+        got = lab.cpu().numpy()
+    finally:
+        net.close()
+    padded = np.full((2, 368 + 8, 488 + 8), -np.inf, np.float32)
+    padded[:, 4:4 + 361, 4:4 + 481] = pb
+    ref = np.maximum(padded[:, :368, :488].reshape(2, 46, 8, 61, 8)
+                     .max(axis=(2, 4)), -1.2)
+    assert np.array_equal(got, ref)
+
+
+def _search(torch, batch, grid, speeds):
+    S = batch["ball"].shape[0]
+    s = pps.Searcher(max_states=S, max_opp=8)
+    try:
+        out = s.search(s.states_to_device(batch), S, grid, speeds, PARAMS,
+                       mask=False)
+        torch.cuda.synchronize()
+        return pps.unpack_best(out["best"].cpu().numpy())
+    finally:
+        s.close()
+
+
+def _propose(torch, batch, weights, topk, flags=0):
+    S = batch["ball"].shape[0]
+    s = pps.Searcher(max_states=S, max_opp=8)
+    net = pps.Net(max_batch=S, weights=weights)
+    try:
+        dev = s.states_to_device(batch)
+        best = torch.empty(S * 32, dtype=torch.uint8, device="cuda")
+        cells = torch.empty((S, topk), dtype=torch.int32, device="cuda")
+        pps.pps_propose(s.ctx, net.net, dev.data_ptr(), S,
+                        pps.fine_grid_12x9(), SPEEDS,
+                        pps.params_from_dict(PARAMS), topk, flags,
+                        best.data_ptr(), cells.data_ptr())
+        pred = net.forward(dev, S).cpu().numpy()
+        torch.cuda.synchronize()
+        return (pps.unpack_best(best.cpu().numpy()), cells.cpu().numpy(),
+                pred)
+    finally:
+        net.close()
+        s.close()
+
+
+def test_topk_order(torch):
+    batch = synth.ssl_states(505, 3, K=32)
+    _, cells, pred = _propose(torch, batch, pps.init_weights(12), 256)
+    for s in range(3):
+        flat = pred[s].reshape(-1)
+        order = np.lexsort((np.arange(flat.size), -flat))[:256]
+        assert np.array_equal(cells[s], order)
+
+
+def test_all_cells_equal_the_full_search(torch):
+    """Refining every cell visits every fine point exactly once."""
+    batch = synth.ssl_states(506, 4, K=32)
+    best, _, _ = _propose(torch, batch, pps.init_weights(13), 2806)
+    ref = _search(torch, batch, pps.fine_grid_12x9(), SPEEDS)
+    assert best.tobytes() == ref.tobytes()
+
+
+def test_fallback_recovers_the_full_search(torch):
+    """Zero weights rank the corner cells first; states with no feasible
+    pass there fall back to the full grid."""
+    batch = synth.ssl_states(507, 24, K=32)
+    zero = np.zeros(pps.PPS_NET_PARAMS, np.float32)
+    no_fb, cells, _ = _propose(torch, batch, zero, 2)
+    fb, _, _ = _propose(torch, batch, zero, 2, pps.PPS_PROPOSE_FALLBACK)
+    ref = _search(torch, batch, pps.fine_grid_12x9(), SPEEDS)
+    assert np.array_equal(cells[:, :2], np.tile([0, 1], (24, 1)))
+    missed = no_fb["idx"] == -1
+    assert missed.any()
+    assert fb[missed].tobytes() == ref[missed].tobytes()
+    assert fb[~missed].tobytes() == no_fb[~missed].tobytes()
