@@ -441,11 +441,22 @@ pps_status pps_server_get_stats(pps_server* srv, pps_server_stats* out);
  * Not in the paper: a small network ranks coarse cells of the field so that
  * the exact search (Sec. 4.2-4.3) only has to run on the best of them.  The
  * network reads a 46 x 61 map of a 12 x 9 m field (0.2 m pixels, pixel
- * (y, x) at (-6 + 0.2 x, -4.5 + 0.2 y)) with 8 channels rasterised from the
- * state (opponent density, its two velocity-weighted components, ball
- * proximity, distance to the ball, distance to the nearest opponent, x and
- * y) and predicts, per pixel, the best exact score among the fine grid
- * points of that pixel's cell: 4 layers of 3x3 convolutions
+ * (y, x) centred at ((x - 30) / 5, (y - 22.5) / 5)) with 8 channels
+ * rasterised from the state; c is the pixel centre, q the cell's four
+ * sub-points c + (+-0.05, +-0.05) m (clamped into the field):
+ *   0  opponent density at c, sum_j exp(-|c - o_j|^2 / (2 * 0.3^2))
+ *   1  coarse score of the cell: the largest over q of the value function
+ *      (Sec. 4.3) with the margin below, -1.2 where no speed is feasible
+ *   2  |c - b| / diag
+ *   3  margin of the cell: the largest over q and the feature kick speeds
+ *      of the pass's safety margin (Sec. 4.2) with 16 pass-line samples,
+ *      clamped to [-2, 1] (ball stopping short: -2; no opponents: 1)
+ *   4  largest open shot angle over q (Sec. 4.3) / pi
+ *   5  |goal centre - c| / diag
+ *   6  c_x / (L / 2),  7  c_y / (W / 2)
+ * and predicts, per pixel, the best exact score among the fine grid
+ * points of that pixel's cell, as channel 1 plus a learned correction:
+ * 4 layers of 3x3 convolutions
  * (8 -> 32 -> 32 -> 32 -> 1, ReLU between), bfloat16 weights and
  * activations with float32 accumulation, all on the tensor cores, trained
  * on the GPU with the library's own forward and backward kernels (Adam). */
@@ -462,6 +473,27 @@ pps_status pps_net_create(int device, void* stream, int max_batch,
                           pps_net** out);
 void pps_net_destroy(pps_net* net);
 
+/* Kick speeds (host, 1..8, each > 0) and value-function parameters (host,
+ * NULL = pps_default_params) that channels 1, 3 and 4 of the input map are
+ * computed for.  A new network uses speeds {2, 3.5, 5, 6.5} m/s and the
+ * default parameters.  EINVAL on a bad speed or a non-finite parameter. */
+pps_status pps_net_set_features(pps_net* net, const float* speeds,
+                                int n_speeds, const pps_params* params);
+
+/* The training loss of pps_net_grad and pps_net_train_step: the mean over
+ * all map pixels of w (prediction - label)^2, where w = 1 for a pixel whose
+ * label or prediction comes within top_band of its state's best label and
+ * w = low_weight elsewhere, times under_weight where the prediction is
+ * below the label (the weight is held constant in the gradient).  The
+ * proposal only needs the best cells ranked high enough to be refined:
+ * the band focuses the fit on them, and under_weight > 1 makes the
+ * prediction err on the high side where a cell may or may not hold a
+ * feasible pass.  A new network has top_band = +inf, low_weight = 1,
+ * under_weight = 1 (plain mean squared error).  EINVAL unless top_band > 0,
+ * 0 <= low_weight <= 1 and 1 <= under_weight <= 1000. */
+pps_status pps_net_set_loss(pps_net* net, float top_band, float low_weight,
+                            float under_weight);
+
 /* Weights as PPS_NET_PARAMS floats (host).  Setting them resets Adam. */
 pps_status pps_net_set_weights(pps_net* net, const float* w);
 pps_status pps_net_get_weights(pps_net* net, float* w);
@@ -475,9 +507,9 @@ pps_status pps_net_raster(pps_net* net, const pps_state* states, int n,
 pps_status pps_net_forward(pps_net* net, const pps_state* states, int n,
                            float* out);
 
-/* Mean squared error of the prediction against labels[n][46][61] (device)
- * and its gradient with respect to the weights (grads: PPS_NET_PARAMS floats,
- * host, or NULL).  Waits for the result. */
+/* The loss (pps_net_set_loss) of the prediction against labels[n][46][61]
+ * (device) and its gradient with respect to the weights (grads:
+ * PPS_NET_PARAMS floats, host, or NULL).  Waits for the result. */
 pps_status pps_net_grad(pps_net* net, const pps_state* states,
                         const float* labels, int n, float* grads,
                         float* loss);

@@ -30,6 +30,9 @@ struct pps_net {
     float* loss = nullptr;
     int* cells = nullptr;  // proposal scratch: max_batch x NPIX
     int* skip = nullptr;   // proposal scratch: max_batch
+    float* smax = nullptr; // training scratch: max_batch best labels
+    RasterCfg cfg{};       // speeds and parameters of the input features
+    float top_band = 3.0e38f, low_w = 1.f, under_w = 1.f;  // the loss
 };
 
 namespace {
@@ -52,6 +55,21 @@ pps_status fail(pps_status s, const char* msg, cudaError_t e = cudaSuccess) {
     return s;
 }
 
+constexpr float kDefaultSpeeds[4] = {2.f, 3.5f, 5.f, 6.5f};
+
+void set_cfg(RasterCfg& c, const float* speeds, int n, const pps_params* prm) {
+    for (int v = 0; v < PPS_MAX_SPEEDS; ++v) {
+        const float sv = speeds[v < n ? v : n - 1];
+        c.sp[v] = sv;
+        c.sp2[v] = sv * sv;
+    }
+    c.V = n;
+    if (prm)
+        c.prm = *prm;
+    else
+        pps_default_params(&c.prm);
+}
+
 unsigned blocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 cudaError_t cast_weights(pps_net* nt) {
@@ -64,7 +82,7 @@ cudaError_t forward(pps_net* nt, const pps_state* states, int n) {
     const long long P = (long long)n * NPIX;
     const unsigned g = blocks(P, 64);
     cudaStream_t st = nt->stream;
-    raster_kernel<<<blocks(P, 256), 256, 0, st>>>(states, n, nt->a0);
+    raster_kernel<<<blocks(P, 128), 128, 0, st>>>(states, n, nt->cfg, nt->a0);
     conv_kernel<C0, CH, kHidden><<<g, 128, 0, st>>>(
         nt->a0, nt->Wf + wf_off(0), nt->w + bias_off(0), P, nt->a1, nullptr);
     conv_kernel<CH, CH, kHidden><<<g, 128, 0, st>>>(
@@ -72,7 +90,7 @@ cudaError_t forward(pps_net* nt, const pps_state* states, int n) {
     conv_kernel<CH, CH, kHidden><<<g, 128, 0, st>>>(
         nt->a2, nt->Wf + wf_off(2), nt->w + bias_off(2), P, nt->a3, nullptr);
     conv_kernel<CH, CO, kOutput><<<g, 128, 0, st>>>(
-        nt->a3, nt->Wf + wf_off(3), nt->w + bias_off(3), P, nt->out, nullptr);
+        nt->a3, nt->Wf + wf_off(3), nt->w + bias_off(3), P, nt->out, nt->a0);
     return cudaGetLastError();
 }
 
@@ -85,8 +103,10 @@ cudaError_t backward(pps_net* nt, const float* labels, int n) {
     cudaStream_t st = nt->stream;
     cudaError_t e = cudaMemsetAsync(nt->loss, 0, sizeof(float), st);
     if (e != cudaSuccess) return e;
-    loss_kernel<<<blocks(P, 256), 256, 0, st>>>(nt->out, labels, P,
-                                                1.f / (float)P, nt->g4,
+    state_max_kernel<<<n, 256, 0, st>>>(labels, nt->smax);
+    loss_kernel<<<blocks(P, 256), 256, 0, st>>>(nt->out, labels, nt->smax, P,
+                                                1.f / (float)P, nt->top_band,
+                                                nt->low_w, nt->under_w, nt->g4,
                                                 nt->loss);
     // layer 4 (32 -> 1)
     wgrad_kernel<CH, CO><<<gw, 288, 0, st>>>(nt->g4, nt->a3, P, chunk,
@@ -175,6 +195,7 @@ extern "C" pps_status pps_net_create(int device, void* stream, int max_batch,
     nt->device = device;
     nt->stream = (cudaStream_t)stream;
     nt->max_batch = max_batch;
+    set_cfg(nt->cfg, kDefaultSpeeds, 4, nullptr);
     const size_t P = (size_t)max_batch * NPIX;
     cudaError_t e = cudaSetDevice(device);
     auto al = [&](auto** p, size_t bytes) {
@@ -199,6 +220,7 @@ extern "C" pps_status pps_net_create(int device, void* stream, int max_batch,
     al(&nt->loss, sizeof(float));
     al(&nt->cells, sizeof(int) * P);
     al(&nt->skip, sizeof(int) * (size_t)max_batch);
+    al(&nt->smax, sizeof(float) * (size_t)max_batch);
     if (e != cudaSuccess) {
         cudaGetLastError();
         pps_net_destroy(nt);
@@ -217,7 +239,8 @@ extern "C" void pps_net_destroy(pps_net* nt) {
                     (void*)nt->Wf, (void*)nt->WT, (void*)nt->a0, (void*)nt->a1,
                     (void*)nt->a2, (void*)nt->a3, (void*)nt->g1, (void*)nt->g2,
                     (void*)nt->g3, (void*)nt->g4, (void*)nt->out,
-                    (void*)nt->loss, (void*)nt->cells, (void*)nt->skip})
+                    (void*)nt->loss, (void*)nt->cells, (void*)nt->skip,
+                    (void*)nt->smax})
         if (p) cudaFree(p);
     cudaGetLastError();
     delete nt;
@@ -240,6 +263,42 @@ extern "C" pps_status pps_net_set_weights(pps_net* nt, const float* w) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(nt->stream);
     nt->step = 0;
     return e == cudaSuccess ? PPS_OK : fail(PPS_ECUDA, "pps_net_set_weights", e);
+}
+
+extern "C" pps_status pps_net_set_features(pps_net* nt, const float* speeds,
+                                           int n_speeds,
+                                           const pps_params* params) {
+    if (!nt || !speeds || n_speeds < 1 || n_speeds > PPS_MAX_SPEEDS)
+        return fail(PPS_EINVAL, "pps_net_set_features: 1..8 speeds");
+    for (int v = 0; v < n_speeds; ++v)
+        if (!std::isfinite(speeds[v]) || !(speeds[v] > 0.f))
+            return fail(PPS_EINVAL, "pps_net_set_features: speeds must be > 0");
+    if (params) {
+        const float pv[] = {params->w_angle, params->w_dist, params->w_margin,
+                            params->margin_cap, params->tau_safe,
+                            params->robot_radius, params->reach_radius,
+                            params->min_pass_dist};
+        for (float x : pv)
+            if (!std::isfinite(x))
+                return fail(PPS_EINVAL, "pps_net_set_features: params must be finite");
+        if (params->robot_radius < 0.f || params->reach_radius < 0.f)
+            return fail(PPS_EINVAL, "pps_net_set_features: negative radius");
+    }
+    set_cfg(nt->cfg, speeds, n_speeds, params);
+    return PPS_OK;
+}
+
+extern "C" pps_status pps_net_set_loss(pps_net* nt, float top_band,
+                                       float low_weight, float under_weight) {
+    if (!nt || !(top_band > 0.f) || !(low_weight >= 0.f && low_weight <= 1.f) ||
+        !(under_weight >= 1.f && under_weight <= 1e3f))
+        return fail(PPS_EINVAL,
+                    "pps_net_set_loss: top_band > 0, low_weight in [0, 1], "
+                    "under_weight in [1, 1000]");
+    nt->top_band = std::isinf(top_band) ? 3.0e38f : top_band;
+    nt->low_w = low_weight;
+    nt->under_w = under_weight;
+    return PPS_OK;
 }
 
 extern "C" pps_status pps_net_get_weights(pps_net* nt, float* w) {
@@ -271,7 +330,8 @@ extern "C" pps_status pps_net_raster(pps_net* nt, const pps_state* states,
     if (!out) return PPS_EINVAL;
     cudaSetDevice(nt->device);
     const long long P = (long long)n * NPIX;
-    raster_kernel<<<blocks(P, 256), 256, 0, nt->stream>>>(states, n, nt->a0);
+    raster_kernel<<<blocks(P, 128), 128, 0, nt->stream>>>(states, n, nt->cfg,
+                                                          nt->a0);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
         e = cudaMemcpy2DAsync(out, 8 * sizeof(uint16_t), nt->a0,

@@ -16,6 +16,7 @@
 #include <stdint.h>
 
 #include "pps.h"
+#include "pps_search.cuh"
 
 namespace pps {
 namespace net {
@@ -24,7 +25,7 @@ constexpr int H = 46, W = 61, NPIX = H * W;
 constexpr int C0 = 16;  // padded input channels (8 used)
 constexpr int CH = 32;  // hidden channels
 constexpr int CO = 16;  // padded output channels (1 used)
-constexpr float kSigOpp = 0.3f, kSigBall = 0.5f, kDiag = 15.f;
+constexpr float kSigOpp = 0.3f;
 
 // Padded parameter layout (float32 master copy): per layer W[9][cout][cin]
 // then bias[cout].
@@ -55,36 +56,134 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0,
 }
 
 // ------------------------------------------------------------ rasteriser
-// One thread per (state, pixel): the 8 input channels, bf16, 16-channel rows.
+// Kick speeds and value-function parameters the input features are
+// computed for (the network is trained for one such set).
+struct RasterCfg {
+    float sp[PPS_MAX_SPEEDS], sp2[PPS_MAX_SPEEDS];
+    int V;
+    pps_params prm;
+};
+constexpr int kFeatK = 16;          // pass-line samples of the features
+constexpr float kScoreFloor = -1.2f;  // below every score of a 12 x 9 m field
+constexpr float kSubOff = 0.05f;      // sub-points: the cell's quadrant centres
+
+// The cell features of the pixel centred at (cx, cy), each the largest over
+// the four sub-points (cx +- 0.05, cy +- 0.05) (clamped into the field):
+// f[0] the coarse score (the value function with the margin of kFeatK
+// samples; kScoreFloor where no speed is feasible), f[1] the margin (best
+// speed, clamped to [-2, 1]), f[2] the open shot angle / pi.
+template <int J, bool GEN>
+__device__ __forceinline__ void cell_features(const pps_state& st,
+                                              const StateK& sk,
+                                              const RasterCfg& cfg, float cx,
+                                              float cy, float (&f)[3]) {
+    OppRegs<J> o;
+    load_opps<J>(st, sk, o);
+    const float hw = 0.5f * st.field_wid;
+    float mbest = -CUDART_INF_F, tbest = 0.f, sbest = kScoreFloor;
+#pragma unroll 1
+    for (int sub = 0; sub < 4; ++sub) {
+        const float qx =
+            fminf(fmaxf(cx + ((sub & 1) ? kSubOff : -kSubOff), -sk.Lh), sk.Lh);
+        const float qy =
+            fminf(fmaxf(cy + ((sub & 2) ? kSubOff : -kSubOff), -hw), hw);
+        const float dx = qx - sk.bx, dy = qy - sk.by;
+        const float D = sqrtf(dx * dx + dy * dy);
+        const float cbx = sk.kappa * dx, cby = sk.kappa * dy;
+        const float twoabD = sk.two_ab * D;
+        float mv[PPS_MAX_SPEEDS];
+#pragma unroll
+        for (int v = 0; v < PPS_MAX_SPEEDS; ++v) mv[v] = CUDART_INF_F;
+#pragma unroll 1
+        for (int k = 1; k <= kFeatK; ++k) {
+            const float fr = (float)k / (float)kFeatK;
+            float t = CUDART_INF_F;
+#pragma unroll
+            for (int j = 0; j < J; ++j)
+                t = fminf(t, sbip_num<GEN>(fr, cbx, cby, o.bx[j], o.by[j],
+                                           o.ux[j], o.uy[j], sk.reach));
+            const float aT = t * sk.at_scale;
+#pragma unroll
+            for (int v = 0; v < PPS_MAX_SPEEDS; ++v)
+                mv[v] = fminf(mv[v],
+                              aT + sqrtf(fmaxf(cfg.sp2[v] - fr * twoabD, 0.f)));
+        }
+        float m = -CUDART_INF_F;
+#pragma unroll
+        for (int v = 0; v < PPS_MAX_SPEEDS; ++v) {
+            if (v >= cfg.V) continue;
+            float mm;
+            if (cfg.sp2[v] - twoabD < 0.f)
+                mm = -CUDART_INF_F;
+            else if (sk.nopp == 0)
+                mm = CUDART_INF_F;
+            else
+                mm = (mv[v] - cfg.sp[v]) / sk.ab;
+            m = fmaxf(m, mm);
+        }
+        const float th = shot_angle<J>(st, sk, qx < sk.Lh, qx, qy, sk.Lh - qx,
+                                       cfg.prm.robot_radius) *
+                         0.318309886183790672f;
+        const float gx = sk.Lh - qx;
+        const float dg = sqrtf(gx * gx + qy * qy) * sk.inv_diag;
+        const bool feas = m > cfg.prm.tau_safe && D >= cfg.prm.min_pass_dist;
+        const float sc = feas ? cfg.prm.w_angle * th - cfg.prm.w_dist * dg +
+                                    cfg.prm.w_margin * fminf(m, cfg.prm.margin_cap)
+                              : kScoreFloor;
+        mbest = fmaxf(mbest, m);
+        tbest = fmaxf(tbest, th);
+        sbest = fmaxf(sbest, sc);
+    }
+    f[0] = sbest;
+    f[1] = fminf(fmaxf(mbest, -2.f), 1.f);
+    f[2] = tbest;
+}
+
+// One thread per (state, pixel): the 8 input channels of the pixel centred
+// at c = ((x - 30) / 5, (y - 22.5) / 5), bf16, written as 16-channel rows
+// (channels 8..15 zero):
+//   0  sum_j exp(-|c - o_j|^2 / (2 0.3^2))      opponent density
+//   1  coarse score of the cell  (cell_features f[0])
+//   2  |c - b| / diag
+//   3  margin of the cell        (f[1])
+//   4  shot angle of the cell    (f[2])
+//   5  |goal centre - c| / diag
+//   6  c_x / (L / 2),  7  c_y / (W / 2)
 __global__ void raster_kernel(const pps_state* __restrict__ states, int n,
+                              const RasterCfg cfg,
                               __nv_bfloat16* __restrict__ out) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)n * NPIX) return;
     const int s = (int)(i / NPIX), q = (int)(i - (long long)s * NPIX);
     const int y = q / W, x = q - y * W;
     const pps_state& st = states[s];
-    const float cx = -6.f + 0.2f * x, cy = -4.5f + 0.2f * y;
-    const float inv_v = 1.f / st.vmax;
-    float dens = 0.f, vx = 0.f, vy = 0.f, dmin2 = 3.0e38f;
-    const int nopp = st.n_opp < 0 ? 0 : (st.n_opp > PPS_MAX_OPP ? PPS_MAX_OPP : st.n_opp);
-    for (int j = 0; j < nopp; ++j) {
+    const float cx = __fdiv_rn((float)(x - 30), 5.f);
+    const float cy = __fdiv_rn(__fsub_rn((float)y, 22.5f), 5.f);
+    const StateK sk = derive_state(st, cfg.prm, PPS_MAX_OPP, PPS_MAX_K);
+
+    float dens = 0.f;
+    for (int j = 0; j < sk.nopp; ++j) {
         const float dx = cx - st.opp_pos[j][0], dy = cy - st.opp_pos[j][1];
-        const float r2 = dx * dx + dy * dy;
-        const float g = expf(-r2 / (2.f * kSigOpp * kSigOpp));
-        dens += g;
-        vx += st.opp_vel[j][0] * inv_v * g;
-        vy += st.opp_vel[j][1] * inv_v * g;
-        dmin2 = fminf(dmin2, r2);
+        dens += expf(-(dx * dx + dy * dy) / (2.f * kSigOpp * kSigOpp));
     }
-    const float bx = cx - st.ball[0], by = cy - st.ball[1];
-    const float rb2 = bx * bx + by * by;
+    float f[3] = {kScoreFloor, -2.f, 0.f};
+    if (sk.valid) {
+        if (sk.nopp <= 8)
+            sk.general ? cell_features<8, true>(st, sk, cfg, cx, cy, f)
+                       : cell_features<8, false>(st, sk, cfg, cx, cy, f);
+        else
+            sk.general ? cell_features<PPS_MAX_OPP, true>(st, sk, cfg, cx, cy, f)
+                       : cell_features<PPS_MAX_OPP, false>(st, sk, cfg, cx, cy, f);
+    }
+    const float dxm = cx - sk.bx, dym = cy - sk.by;
+    const float gx = sk.Lh - cx;
     float c[8];
     c[0] = dens;
-    c[1] = vx;
-    c[2] = vy;
-    c[3] = expf(-rb2 / (2.f * kSigBall * kSigBall));
-    c[4] = sqrtf(rb2) / kDiag;
-    c[5] = nopp ? sqrtf(dmin2) / kDiag : 1.f;
+    c[1] = f[0];
+    c[2] = sqrtf(dxm * dxm + dym * dym) * sk.inv_diag;
+    c[3] = f[1];
+    c[4] = f[2];
+    c[5] = sqrtf(gx * gx + cy * cy) * sk.inv_diag;
     c[6] = cx / (0.5f * st.field_len);
     c[7] = cy / (0.5f * st.field_wid);
     uint4 lo, hi;
@@ -93,21 +192,24 @@ __global__ void raster_kernel(const pps_state* __restrict__ states, int n,
     lo.z = pack_bf16(c[4], c[5]);
     lo.w = pack_bf16(c[6], c[7]);
     hi.x = hi.y = hi.z = hi.w = 0u;
-    uint4* o = reinterpret_cast<uint4*>(out + i * C0);
-    o[0] = lo;
-    o[1] = hi;
+    uint4* op = reinterpret_cast<uint4*>(out + i * C0);
+    op[0] = lo;
+    op[1] = hi;
 }
 
 // --------------------------------------------------------- convolution
 // Epilogues of the implicit-GEMM convolution.
 enum Epi {
     kHidden = 0,  // + bias, ReLU, bf16 out (hidden layers)
-    kOutput = 1,  // + bias, channel 0 as float32 (output layer)
-    kMaskedGrad = 2  // input gradient: bf16(acc) where the layer's input > 0
+    kOutput = 1,  // + bias + the input map's coarse score (channel 1 of
+                  // aux), channel 0 as float32 (output layer)
+    kMaskedGrad = 2  // input gradient: bf16(acc) where aux (the layer's
+                     // input) > 0
 };
 
 // out[p][co] = sum over taps and ci of Wt[tap][co][ci] * in[p + off(tap)][ci]
-// for every pixel p of n images; a CTA of 4 warps owns 64 consecutive
+// for every pixel p of n images (aux: the layer input that masks an input
+// gradient, or the input map whose coarse score the output adds); a CTA of 4 warps owns 64 consecutive
 // pixels, each warp 16 of them across all COUT output channels.
 template <int CIN, int COUT, int EPI>
 __global__ void __launch_bounds__(128)
@@ -115,7 +217,7 @@ __global__ void __launch_bounds__(128)
                 const __nv_bfloat16* __restrict__ Wt,
                 const float* __restrict__ bias, long long n_pix,
                 void* __restrict__ out,
-                const __nv_bfloat16* __restrict__ mask_src) {
+                const __nv_bfloat16* __restrict__ aux) {
     static_assert(CIN % 16 == 0 && COUT % 8 == 0, "padded channel counts");
     __shared__ __align__(16) __nv_bfloat16 sw[9 * COUT * CIN];
     for (int i = threadIdx.x; i < 9 * COUT * CIN / 8; i += blockDim.x)
@@ -180,10 +282,11 @@ __global__ void __launch_bounds__(128)
                 reinterpret_cast<uint32_t*>(out)[(p * COUT + c) / 2] = pack_bf16(v0, v1);
             } else if (EPI == kOutput) {
                 if (t == 0 && tig == 0)
-                    reinterpret_cast<float*>(out)[p] = v0 + bias[0];
+                    reinterpret_cast<float*>(out)[p] =
+                        v0 + bias[0] + __bfloat162float(aux[p * C0 + 1]);
             } else {
                 const __nv_bfloat162 m = reinterpret_cast<const __nv_bfloat162*>(
-                    mask_src)[(p * COUT + c) / 2];
+                    aux)[(p * COUT + c) / 2];
                 v0 = __bfloat162float(m.x) > 0.f ? v0 : 0.f;
                 v1 = __bfloat162float(m.y) > 0.f ? v1 : 0.f;
                 reinterpret_cast<uint32_t*>(out)[(p * COUT + c) / 2] = pack_bf16(v0, v1);
@@ -193,22 +296,51 @@ __global__ void __launch_bounds__(128)
 }
 
 // ------------------------------------------------------------ training
-// Mean squared error over n_pix pixels: the loss (accumulated) and its
-// gradient 2 (out - label) / n_pix into channel 0 of a CO-channel bf16 map.
+// Per state: the largest label of its map.
+__global__ void __launch_bounds__(256)
+    state_max_kernel(const float* __restrict__ label,
+                     float* __restrict__ smax) {
+    __shared__ float red[8];
+    const float* l = label + (long long)blockIdx.x * NPIX;
+    float m = -CUDART_INF_F;
+    for (int i = threadIdx.x; i < NPIX; i += blockDim.x) m = fmaxf(m, l[i]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
+        smax[blockIdx.x] = fmaxf(m, red[0]);
+    }
+}
+
+// Top-focused, asymmetric mean squared error over n_pix pixels: pixel p of
+// state s weighs 1 where its label or its prediction comes within top_band
+// of the state's best label smax[s], low_w elsewhere, times under_w where
+// the prediction is below the label (the weight is a constant of the
+// gradient).  The loss (accumulated) and its gradient 2 w (out - label) /
+// n_pix into channel 0 of a CO-channel bf16 map.
 __global__ void loss_kernel(const float* __restrict__ out,
-                            const float* __restrict__ label, long long n_pix,
-                            float inv_n, __nv_bfloat16* __restrict__ g,
+                            const float* __restrict__ label,
+                            const float* __restrict__ smax, long long n_pix,
+                            float inv_n, float top_band, float low_w,
+                            float under_w, __nv_bfloat16* __restrict__ g,
                             float* __restrict__ loss_sum) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     float sq = 0.f;
     if (i < n_pix) {
-        const float d = out[i] - label[i];
-        sq = d * d * inv_n;
-        uint4 lo = {pack_bf16(2.f * d * inv_n, 0.f), 0u, 0u, 0u};
+        const float o = out[i], l = label[i];
+        const float cut = smax[i / NPIX] - top_band;
+        const float d = o - l;
+        const float w = ((l >= cut || o >= cut) ? 1.f : low_w) *
+                        (d < 0.f ? under_w : 1.f);
+        sq = w * d * d * inv_n;
+        uint4 lo = {pack_bf16(2.f * w * d * inv_n, 0.f), 0u, 0u, 0u};
         uint4 z = {0u, 0u, 0u, 0u};
-        uint4* o = reinterpret_cast<uint4*>(g + i * CO);
-        o[0] = lo;
-        o[1] = z;
+        uint4* op = reinterpret_cast<uint4*>(g + i * CO);
+        op[0] = lo;
+        op[1] = z;
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, off);

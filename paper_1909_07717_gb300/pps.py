@@ -145,7 +145,8 @@ EXPORTS = ("pps_abi_version", "pps_status_string", "pps_last_error",
            "pps_plan_groups", "pps_server_create", "pps_server_destroy",
            "pps_server_submit", "pps_server_wait", "pps_server_replay",
            "pps_server_get_stats", "pps_net_create", "pps_net_destroy",
-           "pps_net_set_weights", "pps_net_get_weights", "pps_net_raster",
+           "pps_net_set_features", "pps_net_set_loss", "pps_net_set_weights",
+           "pps_net_get_weights", "pps_net_raster",
            "pps_net_forward", "pps_net_grad", "pps_net_train_step",
            "pps_net_labels", "pps_propose")
 
@@ -226,6 +227,10 @@ def lib():
                                          P(c_void_p)]
             L.pps_net_destroy.restype = None
             L.pps_net_destroy.argtypes = [c_void_p]
+            L.pps_net_set_features.argtypes = [c_void_p, c_void_p,
+                                               ctypes.c_int, P(pps_params)]
+            L.pps_net_set_loss.argtypes = [c_void_p, ctypes.c_float,
+                                           ctypes.c_float, ctypes.c_float]
             L.pps_net_set_weights.argtypes = [c_void_p, c_void_p]
             L.pps_net_get_weights.argtypes = [c_void_p, c_void_p]
             L.pps_net_raster.argtypes = [c_void_p, c_void_p, ctypes.c_int,
@@ -409,6 +414,21 @@ def pps_net_destroy(net) -> None:
     lib().pps_net_destroy(net)
 
 
+def pps_net_set_features(net, speeds, params=None) -> int:
+    sp = np.ascontiguousarray(np.asarray(speeds, np.float32))
+    prm = params if params is None or isinstance(params, pps_params) else \
+        params_from_dict(params)
+    return _check(lib().pps_net_set_features(
+        net, sp.ctypes.data, len(sp),
+        ctypes.byref(prm) if prm is not None else None))
+
+
+def pps_net_set_loss(net, top_band=float("inf"), low_weight=1.0,
+                     under_weight=1.0) -> int:
+    return _check(lib().pps_net_set_loss(net, top_band, low_weight,
+                                         under_weight))
+
+
 def pps_net_set_weights(net, w) -> int:
     w = np.ascontiguousarray(np.asarray(w, np.float32))
     assert w.size == PPS_NET_PARAMS
@@ -561,19 +581,23 @@ class Searcher:
         return out
 
     def search(self, states_dev, n_states, grid, speeds, params=None,
-               out=None, mask=True, debug=False, T_stride=0):
-        """Enqueue the search on the context's stream (device buffers)."""
+               out=None, mask=True, debug=False, T_stride=0,
+               point_best=None):
+        """Enqueue the search on the context's stream (device buffers).
+        ``point_best``: optional float32 device tensor of n_states x P that
+        receives every point's best score over the speeds."""
         sp = np.ascontiguousarray(np.asarray(speeds, np.float32))
         if out is None:
             out = self.alloc_outputs(n_states, grid, len(sp), mask, debug,
                                      T_stride)
         dbg = None
-        if "margin" in out or "T" in out:
+        if "margin" in out or "T" in out or point_best is not None:
             dbg = pps_debug_out(
                 out["margin"].data_ptr() if "margin" in out else None,
                 out["score"].data_ptr() if "score" in out else None,
                 out["T"].data_ptr() if "T" in out else None,
-                out["T"].shape[2] if "T" in out else 0)
+                out["T"].shape[2] if "T" in out else 0,
+                point_best.data_ptr() if point_best is not None else None)
         prm = params if isinstance(params, pps_params) else \
             params_from_dict(params)
         pps_search(self.ctx, states_dev.data_ptr(), n_states, grid,
@@ -702,11 +726,53 @@ def fine_grid_12x9():
     return pps_grid_from_field(12.0, 9.0, 0.025)
 
 
-def init_weights(seed: int) -> np.ndarray:
-    """He-style random weights in the flat layout (biases zero)."""
+def init_weights(seed: int, zero_output: bool = False) -> np.ndarray:
+    """He-style random weights in the flat layout (biases zero).  With
+    zero_output the last layer starts at zero, so that the network starts
+    as its input's coarse score and training learns the correction."""
     rng = np.random.default_rng(seed)
     out = []
     for ci, co in [(8, 32), (32, 32), (32, 32), (32, 1)]:
-        out.append(rng.normal(0.0, np.sqrt(2.0 / (9 * ci)), 9 * co * ci))
+        w = rng.normal(0.0, np.sqrt(2.0 / (9 * ci)), 9 * co * ci)
+        out.append(w * 0.0 if zero_output and co == 1 else w)
         out.append(np.zeros(co))
     return np.concatenate(out).astype(np.float32)
+
+
+# ------------------------------------------------------- proposal weights
+WEIGHTS_DIR = os.path.join(PKG, "weights")
+# Weights trained by paper_1909_07717_gb300.train_proposal on exact labels
+# of 12 x 9 m, 8-opponent states (kick speeds 2, 3.5, 5, 6.5 m/s, K = 64).
+PROPOSAL_WEIGHTS = os.path.join(WEIGHTS_DIR, "proposal_12x9_v4_K64_J8.bin")
+_WMAGIC = b"PPSNET\x00\x01"
+
+
+def save_net_weights(path: str, w) -> None:
+    """Flat float32 weights -> file: 8-byte magic, uint32 count, uint32
+    CRC-32 of the data, then the little-endian float32 values."""
+    import zlib
+    w = np.ascontiguousarray(np.asarray(w, "<f4"))
+    if w.size != PPS_NET_PARAMS or not np.all(np.isfinite(w)):
+        raise ValueError("weights must be PPS_NET_PARAMS finite values")
+    data = w.tobytes()
+    hdr = _WMAGIC + np.array([w.size, zlib.crc32(data)], "<u4").tobytes()
+    tmp = path + ".tmp"
+    with open(tmp, "wb") as f:
+        f.write(hdr + data)
+    os.replace(tmp, path)
+
+
+def load_net_weights(path: str = PROPOSAL_WEIGHTS) -> np.ndarray:
+    """Inverse of save_net_weights; raises on a bad magic, size or CRC."""
+    import zlib
+    with open(path, "rb") as f:
+        raw = f.read()
+    if raw[:8] != _WMAGIC or len(raw) < 16:
+        raise ValueError(f"{path}: not a proposal weight file")
+    n, crc = np.frombuffer(raw[8:16], "<u4")
+    data = raw[16:]
+    if n != PPS_NET_PARAMS or len(data) != 4 * n:
+        raise ValueError(f"{path}: expected {PPS_NET_PARAMS} weights")
+    if zlib.crc32(data) != crc:
+        raise ValueError(f"{path}: checksum mismatch")
+    return np.frombuffer(data, "<f4").astype(np.float32)

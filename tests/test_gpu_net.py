@@ -34,7 +34,8 @@ def _bits_to_float(bits):
 
 def _state_dict(batch, s):
     return {k: batch[k][s] for k in ("ball", "n_opp", "opp_pos", "opp_vel",
-                                     "vmax", "field_len", "field_wid")}
+                                     "ball_decel", "vmax", "amax",
+                                     "field_len", "field_wid", "goal_width")}
 
 
 def _gpu_raster(torch, net, batch):
@@ -65,10 +66,19 @@ def test_raster_matches_reference(torch):
         _, x = _gpu_raster(torch, net, batch)
     finally:
         net.close()
+    # one bfloat16 rounding step apart at most; the margin and the coarse
+    # score (FP32 intercept and ball times against FP64) also get 2 ms
+    # absolute, the shot angle 1e-5 for the FP32 arc functions.  Where a
+    # cell's feasibility decision sits within 5 ms of its threshold the two
+    # sides may decide it differently: the coarse score is not compared
+    # there.
+    absol = np.array([1e-6, 2e-3, 1e-6, 2e-3, 1e-5, 1e-6, 1e-6, 1e-6])
     for s in range(3):
-        ref = net_ref.raster(_state_dict(batch, s))
-        tol = 2.0 ** -7 * np.abs(ref) + 1e-6
-        assert np.all(np.abs(x[s] - ref) <= tol), s
+        ref, band = net_ref.raster(_state_dict(batch, s), with_band=True)
+        tol = 2.0 ** -7 * np.abs(ref) + absol
+        bad = np.abs(x[s] - ref) > tol
+        bad[..., 1] &= band >= 5e-3
+        assert not bad.any(), (s, np.argwhere(bad)[:5])
 
 
 def test_forward_matches_reference(torch):
@@ -87,25 +97,29 @@ def test_forward_matches_reference(torch):
     assert np.mean(err) <= 2e-3 * scale
 
 
-def test_gradients_match_reference(torch):
+@pytest.mark.parametrize("band,low,under", [(np.inf, 1.0, 1.0),
+                                            (0.4, 0.1, 3.0)])
+def test_gradients_match_reference(torch, band, low, under):
     batch = synth.ssl_states(503, 2, K=64)
     rng = np.random.default_rng(8)
     labels = rng.normal(0.5, 0.3, size=(2, 46, 61)).astype(np.float32)
     w = pps.init_weights(9)
     net = pps.Net(max_batch=4, weights=w)
     try:
+        pps.pps_net_set_loss(net.net, band, low, under)
         dev, x = _gpu_raster(torch, net, batch)
         lab = torch.from_numpy(labels).cuda()
         loss, g = pps.pps_net_grad(net.net, dev.data_ptr(), lab.data_ptr(), 2)
     finally:
         net.close()
-    ref_loss, ref_grads = net_ref.loss_and_grads(x, labels.astype(np.float64),
-                                                 _layers_as_gpu(w))
+    ref_loss, ref_grads = net_ref.loss_and_grads(
+        x, labels.astype(np.float64), _layers_as_gpu(w), top_band=band,
+        low_weight=low, under_weight=under)
     assert abs(loss - ref_loss) <= 1e-3 * abs(ref_loss)
     ref = net_ref.flatten(ref_grads)
     got = g.astype(np.float64)
     for (Wl, bl), (Wr, br) in zip(net_ref.unflatten(got),
-                                   net_ref.unflatten(ref)):
+                                  net_ref.unflatten(ref)):
         for a, b in ((Wl, Wr), (bl, br)):
             a, b = a.reshape(-1), b.reshape(-1)
             if np.linalg.norm(b) == 0:
@@ -201,14 +215,29 @@ def test_all_cells_equal_the_full_search(torch):
     assert best.tobytes() == ref.tobytes()
 
 
+def _cancel_weights():
+    """Weights whose last convolution is minus the coarse-score channel, so
+    that the network's output (that channel plus the last convolution) is
+    0 everywhere: relu(c) and relu(-c) through the hidden layers' centre
+    taps, recombined as -c."""
+    layers = net_ref.unflatten(np.zeros(net_ref.n_params()))
+    W0, W1, W2, W3 = (Wl for Wl, _ in layers)
+    W0[1, 1, 0, 1], W0[1, 1, 1, 1] = 1.0, -1.0
+    for Wl in (W1, W2):
+        Wl[1, 1, 0, 0] = Wl[1, 1, 1, 1] = 1.0
+    W3[1, 1, 0, 0], W3[1, 1, 0, 1] = -1.0, 1.0
+    return net_ref.flatten(layers).astype(np.float32)
+
+
 def test_fallback_recovers_the_full_search(torch):
-    """Zero weights rank the corner cells first; states with no feasible
-    pass there fall back to the full grid."""
+    """A network that predicts 0 everywhere ranks the corner cells first;
+    states with no feasible pass there fall back to the full grid."""
     batch = synth.ssl_states(507, 24, K=32)
-    zero = np.zeros(pps.PPS_NET_PARAMS, np.float32)
-    no_fb, cells, _ = _propose(torch, batch, zero, 2)
-    fb, _, _ = _propose(torch, batch, zero, 2, pps.PPS_PROPOSE_FALLBACK)
+    w = _cancel_weights()
+    no_fb, cells, pred = _propose(torch, batch, w, 2)
+    fb, _, _ = _propose(torch, batch, w, 2, pps.PPS_PROPOSE_FALLBACK)
     ref = _search(torch, batch, pps.fine_grid_12x9(), SPEEDS)
+    assert np.all(pred == 0.0)
     assert np.array_equal(cells[:, :2], np.tile([0, 1], (24, 1)))
     missed = no_fb["idx"] == -1
     assert missed.any()
