@@ -379,6 +379,8 @@ def run_pps(args):
             line["uneven"] = _uneven(args, dev, stream)
         if world == 1 and not args.no_serving:
             line["serving"] = _serving(dev)
+        if world == 1 and not args.no_proposal:
+            line["proposal"] = _proposal(args, dev, stream)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
@@ -435,6 +437,60 @@ def _uneven(args, dev, stream):
     return out
 
 
+def _proposal(args, dev, stream):
+    """The learned proposal against the plain search on the same 4096
+    held-out states (12x9 m, 8 v 8, K = 64, 4 speeds, 0.025 m grid =
+    481x361): one pps_propose (rasterise, predict, top-256 cells, exact
+    refinement, full-grid fallback) against one pps_search per batch, both
+    timed like the main step; the agreement is the share of states whose
+    proposal score is within 2 % of the plain search's."""
+    import torch
+    from paper_1909_07717_gb300 import pps, synth
+    from paper_1909_07717_gb300.proposal import TOPK, Proposal, agreement
+    w = synth.PROPOSAL
+    S = w.n_states
+    batch = w.states()
+    pr = Proposal(S, device=dev.index, stream=stream)
+    st = pr.searcher.states_to_device(batch)
+    exo = pr.searcher.alloc_outputs(S, pr.grid, len(w.speeds), mask=False)
+    pro = pr.alloc(S)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn, steps):
+        for _ in range(2):
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / steps
+
+    steps = max(3, min(args.steps, 5))
+    ms_plain = timed(lambda: pr.exact(st, S, w.speeds, out=exo), steps)
+    ms_prop = timed(lambda: pr.run(st, S, w.speeds, out=pro), steps)
+    ms_pred = timed(lambda: pr.net.forward(st, S), steps)
+    ex = pps.unpack_best(exo["best"].cpu().numpy())
+    pb = pps.unpack_best(pro[0].cpu().numpy())
+    nofb = pps.unpack_best(pr.run(st, S, w.speeds, fallback=False)[0]
+                           .cpu().numpy())
+    pr.close()
+    ok = agreement(pb, ex)
+    return {"workload": f"{w.name} (seed {w.seed}, held out of training)",
+            "topk": TOPK, "ms_plain": ms_plain, "ms_proposal": ms_prop,
+            "ms_predict": ms_pred,
+            "plain_states_per_s": S / (ms_plain / 1e3),
+            "proposal_states_per_s": S / (ms_prop / 1e3),
+            "speedup": ms_plain / ms_prop,
+            "agree_2pct": float(ok.mean()),
+            "same_point": float((pb["idx"] == ex["idx"]).mean()),
+            "fallback_states": int((nofb["idx"] == -1).sum()),
+            "refined_points_frac": TOPK * 64 / (481 * 361)}
+
+
 def _serving(dev, seconds=2.0):
     """The serving loop: 512 simulated matches at 60 Hz (12x9 or 9x6 fields,
     6-11 opponents, 0.05 m grid, 4 speeds, K = 32) replayed in real time
@@ -479,6 +535,8 @@ def main():
                     help="skip the uneven-batch plan measurement")
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the serving-loop replay")
+    ap.add_argument("--no-proposal", action="store_true",
+                    help="skip the learned-proposal comparison")
     ap.add_argument("--states", type=int, default=0,
                     help="states per GPU (default: the workload's 4096); "
                          "smaller only for profiling captures")

@@ -536,8 +536,14 @@ pps_status pps_net_labels(pps_net* net, const float* point_best, int n,
  * (fine_grid must be the 481 x 361 grid of the 12 x 9 m field at 0.025 m).
  * states, out_best and out_cells (n x topk pixel indices y * 61 + x, or
  * NULL) are device memory; 1 <= topk <= 2806; n <= both the context's
- * max_states and the network's max_batch.  out_best.n_feasible counts the
- * refined points only.  Enqueued on the context's stream. */
+ * max_states and the network's max_batch.  The network's input features
+ * use its own speeds and parameters (pps_net_set_features); the exact
+ * refinement uses speeds and params of this call.  out_best.n_feasible
+ * counts the feasible candidates among the refined points (the whole
+ * grid's for a state that fell back).  The prediction runs on the
+ * network's stream and the refinement on the context's (ordered by an
+ * event); the call returns without waiting.  One network serves one
+ * pps_propose at a time (it holds the call's scratch). */
 pps_status pps_propose(pps_ctx* ctx, pps_net* net, const pps_state* states,
                        int n, const pps_grid* fine_grid, const float* speeds,
                        int n_speeds, const pps_params* params, int topk,

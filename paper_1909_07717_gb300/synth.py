@@ -157,6 +157,14 @@ BATCHED = Workload("batched_4096x241x181_v4_K64_J8", seed=1, n_states=4096,
                    spacing=0.05, speeds=[2.0, 3.5, 5.0, 6.5], K=64)
 
 
+# Learned-proposal workload: 4096 states of the batched kind (12x9 m, 8 v 8,
+# K = 64, speeds {2, 3.5, 5, 6.5}) searched on the 0.025 m grid (481x361),
+# plain and through the proposal.  Seed 7 is held out of the network's
+# training set (seeds 100000 and up).
+PROPOSAL = Workload("proposal_4096x481x361_v4_K64_J8", seed=7, n_states=4096,
+                    spacing=0.025, speeds=[2.0, 3.5, 5.0, 6.5], K=64)
+
+
 def uneven_batch(seed: int, n_states: int, *,
                  spacings=(0.025, 0.05, 0.1), k_range=(32, 128),
                  speed_range=(2.0, 6.5), decel_range=(0.3, 0.7),
