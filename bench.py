@@ -448,8 +448,8 @@ def _proposal(args, dev, stream):
     from paper_1909_07717_gb300 import pps, synth
     from paper_1909_07717_gb300.proposal import TOPK, Proposal, agreement
     w = synth.PROPOSAL
-    S = w.n_states
-    batch = w.states()
+    S = args.states or w.n_states
+    batch = w.states(S)
     pr = Proposal(S, device=dev.index, stream=stream)
     st = pr.searcher.states_to_device(batch)
     exo = pr.searcher.alloc_outputs(S, pr.grid, len(w.speeds), mask=False)

@@ -120,12 +120,12 @@ pps_status check_state(pps_ctx* ctx, const pps_state& s, int i) {
     return PPS_OK;
 }
 
-template <int J, int V>
+template <int J, int V, bool EXT>
 cudaError_t launch(const pps::SearchArgs& a, int num_sms, cudaStream_t st) {
     static int occ = 0;  // CTAs per SM of this instance (per process)
     if (occ == 0) {
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &occ, pps::search_kernel<J, V>, pps::kTPB, 0);
+            &occ, pps::search_kernel<J, V, EXT>, pps::kTPB, 0);
         if (e != cudaSuccess) return e;
         if (occ < 1) occ = 1;
     }
@@ -134,17 +134,23 @@ cudaError_t launch(const pps::SearchArgs& a, int num_sms, cudaStream_t st) {
     long long grid = (long long)num_sms * occ;
     const long long need = (items + pps::kTPB / 32 - 1) / (pps::kTPB / 32);
     if (grid > need) grid = need;
-    pps::search_kernel<J, V><<<(unsigned)grid, pps::kTPB, 0, st>>>(a);
+    pps::search_kernel<J, V, EXT><<<(unsigned)grid, pps::kTPB, 0, st>>>(a);
     pps::finalize_kernel<J, V><<<(a.n_states + 127) / 128, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 
+template <int J, int V>
+cudaError_t launch_e(const pps::SearchArgs& a, int num_sms, cudaStream_t st) {
+    return a.dbg_point ? launch<J, V, true>(a, num_sms, st)
+                       : launch<J, V, false>(a, num_sms, st);
+}
+
 template <int J>
 cudaError_t launch_v(const pps::SearchArgs& a, int num_sms, cudaStream_t st) {
-    if (a.V <= 1) return launch<J, 1>(a, num_sms, st);
-    if (a.V <= 2) return launch<J, 2>(a, num_sms, st);
-    if (a.V <= 4) return launch<J, 4>(a, num_sms, st);
-    return launch<J, 8>(a, num_sms, st);
+    if (a.V <= 1) return launch_e<J, 1>(a, num_sms, st);
+    if (a.V <= 2) return launch_e<J, 2>(a, num_sms, st);
+    if (a.V <= 4) return launch_e<J, 4>(a, num_sms, st);
+    return launch_e<J, 8>(a, num_sms, st);
 }
 
 template <int J, int V>

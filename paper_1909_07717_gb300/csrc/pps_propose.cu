@@ -87,7 +87,7 @@ int occupancy() {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, refine_kernel<J, V>,
                                                       pps::kTPB, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &b, pps::search_kernel<J, V>, pps::kTPB, 0);
+            &b, pps::search_kernel<J, V, true>, pps::kTPB, 0);
         occ = a < b ? a : b;
         if (occ < 1) occ = 1;
     }
@@ -116,7 +116,7 @@ cudaError_t run(const pps::SearchArgs& base, const int* cells, int topk,
     const long long fitems = (long long)a.n_states * a.words;
     grid = (fitems + pps::kTPB / 32 - 1) / (pps::kTPB / 32);
     if (grid > cap) grid = cap;
-    pps::search_kernel<J, V><<<(unsigned)grid, pps::kTPB, 0, st>>>(a);
+    pps::search_kernel<J, V, true><<<(unsigned)grid, pps::kTPB, 0, st>>>(a);
     pps::finalize_kernel<J, V><<<(a.n_states + 127) / 128, 128, 0, st>>>(a);
     return cudaGetLastError();
 }

@@ -462,7 +462,10 @@ __device__ __forceinline__ unsigned long long warp_max_u64(
 // because none of its points needed a shot angle) starts its next item at
 // once.  The state record is read through the read-only cache (all lanes
 // read the same address, one transaction per warp).
-template <int JMAX, int VMAX>
+//
+// EXT instances also honour a.skip (states to leave untouched) and write
+// a.dbg_point; the plain instances carry neither check in their loop.
+template <int JMAX, int VMAX, bool EXT = false>
 __global__ void __launch_bounds__(kTPB, PPS_MIN_BLOCKS)
     search_kernel(const SearchArgs a) {
     const int lane = threadIdx.x & 31;
@@ -473,7 +476,7 @@ __global__ void __launch_bounds__(kTPB, PPS_MIN_BLOCKS)
     for (long long item = gw; item < n_items; item += warps) {
         const int s = (int)(item / a.words);
         const int chunk = (int)(item - (long long)s * a.words);
-        if (a.skip && a.skip[s]) continue;
+        if (EXT && a.skip && a.skip[s]) continue;
         const pps_state& st = a.states[s];
         const StateK sk = derive_state(st, a.prm, JMAX, a.kmax);
         OppRegs<JMAX> o;
@@ -522,7 +525,7 @@ __global__ void __launch_bounds__(kTPB, PPS_MIN_BLOCKS)
                 }
             }
         }
-        if (a.dbg_point && active) {
+        if (EXT && a.dbg_point && active) {
             float bs = -CUDART_INF_F;
 #pragma unroll
             for (int v = 0; v < VMAX; ++v)
