@@ -530,6 +530,8 @@ pps_status pps_net_labels(pps_net* net, const float* point_best, int n,
 /* pps_propose flags. */
 #define PPS_PROPOSE_FALLBACK 1u /* states whose top-k cells hold no feasible
                                    pass are searched on the full grid */
+#define PPS_PROPOSE_NO_PRUNE 2u /* evaluate every point of the top-k cells
+                                   (n_feasible then counts them all) */
 
 /* The proposal path: rasterise, predict, take each state's topk best map
  * pixels, and run the exact search only on their cells' fine grid points
@@ -538,9 +540,14 @@ pps_status pps_net_labels(pps_net* net, const float* point_best, int n,
  * NULL) are device memory; 1 <= topk <= 2806; n <= both the context's
  * max_states and the network's max_batch.  The network's input features
  * use its own speeds and parameters (pps_net_set_features); the exact
- * refinement uses speeds and params of this call.  out_best.n_feasible
- * counts the feasible candidates among the refined points (the whole
- * grid's for a state that fell back).  The prediction runs on the
+ * refinement uses speeds and params of this call.  Refinement items run
+ * every state's best-ranked cells first; unless PPS_PROPOSE_NO_PRUNE is set,
+ * and when w_angle >= 0 and w_margin >= 0, a half cell whose score bound (its points' whole-mouth
+ * angle and capped margin) is below the state's best so far is skipped --
+ * it cannot hold the best, so the result is the exact best over the top-k
+ * cells either way.  out_best.n_feasible counts the feasible candidates
+ * among the points evaluated (it depends on what was skipped; the whole
+ * grid's count for a state that fell back).  The prediction runs on the
  * network's stream and the refinement on the context's (ordered by an
  * event); the call returns without waiting.  One network serves one
  * pps_propose at a time (it holds the call's scratch). */

@@ -27,9 +27,15 @@ void pps_ctx_scratch(pps_ctx* ctx, unsigned long long** keys, int** counts);
 int pps_ctx_max_states(const pps_ctx* ctx);
 int pps_ctx_jmax(const pps_ctx* ctx);
 
-// Network internals for the proposal path (pps_net.cu).
+// Network internals for the proposal path (pps_net.cu): the fallback's
+// per-state skip flags, the list of states to re-search and its length.
+struct pps_net_scratch {
+    int* skip;
+    int* list;
+    int* list_n;
+};
 cudaError_t pps_net_predict(pps_net* net, const pps_state* states, int n,
                             cudaStream_t* st, float** scores, int** cells,
-                            int** skip);
+                            pps_net_scratch* scratch);
 cudaError_t pps_net_topk(pps_net* net, int n, int k, int* cells);
 int pps_net_max_batch(const pps_net* net);

@@ -30,6 +30,8 @@ struct pps_net {
     float* loss = nullptr;
     int* cells = nullptr;  // proposal scratch: max_batch x NPIX
     int* skip = nullptr;   // proposal scratch: max_batch
+    int* list = nullptr;   // proposal scratch: max_batch states to re-search
+    int* list_n = nullptr; // proposal scratch: their number
     float* smax = nullptr; // training scratch: max_batch best labels
     RasterCfg cfg{};       // speeds and parameters of the input features
     float top_band = 3.0e38f, low_w = 1.f, under_w = 1.f;  // the loss
@@ -169,11 +171,13 @@ static_assert(PPS_NET_PARAMS == 21121, "flat layout");
 // and the proposal scratch.
 cudaError_t pps_net_predict(pps_net* nt, const pps_state* states, int n,
                             cudaStream_t* st, float** scores, int** cells,
-                            int** skip) {
+                            pps_net_scratch* scratch) {
     *st = nt->stream;
     *scores = nt->out;
     *cells = nt->cells;
-    *skip = nt->skip;
+    scratch->skip = nt->skip;
+    scratch->list = nt->list;
+    scratch->list_n = nt->list_n;
     return forward(nt, states, n);
 }
 
@@ -221,6 +225,8 @@ extern "C" pps_status pps_net_create(int device, void* stream, int max_batch,
     al(&nt->cells, sizeof(int) * P);
     al(&nt->skip, sizeof(int) * (size_t)max_batch);
     al(&nt->smax, sizeof(float) * (size_t)max_batch);
+    al(&nt->list, sizeof(int) * (size_t)max_batch);
+    al(&nt->list_n, sizeof(int));
     if (e != cudaSuccess) {
         cudaGetLastError();
         pps_net_destroy(nt);
@@ -240,7 +246,7 @@ extern "C" void pps_net_destroy(pps_net* nt) {
                     (void*)nt->a2, (void*)nt->a3, (void*)nt->g1, (void*)nt->g2,
                     (void*)nt->g3, (void*)nt->g4, (void*)nt->out,
                     (void*)nt->loss, (void*)nt->cells, (void*)nt->skip,
-                    (void*)nt->smax})
+                    (void*)nt->smax, (void*)nt->list, (void*)nt->list_n})
         if (p) cudaFree(p);
     cudaGetLastError();
     delete nt;

@@ -64,6 +64,7 @@ struct RasterCfg {
     pps_params prm;
 };
 constexpr int kFeatK = 16;          // pass-line samples of the features
+static_assert((kFeatK & (kFeatK - 1)) == 0, "1 / kFeatK must be exact");
 constexpr float kScoreFloor = -1.2f;  // below every score of a 12 x 9 m field
 constexpr float kSubOff = 0.05f;      // sub-points: the cell's quadrant centres
 
@@ -96,17 +97,23 @@ __device__ __forceinline__ void cell_features(const pps_state& st,
         for (int v = 0; v < PPS_MAX_SPEEDS; ++v) mv[v] = CUDART_INF_F;
 #pragma unroll 1
         for (int k = 1; k <= kFeatK; ++k) {
-            const float fr = (float)k / (float)kFeatK;
-            float t = CUDART_INF_F;
+            const float fr = (float)k * (1.f / kFeatK);  // exact: kFeatK = 2^n
+            float t[J];
 #pragma unroll
             for (int j = 0; j < J; ++j)
-                t = fminf(t, sbip_num<GEN>(fr, cbx, cby, o.bx[j], o.by[j],
-                                           o.ux[j], o.uy[j], sk.reach));
-            const float aT = t * sk.at_scale;
+                t[j] = sbip_num<GEN>(fr, cbx, cby, o.bx[j], o.by[j], o.ux[j],
+                                     o.uy[j], sk.reach);
+#pragma unroll
+            for (int w = 1; w < J; w *= 2)
+#pragma unroll
+                for (int j = 0; j + w < J; j += 2 * w) t[j] = fminf(t[j], t[j + w]);
+            const float aT = t[0] * sk.at_scale;
+            const float nf = -fr * twoabD;
 #pragma unroll
             for (int v = 0; v < PPS_MAX_SPEEDS; ++v)
-                mv[v] = fminf(mv[v],
-                              aT + sqrtf(fmaxf(cfg.sp2[v] - fr * twoabD, 0.f)));
+                if (v < cfg.V)
+                    mv[v] = fminf(mv[v],
+                                  aT + sqrt_ball(fmaxf(cfg.sp2[v] + nf, 0.f)));
         }
         float m = -CUDART_INF_F;
 #pragma unroll
@@ -149,7 +156,8 @@ __device__ __forceinline__ void cell_features(const pps_state& st,
 //   4  shot angle of the cell    (f[2])
 //   5  |goal centre - c| / diag
 //   6  c_x / (L / 2),  7  c_y / (W / 2)
-__global__ void raster_kernel(const pps_state* __restrict__ states, int n,
+__global__ void __launch_bounds__(128, 4)
+    raster_kernel(const pps_state* __restrict__ states, int n,
                               const RasterCfg cfg,
                               __nv_bfloat16* __restrict__ out) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;

@@ -21,19 +21,24 @@ constexpr int kMapW = PPS_NET_W, kMapPix = PPS_NET_H * PPS_NET_W;
 constexpr int kFineNx = 481, kFineNy = 361;
 
 // Exact search (eval_point) on the cells' fine points: a work item is half
-// a cell (8 x 4 fine points centred on the map pixel's 8 x 8 block).
+// a cell (8 x 4 fine points centred on the map pixel's 8 x 8 block).  Items
+// run rank-major -- every state's best-ranked cell first -- so that when a
+// lower-ranked item starts, its state usually has a pass already; with
+// `prune` an item whose score bound (score_bound, max over its points)
+// falls below that pass's score is skipped: it cannot hold the best.
 template <int JMAX, int VMAX>
 __global__ void __launch_bounds__(pps::kTPB)
     refine_kernel(const pps::SearchArgs a, const int* __restrict__ cells,
-                  int topk) {
+                  int topk, bool prune) {
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (pps::kTPB / 32);
     const long long gw =
         (long long)blockIdx.x * (pps::kTPB / 32) + (threadIdx.x >> 5);
     const long long n_items = (long long)a.n_states * topk * 2;
+    const pps::ItemGrid gr{a.g, a.x0, a.y0, a.V};
     for (long long item = gw; item < n_items; item += warps) {
-        const int s = (int)(item / (2LL * topk));
-        const int r = (int)(item - (long long)s * 2 * topk);
+        const int r = (int)(item / a.n_states);     // rank x 2 + half
+        const int s = (int)(item - (long long)r * a.n_states);
         const int cell = cells[(long long)s * topk + (r >> 1)];
         const int cy = cell / kMapW, cx = cell - cy * kMapW;
         const int fx = 8 * cx - 4 + (lane & 7);
@@ -43,10 +48,23 @@ __global__ void __launch_bounds__(pps::kTPB)
         const int p = iy * a.nx + ix;
         const pps_state& st = a.states[s];
         const pps::StateK sk = pps::derive_state(st, a.prm, JMAX, a.kmax);
+        if (prune) {
+            // one read of the state's best so far, shared by the warp
+            const unsigned long long cur =
+                __shfl_sync(0xffffffffu, __ldcg(a.keys + s), 0);
+            if (cur) {
+                const float b = active ? pps::score_bound(a.prm, gr, sk, ix, iy)
+                                       : -CUDART_INF_F;
+                // order_bits is monotone: compare the bound's key with the
+                // score half of the best key
+                const uint32_t bk =
+                    __reduce_max_sync(0xffffffffu, pps::order_bits(b));
+                if (bk < (uint32_t)(cur >> 32)) continue;
+            }
+        }
         pps::OppRegs<JMAX> o;
         pps::load_opps<JMAX>(st, sk, o);
         pps::PointResult<JMAX, VMAX> res;
-        const pps::ItemGrid gr{a.g, a.x0, a.y0, a.V};
         pps::eval_point<JMAX, VMAX, false>(a.prm, gr, a.speed, a.speed2, st, sk,
                                            o, ix, iy, nullptr, res);
         int cnt = 0;
@@ -72,11 +90,17 @@ __global__ void __launch_bounds__(pps::kTPB)
     }
 }
 
-// skip[s] = 1 when the refined cells already gave state s a pass.
-__global__ void skip_kernel(const pps_best* __restrict__ best, int n,
-                            int* __restrict__ skip) {
+// After the refinement: skip[s] = 1 when the refined cells gave state s a
+// pass (or the state is invalid); the others are appended to list.
+__global__ void fallback_list_kernel(const pps_best* __restrict__ best, int n,
+                                     int* __restrict__ skip,
+                                     int* __restrict__ list,
+                                     int* __restrict__ list_n) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < n) skip[s] = best[s].idx != -1;
+    if (s >= n) return;
+    const bool done = best[s].idx != -1;
+    skip[s] = done;
+    if (!done) list[atomicAdd(list_n, 1)] = s;
 }
 
 template <int J, int V>
@@ -96,7 +120,8 @@ int occupancy() {
 
 template <int J, int V>
 cudaError_t run(const pps::SearchArgs& base, const int* cells, int topk,
-                bool fallback, int* skip, int num_sms, cudaStream_t st) {
+                bool fallback, bool prune, const pps_net_scratch& ns,
+                int num_sms, cudaStream_t st) {
     const long long cap = (long long)num_sms * occupancy<J, V>();
     pps::SearchArgs a = base;
     cudaError_t e = cudaMemsetAsync(a.keys, 0, sizeof(unsigned long long) * a.n_states, st);
@@ -105,29 +130,34 @@ cudaError_t run(const pps::SearchArgs& base, const int* cells, int topk,
     const long long items = (long long)a.n_states * topk * 2;
     long long grid = (items + pps::kTPB / 32 - 1) / (pps::kTPB / 32);
     if (grid > cap) grid = cap;
-    refine_kernel<J, V><<<(unsigned)grid, pps::kTPB, 0, st>>>(a, cells, topk);
+    refine_kernel<J, V><<<(unsigned)grid, pps::kTPB, 0, st>>>(a, cells, topk,
+                                                              prune);
     pps::finalize_kernel<J, V><<<(a.n_states + 127) / 128, 128, 0, st>>>(a);
     if (!fallback) return cudaGetLastError();
-    skip_kernel<<<(a.n_states + 127) / 128, 128, 0, st>>>(a.best, a.n_states, skip);
+    e = cudaMemsetAsync(ns.list_n, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    fallback_list_kernel<<<(a.n_states + 127) / 128, 128, 0, st>>>(
+        a.best, a.n_states, ns.skip, ns.list, ns.list_n);
     e = cudaMemsetAsync(a.keys, 0, sizeof(unsigned long long) * a.n_states, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.counts, 0, sizeof(int) * a.n_states, st);
     if (e != cudaSuccess) return e;
-    a.skip = skip;
-    const long long fitems = (long long)a.n_states * a.words;
-    grid = (fitems + pps::kTPB / 32 - 1) / (pps::kTPB / 32);
-    if (grid > cap) grid = cap;
-    pps::search_kernel<J, V, true><<<(unsigned)grid, pps::kTPB, 0, st>>>(a);
+    a.skip = ns.skip;
+    a.list = ns.list;
+    a.list_n = ns.list_n;
+    // one CTA per SM at most: the list is usually empty or short
+    pps::search_kernel<J, V, true><<<(unsigned)num_sms, pps::kTPB, 0, st>>>(a);
     pps::finalize_kernel<J, V><<<(a.n_states + 127) / 128, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 
 template <int J>
 cudaError_t run_v(const pps::SearchArgs& a, const int* cells, int topk,
-                  bool fb, int* skip, int sms, cudaStream_t st) {
-    if (a.V <= 1) return run<J, 1>(a, cells, topk, fb, skip, sms, st);
-    if (a.V <= 2) return run<J, 2>(a, cells, topk, fb, skip, sms, st);
-    if (a.V <= 4) return run<J, 4>(a, cells, topk, fb, skip, sms, st);
-    return run<J, 8>(a, cells, topk, fb, skip, sms, st);
+                  bool fb, bool pr, const pps_net_scratch& ns, int sms,
+                  cudaStream_t st) {
+    if (a.V <= 1) return run<J, 1>(a, cells, topk, fb, pr, ns, sms, st);
+    if (a.V <= 2) return run<J, 2>(a, cells, topk, fb, pr, ns, sms, st);
+    if (a.V <= 4) return run<J, 4>(a, cells, topk, fb, pr, ns, sms, st);
+    return run<J, 8>(a, cells, topk, fb, pr, ns, sms, st);
 }
 
 bool finite_pos(float x) { return std::isfinite(x) && x > 0.f; }
@@ -154,7 +184,7 @@ extern "C" pps_status pps_propose(pps_ctx* ctx, pps_net* net,
                              "pps_propose: fine grid must be 12x9 m at 0.025 m");
     if (topk < 1 || topk > kMapPix)
         return pps_ctx_error(ctx, PPS_EINVAL, "pps_propose: topk outside 1..2806");
-    if (flags & ~PPS_PROPOSE_FALLBACK)
+    if (flags & ~(PPS_PROPOSE_FALLBACK | PPS_PROPOSE_NO_PRUNE))
         return pps_ctx_error(ctx, PPS_EINVAL, "pps_propose: unknown flags");
     if (!speeds || n_speeds < 1 || n_speeds > PPS_MAX_SPEEDS)
         return pps_ctx_error(ctx, PPS_EINVAL, "pps_propose: bad speeds");
@@ -176,8 +206,9 @@ extern "C" pps_status pps_propose(pps_ctx* ctx, pps_net* net,
     cudaError_t e = cudaSetDevice(pps_ctx_device(ctx));
     cudaStream_t nst = nullptr;
     float* scores = nullptr;
-    int *cells = nullptr, *skip = nullptr;
-    if (e == cudaSuccess) e = pps_net_predict(net, states, n, &nst, &scores, &cells, &skip);
+    int* cells = nullptr;
+    pps_net_scratch ns{};
+    if (e == cudaSuccess) e = pps_net_predict(net, states, n, &nst, &scores, &cells, &ns);
     if (out_cells) cells = out_cells;
     if (e == cudaSuccess) e = pps_net_topk(net, n, topk, cells);
     cudaStream_t st = pps_ctx_stream(ctx);
@@ -213,9 +244,12 @@ extern "C" pps_status pps_propose(pps_ctx* ctx, pps_net* net,
     a.best = out_best;
     pps_ctx_scratch(ctx, &a.keys, &a.counts);
     const bool fb = flags & PPS_PROPOSE_FALLBACK;
+    const bool prune = !(flags & PPS_PROPOSE_NO_PRUNE) && prm.w_angle >= 0.f &&
+                       prm.w_margin >= 0.f;
     const int sms = pps_ctx_num_sms(ctx);
-    e = pps_ctx_jmax(ctx) == 8 ? run_v<8>(a, cells, topk, fb, skip, sms, st)
-                               : run_v<16>(a, cells, topk, fb, skip, sms, st);
+    e = pps_ctx_jmax(ctx) == 8
+            ? run_v<8>(a, cells, topk, fb, prune, ns, sms, st)
+            : run_v<16>(a, cells, topk, fb, prune, ns, sms, st);
     if (e != cudaSuccess) return pps_ctx_cuda_error(ctx, e, "pps_propose: refine");
     return PPS_OK;
 }

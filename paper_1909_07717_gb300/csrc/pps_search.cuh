@@ -73,6 +73,8 @@ struct SearchArgs {
     int* counts;               // scratch: per-state feasible count
     float* dbg_point;          // may be null: per (s, p) best score
     const int* skip;           // may be null: states to leave untouched
+    const int* list;           // may be null: search only states list[i],
+    const int* list_n;         //   i < *list_n (EXT instances)
 };
 
 // ---------------------------------------------------------------- helpers
@@ -444,6 +446,34 @@ __device__ __forceinline__ void eval_point(const pps_params& prm,
                 : -CUDART_INF_F;
 }
 
+// An upper bound of every score eval_point can give the point (ix, iy):
+// the same arithmetic with the shot angle replaced by the whole mouth's
+// angle hi - lo (every open gap lies inside [lo, hi], and FP32 subtraction
+// is monotone) and the capped margin by the cap.  Valid when w_angle >= 0
+// and w_margin >= 0 (rounding is monotone, so no slack is needed); the
+// caller checks those.
+__device__ __forceinline__ float score_bound(const pps_params& prm,
+                                             const ItemGrid& gr,
+                                             const StateK& sk, int ix, int iy) {
+    const double cxd = fma((double)ix, (double)gr.g, (double)gr.x0);
+    const double cyd = fma((double)iy, (double)gr.g, (double)gr.y0);
+    const float cy = (float)cyd;
+    const bool front = cxd < (double)sk.Lh;
+    const float gx = (float)((double)sk.Lh - cxd);
+    float theta = 0.f;
+    if (front) {
+        const float lo = atan2f(__fsub_rn(-sk.hw, cy), gx);
+        const float hi = atan2f(__fsub_rn(sk.hw, cy), gx);
+        theta = fmaxf(__fsub_rn(hi, lo), 0.f);
+    }
+    const float dg = __fsqrt_rn(__fmaf_rn(gx, gx, __fmul_rn(cy, cy)));
+    const float base =
+        __fsub_rn(__fmul_rn(prm.w_angle,
+                            __fmul_rn(theta, 0.318309886183790672f)),
+                  __fmul_rn(prm.w_dist, __fmul_rn(dg, sk.inv_diag)));
+    return __fadd_rn(base, __fmul_rn(prm.w_margin, prm.margin_cap));
+}
+
 __device__ __forceinline__ unsigned long long warp_max_u64(
     unsigned long long x) {
 #pragma unroll
@@ -463,19 +493,23 @@ __device__ __forceinline__ unsigned long long warp_max_u64(
 // once.  The state record is read through the read-only cache (all lanes
 // read the same address, one transaction per warp).
 //
-// EXT instances also honour a.skip (states to leave untouched) and write
-// a.dbg_point; the plain instances carry neither check in their loop.
+// EXT instances also honour a.list (search only the listed states), a.skip
+// (states to leave untouched) and write a.dbg_point; the plain instances
+// carry none of these checks in their loop.
 template <int JMAX, int VMAX, bool EXT = false>
 __global__ void __launch_bounds__(kTPB, PPS_MIN_BLOCKS)
     search_kernel(const SearchArgs a) {
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (kTPB / 32);
     const long long gw = (long long)blockIdx.x * (kTPB / 32) + (threadIdx.x >> 5);
-    const long long n_items = (long long)a.n_states * a.words;
+    const bool listed = EXT && a.list;
+    const long long n_items =
+        (long long)(listed ? *a.list_n : a.n_states) * a.words;
 
     for (long long item = gw; item < n_items; item += warps) {
-        const int s = (int)(item / a.words);
-        const int chunk = (int)(item - (long long)s * a.words);
+        const int i = (int)(item / a.words);
+        const int chunk = (int)(item - (long long)i * a.words);
+        const int s = listed ? a.list[i] : i;
         if (EXT && a.skip && a.skip[s]) continue;
         const pps_state& st = a.states[s];
         const StateK sk = derive_state(st, a.prm, JMAX, a.kmax);

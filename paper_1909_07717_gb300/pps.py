@@ -30,6 +30,7 @@ PPS_MAX_K = 4096
 PPS_NOALLOC_MAX_STATES = 16384
 PPS_NET_H, PPS_NET_W, PPS_NET_PARAMS = 46, 61, 21121
 PPS_PROPOSE_FALLBACK = 1
+PPS_PROPOSE_NO_PRUNE = 2
 
 PPS_OK, PPS_EINVAL, PPS_ENOMEM, PPS_ECUDA, PPS_ETIMEOUT, PPS_ENOTIMPL = range(6)
 PPS_DEVICE_PTRS = 1

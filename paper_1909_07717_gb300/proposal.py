@@ -44,14 +44,16 @@ class Proposal:
                 t.empty((n, topk), dtype=t.int32, device=self.searcher.device))
 
     def run(self, states_dev, n, speeds=SPEEDS, params=None, topk=TOPK,
-            fallback=True, out=None):
+            fallback=True, out=None, prune=True):
         """Enqueue the proposal search; returns (best bytes, cells)."""
         best, cells = out if out is not None else self.alloc(n, topk)
         prm = params if isinstance(params, pps.pps_params) else \
             pps.params_from_dict(params)
         pps.pps_propose(self.searcher.ctx, self.net.net,
                         states_dev.data_ptr(), n, self.grid, speeds, prm,
-                        topk, pps.PPS_PROPOSE_FALLBACK if fallback else 0,
+                        topk,
+                        (pps.PPS_PROPOSE_FALLBACK if fallback else 0)
+                        | (0 if prune else pps.PPS_PROPOSE_NO_PRUNE),
                         best.data_ptr(), cells.data_ptr())
         return best, cells
 

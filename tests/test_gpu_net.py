@@ -207,12 +207,23 @@ def test_topk_order(torch):
         assert np.array_equal(cells[s], order)
 
 
+BEST_FIELDS = ("idx", "ix", "iy", "speed_idx", "score", "margin", "status")
+
+
+def _same_best(a, b):
+    """Equal best records; n_feasible counts only the points a pruned
+    refinement evaluated, so it is compared separately."""
+    return all(a[f].tobytes() == b[f].tobytes() for f in BEST_FIELDS)
+
+
 def test_all_cells_equal_the_full_search(torch):
-    """Refining every cell visits every fine point exactly once."""
+    """Refining every cell covers every fine point exactly once (cells that
+    cannot beat the best so far are skipped, which never changes it)."""
     batch = synth.ssl_states(506, 4, K=32)
     best, _, _ = _propose(torch, batch, pps.init_weights(13), 2806)
     ref = _search(torch, batch, pps.fine_grid_12x9(), SPEEDS)
-    assert best.tobytes() == ref.tobytes()
+    assert _same_best(best, ref)
+    assert np.all(best["n_feasible"] <= ref["n_feasible"])
 
 
 def _cancel_weights():
@@ -242,20 +253,32 @@ def test_fallback_recovers_the_full_search(torch):
     missed = no_fb["idx"] == -1
     assert missed.any()
     assert fb[missed].tobytes() == ref[missed].tobytes()
-    assert fb[~missed].tobytes() == no_fb[~missed].tobytes()
+    assert _same_best(fb[~missed], no_fb[~missed])
 
 
-def _proposal_vs_exact(batch, weights, fallback=True):
+def _proposal_vs_exact(batch, weights, fallback=True, prune=True):
     from paper_1909_07717_gb300.proposal import Proposal
     S = batch["ball"].shape[0]
     pr = Proposal(S, weights)
     try:
         st = pr.searcher.states_to_device(batch)
         ex = pps.unpack_best(pr.exact(st, S).cpu().numpy())
-        best, _ = pr.run(st, S, fallback=fallback)
+        best, _ = pr.run(st, S, fallback=fallback, prune=prune)
         return pps.unpack_best(best.cpu().numpy()), ex
     finally:
         pr.close()
+
+
+def test_pruning_keeps_the_best(torch):
+    """Skipping half cells whose score bound is below the best so far never
+    changes the best over the top-256 cells; it only evaluates fewer points."""
+    batch = synth.ssl_states(9, 1024, K=64)
+    w = pps.load_net_weights()
+    pruned, _ = _proposal_vs_exact(batch, w, prune=True)
+    full, _ = _proposal_vs_exact(batch, w, prune=False)
+    assert _same_best(pruned, full)
+    assert np.all(pruned["n_feasible"] <= full["n_feasible"])
+    assert pruned["n_feasible"].sum() < full["n_feasible"].sum()
 
 
 def test_trained_network_gain(torch):
