@@ -507,6 +507,12 @@ pps_status pps_net_raster(pps_net* net, const pps_state* states, int n,
 pps_status pps_net_forward(pps_net* net, const pps_state* states, int n,
                            float* out);
 
+/* The same prediction computed layer by layer, as training does (every
+ * activation written to device memory for the backward pass); equal to
+ * pps_net_forward bit for bit, which keeps them in shared memory. */
+pps_status pps_net_forward_layers(pps_net* net, const pps_state* states,
+                                  int n, float* out);
+
 /* The loss (pps_net_set_loss) of the prediction against labels[n][46][61]
  * (device) and its gradient with respect to the weights (grads:
  * PPS_NET_PARAMS floats, host, or NULL).  Waits for the result. */
@@ -541,11 +547,13 @@ pps_status pps_net_labels(pps_net* net, const float* point_best, int n,
  * max_states and the network's max_batch.  The network's input features
  * use its own speeds and parameters (pps_net_set_features); the exact
  * refinement uses speeds and params of this call.  Refinement items run
- * every state's best-ranked cells first; unless PPS_PROPOSE_NO_PRUNE is set,
- * and when w_angle >= 0 and w_margin >= 0, a half cell whose score bound (its points' whole-mouth
- * angle and capped margin) is below the state's best so far is skipped --
- * it cannot hold the best, so the result is the exact best over the top-k
- * cells either way.  out_best.n_feasible counts the feasible candidates
+ * every state's best-ranked cells first.  Unless PPS_PROPOSE_NO_PRUNE is
+ * set, and when w_angle >= 0 and w_margin >= 0, a half cell is skipped
+ * when its score bound is below the state's best so far: the bound takes
+ * the whole goal mouth's angle for the shot angle and the last pass-line
+ * sample's term alone for each speed's margin.  Such a cell cannot hold
+ * the best, so the result is the exact best over the top-k cells either
+ * way.  out_best.n_feasible counts the feasible candidates
  * among the points evaluated (it depends on what was skipped; the whole
  * grid's count for a state that fell back).  The prediction runs on the
  * network's stream and the refinement on the context's (ordered by an

@@ -19,6 +19,7 @@ char* pps_thread_error_buffer();
 
 struct pps_net {
     int device = 0;
+    int num_sms = 1;
     cudaStream_t stream = nullptr;
     int max_batch = 0;
     int step = 0;
@@ -80,11 +81,27 @@ cudaError_t cast_weights(pps_net* nt) {
     return cudaGetLastError();
 }
 
-cudaError_t forward(pps_net* nt, const pps_state* states, int n) {
+// Forward pass of n states into nt->out.  keep: layer by layer, keeping
+// every activation for the backward pass (training); otherwise the fused
+// kernel, which keeps them in shared memory (same output bit for bit).
+cudaError_t forward(pps_net* nt, const pps_state* states, int n, bool keep) {
     const long long P = (long long)n * NPIX;
     const unsigned g = blocks(P, 64);
     cudaStream_t st = nt->stream;
     raster_kernel<<<blocks(P, 128), 128, 0, st>>>(states, n, nt->cfg, nt->a0);
+    if (!keep) {
+        cudaError_t e = cudaFuncSetAttribute(
+            fused_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            (int)fused::kSmemBytes);
+        if (e != cudaSuccess) return e;
+        const long long units = (long long)n * fused::kBands;
+        const unsigned grid =
+            (unsigned)(units < nt->num_sms ? units : nt->num_sms);
+        fused_forward_kernel<<<grid, fused::kThreads, fused::kSmemBytes, st>>>(
+            nt->a0, n, nt->Wf, nt->w, nt->out, wf_off(1), wf_off(2), wf_off(3),
+            bias_off(0), bias_off(1), bias_off(2), bias_off(3));
+        return cudaGetLastError();
+    }
     conv_kernel<C0, CH, kHidden><<<g, 128, 0, st>>>(
         nt->a0, nt->Wf + wf_off(0), nt->w + bias_off(0), P, nt->a1, nullptr);
     conv_kernel<CH, CH, kHidden><<<g, 128, 0, st>>>(
@@ -178,7 +195,7 @@ cudaError_t pps_net_predict(pps_net* nt, const pps_state* states, int n,
     scratch->skip = nt->skip;
     scratch->list = nt->list;
     scratch->list_n = nt->list_n;
-    return forward(nt, states, n);
+    return forward(nt, states, n, false);
 }
 
 int pps_net_max_batch(const pps_net* nt) { return nt->max_batch; }
@@ -202,6 +219,9 @@ extern "C" pps_status pps_net_create(int device, void* stream, int max_batch,
     set_cfg(nt->cfg, kDefaultSpeeds, 4, nullptr);
     const size_t P = (size_t)max_batch * NPIX;
     cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&nt->num_sms, cudaDevAttrMultiProcessorCount,
+                                   device);
     auto al = [&](auto** p, size_t bytes) {
         if (e == cudaSuccess) e = cudaMalloc((void**)p, bytes);
         if (e == cudaSuccess) e = cudaMemset(*p, 0, bytes);
@@ -346,17 +366,30 @@ extern "C" pps_status pps_net_raster(pps_net* nt, const pps_state* states,
     return e == cudaSuccess ? PPS_OK : fail(PPS_ECUDA, "pps_net_raster", e);
 }
 
-extern "C" pps_status pps_net_forward(pps_net* nt, const pps_state* states,
-                                      int n, float* out) {
+namespace {
+pps_status forward_to(pps_net* nt, const pps_state* states, int n, float* out,
+                      bool keep, const char* who) {
     pps_status s = check_batch(nt, states, n);
     if (s != PPS_OK) return s;
     if (!out) return PPS_EINVAL;
     cudaSetDevice(nt->device);
-    cudaError_t e = forward(nt, states, n);
+    cudaError_t e = forward(nt, states, n, keep);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out, nt->out, sizeof(float) * (size_t)n * NPIX,
                             cudaMemcpyDeviceToDevice, nt->stream);
-    return e == cudaSuccess ? PPS_OK : fail(PPS_ECUDA, "pps_net_forward", e);
+    return e == cudaSuccess ? PPS_OK : fail(PPS_ECUDA, who, e);
+}
+}  // namespace
+
+extern "C" pps_status pps_net_forward(pps_net* nt, const pps_state* states,
+                                      int n, float* out) {
+    return forward_to(nt, states, n, out, false, "pps_net_forward");
+}
+
+extern "C" pps_status pps_net_forward_layers(pps_net* nt,
+                                             const pps_state* states, int n,
+                                             float* out) {
+    return forward_to(nt, states, n, out, true, "pps_net_forward_layers");
 }
 
 extern "C" pps_status pps_net_grad(pps_net* nt, const pps_state* states,
@@ -368,7 +401,7 @@ extern "C" pps_status pps_net_grad(pps_net* nt, const pps_state* states,
     cudaSetDevice(nt->device);
     cudaError_t e = cudaMemsetAsync(nt->grad, 0, sizeof(float) * kPadParams,
                                     nt->stream);
-    if (e == cudaSuccess) e = forward(nt, states, n);
+    if (e == cudaSuccess) e = forward(nt, states, n, true);
     if (e == cudaSuccess) e = backward(nt, labels, n);
     std::vector<float> pad(kPadParams);
     float l = 0.f;
@@ -395,7 +428,7 @@ extern "C" pps_status pps_net_train_step(pps_net* nt, const pps_state* states,
     if (!labels || !(lr > 0.f) || !std::isfinite(lr))
         return fail(PPS_EINVAL, "pps_net_train_step: labels and lr > 0");
     cudaSetDevice(nt->device);
-    cudaError_t e = forward(nt, states, n);
+    cudaError_t e = forward(nt, states, n, true);
     if (e == cudaSuccess) e = backward(nt, labels, n);
     ++nt->step;
     const float b1 = 0.9f, b2 = 0.999f;

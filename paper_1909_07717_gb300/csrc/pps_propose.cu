@@ -24,8 +24,9 @@ constexpr int kFineNx = 481, kFineNy = 361;
 // a cell (8 x 4 fine points centred on the map pixel's 8 x 8 block).  Items
 // run rank-major -- every state's best-ranked cell first -- so that when a
 // lower-ranked item starts, its state usually has a pass already; with
-// `prune` an item whose score bound (score_bound, max over its points)
-// falls below that pass's score is skipped: it cannot hold the best.
+// `prune` an item whose score bound (score_bound: the whole mouth's angle
+// and the last pass-line sample's margin, max over its points) falls below
+// that pass's score is skipped: it cannot hold the best.
 template <int JMAX, int VMAX>
 __global__ void __launch_bounds__(pps::kTPB)
     refine_kernel(const pps::SearchArgs a, const int* __restrict__ cells,
@@ -48,13 +49,17 @@ __global__ void __launch_bounds__(pps::kTPB)
         const int p = iy * a.nx + ix;
         const pps_state& st = a.states[s];
         const pps::StateK sk = pps::derive_state(st, a.prm, JMAX, a.kmax);
+        pps::OppRegs<JMAX> o;
+        pps::load_opps<JMAX>(st, sk, o);
         if (prune) {
             // one read of the state's best so far, shared by the warp
             const unsigned long long cur =
                 __shfl_sync(0xffffffffu, __ldcg(a.keys + s), 0);
             if (cur) {
-                const float b = active ? pps::score_bound(a.prm, gr, sk, ix, iy)
-                                       : -CUDART_INF_F;
+                const float b =
+                    active ? pps::score_bound<JMAX, VMAX>(a.prm, gr, a.speed,
+                                                          a.speed2, sk, o, ix, iy)
+                           : -CUDART_INF_F;
                 // order_bits is monotone: compare the bound's key with the
                 // score half of the best key
                 const uint32_t bk =
@@ -62,8 +67,6 @@ __global__ void __launch_bounds__(pps::kTPB)
                 if (bk < (uint32_t)(cur >> 32)) continue;
             }
         }
-        pps::OppRegs<JMAX> o;
-        pps::load_opps<JMAX>(st, sk, o);
         pps::PointResult<JMAX, VMAX> res;
         pps::eval_point<JMAX, VMAX, false>(a.prm, gr, a.speed, a.speed2, st, sk,
                                            o, ix, iy, nullptr, res);

@@ -446,18 +446,60 @@ __device__ __forceinline__ void eval_point(const pps_params& prm,
                 : -CUDART_INF_F;
 }
 
-// An upper bound of every score eval_point can give the point (ix, iy):
-// the same arithmetic with the shot angle replaced by the whole mouth's
-// angle hi - lo (every open gap lies inside [lo, hi], and FP32 subtraction
-// is monotone) and the capped margin by the cap.  Valid when w_angle >= 0
-// and w_margin >= 0 (rounding is monotone, so no slack is needed); the
-// caller checks those.
+// An upper bound of every score eval_point can give the point (ix, iy),
+// from the same arithmetic with (a) the shot angle replaced by the whole
+// mouth's angle hi - lo (every open gap lies inside [lo, hi]) and (b) each
+// speed's margin replaced by its last sample's term alone (the margin is
+// the minimum over the samples; the last one is computed exactly as the
+// sample loop's last iteration).  FP32 rounding is monotone, so the bound
+// needs no slack; it holds when w_angle >= 0 and w_margin >= 0, which the
+// caller checks.
+template <int JMAX, int VMAX>
 __device__ __forceinline__ float score_bound(const pps_params& prm,
                                              const ItemGrid& gr,
-                                             const StateK& sk, int ix, int iy) {
+                                             const float (&sp)[PPS_MAX_SPEEDS],
+                                             const float (&sp2)[PPS_MAX_SPEEDS],
+                                             const StateK& sk,
+                                             const OppRegs<JMAX>& o, int ix,
+                                             int iy) {
     const double cxd = fma((double)ix, (double)gr.g, (double)gr.x0);
     const double cyd = fma((double)iy, (double)gr.g, (double)gr.y0);
+    const double dxd = cxd - (double)sk.bx, dyd = cyd - (double)sk.by;
     const float cy = (float)cyd;
+    const float cbx = (float)((double)sk.kappa * dxd);
+    const float cby = (float)((double)sk.kappa * dyd);
+    const float dxm = (float)dxd, dym = (float)dyd;
+    const float D = __fsqrt_rn(__fmaf_rn(dxm, dxm, __fmul_rn(dym, dym)));
+    const float twoabD = __fmul_rn(sk.two_ab, D);
+    // the sample loop's last sample: kf = K, f = K * (1 / K)
+    const float f = __fmul_rn((float)sk.K, sk.invK);
+    float t[JMAX];
+#pragma unroll
+    for (int j = 0; j < JMAX; ++j)
+        t[j] = sk.general
+                   ? sbip_num<true>(f, cbx, cby, o.bx[j], o.by[j], o.ux[j],
+                                    o.uy[j], sk.reach)
+                   : sbip_num<false>(f, cbx, cby, o.bx[j], o.by[j], o.ux[j],
+                                     o.uy[j], sk.reach);
+    float n = t[0];
+#pragma unroll
+    for (int j = 1; j < JMAX; ++j) n = fminf(n, t[j]);
+    const float aT = __fmul_rn(n, sk.at_scale);
+    const float nf = -f;
+    float mb = -CUDART_INF_F;
+#pragma unroll
+    for (int v = 0; v < VMAX; ++v) {
+        if (v >= gr.V) continue;
+        if (!(__fmaf_rn(-sk.fK, twoabD, sp2[v]) >= 0.f)) continue;
+        const float m =
+            sk.nopp == 0
+                ? CUDART_INF_F
+                : __fdiv_rn(__fsub_rn(__fadd_rn(aT, sqrt_ball(__fmaf_rn(
+                                                     nf, twoabD, sp2[v]))),
+                                      sp[v]),
+                            sk.ab);
+        mb = fmaxf(mb, m);
+    }
     const bool front = cxd < (double)sk.Lh;
     const float gx = (float)((double)sk.Lh - cxd);
     float theta = 0.f;
@@ -471,7 +513,8 @@ __device__ __forceinline__ float score_bound(const pps_params& prm,
         __fsub_rn(__fmul_rn(prm.w_angle,
                             __fmul_rn(theta, 0.318309886183790672f)),
                   __fmul_rn(prm.w_dist, __fmul_rn(dg, sk.inv_diag)));
-    return __fadd_rn(base, __fmul_rn(prm.w_margin, prm.margin_cap));
+    return __fadd_rn(base,
+                     __fmul_rn(prm.w_margin, fminf(mb, prm.margin_cap)));
 }
 
 __device__ __forceinline__ unsigned long long warp_max_u64(

@@ -147,7 +147,7 @@ EXPORTS = ("pps_abi_version", "pps_status_string", "pps_last_error",
            "pps_server_submit", "pps_server_wait", "pps_server_replay",
            "pps_server_get_stats", "pps_net_create", "pps_net_destroy",
            "pps_net_set_features", "pps_net_set_loss", "pps_net_set_weights",
-           "pps_net_get_weights", "pps_net_raster",
+           "pps_net_get_weights", "pps_net_raster", "pps_net_forward_layers",
            "pps_net_forward", "pps_net_grad", "pps_net_train_step",
            "pps_net_labels", "pps_propose")
 
@@ -238,6 +238,8 @@ def lib():
                                          c_void_p]
             L.pps_net_forward.argtypes = [c_void_p, c_void_p, ctypes.c_int,
                                           c_void_p]
+            L.pps_net_forward_layers.argtypes = [c_void_p, c_void_p,
+                                                 ctypes.c_int, c_void_p]
             L.pps_net_grad.argtypes = [c_void_p, c_void_p, c_void_p,
                                        ctypes.c_int, c_void_p,
                                        P(ctypes.c_float)]
@@ -448,6 +450,10 @@ def pps_net_raster(net, states, n, out) -> int:
 
 def pps_net_forward(net, states, n, out) -> int:
     return _check(lib().pps_net_forward(net, states, n, out))
+
+
+def pps_net_forward_layers(net, states, n, out) -> int:
+    return _check(lib().pps_net_forward_layers(net, states, n, out))
 
 
 def pps_net_grad(net, states, labels, n):

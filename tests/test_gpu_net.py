@@ -88,8 +88,14 @@ def test_forward_matches_reference(torch):
     try:
         dev, x = _gpu_raster(torch, net, batch)
         y = net.forward(dev, 2).cpu().numpy().astype(np.float64)
+        lay = torch.empty((2, 46, 61), dtype=torch.float32, device="cuda")
+        pps.pps_net_forward_layers(net.net, dev.data_ptr(), 2, lay.data_ptr())
+        lay = lay.cpu().numpy().astype(np.float64)
     finally:
         net.close()
+    # the fused pass (activations in shared memory) and the layer-by-layer
+    # one of training compute the same products in the same order
+    assert np.array_equal(y, lay)
     _, ref = net_ref.forward(x, _layers_as_gpu(w))
     scale = np.mean(np.abs(ref)) + 1e-3
     err = np.abs(y - ref)
@@ -196,6 +202,23 @@ def _propose(torch, batch, weights, topk, flags=0):
     finally:
         net.close()
         s.close()
+
+
+def test_fused_forward_equals_layers_on_a_batch(torch):
+    """Bands of rows, map edges and many states: every unit of the fused
+    kernel's schedule against the layer-by-layer pass."""
+    batch = synth.ssl_states(510, 300, K=64)
+    net = pps.Net(max_batch=300, weights=pps.init_weights(21))
+    try:
+        dev = torch.from_numpy(pps.pack_states(batch).view(np.uint8)
+                               .copy()).cuda()
+        y = net.forward(dev, 300)
+        lay = torch.empty_like(y)
+        pps.pps_net_forward_layers(net.net, dev.data_ptr(), 300,
+                                   lay.data_ptr())
+        assert torch.equal(y, lay)
+    finally:
+        net.close()
 
 
 def test_topk_order(torch):
