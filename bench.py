@@ -65,12 +65,14 @@ def _peaks():
 
 
 def _kernel_src_digest():
+    """Digest of the sources the timed search kernel is built from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1909_07717_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + f.read())
+    for path in (os.path.join(csrc, "pps_search.cuh"),
+                 os.path.join(csrc, "pps_lib.cu"),
+                 os.path.join(ROOT, "include", "pps.h")):
+        with open(path, "rb") as f:
+            h.update(os.path.basename(path).encode() + f.read())
     return h.hexdigest()[:16]
 
 
@@ -395,8 +397,8 @@ def _uneven(args, dev, stream):
     step (L2 flushed between runs, CUDA events on the plan's stream)."""
     import torch
     from paper_1909_07717_gb300 import pps, synth
-    batch = synth.uneven_batch(synth.UNEVEN_SEED, synth.UNEVEN_STATES)
-    S = synth.UNEVEN_STATES
+    S = args.states or synth.UNEVEN_STATES
+    batch = synth.uneven_batch(synth.UNEVEN_SEED, S)
     jobs = pps.jobs_from_batch(batch)
     searcher = pps.Searcher(max_states=S, max_opp=16, device=dev.index,
                             stream=stream)
