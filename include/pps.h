@@ -494,6 +494,11 @@ pps_status pps_net_set_features(pps_net* net, const float* speeds,
 pps_status pps_net_set_loss(pps_net* net, float top_band, float low_weight,
                             float under_weight);
 
+/* Waits for the network's stream.  PPS_ETIMEOUT when a bounded wait of the
+ * tensor-core inference kernel ran out since the last call (the outputs of
+ * that pass are invalid; the flag is cleared). */
+pps_status pps_net_sync(pps_net* net);
+
 /* Weights as PPS_NET_PARAMS floats (host).  Setting them resets Adam. */
 pps_status pps_net_set_weights(pps_net* net, const float* w);
 pps_status pps_net_get_weights(pps_net* net, float* w);
@@ -503,13 +508,16 @@ pps_status pps_net_raster(pps_net* net, const pps_state* states, int n,
                           uint16_t* out);
 
 /* Predicted cell scores, out[n][46][61] float (device).  States (device)
- * must be 12 x 9 m; n <= max_batch. */
+ * must be 12 x 9 m; n <= max_batch.  The four convolutions run in one
+ * tcgen05 kernel (activations stay on the SM); enqueued on the network's
+ * stream. */
 pps_status pps_net_forward(pps_net* net, const pps_state* states, int n,
                            float* out);
 
-/* The same prediction computed layer by layer, as training does (every
- * activation written to device memory for the backward pass); equal to
- * pps_net_forward bit for bit, which keeps them in shared memory. */
+/* The same prediction computed layer by layer on mma.sync, as training does
+ * (every activation written to device memory for the backward pass).  It
+ * differs from pps_net_forward only by FP32 summation order (and the
+ * bfloat16 roundings that order can flip). */
 pps_status pps_net_forward_layers(pps_net* net, const pps_state* states,
                                   int n, float* out);
 

@@ -13,6 +13,7 @@
 #include "pps.h"
 #include "pps_internal.h"
 #include "pps_net.cuh"
+#include "pps_net_tc.cuh"
 
 using namespace pps::net;
 char* pps_thread_error_buffer();
@@ -34,6 +35,7 @@ struct pps_net {
     int* list = nullptr;   // proposal scratch: max_batch states to re-search
     int* list_n = nullptr; // proposal scratch: their number
     float* smax = nullptr; // training scratch: max_batch best labels
+    int* err = nullptr;    // set by a kernel whose bounded wait ran out
     RasterCfg cfg{};       // speeds and parameters of the input features
     float top_band = 3.0e38f, low_w = 1.f, under_w = 1.f;  // the loss
 };
@@ -81,9 +83,9 @@ cudaError_t cast_weights(pps_net* nt) {
     return cudaGetLastError();
 }
 
-// Forward pass of n states into nt->out.  keep: layer by layer, keeping
-// every activation for the backward pass (training); otherwise the fused
-// kernel, which keeps them in shared memory (same output bit for bit).
+// Forward pass of n states into nt->out.  keep: layer by layer on mma.sync,
+// keeping every activation for the backward pass (training); otherwise the
+// tcgen05 kernel, which keeps them on the SM.
 cudaError_t forward(pps_net* nt, const pps_state* states, int n, bool keep) {
     const long long P = (long long)n * NPIX;
     const unsigned g = blocks(P, 64);
@@ -91,15 +93,15 @@ cudaError_t forward(pps_net* nt, const pps_state* states, int n, bool keep) {
     raster_kernel<<<blocks(P, 128), 128, 0, st>>>(states, n, nt->cfg, nt->a0);
     if (!keep) {
         cudaError_t e = cudaFuncSetAttribute(
-            fused_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-            (int)fused::kSmemBytes);
+            tcf::tc_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            (int)tcf::kSmemBytes);
         if (e != cudaSuccess) return e;
-        const long long units = (long long)n * fused::kBands;
+        const long long units = (long long)n * tcf::kBands;
         const unsigned grid =
             (unsigned)(units < nt->num_sms ? units : nt->num_sms);
-        fused_forward_kernel<<<grid, fused::kThreads, fused::kSmemBytes, st>>>(
+        tcf::tc_forward_kernel<<<grid, tcf::kThreads, tcf::kSmemBytes, st>>>(
             nt->a0, n, nt->Wf, nt->w, nt->out, wf_off(1), wf_off(2), wf_off(3),
-            bias_off(0), bias_off(1), bias_off(2), bias_off(3));
+            bias_off(0), bias_off(1), bias_off(2), bias_off(3), nt->err);
         return cudaGetLastError();
     }
     conv_kernel<C0, CH, kHidden><<<g, 128, 0, st>>>(
@@ -247,6 +249,7 @@ extern "C" pps_status pps_net_create(int device, void* stream, int max_batch,
     al(&nt->smax, sizeof(float) * (size_t)max_batch);
     al(&nt->list, sizeof(int) * (size_t)max_batch);
     al(&nt->list_n, sizeof(int));
+    al(&nt->err, sizeof(int));
     if (e != cudaSuccess) {
         cudaGetLastError();
         pps_net_destroy(nt);
@@ -266,7 +269,8 @@ extern "C" void pps_net_destroy(pps_net* nt) {
                     (void*)nt->a2, (void*)nt->a3, (void*)nt->g1, (void*)nt->g2,
                     (void*)nt->g3, (void*)nt->g4, (void*)nt->out,
                     (void*)nt->loss, (void*)nt->cells, (void*)nt->skip,
-                    (void*)nt->smax, (void*)nt->list, (void*)nt->list_n})
+                    (void*)nt->smax, (void*)nt->list, (void*)nt->list_n,
+                    (void*)nt->err})
         if (p) cudaFree(p);
     cudaGetLastError();
     delete nt;
@@ -289,6 +293,23 @@ extern "C" pps_status pps_net_set_weights(pps_net* nt, const float* w) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(nt->stream);
     nt->step = 0;
     return e == cudaSuccess ? PPS_OK : fail(PPS_ECUDA, "pps_net_set_weights", e);
+}
+
+extern "C" pps_status pps_net_sync(pps_net* nt) {
+    if (!nt) return PPS_EINVAL;
+    cudaSetDevice(nt->device);
+    int flag = 0;
+    cudaError_t e = cudaMemcpyAsync(&flag, nt->err, sizeof(int),
+                                    cudaMemcpyDeviceToHost, nt->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nt->stream);
+    if (e != cudaSuccess) return fail(PPS_ECUDA, "pps_net_sync", e);
+    if (flag) {
+        cudaMemsetAsync(nt->err, 0, sizeof(int), nt->stream);
+        cudaStreamSynchronize(nt->stream);
+        return fail(PPS_ETIMEOUT,
+                    "pps_net_sync: a tensor-core wait ran out; outputs invalid");
+    }
+    return PPS_OK;
 }
 
 extern "C" pps_status pps_net_set_features(pps_net* nt, const float* speeds,

@@ -55,25 +55,6 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0,
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-// ldmatrix: four (two) 8x8 b16 matrices from shared memory; lane l gives
-// the address of row l & 7 of matrix l >> 3.
-__device__ __forceinline__ void ldsm_x4(const __nv_bfloat16* p, uint32_t& r0,
-                                        uint32_t& r1, uint32_t& r2,
-                                        uint32_t& r3) {
-    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(a));
-}
-
-__device__ __forceinline__ void ldsm_x2(const __nv_bfloat16* p, uint32_t& r0,
-                                        uint32_t& r1) {
-    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];"
-                 : "=r"(r0), "=r"(r1)
-                 : "r"(a));
-}
-
 // ------------------------------------------------------------ rasteriser
 // Kick speeds and value-function parameters the input features are
 // computed for (the network is trained for one such set).
@@ -320,214 +301,6 @@ __global__ void __launch_bounds__(128)
             }
         }
     }
-}
-
-// ------------------------------------------------------ fused inference
-// The whole forward pass of one band of output rows in shared memory: the
-// band's input rows (with a 4-row halo: four 3x3 layers) are read once,
-// the hidden activations never leave the SM, and only the output map is
-// written.  Persistent CTAs (one per SM: the buffers take ~221 KB) walk
-// the (state, band) units; while layers 2-4 of one unit run, the next
-// unit's input rows stream into the input buffer (cp.async).  The products
-// run in the same order as
-// conv_kernel's (tap, then 16-channel chunk, then 8-channel output tile),
-// so the output equals the layer-by-layer pass bit for bit.
-//
-// Buffers are [row][col][channel] with 66 columns per row: image column c
-// sits at buffer column c + 1; columns 0 and 62..65 stay zero (the zero
-// padding, and room for the last 16-pixel tile's reads).  Channel strides
-// are padded (16 -> 24, 32 -> 40 bf16) so that the eight pixel rows of an
-// mma fragment fall into distinct shared-memory banks.
-namespace fused {
-constexpr int kBand = 6;                 // output rows per unit
-constexpr int kBands = (H + kBand - 1) / kBand;
-constexpr int kCols = 66;
-constexpr int kS16 = 24, kS32 = 40;      // channel strides (bf16)
-constexpr int kInRows = kBand + 8, kARows = kBand + 6, kBRows = kBand + 4;
-constexpr int kCoOut = 8;                // output-layer channels computed
-constexpr int kInElems = kInRows * kCols * kS16;
-constexpr int kAElems = kARows * kCols * kS32;
-constexpr int kBElems = kBRows * kCols * kS32;
-constexpr int kW0 = 9 * CH * kS16;       // layer 1: 16 -> 32
-constexpr int kW1 = 9 * CH * kS32;       // layers 2, 3: 32 -> 32
-constexpr int kW3 = 9 * kCoOut * kS32;   // layer 4: 32 -> 8 (1 used)
-constexpr int kElems = kInElems + kAElems + kBElems + kW0 + 2 * kW1 + kW3;
-constexpr int kSkip = kBand * W;          // the band's coarse-score inputs
-constexpr size_t kSmemBytes =
-    sizeof(__nv_bfloat16) * (size_t)kElems + sizeof(float) * kSkip;
-constexpr int kThreads = 512;
-static_assert(kSmemBytes <= 232448, "fits one CTA per SM");
-static_assert((kS16 * 2) % 16 == 0 && (kS32 * 2) % 16 == 0, "16-byte rows");
-}  // namespace fused
-
-// Copy one layer's bf16 weights [tap][co][cin] (co < cout_copy of cout) to
-// shared memory rows of stride `stride`.
-__device__ __forceinline__ void stage_weights(__nv_bfloat16* dst,
-                                              const __nv_bfloat16* src,
-                                              int cout, int cout_copy, int cin,
-                                              int stride) {
-    const int chunks = cin / 8;  // 16-byte pieces per row
-    const int total = 9 * cout_copy * chunks;
-    for (int i = threadIdx.x; i < total; i += blockDim.x) {
-        const int c = i % chunks, row = i / chunks;
-        const int tap = row / cout_copy, co = row - tap * cout_copy;
-        reinterpret_cast<uint4*>(dst + (tap * cout_copy + co) * stride)[c] =
-            reinterpret_cast<const uint4*>(src + (tap * cout + co) * cin)[c];
-    }
-}
-
-// One layer over a band: out rows 0..out_rows-1 (image row y_first + i),
-// input rows shifted down by one (the previous layer has one more halo row
-// above).  Hidden layers store bf16 ReLU(acc + bias) (zero outside the
-// image); the output layer writes acc + bias + the coarse-score channel to
-// `out` (float, the state's map).
-template <int CIN, int COUT, int SIN, int SOUT, bool LAST>
-__device__ __forceinline__ void fused_layer(
-    const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ w,
-    const float* __restrict__ bias, int out_rows, int y_first,
-    __nv_bfloat16* __restrict__ outb, const float* __restrict__ skip,
-    float* __restrict__ outmap) {
-    constexpr int NT = COUT / 8, SW = CIN + 8;
-    // a unit: one row, 16 pixels, half of the 8-channel output tiles
-    constexpr int SPLIT = NT >= 2 ? 2 : 1, NTU = NT / SPLIT;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gid = lane >> 2, tig = lane & 3;
-    const int units = out_rows * 4 * SPLIT;
-    // ldmatrix row addresses of this lane: A rows are pixels (lanes 0-15:
-    // k 0-7, lanes 16-31: k 8-15); B rows are output channels (two 8-channel
-    // tiles per x4 load, k halves alternating)
-    const int a_k = 8 * (lane >> 4);
-    const int b_co = NTU >= 2 ? (lane & 7) + 8 * (lane >> 4) : (lane & 7);
-    const int b_k = 8 * ((lane >> 3) & 1);
-    for (int u = warp; u < units; u += fused::kThreads / 32) {
-        const int part = u % SPLIT, cb = (u / SPLIT) & 3, i = u / (4 * SPLIT);
-        const int t0 = part * NTU;
-        const int a_pix = cb * 16 + (lane & 7) + 8 * ((lane >> 3) & 1) + 1;
-        float acc[NTU][4];
-#pragma unroll
-        for (int t = 0; t < NTU; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
-#pragma unroll 1
-        for (int tap = 0; tap < 9; ++tap) {
-            const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-            const __nv_bfloat16* ap =
-                in + ((i + 1 + dy) * fused::kCols + a_pix + dx) * SIN + a_k;
-            const __nv_bfloat16* wp = w + (tap * COUT + t0 * 8 + b_co) * SW + b_k;
-#pragma unroll
-            for (int kc = 0; kc < CIN / 16; ++kc) {
-                uint32_t a0, a1, a2, a3;
-                ldsm_x4(ap + kc * 16, a0, a1, a2, a3);
-#pragma unroll
-                for (int t = 0; t < NTU; t += 2) {
-                    if (t + 1 < NTU) {
-                        uint32_t b0, b1, b2, b3;
-                        ldsm_x4(wp + t * 8 * SW + kc * 16, b0, b1, b2, b3);
-                        mma_bf16(acc[t], a0, a1, a2, a3, b0, b1);
-                        mma_bf16(acc[t + 1], a0, a1, a2, a3, b2, b3);
-                    } else {
-                        uint32_t b0, b1;
-                        ldsm_x2(wp + t * 8 * SW + kc * 16, b0, b1);
-                        mma_bf16(acc[t], a0, a1, a2, a3, b0, b1);
-                    }
-                }
-            }
-        }
-        const int Y = y_first + i;
-        const bool row_in = Y >= 0 && Y < H;
-#pragma unroll
-        for (int t = 0; t < NTU; ++t) {
-            const int c = (t0 + t) * 8 + tig * 2;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int x = cb * 16 + gid + 8 * h;
-                if (x >= W) continue;
-                if (LAST) {
-                    if (t0 + t == 0 && tig == 0 && row_in)
-                        outmap[Y * W + x] = acc[0][2 * h] + bias[0] + skip[i * W + x];
-                } else {
-                    const float v0 = row_in ? fmaxf(acc[t][2 * h] + bias[c], 0.f) : 0.f;
-                    const float v1 = row_in ? fmaxf(acc[t][2 * h + 1] + bias[c + 1], 0.f) : 0.f;
-                    *reinterpret_cast<uint32_t*>(outb + (i * fused::kCols + x + 1) * SOUT + c) =
-                        pack_bf16(v0, v1);
-                }
-            }
-        }
-    }
-}
-
-// Start the copy of unit u's input rows (y0 - 4 .. y0 + 9 of state s) into
-// the input buffer; rows outside the image are zero-filled.
-__device__ __forceinline__ void fused_prefetch(const __nv_bfloat16* __restrict__ a0,
-                                               long long u,
-                                               __nv_bfloat16* __restrict__ bin) {
-    const int s = (int)(u / fused::kBands);
-    const int y0 = (int)(u - (long long)s * fused::kBands) * fused::kBand;
-    const __nv_bfloat16* src = a0 + (long long)s * NPIX * C0;
-    for (int i = threadIdx.x; i < fused::kInRows * W * 2; i += blockDim.x) {
-        const int half = i & 1, q = i >> 1;
-        const int r = q / W, x = q - r * W;
-        const int Y = y0 - 4 + r;
-        const bool ok = Y >= 0 && Y < H;
-        const __nv_bfloat16* g = src + ((ok ? Y : 0) * W + x) * C0 + half * 8;
-        const uint32_t d = (uint32_t)__cvta_generic_to_shared(
-            bin + (r * fused::kCols + x + 1) * fused::kS16 + half * 8);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d),
-                     "l"(g), "r"(ok ? 16 : 0));
-    }
-    asm volatile("cp.async.commit_group;");
-}
-
-__global__ void __launch_bounds__(fused::kThreads, 1)
-    fused_forward_kernel(const __nv_bfloat16* __restrict__ a0, int n,
-                         const __nv_bfloat16* __restrict__ Wf,
-                         const float* __restrict__ w32, float* __restrict__ out,
-                         int wf1, int wf2, int wf3, int b0, int b1, int b2,
-                         int b3) {
-    extern __shared__ __align__(16) __nv_bfloat16 sm[];
-    __nv_bfloat16* bin = sm;
-    __nv_bfloat16* ba = bin + fused::kInElems;
-    __nv_bfloat16* bb = ba + fused::kAElems;
-    __nv_bfloat16* w0 = bb + fused::kBElems;
-    __nv_bfloat16* w1 = w0 + fused::kW0;
-    __nv_bfloat16* w2 = w1 + fused::kW1;
-    __nv_bfloat16* w3 = w2 + fused::kW1;
-    float* skip = reinterpret_cast<float*>(w3 + fused::kW3);
-    // zero everything once: the pad columns are never written again
-    for (int i = threadIdx.x; i < (fused::kInElems + fused::kAElems + fused::kBElems) / 8;
-         i += blockDim.x)
-        reinterpret_cast<uint4*>(sm)[i] = make_uint4(0u, 0u, 0u, 0u);
-    stage_weights(w0, Wf, CH, CH, C0, fused::kS16);
-    stage_weights(w1, Wf + wf1, CH, CH, CH, fused::kS32);
-    stage_weights(w2, Wf + wf2, CH, CH, CH, fused::kS32);
-    stage_weights(w3, Wf + wf3, CO, fused::kCoOut, CH, fused::kS32);
-    const long long units = (long long)n * fused::kBands;
-    __syncthreads();  // zeroed before the first copy lands
-    if (blockIdx.x < units) fused_prefetch(a0, blockIdx.x, bin);
-    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
-        const int s = (int)(u / fused::kBands);
-        const int y0 = (int)(u - (long long)s * fused::kBands) * fused::kBand;
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        __syncthreads();  // input landed; the previous unit is done
-        // the output rows' coarse scores (input channel 1, rows 4..9)
-        for (int i = threadIdx.x; i < fused::kSkip; i += blockDim.x) {
-            const int r = i / W, x = i - r * W;
-            skip[i] = __bfloat162float(
-                bin[((r + 4) * fused::kCols + x + 1) * fused::kS16 + 1]);
-        }
-        fused_layer<C0, CH, fused::kS16, fused::kS32, false>(
-            bin, w0, w32 + b0, fused::kARows, y0 - 3, ba, nullptr, nullptr);
-        __syncthreads();  // the input buffer is free: fetch the next unit
-        if (u + gridDim.x < units) fused_prefetch(a0, u + gridDim.x, bin);
-        fused_layer<CH, CH, fused::kS32, fused::kS32, false>(
-            ba, w1, w32 + b1, fused::kBRows, y0 - 2, bb, nullptr, nullptr);
-        __syncthreads();
-        fused_layer<CH, CH, fused::kS32, fused::kS32, false>(
-            bb, w2, w32 + b2, fused::kBand + 2, y0 - 1, ba, nullptr, nullptr);
-        __syncthreads();
-        fused_layer<CH, fused::kCoOut, fused::kS32, 0, true>(
-            ba, w3, w32 + b3, fused::kBand, y0, nullptr, skip,
-            out + (long long)s * NPIX);
-    }
-    asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // ------------------------------------------------------------ training

@@ -93,14 +93,15 @@ def test_forward_matches_reference(torch):
         lay = lay.cpu().numpy().astype(np.float64)
     finally:
         net.close()
-    # the fused pass (activations in shared memory) and the layer-by-layer
-    # one of training compute the same products in the same order
-    assert np.array_equal(y, lay)
+    # the tcgen05 pass and the layer-by-layer mma.sync one of training sum
+    # in different orders: both are held to the reference below
+    assert np.abs(y - lay).max() <= 5e-2
     _, ref = net_ref.forward(x, _layers_as_gpu(w))
     scale = np.mean(np.abs(ref)) + 1e-3
-    err = np.abs(y - ref)
-    assert np.max(err) <= 2e-2 * scale + 1e-2 * np.abs(ref).max()
-    assert np.mean(err) <= 2e-3 * scale
+    for got in (y, lay):
+        err = np.abs(got - ref)
+        assert np.max(err) <= 2e-2 * scale + 1e-2 * np.abs(ref).max()
+        assert np.mean(err) <= 2e-3 * scale
 
 
 @pytest.mark.parametrize("band,low,under", [(np.inf, 1.0, 1.0),
@@ -204,9 +205,11 @@ def _propose(torch, batch, weights, topk, flags=0):
         s.close()
 
 
-def test_fused_forward_equals_layers_on_a_batch(torch):
-    """Bands of rows, map edges and many states: every unit of the fused
-    kernel's schedule against the layer-by-layer pass."""
+def test_tensor_core_forward_on_a_batch(torch):
+    """Bands of rows, map edges and many states: every unit of the tcgen05
+    kernel's schedule against the layer-by-layer pass (FP32 summation order
+    differs; the bfloat16 activations it flips move the output little), and
+    no bounded wait ran out."""
     batch = synth.ssl_states(510, 300, K=64)
     net = pps.Net(max_batch=300, weights=pps.init_weights(21))
     try:
@@ -216,7 +219,11 @@ def test_fused_forward_equals_layers_on_a_batch(torch):
         lay = torch.empty_like(y)
         pps.pps_net_forward_layers(net.net, dev.data_ptr(), 300,
                                    lay.data_ptr())
-        assert torch.equal(y, lay)
+        pps.pps_net_sync(net.net)
+        d = (y - lay).abs()
+        assert float(d.max()) <= 5e-2, float(d.max())
+        assert float(d.mean()) <= 1e-3, float(d.mean())
+        assert torch.isfinite(y).all()
     finally:
         net.close()
 
