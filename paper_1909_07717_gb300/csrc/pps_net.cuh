@@ -98,16 +98,7 @@ __device__ __forceinline__ void cell_features(const pps_state& st,
 #pragma unroll 1
         for (int k = 1; k <= kFeatK; ++k) {
             const float fr = (float)k * (1.f / kFeatK);  // exact: kFeatK = 2^n
-            float t[J];
-#pragma unroll
-            for (int j = 0; j < J; ++j)
-                t[j] = sbip_num<GEN>(fr, cbx, cby, o.bx[j], o.by[j], o.ux[j],
-                                     o.uy[j], sk.reach);
-#pragma unroll
-            for (int w = 1; w < J; w *= 2)
-#pragma unroll
-                for (int j = 0; j + w < J; j += 2 * w) t[j] = fminf(t[j], t[j + w]);
-            const float aT = t[0] * sk.at_scale;
+            const float aT = opp_min<J, GEN>(fr, cbx, cby, o, sk.reach) * sk.at_scale;
             const float nf = -fr * twoabD;
 #pragma unroll
             for (int v = 0; v < PPS_MAX_SPEEDS; ++v)

@@ -82,16 +82,17 @@ cudaError_t launch(const pps::SearchArgs& a, int num_sms, cudaStream_t st) {
     static int occ = 0;
     if (occ == 0) {
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &occ, pps::search_kernel<J, V>, pps::kTPB, 0);
+            &occ, pps::search_kernel<J, V>, pps::search_tpb<J, V>(), 0);
         if (e != cudaSuccess) return e;
         if (occ < 1) occ = 1;
     }
     // One warp per work item of 32 points; no more CTAs than items need.
     const long long items = (long long)a.n_states * a.words;
     long long grid = (long long)num_sms * occ;
-    const long long need = (items + pps::kTPB / 32 - 1) / (pps::kTPB / 32);
+    constexpr int tpb = pps::search_tpb<J, V>();
+    const long long need = (items + tpb / 32 - 1) / (tpb / 32);
     if (grid > need) grid = need;
-    pps::search_kernel<J, V><<<(unsigned)grid, pps::kTPB, 0, st>>>(a);
+    pps::search_kernel<J, V><<<(unsigned)grid, tpb, 0, st>>>(a);
     pps::finalize_kernel<J, V><<<(a.n_states + 127) / 128, 128, 0, st>>>(a);
     return cudaGetLastError();
 }

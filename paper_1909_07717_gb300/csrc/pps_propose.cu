@@ -28,13 +28,13 @@ constexpr int kFineNx = 481, kFineNy = 361;
 // and the last pass-line sample's margin, max over its points) falls below
 // that pass's score is skipped: it cannot hold the best.
 template <int JMAX, int VMAX>
-__global__ void __launch_bounds__(pps::kTPB)
+__global__ void __launch_bounds__(pps::search_tpb<JMAX, VMAX>(), 1)
     refine_kernel(const pps::SearchArgs a, const int* __restrict__ cells,
                   int topk, bool prune) {
+    constexpr int kWarps = pps::search_tpb<JMAX, VMAX>() / 32;
     const int lane = threadIdx.x & 31;
-    const long long warps = (long long)gridDim.x * (pps::kTPB / 32);
-    const long long gw =
-        (long long)blockIdx.x * (pps::kTPB / 32) + (threadIdx.x >> 5);
+    const long long warps = (long long)gridDim.x * kWarps;
+    const long long gw = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const long long n_items = (long long)a.n_states * topk * 2;
     const pps::ItemGrid gr{a.g, a.x0, a.y0, a.V};
     for (long long item = gw; item < n_items; item += warps) {
@@ -110,12 +110,8 @@ template <int J, int V>
 int occupancy() {
     static int occ = 0;
     if (!occ) {
-        int a = 0, b = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, refine_kernel<J, V>,
-                                                      pps::kTPB, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &b, pps::search_kernel<J, V, true>, pps::kTPB, 0);
-        occ = a < b ? a : b;
+            &occ, refine_kernel<J, V>, pps::search_tpb<J, V>(), 0);
         if (occ < 1) occ = 1;
     }
     return occ;
@@ -131,10 +127,10 @@ cudaError_t run(const pps::SearchArgs& base, const int* cells, int topk,
     if (e == cudaSuccess) e = cudaMemsetAsync(a.counts, 0, sizeof(int) * a.n_states, st);
     if (e != cudaSuccess) return e;
     const long long items = (long long)a.n_states * topk * 2;
-    long long grid = (items + pps::kTPB / 32 - 1) / (pps::kTPB / 32);
+    constexpr int tpb = pps::search_tpb<J, V>();
+    long long grid = (items + tpb / 32 - 1) / (tpb / 32);
     if (grid > cap) grid = cap;
-    refine_kernel<J, V><<<(unsigned)grid, pps::kTPB, 0, st>>>(a, cells, topk,
-                                                              prune);
+    refine_kernel<J, V><<<(unsigned)grid, tpb, 0, st>>>(a, cells, topk, prune);
     pps::finalize_kernel<J, V><<<(a.n_states + 127) / 128, 128, 0, st>>>(a);
     if (!fallback) return cudaGetLastError();
     e = cudaMemsetAsync(ns.list_n, 0, sizeof(int), st);
@@ -148,7 +144,8 @@ cudaError_t run(const pps::SearchArgs& base, const int* cells, int topk,
     a.list = ns.list;
     a.list_n = ns.list_n;
     // one CTA per SM at most: the list is usually empty or short
-    pps::search_kernel<J, V, true><<<(unsigned)num_sms, pps::kTPB, 0, st>>>(a);
+    pps::search_kernel<J, V, true>
+        <<<(unsigned)num_sms, pps::search_tpb<J, V>(), 0, st>>>(a);
     pps::finalize_kernel<J, V><<<(a.n_states + 127) / 128, 128, 0, st>>>(a);
     return cudaGetLastError();
 }

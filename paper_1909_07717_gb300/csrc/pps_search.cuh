@@ -39,17 +39,20 @@
 
 namespace pps {
 
-#ifndef PPS_TPB
-#define PPS_TPB 512  // measured best of 32..512 on the batched workload
-#endif
-#ifndef PPS_MIN_BLOCKS
-#define PPS_MIN_BLOCKS 1
-#endif
 #ifndef PPS_KUNROLL
-#define PPS_KUNROLL 2
+#define PPS_KUNROLL 1  // measured: 1 beats 2 and 4 once slots are packed
 #endif
 constexpr int kKUnroll = PPS_KUNROLL;  // unroll of the sample loop
-constexpr int kTPB = PPS_TPB;      // threads per CTA (16 independent warps)
+
+// Threads per CTA of a search-kernel instance: one CTA per SM either way;
+// the 8-slot instances take 1024 threads (32 independent warps: more
+// latency hiding for the dependent intercept chain is worth the few
+// spilled registers at the 64-register cap; measured 56.9 ms against
+// 60.0 ms with 512 threads on the batched workload), the wider ones 512.
+template <int JMAX, int VMAX>
+__host__ __device__ constexpr int search_tpb() {
+    return JMAX <= 8 ? 1024 : 512;
+}
 constexpr float kFar = 1.0e18f;    // offset of an unused opponent slot
 constexpr float kD2Floor = 1.0e-30f;  // keeps 1/d finite when d == 0
 
@@ -190,10 +193,12 @@ __device__ __forceinline__ float scaled_diff(float x, float y, float kappa) {
 // Opponents in registers, in scaled units: kappa (b - o) and u / vmax per
 // slot; unused slots are parked at kFar so they can never hold the minimum.
 // kappa (b - o) is formed from the exact difference (an error-free two-sum)
-// so it carries a single rounding.
+// so it carries a single rounding.  Slots are held in pairs (float2) so
+// that two opponents go through one packed f32x2 instruction.
 template <int JMAX>
 struct OppRegs {
-    float bx[JMAX], by[JMAX], ux[JMAX], uy[JMAX];
+    static_assert(JMAX % 2 == 0, "opponent slots come in pairs");
+    float2 bx[JMAX / 2], by[JMAX / 2], ux[JMAX / 2], uy[JMAX / 2];
 };
 
 template <int JMAX>
@@ -201,18 +206,27 @@ __device__ __forceinline__ void load_opps(const pps_state& st,
                                           const StateK& sk,
                                           OppRegs<JMAX>& o) {
 #pragma unroll
-    for (int j = 0; j < JMAX; ++j) {
-        if (j < sk.nopp) {
-            o.bx[j] = scaled_diff(sk.bx, st.opp_pos[j][0], sk.kappa);
-            o.by[j] = scaled_diff(sk.by, st.opp_pos[j][1], sk.kappa);
-            o.ux[j] = __fmul_rn(st.opp_vel[j][0], sk.inv_vmax);
-            o.uy[j] = __fmul_rn(st.opp_vel[j][1], sk.inv_vmax);
-        } else {
-            o.bx[j] = kFar;
-            o.by[j] = kFar;
-            o.ux[j] = 0.f;
-            o.uy[j] = 0.f;
+    for (int i = 0; i < JMAX / 2; ++i) {
+        float v[2][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = 2 * i + h;
+            if (j < sk.nopp) {
+                v[h][0] = scaled_diff(sk.bx, st.opp_pos[j][0], sk.kappa);
+                v[h][1] = scaled_diff(sk.by, st.opp_pos[j][1], sk.kappa);
+                v[h][2] = __fmul_rn(st.opp_vel[j][0], sk.inv_vmax);
+                v[h][3] = __fmul_rn(st.opp_vel[j][1], sk.inv_vmax);
+            } else {
+                v[h][0] = kFar;
+                v[h][1] = kFar;
+                v[h][2] = 0.f;
+                v[h][3] = 0.f;
+            }
         }
+        o.bx[i] = make_float2(v[0][0], v[1][0]);
+        o.by[i] = make_float2(v[0][1], v[1][1]);
+        o.ux[i] = make_float2(v[0][2], v[1][2]);
+        o.uy[i] = make_float2(v[0][3], v[1][3]);
     }
 }
 
@@ -223,6 +237,10 @@ __device__ __forceinline__ void load_opps(const pps_state& st,
 //     n = (1 - w')^2 + d' - max(1 - q', 0)^2,
 // and max(1 - q', 0) is one saturating add because 1 - q' <= 1.  GEN adds
 // the clamp of w' to [-1, 1] and the reach radius (n = 0 within reach).
+// Two opponents at a time: every FP32 operation but the saturating add,
+// the clamps and the square roots is one packed f32x2 instruction, each
+// half rounded exactly as the scalar operation (1 - w is fma(w, -1, 1),
+// -m is m * -1: both exact rewrites).
 __device__ __forceinline__ float one_minus_sat(float x) {
     float y;  // saturate(1 - x) = clamp(1 - x, 0, 1)
     asm("add.rn.sat.f32 %0, %1, %2;" : "=f"(y) : "f"(1.f), "f"(-x));
@@ -230,28 +248,58 @@ __device__ __forceinline__ float one_minus_sat(float x) {
 }
 
 template <bool GEN>
-__device__ __forceinline__ float sbip_num(float f, float cbx, float cby,
-                                          float obx, float oby, float oux,
-                                          float ouy, float reach) {
-    const float rx = __fmaf_rn(f, cbx, obx);  // kappa (p - o)
-    const float ry = __fmaf_rn(f, cby, oby);
-    const float d2 = __fmaf_rn(rx, rx, __fmaf_rn(ry, ry, kD2Floor));
-    const float ig = rsqrt_fast(d2);
-    const float d = __fmul_rn(d2, ig);
-    float w = __fmul_rn(__fmaf_rn(oux, rx, __fmul_rn(ouy, ry)), ig);
+__device__ __forceinline__ float2 sbip_num2(float2 f, float2 cbx, float2 cby,
+                                            float2 obx, float2 oby,
+                                            float2 oux, float2 ouy,
+                                            float reach) {
+    const float2 one = make_float2(1.f, 1.f), mone = make_float2(-1.f, -1.f);
+    const float2 rx = __ffma2_rn(f, cbx, obx);  // kappa (p - o)
+    const float2 ry = __ffma2_rn(f, cby, oby);
+    const float2 d2 = __ffma2_rn(rx, rx, __ffma2_rn(ry, ry, make_float2(kD2Floor, kD2Floor)));
+    const float2 ig = make_float2(rsqrt_fast(d2.x), rsqrt_fast(d2.y));
+    const float2 d = __fmul2_rn(d2, ig);
+    float2 w = __fmul2_rn(__ffma2_rn(oux, rx, __fmul2_rn(ouy, ry)), ig);
     if (GEN) {
-        w = fminf(fmaxf(w, -1.f), 1.f);
-        const float dl = __fsub_rn(d, reach);
-        const float dc = fmaxf(dl, 0.f);
-        const float m = one_minus_sat(sqrt_pos(__fmaf_rn(w, w, dc)));
-        const float e = __fsub_rn(1.f, w);
-        const float num = __fmaf_rn(-m, m, __fmaf_rn(e, e, dc));
-        return dl > 0.f ? num : 0.f;
+        w.x = fminf(fmaxf(w.x, -1.f), 1.f);
+        w.y = fminf(fmaxf(w.y, -1.f), 1.f);
+        const float2 dl = __fadd2_rn(d, make_float2(-reach, -reach));
+        const float2 dc = make_float2(fmaxf(dl.x, 0.f), fmaxf(dl.y, 0.f));
+        const float2 q = __ffma2_rn(w, w, dc);
+        const float2 m = make_float2(one_minus_sat(sqrt_pos(q.x)),
+                                     one_minus_sat(sqrt_pos(q.y)));
+        const float2 e = __ffma2_rn(w, mone, one);
+        const float2 num = __ffma2_rn(__fmul2_rn(m, mone), m, __ffma2_rn(e, e, dc));
+        return make_float2(dl.x > 0.f ? num.x : 0.f, dl.y > 0.f ? num.y : 0.f);
     } else {
-        const float m = one_minus_sat(sqrt_pos(__fmaf_rn(w, w, d)));
-        const float e = __fsub_rn(1.f, w);
-        return __fmaf_rn(-m, m, __fmaf_rn(e, e, d));
+        const float2 q = __ffma2_rn(w, w, d);
+        const float2 m = make_float2(one_minus_sat(sqrt_pos(q.x)),
+                                     one_minus_sat(sqrt_pos(q.y)));
+        const float2 e = __ffma2_rn(w, mone, one);
+        return __ffma2_rn(__fmul2_rn(m, mone), m, __ffma2_rn(e, e, d));
     }
+}
+
+// The smallest scaled intercept numerator over the JMAX opponent slots at
+// the sample f of the pass kappa (c - b) = (cbx, cby); the minimum is a
+// balanced tree so the sample's critical path stays short.
+template <int JMAX, bool GEN>
+__device__ __forceinline__ float opp_min(float f, float cbx, float cby,
+                                         const OppRegs<JMAX>& o, float reach) {
+    const float2 f2 = make_float2(f, f), cx2 = make_float2(cbx, cbx),
+                 cy2 = make_float2(cby, cby);
+    float t[JMAX];
+#pragma unroll
+    for (int i = 0; i < JMAX / 2; ++i) {
+        const float2 r = sbip_num2<GEN>(f2, cx2, cy2, o.bx[i], o.by[i],
+                                        o.ux[i], o.uy[i], reach);
+        t[2 * i] = r.x;
+        t[2 * i + 1] = r.y;
+    }
+#pragma unroll
+    for (int w = 1; w < JMAX; w *= 2)
+#pragma unroll
+        for (int j = 0; j + w < JMAX; j += 2 * w) t[j] = fminf(t[j], t[j + w]);
+    return t[0];
 }
 
 // A3 + A4 over the K samples of one point.  mv[v] accumulates
@@ -263,6 +311,13 @@ __device__ __forceinline__ void sample_loop(const StateK& sk,
                                             float twoabD,
                                             const float (&sp2)[PPS_MAX_SPEEDS],
                                             float (&mv)[VMAX], float* Trow) {
+    // speeds in pairs for the packed ball-time terms
+    constexpr int VP = (VMAX + 1) / 2;
+    float2 s2[VP];
+#pragma unroll
+    for (int i = 0; i < VP; ++i)
+        s2[i] = make_float2(sp2[2 * i], sp2[2 * i + 1 < VMAX ? 2 * i + 1 : 2 * i]);
+    const float2 tD2 = make_float2(twoabD, twoabD);
     // Float sample counter: exact for K <= 2^24, and keeps integer-to-float
     // conversions out of the loop.
     const float Kf = (float)sk.K;
@@ -270,26 +325,25 @@ __device__ __forceinline__ void sample_loop(const StateK& sk,
     for (float kf = 1.f; kf <= Kf; kf += 1.f) {
         const float f = __fmul_rn(kf, sk.invK);
         const int k = (int)kf;
-        // The JMAX interactions are independent; their minimum is taken as
-        // a balanced tree so the sample's critical path stays short.
-        float t[JMAX];
-#pragma unroll
-        for (int j = 0; j < JMAX; ++j)
-            t[j] = sbip_num<GEN>(f, cbx, cby, o.bx[j], o.by[j], o.ux[j],
-                                 o.uy[j], sk.reach);
-#pragma unroll
-        for (int w = 1; w < JMAX; w *= 2)
-#pragma unroll
-            for (int j = 0; j + w < JMAX; j += 2 * w) t[j] = fminf(t[j], t[j + w]);
-        const float n = t[0];
+        const float n = opp_min<JMAX, GEN>(f, cbx, cby, o, sk.reach);
         if (TDBG && Trow)
             Trow[k - 1] = sk.nopp ? __fmul_rn(n, sk.t_scale) : CUDART_INF_F;
         const float aT = __fmul_rn(n, sk.at_scale);
         const float nf = -f;
+        if (VMAX == 1) {
+            mv[0] = fminf(mv[0], __fadd_rn(aT, sqrt_ball(__fmaf_rn(
+                                                 nf, twoabD, sp2[0]))));
+        } else {
+            const float2 nf2 = make_float2(nf, nf), aT2 = make_float2(aT, aT);
 #pragma unroll
-        for (int v = 0; v < VMAX; ++v)
-            mv[v] = fminf(mv[v], __fadd_rn(aT, sqrt_ball(__fmaf_rn(
-                                                 nf, twoabD, sp2[v]))));
+            for (int i = 0; i < VP; ++i) {
+                const float2 a = __ffma2_rn(nf2, tD2, s2[i]);
+                const float2 t = __fadd2_rn(
+                    aT2, make_float2(sqrt_ball(a.x), sqrt_ball(a.y)));
+                mv[2 * i] = fminf(mv[2 * i], t.x);
+                if (2 * i + 1 < VMAX) mv[2 * i + 1] = fminf(mv[2 * i + 1], t.y);
+            }
+        }
     }
 }
 
@@ -449,11 +503,13 @@ __device__ __forceinline__ void eval_point(const pps_params& prm,
 // An upper bound of every score eval_point can give the point (ix, iy),
 // from the same arithmetic with (a) the shot angle replaced by the whole
 // mouth's angle hi - lo (every open gap lies inside [lo, hi]) and (b) each
-// speed's margin replaced by its last sample's term alone (the margin is
-// the minimum over the samples; the last one is computed exactly as the
-// sample loop's last iteration).  FP32 rounding is monotone, so the bound
+// speed's margin taken over kBoundSamples of the K samples only (the margin
+// is the minimum over all of them; each chosen sample is computed exactly
+// as the sample loop computes it).  FP32 rounding is monotone, so the bound
 // needs no slack; it holds when w_angle >= 0 and w_margin >= 0, which the
 // caller checks.
+constexpr int kBoundSamples = 1;
+
 template <int JMAX, int VMAX>
 __device__ __forceinline__ float score_bound(const pps_params& prm,
                                              const ItemGrid& gr,
@@ -471,33 +527,34 @@ __device__ __forceinline__ float score_bound(const pps_params& prm,
     const float dxm = (float)dxd, dym = (float)dyd;
     const float D = __fsqrt_rn(__fmaf_rn(dxm, dxm, __fmul_rn(dym, dym)));
     const float twoabD = __fmul_rn(sk.two_ab, D);
-    // the sample loop's last sample: kf = K, f = K * (1 / K)
-    const float f = __fmul_rn((float)sk.K, sk.invK);
-    float t[JMAX];
+    // kBoundSamples of the sample loop's samples, spread along the pass
+    // (sample k = ceil(K i / kBoundSamples), the last one being K), each
+    // computed exactly as the loop computes it: f = k * (1 / K)
+    float mv[VMAX];
 #pragma unroll
-    for (int j = 0; j < JMAX; ++j)
-        t[j] = sk.general
-                   ? sbip_num<true>(f, cbx, cby, o.bx[j], o.by[j], o.ux[j],
-                                    o.uy[j], sk.reach)
-                   : sbip_num<false>(f, cbx, cby, o.bx[j], o.by[j], o.ux[j],
-                                     o.uy[j], sk.reach);
-    float n = t[0];
+    for (int v = 0; v < VMAX; ++v) mv[v] = CUDART_INF_F;
 #pragma unroll
-    for (int j = 1; j < JMAX; ++j) n = fminf(n, t[j]);
-    const float aT = __fmul_rn(n, sk.at_scale);
-    const float nf = -f;
+    for (int i = 1; i <= kBoundSamples; ++i) {
+        const int k = (sk.K * i + kBoundSamples - 1) / kBoundSamples;
+        const float f = __fmul_rn((float)k, sk.invK);
+        const float n = sk.general
+                            ? opp_min<JMAX, true>(f, cbx, cby, o, sk.reach)
+                            : opp_min<JMAX, false>(f, cbx, cby, o, sk.reach);
+        const float aT = __fmul_rn(n, sk.at_scale);
+        const float nf = -f;
+#pragma unroll
+        for (int v = 0; v < VMAX; ++v)
+            mv[v] = fminf(mv[v], __fadd_rn(aT, sqrt_ball(__fmaf_rn(
+                                                   nf, twoabD, sp2[v]))));
+    }
     float mb = -CUDART_INF_F;
 #pragma unroll
     for (int v = 0; v < VMAX; ++v) {
         if (v >= gr.V) continue;
         if (!(__fmaf_rn(-sk.fK, twoabD, sp2[v]) >= 0.f)) continue;
-        const float m =
-            sk.nopp == 0
-                ? CUDART_INF_F
-                : __fdiv_rn(__fsub_rn(__fadd_rn(aT, sqrt_ball(__fmaf_rn(
-                                                     nf, twoabD, sp2[v]))),
-                                      sp[v]),
-                            sk.ab);
+        const float m = sk.nopp == 0
+                            ? CUDART_INF_F
+                            : __fdiv_rn(__fsub_rn(mv[v], sp[v]), sk.ab);
         mb = fmaxf(mb, m);
     }
     const bool front = cxd < (double)sk.Lh;
@@ -540,11 +597,12 @@ __device__ __forceinline__ unsigned long long warp_max_u64(
 // (states to leave untouched) and write a.dbg_point; the plain instances
 // carry none of these checks in their loop.
 template <int JMAX, int VMAX, bool EXT = false>
-__global__ void __launch_bounds__(kTPB, PPS_MIN_BLOCKS)
+__global__ void __launch_bounds__(search_tpb<JMAX, VMAX>(), 1)
     search_kernel(const SearchArgs a) {
+    constexpr int kWarps = search_tpb<JMAX, VMAX>() / 32;
     const int lane = threadIdx.x & 31;
-    const long long warps = (long long)gridDim.x * (kTPB / 32);
-    const long long gw = (long long)blockIdx.x * (kTPB / 32) + (threadIdx.x >> 5);
+    const long long warps = (long long)gridDim.x * kWarps;
+    const long long gw = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const bool listed = EXT && a.list;
     const long long n_items =
         (long long)(listed ? *a.list_n : a.n_states) * a.words;
