@@ -147,7 +147,7 @@ __device__ __forceinline__ void cell_features(const pps_state& st,
 //   4  shot angle of the cell    (f[2])
 //   5  |goal centre - c| / diag
 //   6  c_x / (L / 2),  7  c_y / (W / 2)
-__global__ void __launch_bounds__(128, 4)
+__global__ void __launch_bounds__(128, 8)
     raster_kernel(const pps_state* __restrict__ states, int n,
                               const RasterCfg cfg,
                               __nv_bfloat16* __restrict__ out) {
