@@ -10,6 +10,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_1909_07717_gb300 import build, pps
@@ -80,3 +81,27 @@ def test_create_without_device_fails_cleanly(lib):
     with pytest.raises(pps.PpsError) as e:
         pps.pps_create(pps.pps_ctx_desc(max_states=0))
     assert e.value.status == pps.PPS_EINVAL
+
+
+def test_weight_file_round_trip_and_checks(tmp_path):
+    """The proposal weight file: magic, count, CRC-32, float32 data."""
+    w = pps.init_weights(3)
+    p = str(tmp_path / "w.bin")
+    pps.save_net_weights(p, w)
+    assert np.array_equal(pps.load_net_weights(p), w)
+    raw = bytearray(open(p, "rb").read())
+    raw[100] ^= 1
+    open(p, "wb").write(bytes(raw))
+    with pytest.raises(ValueError, match="checksum"):
+        pps.load_net_weights(p)
+    with pytest.raises(ValueError):
+        pps.save_net_weights(p, w[:-1])
+    bad = w.copy()
+    bad[5] = np.nan
+    with pytest.raises(ValueError):
+        pps.save_net_weights(p, bad)
+
+
+def test_committed_weights_load():
+    w = pps.load_net_weights()
+    assert w.shape == (pps.PPS_NET_PARAMS,) and np.all(np.isfinite(w))
