@@ -16,7 +16,8 @@ template <int V>
 cudaError_t go_t(const BatchArgs& a, int tpb, int grid, cudaStream_t st) {
     if (tpb == 128) return go<V, 128>(a, grid, st);
     if (tpb == 256) return go<V, 256>(a, grid, st);
-    return go<V, 512>(a, grid, st);
+    if (tpb == 512) return go<V, 512>(a, grid, st);
+    return go<V, 1024>(a, grid, st);
 }
 
 template <int V, int T>
@@ -34,7 +35,8 @@ template <int V>
 int occ_t(int tpb) {
     if (tpb == 128) return occ<V, 128>();
     if (tpb == 256) return occ<V, 256>();
-    return occ<V, 512>();
+    if (tpb == 512) return occ<V, 512>();
+    return occ<V, 1024>();
 }
 
 }  // namespace

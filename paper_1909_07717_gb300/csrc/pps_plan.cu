@@ -17,7 +17,8 @@
 
 namespace {
 
-constexpr int kCandidates[3] = {128, 256, 512};  // CTA sizes the tuner tries
+constexpr int kNumCand = 4;
+constexpr int kCandidates[kNumCand] = {128, 256, 512, 1024};  // CTA sizes tried
 constexpr int kMaxDevices = 64;
 
 // Autotuner choices per (device, opponent slots, speed slots), shared by all
@@ -39,7 +40,7 @@ struct Group {
     std::vector<int> states;      // state indices
     long long n_items = 0;
     int tpb = 512;
-    float tuned_ms[3] = {0, 0, 0};
+    float tuned_ms[kNumCand] = {0, 0, 0, 0};
     long long states_off = 0;     // offset into the plan's bucket_states array
     long long start_off = 0;      // offset into the plan's item_start array
 };
@@ -325,7 +326,7 @@ pps_status autotune(pps_plan* pl, const pps_state* states, pps_best* best,
         a.n_items = std::min(a.n_items, cap);
         float best_ms = 1e30f;
         int best_tpb = 512;
-        for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+        for (int c = 0; c < kNumCand && e == cudaSuccess; ++c) {
             const int tpb = kCandidates[c];
             e = launch_group(pl, a, g, tpb, st);  // warm-up
             if (e == cudaSuccess) e = cudaEventRecord(e0, st);
@@ -451,7 +452,7 @@ extern "C" pps_status pps_plan_groups(const pps_plan* pl, pps_plan_group* out,
         out[i].n_states = (int32_t)g.states.size();
         out[i].cta_threads = g.tpb;
         out[i].n_items = g.n_items;
-        for (int c = 0; c < 3; ++c) out[i].tuned_ms[c] = g.tuned_ms[c];
+        for (int c = 0; c < kNumCand; ++c) out[i].tuned_ms[c] = g.tuned_ms[c];
     }
     return PPS_OK;
 }
