@@ -203,7 +203,13 @@ cudaError_t pps_net_predict(pps_net* nt, const pps_state* states, int n,
 int pps_net_max_batch(const pps_net* nt) { return nt->max_batch; }
 
 cudaError_t pps_net_topk(pps_net* nt, int n, int k, int* cells) {
-    topk_kernel<<<n, 512, 0, nt->stream>>>(nt->out, k, cells);
+    int p2 = 1;
+    while (p2 < k) p2 <<= 1;
+    const size_t smem = sizeof(unsigned long long) * (size_t)(NPIX + p2);
+    cudaError_t e = cudaFuncSetAttribute(
+        topk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    topk_kernel<<<n, kTopkThreads, smem, nt->stream>>>(nt->out, k, p2, cells);
     return cudaGetLastError();
 }
 

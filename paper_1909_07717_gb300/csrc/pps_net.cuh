@@ -510,42 +510,96 @@ __global__ void cell_label_kernel(const float* __restrict__ point_best,
     labels[i] = m;
 }
 
-// Top-k map pixels of every state (one CTA per state): bitonic sort of
-// (score, ~pixel) keys, best first; equal scores keep the smaller pixel.
-__global__ void __launch_bounds__(512)
-    topk_kernel(const float* __restrict__ scores, int k,
+// Top-k map pixels of every state (one CTA per state), best first; equal
+// scores keep the smaller pixel.  Keys are (order-preserving score bits,
+// ~pixel), all distinct: an 8-pass radix select (8-bit digits, most
+// significant first) finds the k-th largest key T, the k keys >= T are
+// compacted, and only those are sorted (bitonic, next power of two).
+constexpr int kTopkThreads = 256;
+
+__device__ __forceinline__ unsigned long long topk_key(const float* sc, int i) {
+    uint32_t u = __float_as_uint(sc[i]);
+    u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    return ((unsigned long long)u << 32) | (uint32_t)(~(uint32_t)i);
+}
+
+__global__ void __launch_bounds__(kTopkThreads)
+    topk_kernel(const float* __restrict__ scores, int k, int p2,
                 int* __restrict__ cells) {
-    __shared__ unsigned long long key[4096];
-    const int s = blockIdx.x;
+    extern __shared__ __align__(16) unsigned long long tk[];
+    unsigned long long* key = tk;         // NPIX keys
+    unsigned long long* sel = tk + NPIX;  // p2 selected keys
+    __shared__ int hist[256];
+    __shared__ int warp_sum[kTopkThreads / 32];
+    __shared__ unsigned long long s_prefix;
+    __shared__ int s_need, s_count;
+    const int s = blockIdx.x, t = threadIdx.x;
+    const int lane = t & 31, warp = t >> 5;
     const float* sc = scores + (long long)s * NPIX;
-    for (int i = threadIdx.x; i < 4096; i += blockDim.x) {
-        unsigned long long v = 0ull;
-        if (i < NPIX) {
-            uint32_t u = __float_as_uint(sc[i]);
-            u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-            v = ((unsigned long long)u << 32) | (uint32_t)(~(uint32_t)i);
-        }
-        key[i] = v;
+    for (int i = t; i < NPIX; i += blockDim.x) key[i] = topk_key(sc, i);
+    if (t == 0) {
+        s_prefix = 0ull;
+        s_need = k;
+        s_count = 0;
     }
     __syncthreads();
-    for (int size = 2; size <= 4096; size <<= 1) {
+    unsigned long long mask = 0ull;
+    for (int shift = 56; shift >= 0 && k < NPIX; shift -= 8) {
+        hist[t] = 0;
+        __syncthreads();
+        const unsigned long long prefix = s_prefix;
+        for (int i = t; i < NPIX; i += blockDim.x) {
+            const unsigned long long v = key[i];
+            if ((v & mask) == prefix) atomicAdd(&hist[(v >> shift) & 255u], 1);
+        }
+        __syncthreads();
+        // counts of digits 255 - t, inclusive scan from the top digit down
+        const int own = hist[255 - t];
+        int incl = own;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        if (lane == 31) warp_sum[warp] = incl;
+        __syncthreads();
+        for (int w = 0; w < warp; ++w) incl += warp_sum[w];
+        const int need = s_need;
+        __syncthreads();
+        if (incl >= need && incl - own < need) {  // exactly one thread
+            s_prefix = prefix | ((unsigned long long)(255 - t) << shift);
+            s_need = need - (incl - own);
+        }
+        mask |= 0xFFull << shift;
+        __syncthreads();
+    }
+    // the k-th largest key (or every key when k == NPIX)
+    const unsigned long long T = k < NPIX ? s_prefix : 0ull;
+    for (int i = t; i < p2; i += blockDim.x) sel[i] = 0ull;
+    __syncthreads();
+    for (int i = t; i < NPIX; i += blockDim.x) {
+        const unsigned long long v = key[i];
+        if (v >= T) sel[atomicAdd(&s_count, 1)] = v;
+    }
+    __syncthreads();
+    for (int size = 2; size <= p2; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = threadIdx.x; i < 4096; i += blockDim.x) {
+            for (int i = t; i < p2; i += blockDim.x) {
                 const int j = i ^ stride;
                 if (j > i) {
                     const bool desc = (i & size) == 0;
-                    const unsigned long long a = key[i], b = key[j];
+                    const unsigned long long a = sel[i], b = sel[j];
                     if (desc ? a < b : a > b) {
-                        key[i] = b;
-                        key[j] = a;
+                        sel[i] = b;
+                        sel[j] = a;
                     }
                 }
             }
             __syncthreads();
         }
     }
-    for (int i = threadIdx.x; i < k; i += blockDim.x)
-        cells[(long long)s * k + i] = (int)(~(uint32_t)(key[i] & 0xffffffffull));
+    for (int i = t; i < k; i += blockDim.x)
+        cells[(long long)s * k + i] = (int)(~(uint32_t)(sel[i] & 0xffffffffull));
 }
 
 }  // namespace net
