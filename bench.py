@@ -458,13 +458,14 @@ def _proposal(args, dev, stream):
     pro = pr.alloc(S)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    def timed(fn, steps):
+    def timed(fn, steps, flush_l2=True):
         for _ in range(2):
             fn()
         ev = [(torch.cuda.Event(enable_timing=True),
                torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         for i in range(steps):
-            flush.zero_()
+            if flush_l2:
+                flush.zero_()
             ev[i][0].record(stream)
             fn()
             ev[i][1].record(stream)
@@ -479,6 +480,21 @@ def _proposal(args, dev, stream):
     pb = pps.unpack_best(pro[0].cpu().numpy())
     nofb = pps.unpack_best(pr.run(st, S, w.speeds, fallback=False)[0]
                            .cpu().numpy())
+    # small batches (a serving launch holds one or a few frames): latency
+    # of each path, no L2 flush, back-to-back calls
+    small = {}
+    rs = pps.STATE_DTYPE.itemsize
+    for m in (1, 16):
+        if m > S:
+            continue
+        sub = st[:m * rs]
+        eo = pr.searcher.alloc_outputs(m, pr.grid, len(w.speeds), mask=False)
+        po = pr.alloc(m)
+        small[str(m)] = {
+            "plain_us": 1e3 * timed(lambda: pr.exact(sub, m, w.speeds, out=eo),
+                                    10, flush_l2=False),
+            "proposal_us": 1e3 * timed(lambda: pr.run(sub, m, w.speeds, out=po),
+                                       10, flush_l2=False)}
     pr.close()
     ok = agreement(pb, ex)
     return {"workload": f"{w.name} (seed {w.seed}, held out of training)",
@@ -490,6 +506,7 @@ def _proposal(args, dev, stream):
             "agree_2pct": float(ok.mean()),
             "same_point": float((pb["idx"] == ex["idx"]).mean()),
             "fallback_states": int((nofb["idx"] == -1).sum()),
+            "small_batch_latency": small,
             "refined_points_frac": TOPK * 64 / (481 * 361)}
 
 
