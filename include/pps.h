@@ -316,8 +316,8 @@ typedef struct pps_plan_group {
     int32_t n_states;
     int32_t cta_threads;  /* CTA size in use */
     int64_t n_items;      /* (state, 32-point) work items */
-    float tuned_ms[4];    /* autotuner's time per candidate (128, 256, 512,
-                             1024 threads); 0 when not measured */
+    float tuned_ms[5];    /* autotuner's time per candidate (128, 256, 512,
+                             768, 1024 threads); 0 when not measured */
 } pps_plan_group;
 
 /* Build a plan on ctx for n_states (1..2^24) states shaped by jobs (host

@@ -17,6 +17,7 @@ cudaError_t go_t(const BatchArgs& a, int tpb, int grid, cudaStream_t st) {
     if (tpb == 128) return go<V, 128>(a, grid, st);
     if (tpb == 256) return go<V, 256>(a, grid, st);
     if (tpb == 512) return go<V, 512>(a, grid, st);
+    if (tpb == 768) return go<V, 768>(a, grid, st);
     return go<V, 1024>(a, grid, st);
 }
 
@@ -36,6 +37,7 @@ int occ_t(int tpb) {
     if (tpb == 128) return occ<V, 128>();
     if (tpb == 256) return occ<V, 256>();
     if (tpb == 512) return occ<V, 512>();
+    if (tpb == 768) return occ<V, 768>();
     return occ<V, 1024>();
 }
 

@@ -17,8 +17,8 @@
 
 namespace {
 
-constexpr int kNumCand = 4;
-constexpr int kCandidates[kNumCand] = {128, 256, 512, 1024};  // CTA sizes tried
+constexpr int kNumCand = 5;
+constexpr int kCandidates[kNumCand] = {128, 256, 512, 768, 1024};  // CTA sizes tried
 constexpr int kMaxDevices = 64;
 
 // Autotuner choices per (device, opponent slots, speed slots), shared by all
@@ -40,7 +40,7 @@ struct Group {
     std::vector<int> states;      // state indices
     long long n_items = 0;
     int tpb = 512;
-    float tuned_ms[kNumCand] = {0, 0, 0, 0};
+    float tuned_ms[kNumCand] = {0, 0, 0, 0, 0};
     long long states_off = 0;     // offset into the plan's bucket_states array
     long long start_off = 0;      // offset into the plan's item_start array
 };

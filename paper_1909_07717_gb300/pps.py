@@ -92,7 +92,7 @@ class pps_job(ctypes.Structure):
 class pps_plan_group(ctypes.Structure):
     _fields_ = [("opp_slots", c_int32), ("speed_slots", c_int32),
                 ("n_states", c_int32), ("cta_threads", c_int32),
-                ("n_items", ctypes.c_int64), ("tuned_ms", c_float * 4)]
+                ("n_items", ctypes.c_int64), ("tuned_ms", c_float * 5)]
 
 
 class pps_server_desc(ctypes.Structure):

@@ -171,7 +171,7 @@ def test_uneven_full_size_properties(full_uneven):
     batch, jobs, best, mask, off, groups = full_uneven
     S = synth.UNEVEN_STATES
     assert np.all(best["status"] == 0)
-    assert all(g.cta_threads in (128, 256, 512, 1024) for g in groups)
+    assert all(g.cta_threads in (128, 256, 512, 768, 1024) for g in groups)
     has = best["idx"] >= 0
     assert np.all(has == (best["n_feasible"] > 0))
     for s in range(0, S, 97):      # popcounts and best bits, spread over all
