@@ -391,20 +391,30 @@ __device__ __forceinline__ float shot_angle(const pps_state& st,
         }
     }
     if (all) return 0.f;
-    float best = 0.f;
-    // Every maximal gap starts at lo or at the end of a blocked interval.
+    // Sort the blocked intervals by start (odd-even transposition network;
+    // unused slots sit at 1e30, last), then sweep: a gap opens wherever the
+    // next start lies beyond every end so far.  Each gap is the difference
+    // of an end (or lo) and the next start (or hi), as in the definition.
 #pragma unroll
-    for (int i = -1; i < JMAX; ++i) {
-        const float x = (i < 0) ? lo : e[i];
-        bool start = x >= lo && x < hi;
-        float end = hi;
+    for (int round = 0; round < JMAX; ++round)
 #pragma unroll
-        for (int j = 0; j < JMAX; ++j) {
-            start = start && !(s[j] < x && x < e[j]);
-            if (s[j] >= x) end = fminf(end, s[j]);
+        for (int i = round & 1; i + 1 < JMAX; i += 2) {
+            const bool sw = s[i] > s[i + 1];
+            const float s0 = fminf(s[i], s[i + 1]), s1 = fmaxf(s[i], s[i + 1]);
+            const float e0 = sw ? e[i + 1] : e[i], e1 = sw ? e[i] : e[i + 1];
+            s[i] = s0;
+            s[i + 1] = s1;
+            e[i] = e0;
+            e[i + 1] = e1;
         }
-        if (start) best = fmaxf(best, __fsub_rn(end, x));
+    float best = 0.f, cur = lo;
+#pragma unroll
+    for (int j = 0; j < JMAX; ++j) {
+        if (s[j] > cur && cur < hi)
+            best = fmaxf(best, __fsub_rn(fminf(s[j], hi), cur));
+        cur = fmaxf(cur, e[j]);
     }
+    if (cur < hi) best = fmaxf(best, __fsub_rn(hi, cur));
     return best;
 }
 
