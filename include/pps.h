@@ -499,6 +499,15 @@ pps_status pps_net_set_loss(pps_net* net, float top_band, float low_weight,
  * that pass are invalid; the flag is cleared). */
 pps_status pps_net_sync(pps_net* net);
 
+/* Self-test of those bounded waits: runs the inference kernel on n states
+ * (device) with its tensor-core work withheld, so that no mbarrier ever
+ * completes and every wait runs out after a short limit; the kernel then
+ * releases its tensor memory and returns.  Returns what pps_net_sync then
+ * reports -- PPS_ETIMEOUT when the timeout path works.  The output map of
+ * that pass is garbage; the network stays usable. */
+pps_status pps_net_selftest_timeout(pps_net* net, const pps_state* states,
+                                    int n);
+
 /* Weights as PPS_NET_PARAMS floats (host).  Setting them resets Adam. */
 pps_status pps_net_set_weights(pps_net* net, const float* w);
 pps_status pps_net_get_weights(pps_net* net, float* w);

@@ -86,7 +86,8 @@ cudaError_t cast_weights(pps_net* nt) {
 // Forward pass of n states into nt->out.  keep: layer by layer on mma.sync,
 // keeping every activation for the backward pass (training); otherwise the
 // tcgen05 kernel, which keeps them on the SM.
-cudaError_t forward(pps_net* nt, const pps_state* states, int n, bool keep) {
+cudaError_t forward(pps_net* nt, const pps_state* states, int n, bool keep,
+                    bool withhold = false) {
     const long long P = (long long)n * NPIX;
     const unsigned g = blocks(P, 64);
     cudaStream_t st = nt->stream;
@@ -101,7 +102,8 @@ cudaError_t forward(pps_net* nt, const pps_state* states, int n, bool keep) {
             (unsigned)(units < nt->num_sms ? units : nt->num_sms);
         tcf::tc_forward_kernel<<<grid, tcf::kThreads, tcf::kSmemBytes, st>>>(
             nt->a0, n, nt->Wf, nt->w, nt->out, wf_off(1), wf_off(2), wf_off(3),
-            bias_off(0), bias_off(1), bias_off(2), bias_off(3), nt->err);
+            bias_off(0), bias_off(1), bias_off(2), bias_off(3), nt->err,
+            withhold ? 1 : 0);
         return cudaGetLastError();
     }
     conv_kernel<C0, CH, kHidden><<<g, 128, 0, st>>>(
@@ -375,6 +377,16 @@ pps_status check_batch(const pps_net* nt, const void* states, int n) {
     return PPS_OK;
 }
 }  // namespace
+
+extern "C" pps_status pps_net_selftest_timeout(pps_net* nt,
+                                               const pps_state* states, int n) {
+    pps_status s = check_batch(nt, states, n);
+    if (s != PPS_OK) return s;
+    cudaSetDevice(nt->device);
+    cudaError_t e = forward(nt, states, n, false, true);
+    if (e != cudaSuccess) return fail(PPS_ECUDA, "pps_net_selftest_timeout", e);
+    return pps_net_sync(nt);
+}
 
 extern "C" pps_status pps_net_raster(pps_net* nt, const pps_state* states,
                                      int n, uint16_t* out) {

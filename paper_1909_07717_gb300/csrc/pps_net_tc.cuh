@@ -47,7 +47,8 @@ constexpr int kOffTmem = kOffBar + 8 * kMaxTiles;
 constexpr size_t kSmemBytes = kOffTmem + 8;
 constexpr int kThreads = 512;
 constexpr uint32_t kTmemCols = 256;
-constexpr uint32_t kWaitPolls = 1u << 22;
+constexpr uint32_t kWaitPolls = 1u << 22;  // polls per mbarrier wait
+constexpr uint32_t kTestPolls = 1u << 10;  // the self-test's short limit
 static_assert(kSmemBytes <= 232448, "one CTA per SM");
 static_assert(kARows / 2 * CH <= (int)kTmemCols, "accumulators fit");
 static_assert(kOffBar % 8 == 0, "mbarrier alignment");
@@ -123,12 +124,12 @@ __device__ __forceinline__ bool epi_hidden(uint32_t tmem, int ntiles,
                                            const float* __restrict__ bias,
                                            int y_first, uint8_t* out,
                                            int slots_out, uint32_t bars,
-                                           uint32_t phases) {
+                                           uint32_t phases, uint32_t polls) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int q = warp & 3;
     bool ok = true;
     for (int j = warp >> 2; j < ntiles; j += kThreads / 128) {
-        ok = ok && tc::mbar_wait(bars + 8 * j, (phases >> j) & 1u, kWaitPolls);
+        ok = ok && tc::mbar_wait(bars + 8 * j, (phases >> j) & 1u, polls);
         tc::fence_after_sync();
         float v[32];
         tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + j * CH, v);
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                       const __nv_bfloat16* __restrict__ Wf,
                       const float* __restrict__ w32, float* __restrict__ out,
                       int wf1, int wf2, int wf3, int b0, int b1, int b2, int b3,
-                      int* __restrict__ err) {
+                      int* __restrict__ err, int withhold) {
     extern __shared__ __align__(128) uint8_t smem[];
     uint8_t* bin = smem;
     uint8_t* ba = smem + kOffA;
@@ -191,7 +192,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc::fence_async_smem();
         tc::fence_before_sync();
         if (__syncthreads_or(bad)) return false;
-        if (threadIdx.x == 0) {
+        // withhold (self-test of the bounded waits): nothing is issued, no
+        // mbarrier ever completes, every wait runs out
+        if (threadIdx.x == 0 && !withhold) {
             tc::fence_after_sync();
             issue_fn();
         }
@@ -205,6 +208,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         phases ^= (1u << ntiles) - 1u;
     };
 
+    const uint32_t polls = withhold ? kTestPolls : kWaitPolls;
     for (long long u = blockIdx.x; u < units; u += gridDim.x) {
         const int s = (int)(u / kBands);
         const int y0 = (int)(u - (long long)s * kBands) * kBand;
@@ -221,14 +225,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                       t4 = kBand / 2;
         if (!start_layer([&] { issue<C0, CH>(tmem, bin, kSlotsIn, smem + kOffW0, t1, bars); }))
             break;
-        end_layer(t1, epi_hidden(tmem, t1, w32 + b0, y0 - 3, ba, kSlotsA, bars, phases));
+        end_layer(t1, epi_hidden(tmem, t1, w32 + b0, y0 - 3, ba, kSlotsA, bars, phases, polls));
         if (!start_layer([&] { issue<CH, CH>(tmem, ba, kSlotsA, smem + kOffW1, t2, bars); }))
             break;
         if (u + gridDim.x < units) prefetch(a0, u + gridDim.x, bin);
-        end_layer(t2, epi_hidden(tmem, t2, w32 + b1, y0 - 2, bb, kSlotsB, bars, phases));
+        end_layer(t2, epi_hidden(tmem, t2, w32 + b1, y0 - 2, bb, kSlotsB, bars, phases, polls));
         if (!start_layer([&] { issue<CH, CH>(tmem, bb, kSlotsB, smem + kOffW2, t3, bars); }))
             break;
-        end_layer(t3, epi_hidden(tmem, t3, w32 + b2, y0 - 1, ba, kSlotsA, bars, phases));
+        end_layer(t3, epi_hidden(tmem, t3, w32 + b2, y0 - 1, ba, kSlotsA, bars, phases, polls));
         // layer 4: A -> the output map (+ the coarse-score input channel)
         if (!start_layer([&] { issue<CH, kNOut>(tmem, ba, kSlotsA, smem + kOffW3, t4, bars); }))
             break;
@@ -236,7 +240,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         {
             const int lane = threadIdx.x & 31, q = warp & 3;
             for (int j = warp >> 2; j < t4; j += kThreads / 128) {
-                ok = ok && tc::mbar_wait(bars + 8 * j, (phases >> j) & 1u, kWaitPolls);
+                ok = ok && tc::mbar_wait(bars + 8 * j, (phases >> j) & 1u, polls);
                 tc::fence_after_sync();
                 const float v = tc::tmem_ld1(tmem + ((uint32_t)(32 * q) << 16) + j * kNOut);
                 const int r = 32 * q + lane, row = 2 * j + (r >> 6), col = r & 63;

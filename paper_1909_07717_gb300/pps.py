@@ -147,7 +147,7 @@ EXPORTS = ("pps_abi_version", "pps_status_string", "pps_last_error",
            "pps_server_submit", "pps_server_wait", "pps_server_replay",
            "pps_server_get_stats", "pps_net_create", "pps_net_destroy",
            "pps_net_set_features", "pps_net_set_loss", "pps_net_set_weights",
-           "pps_net_sync",
+           "pps_net_sync", "pps_net_selftest_timeout",
            "pps_net_get_weights", "pps_net_raster", "pps_net_forward_layers",
            "pps_net_forward", "pps_net_grad", "pps_net_train_step",
            "pps_net_labels", "pps_propose")
@@ -232,6 +232,8 @@ def lib():
             L.pps_net_set_features.argtypes = [c_void_p, c_void_p,
                                                ctypes.c_int, P(pps_params)]
             L.pps_net_sync.argtypes = [c_void_p]
+            L.pps_net_selftest_timeout.argtypes = [c_void_p, c_void_p,
+                                                   ctypes.c_int]
             L.pps_net_set_loss.argtypes = [c_void_p, ctypes.c_float,
                                            ctypes.c_float, ctypes.c_float]
             L.pps_net_set_weights.argtypes = [c_void_p, c_void_p]
@@ -430,6 +432,11 @@ def pps_net_set_features(net, speeds, params=None) -> int:
 
 def pps_net_sync(net) -> int:
     return _check(lib().pps_net_sync(net))
+
+
+def pps_net_selftest_timeout(net, states, n) -> int:
+    """Status of the bounded-wait self-test (PPS_ETIMEOUT expected)."""
+    return lib().pps_net_selftest_timeout(net, states, n)
 
 
 def pps_net_set_loss(net, top_band=float("inf"), low_weight=1.0,

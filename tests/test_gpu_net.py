@@ -228,6 +228,26 @@ def test_tensor_core_forward_on_a_batch(torch):
         net.close()
 
 
+def test_tensor_core_waits_are_bounded(torch):
+    """With the MMAs withheld no mbarrier completes: every wait gives up
+    after its limit, the kernel frees its tensor memory and returns, the
+    host reads PPS_ETIMEOUT, and the network works normally afterwards."""
+    batch = synth.ssl_states(511, 4, K=64)
+    net = pps.Net(max_batch=4, weights=pps.init_weights(22))
+    try:
+        dev = torch.from_numpy(pps.pack_states(batch).view(np.uint8)
+                               .copy()).cuda()
+        st = pps.pps_net_selftest_timeout(net.net, dev.data_ptr(), 4)
+        assert st == pps.PPS_ETIMEOUT, st
+        y = net.forward(dev, 4)
+        lay = torch.empty_like(y)
+        pps.pps_net_forward_layers(net.net, dev.data_ptr(), 4, lay.data_ptr())
+        pps.pps_net_sync(net.net)
+        assert float((y - lay).abs().max()) <= 5e-2
+    finally:
+        net.close()
+
+
 def test_topk_order(torch):
     batch = synth.ssl_states(505, 3, K=32)
     _, cells, pred = _propose(torch, batch, pps.init_weights(12), 256)
