@@ -29,6 +29,10 @@ SCALARS = ("ball_x", "ball_y", "ball_decel", "vmax", "amax",
            "field_len", "field_wid", "goal_width")
 PARAMS = ("w_angle", "w_dist", "w_margin", "margin_cap", "tau_safe",
           "robot_radius", "reach_radius", "min_pass_dist")
+# Parameters of the direction x power search (pps_oracle.h, PPS_ORACLE_D_*).
+DPPS_PARAMS = ("vlo", "vhi", "slide", "tau_delta", "delta_cap", "w_time",
+               "w_angle", "w_dist", "w_refr", "w_delta", "robot_radius",
+               "reach_radius", "min_time")
 
 
 def build(force: bool = False, src: str = _SRC, out: str = _LIB) -> str:
@@ -70,6 +74,15 @@ def _bind(lib):
         [i, p, p, p, i, p, d, i, i, d, d, p, i, p] + [p] * 8 + [i, i])
     lib.pps_oracle_max_threads.restype = i
     lib.pps_oracle_max_threads.argtypes = []
+    lib.pps_oracle_dpps_path.restype = d
+    lib.pps_oracle_dpps_path.argtypes = [p, d, d, d, p]
+    lib.pps_oracle_dpps_group.restype = d
+    lib.pps_oracle_dpps_group.argtypes = [p, i, p, d, d, d, d, p, p]
+    lib.pps_oracle_dpps_candidate.restype = None
+    lib.pps_oracle_dpps_candidate.argtypes = [p, p, i, i, i, i, p]
+    lib.pps_oracle_dpps_search.restype = i
+    lib.pps_oracle_dpps_search.argtypes = [i, p, p, p, p, p, p, i, i, i, p,
+                                           p, p, p, p, p, p, p, i]
     return lib
 
 
@@ -214,6 +227,122 @@ class Oracle:
     def max_threads(self) -> int:
         return self.lib.pps_oracle_max_threads()
 
+    # -- direction x power search (pps_oracle.h, D) --
+    def dpps_path(self, st: DState, u, v):
+        """(path length, stopped) of the ball rolling at v along u."""
+        stopped = ctypes.c_int()
+        S = self.lib.pps_oracle_dpps_path(st.ref, float(u[0]), float(u[1]),
+                                          float(v), ctypes.byref(stopped))
+        return S, bool(stopped.value)
+
+    def dpps_group(self, st: DState, robots, u, v, reach=0.0):
+        """(time, sample k, robot) of a group's first interception."""
+        r = np.ascontiguousarray(np.asarray(robots, np.float64).reshape(-1, 4))
+        k, who = ctypes.c_int(), ctypes.c_int()
+        t = self.lib.pps_oracle_dpps_group(
+            st.ref, r.shape[0], _ptr(r), float(u[0]), float(u[1]), float(v),
+            float(reach), ctypes.byref(k), ctypes.byref(who))
+        return t, k.value, who.value
+
+    def dpps_candidate(self, st: DState, params: dict, ndir, npow, i, j):
+        prm = np.array([float(params[k]) for k in DPPS_PARAMS], np.float64)
+        out = np.empty(8, np.float64)
+        self.lib.pps_oracle_dpps_candidate(st.ref, _ptr(prm), int(ndir),
+                                           int(npow), int(i), int(j),
+                                           _ptr(out))
+        keys = ("t_team", "t_opp", "k_team", "receiver", "rx", "ry",
+                "feasible", "score")
+        return dict(zip(keys, out.tolist()))
+
+    def dpps_search(self, batch: dict, ndir, npow, params: dict, *,
+                    dense=False, n_threads=0):
+        """The direction x power search over a batch with teammates."""
+        ball = np.asarray(batch["ball"], np.float64)
+        S = ball.shape[0]
+        sc = np.ascontiguousarray(np.stack(
+            [ball[:, 0], ball[:, 1]] + [np.asarray(batch[k], np.float64)
+                                        for k in SCALARS[2:]], axis=1))
+        J = max(batch["opp_pos"].shape[1], batch["team_pos"].shape[1])
+
+        def robots(pos, vel):
+            out = np.zeros((S, J, 4), np.float64)
+            n = pos.shape[1]
+            out[:, :n, :2] = pos
+            out[:, :n, 2:] = vel
+            return np.ascontiguousarray(out)
+
+        team = robots(np.asarray(batch["team_pos"], np.float64),
+                      np.asarray(batch["team_vel"], np.float64))
+        opp = robots(np.asarray(batch["opp_pos"], np.float64),
+                     np.asarray(batch["opp_vel"], np.float64))
+        n_team = np.ascontiguousarray(np.asarray(
+            batch.get("n_team", np.full(S, batch["team_pos"].shape[1])),
+            np.int32))
+        n_opp = np.ascontiguousarray(np.asarray(batch["n_opp"], np.int32))
+        K = np.ascontiguousarray(np.asarray(batch["K"], np.int32))
+        prm = np.array([float(params[k]) for k in DPPS_PARAMS], np.float64)
+        C = int(ndir) * int(npow)
+        out = {"best_idx": np.empty(S, np.int64),
+               "best_score": np.empty(S, np.float64),
+               "n_feasible": np.empty(S, np.int64)}
+        if dense:
+            out["feasible"] = np.empty((S, C), np.uint8)
+            out["score"] = np.empty((S, C), np.float64)
+            out["t_team"] = np.empty((S, C), np.float64)
+            out["t_opp"] = np.empty((S, C), np.float64)
+        rc = self.lib.pps_oracle_dpps_search(
+            S, _ptr(sc), _ptr(n_team), _ptr(team), _ptr(n_opp), _ptr(opp),
+            _ptr(K), J, int(ndir), int(npow), _ptr(prm),
+            _ptr(out["best_idx"]), _ptr(out["best_score"]),
+            _ptr(out["n_feasible"]), _ptr(out.get("feasible")),
+            _ptr(out.get("score")), _ptr(out.get("t_team")),
+            _ptr(out.get("t_opp")), int(n_threads))
+        if rc != 0:
+            raise ValueError("oracle rejected the batch")
+        return out
+
+
+class _DState(ctypes.Structure):
+    _fields_ = [("sc", ctypes.c_void_p), ("n_team", ctypes.c_int),
+                ("team", ctypes.c_void_p), ("n_opp", ctypes.c_int),
+                ("opp", ctypes.c_void_p), ("K", ctypes.c_int)]
+
+
+class DState:
+    """One state of the direction x power search (float64 arrays): scalars
+    as ``State``, receivers ``team`` and ``opp`` as (n, 4) x, y, vx, vy."""
+
+    def __init__(self, scalars: dict, team, opp, K: int):
+        self.sc = np.array([float(scalars[k]) for k in SCALARS], np.float64)
+        self.team = np.ascontiguousarray(
+            np.asarray(team, np.float64).reshape(-1, 4))
+        self.opp = np.ascontiguousarray(
+            np.asarray(opp, np.float64).reshape(-1, 4))
+        self.K = int(K)
+        self._c = _DState(_ptr(self.sc), self.team.shape[0], _ptr(self.team),
+                          self.opp.shape[0], _ptr(self.opp), self.K)
+
+    @property
+    def ref(self):
+        return ctypes.byref(self._c)
+
+
+def dstate_of(batch: dict, s: int) -> DState:
+    """State s of a batch with teammates (team_pos, team_vel)."""
+    n = int(batch["n_opp"][s])
+    nt = int(batch["n_team"][s]) if "n_team" in batch else \
+        batch["team_pos"].shape[1]
+    opp = np.concatenate([np.asarray(batch["opp_pos"][s, :n], np.float64),
+                          np.asarray(batch["opp_vel"][s, :n], np.float64)],
+                         axis=1)
+    team = np.concatenate([np.asarray(batch["team_pos"][s, :nt], np.float64),
+                           np.asarray(batch["team_vel"][s, :nt], np.float64)],
+                          axis=1)
+    sc = {"ball_x": batch["ball"][s][0], "ball_y": batch["ball"][s][1]}
+    for k in SCALARS[2:]:
+        sc[k] = batch[k][s]
+    return DState(sc, team, opp, int(batch["K"][s]))
+
 
 def state_of(batch: dict, s: int) -> State:
     """State ``s`` of a batch, in the oracle's layout."""
@@ -243,6 +372,7 @@ def __getattr__(name):
     # Module-level shortcuts: oracle.ball_time(...) == default().ball_time(...)
     if name in ("grid", "ball_time", "intercept_time", "min_intercept",
                 "min_intercept_many",
-                "margin", "shot_angle", "score", "search", "max_threads"):
+                "margin", "shot_angle", "score", "search", "max_threads",
+                "dpps_path", "dpps_group", "dpps_candidate", "dpps_search"):
         return getattr(default(), name)
     raise AttributeError(name)

@@ -309,6 +309,193 @@ int pps_oracle_search(int S, const double* sc, const int* n_opp,
     return 0;
 }
 
+/* ---- D: the paper's own search, directions x kick powers (Sec. 4.2) ---- */
+
+/* READING: the ball rolls from the holder's position b; the path ends where
+ * the ball stops or first reaches the field edge, whichever comes first. */
+double pps_oracle_dpps_path(const pps_oracle_dpps_state* st, double ux,
+                            double uy, double v, int* stopped)
+{
+    double bx = st->sc[PPS_ORACLE_BALL_X], by = st->sc[PPS_ORACLE_BALL_Y];
+    double a = st->sc[PPS_ORACLE_BALL_DECEL];
+    double hl = 0.5 * st->sc[PPS_ORACLE_FIELD_LEN];
+    double hw = 0.5 * st->sc[PPS_ORACLE_FIELD_WID];
+    double s_stop = v * v / (2.0 * a);
+    double s_out = INFINITY;
+    if (ux > 0.0) s_out = fmin(s_out, (hl - bx) / ux);
+    if (ux < 0.0) s_out = fmin(s_out, (-hl - bx) / ux);
+    if (uy > 0.0) s_out = fmin(s_out, (hw - by) / uy);
+    if (uy < 0.0) s_out = fmin(s_out, (-hw - by) / uy);
+    if (s_out < 0.0) s_out = 0.0;
+    *stopped = s_stop <= s_out;
+    return *stopped ? s_stop : s_out;
+}
+
+/* SBIP of a group (Sec. 4.2): the ball's path is searched sample by sample
+ * (READING: K samples uniform in distance, the start excluded, as in C4)
+ * for the first one a robot of the group can reach no later than the
+ * ball; C3 gives each robot's minimum arrival time. */
+double pps_oracle_dpps_group(const pps_oracle_dpps_state* st, int n,
+                             const double* robots, double ux, double uy,
+                             double v, double reach, int* k_out, int* who)
+{
+    double bx = st->sc[PPS_ORACLE_BALL_X], by = st->sc[PPS_ORACLE_BALL_Y];
+    double a = st->sc[PPS_ORACLE_BALL_DECEL];
+    double vmax = st->sc[PPS_ORACLE_VMAX], amax = st->sc[PPS_ORACLE_AMAX];
+    int stopped = 0;
+    double S = pps_oracle_dpps_path(st, ux, uy, v, &stopped);
+    int K = st->K;
+    *k_out = 0;
+    *who = -1;
+    if (n <= 0) return INFINITY;
+    for (int k = 1; k <= K; ++k) {
+        double s = (double)k / (double)K * S;
+        double px = bx + s * ux, py = by + s * uy;
+        /* READING: a path that ends by stopping leaves the ball at rest at
+         * its last sample, time v / a; any robot gets it there. */
+        int last_stop = stopped && k == K;
+        double tk = last_stop ? v / a : pps_oracle_ball_time(s, v, a);
+        double T = INFINITY;
+        int w = -1;
+        for (int r = 0; r < n; ++r) {
+            const double* o = robots + 4 * r;
+            double t = pps_oracle_intercept_time(o[0], o[1], o[2], o[3], px,
+                                                 py, vmax, amax, reach);
+            if (t < T) {
+                T = t;
+                w = r;
+            }
+        }
+        if (T <= tk || last_stop) {
+            *k_out = k;
+            *who = w;
+            return T <= tk ? tk : T;
+        }
+    }
+    return INFINITY;
+}
+
+void pps_oracle_dpps_candidate(const pps_oracle_dpps_state* st,
+                               const double* prm, int ndir, int npow, int i,
+                               int j, double* out)
+{
+    const double pi = 3.14159265358979323846;
+    double phi = 2.0 * pi * (double)i / (double)ndir;
+    double ux = cos(phi), uy = sin(phi);
+    double vlo = prm[PPS_ORACLE_D_VLO], vhi = prm[PPS_ORACLE_D_VHI];
+    double v0 = npow > 1 ? vlo + (double)j * (vhi - vlo) / (double)(npow - 1)
+                         : vlo;
+    /* Sec. 4.1: the kick speed drops to 5/7 in a short slide whose distance
+     * the paper neglects; the ball then rolls from v = slide * v0. */
+    double v = prm[PPS_ORACLE_D_SLIDE] * v0;
+    double reach = prm[PPS_ORACLE_D_REACH_RADIUS];
+    int k_team, who, k_opp, who_opp;
+    double t_team = pps_oracle_dpps_group(st, st->n_team, st->team, ux, uy, v,
+                                          reach, &k_team, &who);
+    double t_opp = pps_oracle_dpps_group(st, st->n_opp, st->opp, ux, uy, v,
+                                         reach, &k_opp, &who_opp);
+    /* Sec. 4.3: safe only when the first opponent comes later than the
+     * first teammate by more than a threshold. */
+    int ok = isfinite(t_team) && (t_opp - t_team > prm[PPS_ORACLE_D_TAU_DELTA]);
+    double px = NAN, py = NAN, score = -INFINITY;
+    if (k_team > 0) {
+        int stopped;
+        double S = pps_oracle_dpps_path(st, ux, uy, v, &stopped);
+        double s = (double)k_team / (double)st->K * S;
+        px = st->sc[PPS_ORACLE_BALL_X] + s * ux;
+        py = st->sc[PPS_ORACLE_BALL_Y] + s * uy;
+    }
+    if (ok) {
+        double L = st->sc[PPS_ORACLE_FIELD_LEN], W = st->sc[PPS_ORACLE_FIELD_WID];
+        pps_oracle_state os;
+        os.sc = st->sc;
+        os.n_opp = st->n_opp;
+        os.opp = st->opp;
+        os.K = st->K;
+        double theta = pps_oracle_shot_angle(&os, px, py,
+                                             prm[PPS_ORACLE_D_ROBOT_RADIUS]);
+        double gx = 0.5 * L - px, gy = -py;
+        double dg = sqrt(gx * gx + gy * gy);
+        /* READING: the refraction angle of Sec. 4.3 is the turn between the
+         * pass direction and the shot direction from the receive point. */
+        double refr = 0.0;
+        if (dg > 0.0) {
+            double c = (ux * gx + uy * gy) / dg;
+            refr = acos(c > 1.0 ? 1.0 : (c < -1.0 ? -1.0 : c));
+        }
+        double delta = t_opp - t_team;
+        double cap = prm[PPS_ORACLE_D_DELTA_CAP];
+        score = -prm[PPS_ORACLE_D_W_TIME] * t_team
+              + prm[PPS_ORACLE_D_W_ANGLE] * theta / pi
+              - prm[PPS_ORACLE_D_W_DIST] * dg / sqrt(L * L + W * W)
+              - prm[PPS_ORACLE_D_W_REFR] * refr / pi
+              + prm[PPS_ORACLE_D_W_DELTA] * (delta < cap ? delta : cap);
+    }
+    out[0] = t_team;
+    out[1] = t_opp;
+    out[2] = (double)k_team;
+    out[3] = (double)who;
+    out[4] = px;
+    out[5] = py;
+    out[6] = (double)ok;
+    out[7] = score;
+}
+
+int pps_oracle_dpps_search(int S, const double* sc, const int* n_team,
+                           const double* team, const int* n_opp,
+                           const double* opp, const int* K, int jstride,
+                           int ndir, int npow, const double* prm,
+                           int64_t* best_idx, double* best_score,
+                           int64_t* n_feasible, uint8_t* feasible,
+                           double* score, double* t_team, double* t_opp,
+                           int n_threads)
+{
+    if (S < 0 || ndir < 1 || npow < 1) return -1;
+    for (int s = 0; s < S; ++s)
+        if (n_team[s] < 0 || n_team[s] > jstride || n_opp[s] < 0
+            || n_opp[s] > jstride || K[s] < 1)
+            return -1;
+    int64_t C = (int64_t)ndir * npow;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int s = 0; s < S; ++s) {
+        pps_oracle_dpps_state st;
+        st.sc = sc + (int64_t)s * PPS_ORACLE_NSCALAR;
+        st.n_team = n_team[s];
+        st.team = team + (int64_t)s * jstride * 4;
+        st.n_opp = n_opp[s];
+        st.opp = opp + (int64_t)s * jstride * 4;
+        st.K = K[s];
+        int64_t bi = -1, nf = 0;
+        double bs = -INFINITY;
+        for (int i = 0; i < ndir; ++i)
+            for (int j = 0; j < npow; ++j) {
+                double out[8];
+                pps_oracle_dpps_candidate(&st, prm, ndir, npow, i, j, out);
+                int64_t idx = (int64_t)i * npow + j;
+                int64_t o = (int64_t)s * C + idx;
+                if (feasible) feasible[o] = (uint8_t)out[6];
+                if (score) score[o] = out[7];
+                if (t_team) t_team[o] = out[0];
+                if (t_opp) t_opp[o] = out[1];
+                if (out[6] != 0.0) {
+                    ++nf;
+                    if (bi < 0 || out[7] > bs) {
+                        bi = idx;
+                        bs = out[7];
+                    }
+                }
+            }
+        best_idx[s] = bi;
+        best_score[s] = bs;
+        n_feasible[s] = nf;
+    }
+    (void)n_threads;
+    return 0;
+}
+
 int pps_oracle_max_threads(void)
 {
 #ifdef _OPENMP

@@ -122,6 +122,80 @@ int pps_oracle_search(int S, const double* sc, const int* n_opp,
                       double* T, int kstride, int n_threads);
 
 /* Threads the OpenMP runtime will use (1 without OpenMP). */
+/* ---- D: the paper's own search, directions x kick powers (Sec. 4.2) ----
+ *
+ * From the ball holder at b, candidate passes are ndir directions
+ * (phi_i = 2 pi i / ndir) x npow kick powers (v0_j uniform in [vlo, vhi]);
+ * for every candidate the ball's path is searched for the first teammate
+ * and the first opponent interception (SBIP), and feasible candidates are
+ * scored with the features of Sec. 4.3.  Parameters, 13 doubles: */
+enum {
+    PPS_ORACLE_D_VLO = 0,        /* lowest kick power (m/s) */
+    PPS_ORACLE_D_VHI = 1,        /* highest kick power */
+    PPS_ORACLE_D_SLIDE = 2,      /* rolling speed / kick speed (5/7) */
+    PPS_ORACLE_D_TAU_DELTA = 3,  /* feasible iff t_opp - t_team > this */
+    PPS_ORACLE_D_DELTA_CAP = 4,  /* cap of the delta-time feature (s) */
+    PPS_ORACLE_D_W_TIME = 5,     /* weight of -t_team */
+    PPS_ORACLE_D_W_ANGLE = 6,    /* weight of the shot angle / pi */
+    PPS_ORACLE_D_W_DIST = 7,     /* weight of -|g - p| / diag */
+    PPS_ORACLE_D_W_REFR = 8,     /* weight of -refraction angle / pi */
+    PPS_ORACLE_D_W_DELTA = 9,    /* weight of min(t_opp - t_team, cap) */
+    PPS_ORACLE_D_ROBOT_RADIUS = 10,
+    PPS_ORACLE_D_REACH_RADIUS = 11,
+    PPS_ORACLE_D_MIN_TIME = 12,  /* reserved, 0 */
+    PPS_ORACLE_D_NPARAM = 13
+};
+
+/* A state of the direction x power search: scalars as above (the ball is
+ * at the passer's feet), n_team receivers and n_opp opponents (x, y, vx,
+ * vy each), K samples along each ball path. */
+typedef struct {
+    const double* sc;
+    int n_team;
+    const double* team; /* n_team x 4 */
+    int n_opp;
+    const double* opp;  /* n_opp x 4 */
+    int K;
+} pps_oracle_dpps_state;
+
+/* Length of the ball's path from b along direction (ux, uy) at rolling
+ * speed v: the stopping distance, or the distance to the field edge if
+ * that comes first (*stopped = 0 then). */
+double pps_oracle_dpps_path(const pps_oracle_dpps_state* st, double ux,
+                            double uy, double v, int* stopped);
+
+/* First interception of the ball's path by one group of robots (n x 4):
+ * the first sample k = 1..K whose ball time t_k is not earlier than the
+ * group's minimum intercept time there; at the stop sample of a path that
+ * ends by stopping, the group always gets the ball, at max(T, t_K).
+ * Returns the time (+inf if none); *k_out = k (0 if none); *who = the
+ * robot with the minimum intercept time at that sample. */
+double pps_oracle_dpps_group(const pps_oracle_dpps_state* st, int n,
+                             const double* robots, double ux, double uy,
+                             double v, double reach, int* k_out, int* who);
+
+/* One candidate (direction i of ndir, power j of npow): out[0] t_team,
+ * out[1] t_opp, out[2] k_team, out[3] receiver, out[4] receive x,
+ * out[5] receive y, out[6] feasible (0/1), out[7] score (-inf if not). */
+void pps_oracle_dpps_candidate(const pps_oracle_dpps_state* st,
+                               const double* prm, int ndir, int npow, int i,
+                               int j, double* out);
+
+/* The search over S states: state s has scalars sc + 8 s, n_team[s]
+ * receivers at team + 4 jstride s, n_opp[s] opponents at opp + 4 jstride s,
+ * K[s] samples.  Best idx = i * npow + j (-1 if none; equal scores go to
+ * the smaller idx), its score and the feasible count; optional dense
+ * outputs of S x ndir x npow: feasible, score, t_team, t_opp.  Returns 0,
+ * or -1 on bad arguments. */
+int pps_oracle_dpps_search(int S, const double* sc, const int* n_team,
+                           const double* team, const int* n_opp,
+                           const double* opp, const int* K, int jstride,
+                           int ndir, int npow, const double* prm,
+                           int64_t* best_idx, double* best_score,
+                           int64_t* n_feasible, uint8_t* feasible,
+                           double* score, double* t_team, double* t_opp,
+                           int n_threads);
+
 int pps_oracle_max_threads(void);
 
 #ifdef __cplusplus
