@@ -586,6 +586,90 @@ pps_status pps_propose(pps_ctx* ctx, pps_net* net, const pps_state* states,
 pps_status pps_launch_info(const pps_ctx* ctx, int* num_sms,
                            int* ctas_per_sm);
 
+/* ---- Directions x kick powers: the paper's own search (Sec. 4.2) -------
+ *
+ * From the ball holder, candidate passes are n_dir directions
+ * (phi_i = 2 pi i / n_dir) x n_pow kick powers (v0_j uniform in
+ * [v_lo, v_hi]; the paper: 128 x 64 over 1..6.5 m/s).  The ball rolls from
+ * v = slide * v0 (Sec. 4.1: the kick speed drops to 5/7 in a short slide
+ * whose distance is neglected) with the state's deceleration, until it
+ * stops or reaches the field edge.  For every candidate the path is
+ * searched, K samples uniform in distance, for the first sample a teammate
+ * (receiver) can reach no later than the ball (SBIP, with the bang-bang
+ * robot model of pps_search), and likewise for the opponents; at the stop
+ * sample of a path that ends by stopping every robot gets the ball, at
+ * max(its arrival, the stop time).  A candidate is feasible when a
+ * teammate gets the ball and the first opponent comes more than tau_delta
+ * later (the delta-time of Sec. 4.3).  Its score (Sec. 4.3 features):
+ *   - w_time * t_team + w_angle * shot angle at the receive point / pi
+ *   - w_dist * |goal - receive point| / diag
+ *   - w_refr * refraction angle / pi   (the turn from the pass direction to
+ *                                       the shot direction)
+ *   + w_delta * min(t_opp - t_team, delta_cap).
+ * The best candidate is the highest score; equal scores go to the smaller
+ * idx = dir * n_pow + pow. */
+
+#define PPS_MAX_TEAM 16
+
+typedef struct pps_dstate {
+    float ball[2];                   /* the ball, at the passer's feet (m) */
+    int32_t n_team;                  /* receivers, 0..PPS_MAX_TEAM */
+    int32_t n_opp;                   /* opponents, 0..PPS_MAX_OPP */
+    float team_pos[PPS_MAX_TEAM][2]; /* receivers (the passer excluded) */
+    float team_vel[PPS_MAX_TEAM][2];
+    float opp_pos[PPS_MAX_OPP][2];
+    float opp_vel[PPS_MAX_OPP][2];
+    float ball_decel;                /* rolling deceleration (m/s^2) */
+    float vmax, amax;                /* robot limits (both teams) */
+    float field_len, field_wid, goal_width;
+    int32_t K;                       /* samples per ball path, 1..PPS_MAX_K */
+} pps_dstate;
+
+typedef struct pps_dparams {
+    int32_t n_dir, n_pow;  /* 1..1024 directions, 1..256 powers */
+    float v_lo, v_hi;      /* kick power range (m/s), 0 < v_lo <= v_hi */
+    float slide;           /* rolling speed / kick speed, in (0, 1] */
+    float tau_delta;       /* delta-time threshold (s) */
+    float delta_cap;       /* cap of the delta-time feature (s) */
+    float w_time, w_angle, w_dist, w_refr, w_delta;
+    float robot_radius;    /* disc radius for shot blocking (m) */
+    float reach_radius;    /* intercept reach radius (m) */
+} pps_dparams;
+
+typedef struct pps_dbest {
+    int32_t idx;           /* dir * n_pow + pow; -1: none feasible; -2:
+                              invalid state */
+    int32_t dir, pow;      /* -1 when idx < 0 */
+    int32_t receiver;      /* index into team_pos of the first teammate */
+    float score;           /* -inf when idx < 0 */
+    float t_team, t_opp;   /* first teammate / opponent ball time (s);
+                              t_opp = +inf when no opponent gets the ball */
+    float recv[2];         /* receive point (m) */
+    int32_t n_feasible;
+    int32_t status;        /* PPS_STATE_* flags as in pps_best */
+    int32_t reserved;
+} pps_dbest;
+
+/* Defaults: 128 x 64 over 1..6.5 m/s, slide 5/7, tau_delta 0, delta_cap
+ * 1 s, all weights 1, robot radius 0.09 m, reach 0. */
+pps_status pps_dpps_default_params(pps_dparams* out);
+
+/* Mask words per state: ceil(n_dir * n_pow / 32); bit b of word w is the
+ * candidate 32 w + b in idx order. */
+size_t pps_dpps_mask_words(const pps_dparams* params);
+
+/* The search over n_states states (n_states <= the context's max_states).
+ * states, out_best (n_states records), out_mask (n_states x
+ * pps_dpps_mask_words, or NULL) and out_dbg (NULL, or n_states x n_dir x
+ * n_pow x 3 floats: t_team, t_opp, score of every candidate, for tests)
+ * are device memory.  Enqueued on the context's stream.  EINVAL on bad
+ * parameters; a state whose n_team or n_opp exceeds the context's max_opp,
+ * or with values out of range, gets idx -2 and PPS_STATE_INVALID. */
+pps_status pps_dpps_search(pps_ctx* ctx, const pps_dstate* states,
+                           int n_states, const pps_dparams* params,
+                           pps_dbest* out_best, uint32_t* out_mask,
+                           float* out_dbg);
+
 #ifdef __cplusplus
 }
 #endif

@@ -246,12 +246,12 @@ class Oracle:
 
     def dpps_candidate(self, st: DState, params: dict, ndir, npow, i, j):
         prm = np.array([float(params[k]) for k in DPPS_PARAMS], np.float64)
-        out = np.empty(8, np.float64)
+        out = np.empty(10, np.float64)
         self.lib.pps_oracle_dpps_candidate(st.ref, _ptr(prm), int(ndir),
                                            int(npow), int(i), int(j),
                                            _ptr(out))
         keys = ("t_team", "t_opp", "k_team", "receiver", "rx", "ry",
-                "feasible", "score")
+                "feasible", "score", "m_team", "m_opp")
         return dict(zip(keys, out.tolist()))
 
     def dpps_search(self, batch: dict, ndir, npow, params: dict, *,

@@ -339,6 +339,16 @@ double pps_oracle_dpps_group(const pps_oracle_dpps_state* st, int n,
                              const double* robots, double ux, double uy,
                              double v, double reach, int* k_out, int* who)
 {
+    return pps_oracle_dpps_group_margin(st, n, robots, ux, uy, v, reach,
+                                        k_out, who, NULL);
+}
+
+double pps_oracle_dpps_group_margin(const pps_oracle_dpps_state* st, int n,
+                                    const double* robots, double ux,
+                                    double uy, double v, double reach,
+                                    int* k_out, int* who, double* margin)
+{
+    if (margin) *margin = INFINITY;
     double bx = st->sc[PPS_ORACLE_BALL_X], by = st->sc[PPS_ORACLE_BALL_Y];
     double a = st->sc[PPS_ORACLE_BALL_DECEL];
     double vmax = st->sc[PPS_ORACLE_VMAX], amax = st->sc[PPS_ORACLE_AMAX];
@@ -366,6 +376,9 @@ double pps_oracle_dpps_group(const pps_oracle_dpps_state* st, int n,
                 w = r;
             }
         }
+        /* how far from flipping each searched sample's decision was */
+        if (margin && !last_stop && fabs(T - tk) < *margin)
+            *margin = fabs(T - tk);
         if (T <= tk || last_stop) {
             *k_out = k;
             *who = w;
@@ -390,10 +403,13 @@ void pps_oracle_dpps_candidate(const pps_oracle_dpps_state* st,
     double v = prm[PPS_ORACLE_D_SLIDE] * v0;
     double reach = prm[PPS_ORACLE_D_REACH_RADIUS];
     int k_team, who, k_opp, who_opp;
-    double t_team = pps_oracle_dpps_group(st, st->n_team, st->team, ux, uy, v,
-                                          reach, &k_team, &who);
-    double t_opp = pps_oracle_dpps_group(st, st->n_opp, st->opp, ux, uy, v,
-                                         reach, &k_opp, &who_opp);
+    double m_team, m_opp;
+    double t_team = pps_oracle_dpps_group_margin(st, st->n_team, st->team, ux,
+                                                 uy, v, reach, &k_team, &who,
+                                                 &m_team);
+    double t_opp = pps_oracle_dpps_group_margin(st, st->n_opp, st->opp, ux, uy,
+                                                v, reach, &k_opp, &who_opp,
+                                                &m_opp);
     /* Sec. 4.3: safe only when the first opponent comes later than the
      * first teammate by more than a threshold. */
     int ok = isfinite(t_team) && (t_opp - t_team > prm[PPS_ORACLE_D_TAU_DELTA]);
@@ -439,6 +455,8 @@ void pps_oracle_dpps_candidate(const pps_oracle_dpps_state* st,
     out[5] = py;
     out[6] = (double)ok;
     out[7] = score;
+    out[8] = m_team;
+    out[9] = m_opp;
 }
 
 int pps_oracle_dpps_search(int S, const double* sc, const int* n_team,
@@ -472,7 +490,7 @@ int pps_oracle_dpps_search(int S, const double* sc, const int* n_team,
         double bs = -INFINITY;
         for (int i = 0; i < ndir; ++i)
             for (int j = 0; j < npow; ++j) {
-                double out[8];
+                double out[10];
                 pps_oracle_dpps_candidate(&st, prm, ndir, npow, i, j, out);
                 int64_t idx = (int64_t)i * npow + j;
                 int64_t o = (int64_t)s * C + idx;

@@ -174,9 +174,18 @@ double pps_oracle_dpps_group(const pps_oracle_dpps_state* st, int n,
                              const double* robots, double ux, double uy,
                              double v, double reach, int* k_out, int* who);
 
+/* The same, also giving the smallest |T - t_ball| over the samples it
+ * searched before deciding (+inf if none): how far the decision was from
+ * flipping. */
+double pps_oracle_dpps_group_margin(const pps_oracle_dpps_state* st, int n,
+                                    const double* robots, double ux,
+                                    double uy, double v, double reach,
+                                    int* k_out, int* who, double* margin);
+
 /* One candidate (direction i of ndir, power j of npow): out[0] t_team,
  * out[1] t_opp, out[2] k_team, out[3] receiver, out[4] receive x,
- * out[5] receive y, out[6] feasible (0/1), out[7] score (-inf if not). */
+ * out[5] receive y, out[6] feasible (0/1), out[7] score (-inf if not),
+ * out[8] / out[9] the teammate / opponent decision margins. */
 void pps_oracle_dpps_candidate(const pps_oracle_dpps_state* st,
                                const double* prm, int ndir, int npow, int i,
                                int j, double* out);

@@ -347,29 +347,30 @@ __device__ __forceinline__ void sample_loop(const StateK& sk,
     }
 }
 
-// A5: largest opponent-free angular gap of the goal mouth seen from c.
+// A5: largest opponent-free angular gap of the goal mouth seen from c
+// (opponents opp[0..nopp) as discs of radius r; hw = half mouth width).
 template <int JMAX>
-__device__ __forceinline__ float shot_angle(const pps_state& st,
-                                            const StateK& sk, bool front,
-                                            float cx, float cy, float gx,
-                                            float r) {
+__device__ __forceinline__ float shot_angle_of(const float (*opp)[2],
+                                               int nopp, float hw, bool front,
+                                               float cx, float cy, float gx,
+                                               float r) {
     if (!front) return 0.f;
-    const float lo = atan2f(__fsub_rn(-sk.hw, cy), gx);
-    const float hi = atan2f(__fsub_rn(sk.hw, cy), gx);
+    const float lo = atan2f(__fsub_rn(-hw, cy), gx);
+    const float hi = atan2f(__fsub_rn(hw, cy), gx);
     float s[JMAX], e[JMAX];
     bool all = false;
     const float r2 = __fmul_rn(r, r);
     // Post directions from c: A to the lower post, B to the upper one.
-    const float ax = gx, ay = __fsub_rn(-sk.hw, cy), by = __fsub_rn(sk.hw, cy);
+    const float ax = gx, ay = __fsub_rn(-hw, cy), by = __fsub_rn(hw, cy);
     const float a2r2 = __fmul_rn(__fmaf_rn(ax, ax, __fmul_rn(ay, ay)), r2);
     const float b2r2 = __fmul_rn(__fmaf_rn(ax, ax, __fmul_rn(by, by)), r2);
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
         s[j] = 1e30f;
         e[j] = 1e30f;
-        if (j < sk.nopp) {
-            const float dx = __fsub_rn(st.opp_pos[j][0], cx);
-            const float dy = __fsub_rn(st.opp_pos[j][1], cy);
+        if (j < nopp) {
+            const float dx = __fsub_rn(opp[j][0], cx);
+            const float dy = __fsub_rn(opp[j][1], cy);
             const float d2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
             all |= d2 <= r2;
             // A disc can block part of the mouth only if its centre lies in
@@ -416,6 +417,15 @@ __device__ __forceinline__ float shot_angle(const pps_state& st,
     }
     if (cur < hi) best = fmaxf(best, __fsub_rn(hi, cur));
     return best;
+}
+
+template <int JMAX>
+__device__ __forceinline__ float shot_angle(const pps_state& st,
+                                            const StateK& sk, bool front,
+                                            float cx, float cy, float gx,
+                                            float r) {
+    return shot_angle_of<JMAX>(st.opp_pos, sk.nopp, sk.hw, front, cx, cy, gx,
+                               r);
 }
 
 // Everything per grid point (A2..A6): margins, feasibility and scores for

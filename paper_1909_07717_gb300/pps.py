@@ -138,6 +138,36 @@ BEST_DTYPE = np.dtype([("idx", "<i4"), ("ix", "<i4"), ("iy", "<i4"),
 assert STATE_DTYPE.itemsize == ctypes.sizeof(pps_state) == 296
 assert BEST_DTYPE.itemsize == ctypes.sizeof(pps_best) == 32
 
+# the direction x power search (pps_dpps_*)
+PPS_MAX_TEAM = 16
+
+
+class pps_dparams(ctypes.Structure):
+    _fields_ = [("n_dir", c_int32), ("n_pow", c_int32), ("v_lo", c_float),
+                ("v_hi", c_float), ("slide", c_float), ("tau_delta", c_float),
+                ("delta_cap", c_float), ("w_time", c_float),
+                ("w_angle", c_float), ("w_dist", c_float),
+                ("w_refr", c_float), ("w_delta", c_float),
+                ("robot_radius", c_float), ("reach_radius", c_float)]
+
+
+DSTATE_DTYPE = np.dtype([("ball", "<f4", (2,)), ("n_team", "<i4"),
+                         ("n_opp", "<i4"),
+                         ("team_pos", "<f4", (PPS_MAX_TEAM, 2)),
+                         ("team_vel", "<f4", (PPS_MAX_TEAM, 2)),
+                         ("opp_pos", "<f4", (PPS_MAX_OPP, 2)),
+                         ("opp_vel", "<f4", (PPS_MAX_OPP, 2)),
+                         ("ball_decel", "<f4"), ("vmax", "<f4"),
+                         ("amax", "<f4"), ("field_len", "<f4"),
+                         ("field_wid", "<f4"), ("goal_width", "<f4"),
+                         ("K", "<i4")])
+DBEST_DTYPE = np.dtype([("idx", "<i4"), ("dir", "<i4"), ("pow", "<i4"),
+                        ("receiver", "<i4"), ("score", "<f4"),
+                        ("t_team", "<f4"), ("t_opp", "<f4"),
+                        ("recv", "<f4", (2,)), ("n_feasible", "<i4"),
+                        ("status", "<i4"), ("reserved", "<i4")])
+assert DSTATE_DTYPE.itemsize == 556 and DBEST_DTYPE.itemsize == 48
+
 EXPORTS = ("pps_abi_version", "pps_status_string", "pps_last_error",
            "pps_default_params", "pps_grid_from_field", "pps_mask_words",
            "pps_create", "pps_destroy", "pps_search", "pps_sync", "pps_reset",
@@ -150,7 +180,8 @@ EXPORTS = ("pps_abi_version", "pps_status_string", "pps_last_error",
            "pps_net_sync", "pps_net_selftest_timeout",
            "pps_net_get_weights", "pps_net_raster", "pps_net_forward_layers",
            "pps_net_forward", "pps_net_grad", "pps_net_train_step",
-           "pps_net_labels", "pps_propose")
+           "pps_net_labels", "pps_propose", "pps_dpps_default_params",
+           "pps_dpps_mask_words", "pps_dpps_search")
 
 
 class PpsError(RuntimeError):
@@ -257,6 +288,12 @@ def lib():
                                       ctypes.c_int, P(pps_params),
                                       ctypes.c_int, ctypes.c_uint, c_void_p,
                                       c_void_p]
+            L.pps_dpps_default_params.argtypes = [P(pps_dparams)]
+            L.pps_dpps_mask_words.restype = c_size_t
+            L.pps_dpps_mask_words.argtypes = [P(pps_dparams)]
+            L.pps_dpps_search.argtypes = [c_void_p, c_void_p, ctypes.c_int,
+                                          P(pps_dparams), c_void_p, c_void_p,
+                                          c_void_p]
             if L.pps_abi_version() != PPS_ABI_VERSION:
                 raise RuntimeError("libpps ABI version mismatch")
             _lib = L
@@ -497,6 +534,52 @@ def pps_propose(ctx, net, states, n, fine_grid, speeds, params, topk, flags,
         ctx, net, states, n, ctypes.byref(fine_grid), sp.ctypes.data, len(sp),
         ctypes.byref(params) if params is not None else None, topk, flags,
         out_best, out_cells), ctx)
+
+
+def pps_dpps_default_params() -> pps_dparams:
+    p = pps_dparams()
+    _check(lib().pps_dpps_default_params(ctypes.byref(p)))
+    return p
+
+
+def pps_dpps_mask_words(params: pps_dparams) -> int:
+    return int(lib().pps_dpps_mask_words(ctypes.byref(params)))
+
+
+def pps_dpps_search(ctx, states, n_states, params, out_best, out_mask=None,
+                    out_dbg=None):
+    """Device addresses for states, out_best, out_mask and out_dbg."""
+    return _check(lib().pps_dpps_search(
+        ctx, states, n_states,
+        ctypes.byref(params) if params is not None else None, out_best,
+        out_mask, out_dbg), ctx)
+
+
+def dparams_from_dict(d: dict | None) -> pps_dparams:
+    p = pps_dpps_default_params()
+    for k, v in (d or {}).items():
+        setattr(p, k, int(v) if k in ("n_dir", "n_pow") else float(v))
+    return p
+
+
+def pack_dstates(batch: dict) -> np.ndarray:
+    """A batch with teammates (team_pos, team_vel) -> pps_dstate records."""
+    S = batch["ball"].shape[0]
+    out = np.zeros(S, DSTATE_DTYPE)
+    out["ball"] = batch["ball"]
+    nt, no = batch["team_pos"].shape[1], batch["opp_pos"].shape[1]
+    if nt > PPS_MAX_TEAM or no > PPS_MAX_OPP:
+        raise ValueError("more robots than PPS_MAX_TEAM / PPS_MAX_OPP")
+    out["n_team"] = batch.get("n_team", np.full(S, nt))
+    out["n_opp"] = batch["n_opp"]
+    out["team_pos"][:, :nt] = batch["team_pos"]
+    out["team_vel"][:, :nt] = batch["team_vel"]
+    out["opp_pos"][:, :no] = batch["opp_pos"]
+    out["opp_vel"][:, :no] = batch["opp_vel"]
+    for k in ("ball_decel", "vmax", "amax", "field_len", "field_wid",
+              "goal_width", "K"):
+        out[k] = batch[k]
+    return out
 
 
 def pps_sync(ctx) -> int:

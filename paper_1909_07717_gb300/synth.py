@@ -165,6 +165,37 @@ PROPOSAL = Workload("proposal_4096x481x361_v4_K64_J8", seed=7, n_states=4096,
                     spacing=0.025, speeds=[2.0, 3.5, 5.0, 6.5], K=64)
 
 
+# The paper's own search parameterisation (directions x kick powers,
+# Sec. 4.2): 12x9 m, 16 receivers and 16 opponents (the paper's 32 robots on
+# the field), K = 64 samples per ball path, 128 directions x 64 kick powers
+# in [1, 6.5] m/s; the ball at the passer's feet.
+DPPS_SEED = 5
+DPPS_STATES = 1024
+DPPS_PARAMS = {"n_dir": 128, "n_pow": 64, "v_lo": 1.0, "v_hi": 6.5,
+               "slide": 5.0 / 7.0, "tau_delta": 0.0, "delta_cap": 1.0,
+               "w_time": 1.0, "w_angle": 1.0, "w_dist": 1.0, "w_refr": 1.0,
+               "w_delta": 1.0, "robot_radius": 0.09, "reach_radius": 0.0}
+
+
+def dpps_states(seed: int, n_states: int, *, n_team: int = 16,
+                n_opp: int = 16, K: int = 64) -> dict:
+    """States with receivers (team_pos, team_vel) for the direction x power
+    search: uniform positions, speeds U[0, vmax], uniform headings."""
+    b = ssl_states(seed, n_states, n_opp=n_opp, n_team=n_team, K=K)
+    b["n_team"] = np.full(n_states, n_team, np.int32)
+    return b
+
+
+def dpps_oracle_params(p: dict = DPPS_PARAMS) -> dict:
+    """The same parameters under the oracle's names."""
+    return {"vlo": p["v_lo"], "vhi": p["v_hi"], "slide": p["slide"],
+            "tau_delta": p["tau_delta"], "delta_cap": p["delta_cap"],
+            "w_time": p["w_time"], "w_angle": p["w_angle"],
+            "w_dist": p["w_dist"], "w_refr": p["w_refr"],
+            "w_delta": p["w_delta"], "robot_radius": p["robot_radius"],
+            "reach_radius": p["reach_radius"], "min_time": 0.0}
+
+
 def uneven_batch(seed: int, n_states: int, *,
                  spacings=(0.025, 0.05, 0.1), k_range=(32, 128),
                  speed_range=(2.0, 6.5), decel_range=(0.3, 0.7),

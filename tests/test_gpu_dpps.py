@@ -1,0 +1,160 @@
+"""The direction x power search (the paper's own parameterisation,
+Sec. 4.2) on the GPU against the FP64 oracle.
+
+Every candidate's teammate and opponent interception times, feasibility
+and score are compared wherever the oracle's sampled decisions are not
+within 0.1 ms of flipping (FP32 and FP64 may take such a decision
+differently, and then the first interception moves by a sample); the best
+candidate is compared through the oracle's score of it.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_07717_gb300 import pps, synth
+
+pytestmark = pytest.mark.gpu
+EPS = 1e-4
+
+
+@pytest.fixture(scope="module")
+def searcher():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_07717_gb300 import build
+    build.build()
+    s = pps.Searcher(max_states=1024, max_opp=16)
+    yield s
+    s.close()
+
+
+def _run(s, batch, prm, dbg=True):
+    torch = s.torch
+    n = batch["ball"].shape[0]
+    p = pps.dparams_from_dict(prm)
+    rec = torch.from_numpy(pps.pack_dstates(batch).view(np.uint8).copy()).cuda()
+    best = torch.empty(n * 48, dtype=torch.uint8, device="cuda")
+    words = pps.pps_dpps_mask_words(p)
+    mask = torch.full((n, words), -1, dtype=torch.int32, device="cuda")
+    C = p.n_dir * p.n_pow
+    d = torch.empty((n, C, 3), dtype=torch.float32, device="cuda") if dbg else None
+    pps.pps_dpps_search(s.ctx, rec.data_ptr(), n, p, best.data_ptr(),
+                        mask.data_ptr(), d.data_ptr() if dbg else None)
+    torch.cuda.synchronize()
+    b = np.frombuffer(best.cpu().numpy().tobytes(), pps.DBEST_DTYPE)
+    m = mask.cpu().numpy().view(np.uint32)
+    bits = np.unpackbits(m.view(np.uint8), axis=1, bitorder="little")[:, :C]
+    return b, bits, (d.cpu().numpy() if dbg else None)
+
+
+def _oracle_candidates(batch, prm, s):
+    st = oracle.dstate_of(batch, s)
+    op = synth.dpps_oracle_params(prm)
+    return [[oracle.dpps_candidate(st, op, prm["n_dir"], prm["n_pow"], i, j)
+             for j in range(prm["n_pow"])] for i in range(prm["n_dir"])]
+
+
+def _close(a, b, tol):
+    if math.isinf(a) or math.isinf(b):
+        return math.isinf(a) and math.isinf(b)
+    return abs(a - b) <= tol * (1.0 + abs(b))
+
+
+@pytest.mark.parametrize("n_pow", [32, 24])
+def test_candidates_match_the_oracle(searcher, n_pow):
+    prm = dict(synth.DPPS_PARAMS, n_dir=32, n_pow=n_pow)
+    batch = synth.dpps_states(31, 4, n_team=6, n_opp=7, K=32)
+    best, bits, dbg = _run(searcher, batch, prm)
+    checked = total = 0
+    for s in range(4):
+        ref = _oracle_candidates(batch, prm, s)
+        for i in range(prm["n_dir"]):
+            for j in range(n_pow):
+                c = ref[i][j]
+                idx = i * n_pow + j
+                g_tt, g_to, g_sc = dbg[s, idx]
+                total += 1
+                # the mask and the debug output agree everywhere
+                assert bits[s, idx] == (g_sc > -np.inf)
+                if c["m_team"] <= EPS:
+                    continue
+                assert _close(g_tt, c["t_team"], 1e-5), (s, i, j)
+                if math.isinf(c["t_team"]):
+                    assert bits[s, idx] == 0
+                    checked += 1
+                    continue
+                if c["m_opp"] <= EPS:
+                    continue
+                assert _close(g_to, c["t_opp"], 1e-5), (s, i, j)
+                gap = c["t_opp"] - c["t_team"] - prm["tau_delta"]
+                if abs(gap) <= EPS:
+                    continue
+                assert bits[s, idx] == int(c["feasible"]), (s, i, j)
+                if c["feasible"]:
+                    assert abs(g_sc - c["score"]) <= 1e-4, (s, i, j, g_sc, c)
+                checked += 1
+        # the best: its oracle score is the oracle's best
+        fe = [(c["score"], i * n_pow + j) for i in range(prm["n_dir"])
+              for j, c in enumerate(ref[i]) if c["feasible"]]
+        b = best[s]
+        assert b["status"] == 0
+        if not fe:
+            assert b["idx"] == -1
+            continue
+        ob = max(fe)[0]
+        gi = int(b["idx"])
+        assert gi >= 0 and bits[s, gi] == 1
+        gc = ref[gi // n_pow][gi % n_pow]
+        assert gc["feasible"] and abs(gc["score"] - ob) <= 2e-4, (gc, ob)
+        assert abs(float(b["score"]) - ob) <= 2e-4
+        assert b["n_feasible"] == bits[s].sum()
+        assert b["dir"] == gi // n_pow and b["pow"] == gi % n_pow
+    assert checked >= 0.9 * total, (checked, total)
+
+
+def test_full_size_states_against_the_oracle(searcher):
+    """The benchmark's shape (16 v 16, 128 x 64 over 1..6.5 m/s, K = 64) on
+    64 states: every record's bookkeeping, and the best of four states
+    against the oracle's full search."""
+    prm = dict(synth.DPPS_PARAMS)
+    batch = synth.dpps_states(synth.DPPS_SEED, 64)
+    best, bits, _ = _run(searcher, batch, prm, dbg=False)
+    assert np.all(best["status"] == 0)
+    assert np.array_equal(best["n_feasible"], bits.sum(axis=1))
+    has = best["idx"] >= 0
+    assert np.all(bits[has, best["idx"][has]] == 1)
+    take = [0, 1, 2, 3]
+    sub = {k: (v[take] if isinstance(v, np.ndarray) else v)
+           for k, v in batch.items()}
+    ref = oracle.dpps_search(sub, prm["n_dir"], prm["n_pow"],
+                             synth.dpps_oracle_params(prm))
+    for t, s in enumerate(take):
+        if ref["best_idx"][t] < 0:
+            assert best[s]["idx"] == -1
+            continue
+        st = oracle.dstate_of(batch, s)
+        gi = int(best[s]["idx"])
+        gc = oracle.dpps_candidate(st, synth.dpps_oracle_params(prm),
+                                   prm["n_dir"], prm["n_pow"],
+                                   gi // prm["n_pow"], gi % prm["n_pow"])
+        assert gc["feasible"]
+        assert abs(gc["score"] - ref["best_score"][t]) <= 2e-4
+        assert abs(float(best[s]["score"]) - ref["best_score"][t]) <= 2e-4
+
+
+def test_invalid_states_and_empty_teams(searcher):
+    prm = dict(synth.DPPS_PARAMS, n_dir=16, n_pow=32)
+    batch = synth.dpps_states(32, 3, n_team=4, n_opp=4, K=16)
+    batch["K"] = batch["K"].copy()
+    batch["K"][1] = 0
+    batch["n_team"] = batch["n_team"].copy()
+    batch["n_team"][2] = 0
+    best, bits, _ = _run(searcher, batch, prm, dbg=False)
+    assert best[1]["idx"] == -2 and best[1]["status"] & 1
+    assert best[2]["idx"] == -1 and bits[2].sum() == 0
+    assert best[0]["status"] == 0
