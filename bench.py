@@ -383,6 +383,8 @@ def run_pps(args):
             line["serving"] = _serving(dev)
         if world == 1 and not args.no_proposal:
             line["proposal"] = _proposal(args, dev, stream)
+        if world == 1 and not args.no_dpps:
+            line["dpps"] = _dpps(args, dev, stream)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
@@ -510,6 +512,69 @@ def _proposal(args, dev, stream):
             "refined_points_frac": TOPK * 64 / (481 * 361)}
 
 
+def _dpps(args, dev, stream):
+    """The paper's own parameterisation (Sec. 4.2): from the ball holder,
+    128 directions x 64 kick powers, 16 receivers and 16 opponents searched
+    along every ball path (K = 64), 4096 states per run; timed like the
+    main step.  The metric is the paper's unit: SBIP evaluations (one
+    robot's interception search for one candidate pass) per second; the
+    oracle's rate on the host cores (4 states) beside it."""
+    import torch
+    from paper_1909_07717_gb300 import pps, synth
+    S = args.states or synth.DPPS_STATES
+    prm = pps.dparams_from_dict(synth.DPPS_PARAMS)
+    batch = synth.dpps_states(synth.DPPS_SEED, S)
+    searcher = pps.Searcher(max_states=S, max_opp=16, device=dev.index,
+                            stream=stream)
+    rec = torch.from_numpy(pps.pack_dstates(batch).view(np.uint8).copy()).to(dev)
+    best = torch.empty(S * 48, dtype=torch.uint8, device=dev)
+    mask = torch.empty((S, pps.pps_dpps_mask_words(prm)), dtype=torch.int32,
+                       device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def run():
+        pps.pps_dpps_search(searcher.ctx, rec.data_ptr(), S, prm,
+                            best.data_ptr(), mask.data_ptr())
+
+    for _ in range(2):
+        run()
+    steps = max(3, min(args.steps, 5))
+    ev = [(torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        run()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    b = np.frombuffer(best.cpu().numpy().tobytes(), pps.DBEST_DTYPE)
+    searcher.close()
+    robots = int(batch["n_team"][0] + batch["n_opp"][0])
+    sbip = S * prm.n_dir * prm.n_pow * robots
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        sub = {k: (v[:4] if isinstance(v, np.ndarray) else v)
+               for k, v in batch.items()}
+        t0 = time.perf_counter()
+        oracle.dpps_search(sub, prm.n_dir, prm.n_pow,
+                           synth.dpps_oracle_params(synth.DPPS_PARAMS))
+        cpu = {"decisions_per_s": 4 / (time.perf_counter() - t0),
+               "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "first 4 states of the workload"}
+    return {"workload": (f"dpps_{S}x{prm.n_dir}x{prm.n_pow}: 12x9 m, 16 v 16,"
+                         f" K 64, powers 1-6.5 m/s, slide 5/7 (seed "
+                         f"{synth.DPPS_SEED})"),
+            "unit": "SBIP evals/s", "value": sbip / (ms / 1e3),
+            "ms_per_run": ms, "decisions_per_s": S / (ms / 1e3),
+            "sbip_per_decision": prm.n_dir * prm.n_pow * robots,
+            "feasible_frac": float(b["n_feasible"].mean()
+                                   / (prm.n_dir * prm.n_pow)),
+            "cpu_baseline": cpu,
+            "ok": bool(np.all(b["status"] == 0))}
+
+
 def _serving(dev, seconds=2.0):
     """The serving loop: 512 simulated matches at 60 Hz (12x9 or 9x6 fields,
     6-11 opponents, 0.05 m grid, 4 speeds, K = 32) replayed in real time
@@ -556,6 +621,8 @@ def main():
                     help="skip the serving-loop replay")
     ap.add_argument("--no-proposal", action="store_true",
                     help="skip the learned-proposal comparison")
+    ap.add_argument("--no-dpps", action="store_true",
+                    help="skip the direction x power search")
     ap.add_argument("--states", type=int, default=0,
                     help="states per GPU (default: the workload's 4096); "
                          "smaller only for profiling captures")

@@ -170,7 +170,7 @@ PROPOSAL = Workload("proposal_4096x481x361_v4_K64_J8", seed=7, n_states=4096,
 # the field), K = 64 samples per ball path, 128 directions x 64 kick powers
 # in [1, 6.5] m/s; the ball at the passer's feet.
 DPPS_SEED = 5
-DPPS_STATES = 1024
+DPPS_STATES = 4096
 DPPS_PARAMS = {"n_dir": 128, "n_pow": 64, "v_lo": 1.0, "v_hi": 6.5,
                "slide": 5.0 / 7.0, "tau_delta": 0.0, "delta_cap": 1.0,
                "w_time": 1.0, "w_angle": 1.0, "w_dist": 1.0, "w_refr": 1.0,
