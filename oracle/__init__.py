@@ -80,6 +80,12 @@ def _bind(lib):
     lib.pps_oracle_dpps_group.argtypes = [p, i, p, d, d, d, d, p, p]
     lib.pps_oracle_dpps_candidate.restype = None
     lib.pps_oracle_dpps_candidate.argtypes = [p, p, i, i, i, i, p]
+    lib.pps_oracle_pass_power.restype = None
+    lib.pps_oracle_pass_power.argtypes = [p, i, d, d, d, d, d, d, d, p]
+    lib.pps_oracle_shoot.restype = None
+    lib.pps_oracle_shoot.argtypes = [p, d, d, d, d, d, d, d, d, p]
+    lib.pps_oracle_shot_gap.restype = d
+    lib.pps_oracle_shot_gap.argtypes = [p, d, d, d, p]
     lib.pps_oracle_dpps_search.restype = i
     lib.pps_oracle_dpps_search.argtypes = [i, p, p, p, p, p, p, i, i, i, p,
                                            p, p, p, p, p, p, p, i]
@@ -254,6 +260,32 @@ class Oracle:
                 "feasible", "score", "m_team", "m_opp")
         return dict(zip(keys, out.tolist()))
 
+    def pass_power(self, st: DState, receiver, target, buffer=0.3,
+                   slide=5 / 7, v_lo=1.0, v_hi=6.5, reach=0.0):
+        out = np.empty(5, np.float64)
+        self.lib.pps_oracle_pass_power(st.ref, int(receiver), float(target[0]),
+                                       float(target[1]), float(buffer),
+                                       float(slide), float(v_lo), float(v_hi),
+                                       float(reach), _ptr(out))
+        return dict(zip(("v0", "v1", "t_pass", "t_recv", "clamped"),
+                        out.tolist()))
+
+    def shoot(self, st: DState, c, v_shot=6.5, slide=5 / 7, theta_min=0.1,
+              tau=0.0, robot_radius=0.09, reach=0.0):
+        out = np.empty(5, np.float64)
+        self.lib.pps_oracle_shoot(st.ref, float(c[0]), float(c[1]),
+                                  float(v_shot), float(slide),
+                                  float(theta_min), float(tau),
+                                  float(robot_radius), float(reach), _ptr(out))
+        return dict(zip(("theta", "dir", "t_line", "t_opp", "shoot"),
+                        out.tolist()))
+
+    def shot_gap(self, state: State, c, r):
+        start = ctypes.c_double()
+        th = self.lib.pps_oracle_shot_gap(state.ref, float(c[0]), float(c[1]),
+                                          float(r), ctypes.byref(start))
+        return th, start.value
+
     def dpps_search(self, batch: dict, ndir, npow, params: dict, *,
                     dense=False, n_threads=0):
         """The direction x power search over a batch with teammates."""
@@ -373,6 +405,7 @@ def __getattr__(name):
     if name in ("grid", "ball_time", "intercept_time", "min_intercept",
                 "min_intercept_many",
                 "margin", "shot_angle", "score", "search", "max_threads",
-                "dpps_path", "dpps_group", "dpps_candidate", "dpps_search"):
+                "dpps_path", "dpps_group", "dpps_candidate", "dpps_search",
+                "pass_power", "shoot", "shot_gap"):
         return getattr(default(), name)
     raise AttributeError(name)

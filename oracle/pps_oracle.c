@@ -156,6 +156,15 @@ double pps_oracle_margin(const pps_oracle_state* st, double cx, double cy,
 double pps_oracle_shot_angle(const pps_oracle_state* st, double cx,
                              double cy, double r)
 {
+    double start;
+    return pps_oracle_shot_gap(st, cx, cy, r, &start);
+}
+
+/* The shot angle and, in *start, the direction where that gap begins. */
+double pps_oracle_shot_gap(const pps_oracle_state* st, double cx, double cy,
+                           double r, double* start)
+{
+    *start = 0.0;
     double gx = 0.5 * st->sc[PPS_ORACLE_FIELD_LEN];
     double hw = 0.5 * st->sc[PPS_ORACLE_GOAL_WIDTH];
     /* READING: no shot from on or behind the goal line. */
@@ -196,10 +205,16 @@ double pps_oracle_shot_angle(const pps_oracle_state* st, double cx,
     }
     double best = 0.0, cur = lo;
     for (int i = 0; i < n; ++i) {
-        if (s[i] > cur && s[i] - cur > best) best = s[i] - cur;
+        if (s[i] > cur && s[i] - cur > best) {
+            best = s[i] - cur;
+            *start = cur;
+        }
         if (e[i] > cur) cur = e[i];
     }
-    if (hi - cur > best) best = hi - cur;
+    if (hi - cur > best) {
+        best = hi - cur;
+        *start = cur;
+    }
     return best;
 }
 
@@ -512,6 +527,103 @@ int pps_oracle_dpps_search(int S, const double* sc, const int* n_team,
     }
     (void)n_threads;
     return 0;
+}
+
+/* ---- D2: passing power (Sec. 4.1, Eq. 1-2) ---- */
+void pps_oracle_pass_power(const pps_oracle_dpps_state* st, int receiver,
+                           double tx, double ty, double buffer, double slide,
+                           double v_lo, double v_hi, double reach,
+                           double* out)
+{
+    double bx = st->sc[PPS_ORACLE_BALL_X], by = st->sc[PPS_ORACLE_BALL_Y];
+    double a = st->sc[PPS_ORACLE_BALL_DECEL];
+    const double* r = st->team + 4 * receiver;
+    /* the receiver's arrival at the target (C3), plus the buffer time */
+    double T = pps_oracle_intercept_time(r[0], r[1], r[2], r[3], tx, ty,
+                                         st->sc[PPS_ORACLE_VMAX],
+                                         st->sc[PPS_ORACLE_AMAX], reach);
+    double t = T + buffer;
+    double d = sqrt((tx - bx) * (tx - bx) + (ty - by) * (ty - by));
+    /* Eq. 1 (read as d = v1 t - a t^2 / 2): the rolling speed that covers d
+     * in t.  READING: if that ball would have stopped before t (d < a t^2
+     * / 2), the slowest ball that still reaches the target, sqrt(2 a d). */
+    double v1 = t > 0.0 ? (d + 0.5 * a * t * t) / t : INFINITY;
+    double vmin = sqrt(2.0 * a * d);
+    if (v1 < vmin || d < 0.5 * a * t * t) v1 = vmin;
+    /* Eq. 2: the kick power; then the robot's limits */
+    double v0 = v1 / slide;
+    int clamped = 0;
+    if (v0 < v_lo) {
+        v0 = v_lo;
+        clamped = 1;
+    }
+    if (v0 > v_hi) {
+        v0 = v_hi;
+        clamped = 1;
+    }
+    out[0] = v0;
+    out[1] = v1;
+    out[2] = t;
+    out[3] = T;
+    out[4] = clamped;
+}
+
+/* ---- D3: shooting decision (Sec. 4.4) ---- */
+void pps_oracle_shoot(const pps_oracle_dpps_state* st, double cx, double cy,
+                      double v_shot, double slide, double theta_min,
+                      double tau, double robot_radius, double reach,
+                      double* out)
+{
+    double a = st->sc[PPS_ORACLE_BALL_DECEL];
+    double hl = 0.5 * st->sc[PPS_ORACLE_FIELD_LEN];
+    pps_oracle_state os;
+    os.sc = st->sc;
+    os.n_opp = st->n_opp;
+    os.opp = st->opp;
+    os.K = st->K;
+    /* the largest open gap of the mouth and its middle direction */
+    double g0 = 0.0;
+    double theta = pps_oracle_shot_gap(&os, cx, cy, robot_radius, &g0);
+    double dir = g0 + 0.5 * theta;
+    double ux = cos(dir), uy = sin(dir);
+    double v = slide * v_shot;
+    double t_line = INFINITY, t_opp = INFINITY;
+    int shoot = 0;
+    if (theta > 0.0 && ux > 0.0) {
+        /* the ball rolls from (cx, cy) to the goal line x = L/2 */
+        double s_line = (hl - cx) / ux;
+        double disc = v * v - 2.0 * a * s_line;
+        if (disc >= 0.0) {
+            t_line = 2.0 * s_line / (v + sqrt(disc));
+            /* opponents searched along the shot as in D (K samples) */
+            double vmax = st->sc[PPS_ORACLE_VMAX], amax = st->sc[PPS_ORACLE_AMAX];
+            for (int k = 1; k <= st->K; ++k) {
+                double s = (double)k / (double)st->K * s_line;
+                double px = cx + s * ux, py = cy + s * uy;
+                double tk = pps_oracle_ball_time(s, v, a);
+                double T = INFINITY;
+                for (int j = 0; j < st->n_opp; ++j) {
+                    const double* o = st->opp + 4 * j;
+                    double tj = pps_oracle_intercept_time(o[0], o[1], o[2], o[3],
+                                                          px, py, vmax, amax,
+                                                          reach);
+                    if (tj < T) T = tj;
+                }
+                if (T <= tk) {
+                    t_opp = tk;
+                    break;
+                }
+            }
+            /* shoot when the gap is wide enough and no opponent gets the
+             * ball before it crosses the line by more than tau */
+            shoot = theta >= theta_min && (t_opp - t_line > tau || isinf(t_opp));
+        }
+    }
+    out[0] = theta;
+    out[1] = dir;
+    out[2] = t_line;
+    out[3] = t_opp;
+    out[4] = shoot;
 }
 
 int pps_oracle_max_threads(void)

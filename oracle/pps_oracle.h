@@ -205,6 +205,29 @@ int pps_oracle_dpps_search(int S, const double* sc, const int* n_team,
                            double* score, double* t_team, double* t_opp,
                            int n_threads);
 
+/* Passing power (Sec. 4.1, Eq. 1-2) for receiver `receiver` of st and the
+ * target (tx, ty): out[0] kick power v0, out[1] rolling speed v1, out[2]
+ * pass time t = T + buffer, out[3] the receiver's arrival T (C3), out[4]
+ * clamped to [v_lo, v_hi] (0/1). */
+void pps_oracle_pass_power(const pps_oracle_dpps_state* st, int receiver,
+                           double tx, double ty, double buffer, double slide,
+                           double v_lo, double v_hi, double reach,
+                           double* out);
+
+/* Shooting decision (Sec. 4.4) from (cx, cy): out[0] the open angle,
+ * out[1] the shot direction (middle of the largest gap), out[2] the ball's
+ * time to the goal line (+inf if it stops short), out[3] the first
+ * opponent's interception time along the shot (+inf if none), out[4]
+ * shoot (0/1). */
+void pps_oracle_shoot(const pps_oracle_dpps_state* st, double cx, double cy,
+                      double v_shot, double slide, double theta_min,
+                      double tau, double robot_radius, double reach,
+                      double* out);
+
+/* The shot angle (C6) and where its gap starts (*start, radians). */
+double pps_oracle_shot_gap(const pps_oracle_state* st, double cx, double cy,
+                           double r, double* start);
+
 int pps_oracle_max_threads(void);
 
 #ifdef __cplusplus

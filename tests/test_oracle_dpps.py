@@ -175,3 +175,52 @@ def test_search_best_is_the_dense_argmax_and_empty_teams_fail():
     b["team_pos"], b["team_vel"] = b["team_pos"][:, :0], b["team_vel"][:, :0]
     r = oracle.dpps_search(b, 32, 8, PRM)
     assert np.all(r["best_idx"] == -1) and np.all(r["n_feasible"] == 0)
+
+
+def test_pass_power_inverts_the_ball_model():
+    """Eq. 1-2: the rolling speed covers the distance in the receiver's
+    arrival time plus the buffer (d = v1 t - a t^2 / 2), the kick power is
+    7/5 of it, limited to the robot's range."""
+    st = _st(team=[(3.0, 1.0, 0.0, 0.0)])
+    r = oracle.pass_power(st, 0, (3.0, 0.0), buffer=0.3)
+    T = math.sqrt(2 * 1.0 / 3.0)            # from rest, 1 m
+    assert math.isclose(r["t_recv"], T, rel_tol=1e-12)
+    t = T + 0.3
+    assert math.isclose(r["t_pass"], t, rel_tol=1e-12)
+    assert math.isclose(3.0, r["v1"] * t - 0.25 * t * t, rel_tol=1e-12)
+    assert math.isclose(r["v0"], r["v1"] * 7 / 5, rel_tol=1e-12)
+    assert r["clamped"] == 0.0
+    # a late receiver close by: the slowest ball that still gets there
+    slow = oracle.pass_power(_st(team=[(0.5, 4.0, 0.0, 0.0)]), 0, (0.5, 0.0))
+    assert math.isclose(slow["v1"], math.sqrt(2 * 0.5 * 0.5), rel_tol=1e-12)
+    # a far target reached early: more than the robot can kick
+    far = oracle.pass_power(_st(team=[(5.9, 0.0, 0.0, 0.0)]), 0, (6.0, 0.0),
+                            buffer=0.0)
+    assert far["clamped"] == 1.0 and far["v0"] == 6.5
+
+
+def test_shooting_decision():
+    """Sec. 4.4: the open angle and its middle direction, the ball's time
+    to the goal line, and the opponents along the shot."""
+    c = (3.0, 0.5)
+    st = _st()
+    r = oracle.shoot(st, c, theta_min=0.1)
+    lo, hi = math.atan2(-0.9 - 0.5, 3.0), math.atan2(0.9 - 0.5, 3.0)
+    assert math.isclose(r["theta"], hi - lo, rel_tol=1e-12)
+    assert math.isclose(r["dir"], 0.5 * (lo + hi), rel_tol=1e-12)
+    v = 6.5 * 5 / 7
+    s = 3.0 / math.cos(r["dir"])
+    assert math.isclose(r["t_line"], (v - math.sqrt(v * v - s)) / 0.5,
+                        rel_tol=1e-9)
+    assert r["shoot"] == 1.0 and math.isinf(r["t_opp"])
+    # an opponent running in from the side (outside the mouth's angle)
+    # takes a slower shot first
+    side = _st(opp=[(4.5, 2.5, 0.0, -3.0)])
+    blocked = oracle.shoot(side, c, v_shot=3.0, theta_min=0.0)
+    assert math.isclose(blocked["theta"], hi - lo, rel_tol=1e-12)
+    assert blocked["t_opp"] < blocked["t_line"] and blocked["shoot"] == 0.0
+    assert oracle.shoot(side, c, v_shot=6.5, theta_min=0.0)["shoot"] == 1.0
+    # too narrow an angle, or a ball that stops short: no shot
+    assert oracle.shoot(st, c, theta_min=1.0)["shoot"] == 0.0
+    weak = oracle.shoot(st, c, v_shot=1.0)
+    assert math.isinf(weak["t_line"]) and weak["shoot"] == 0.0
