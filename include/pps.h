@@ -670,6 +670,65 @@ pps_status pps_dpps_search(pps_ctx* ctx, const pps_dstate* states,
                            pps_dbest* out_best, uint32_t* out_mask,
                            float* out_dbg);
 
+/* ---- Passing power and shooting decisions (Sec. 4.1, Sec. 4.4) --------- */
+
+/* One passing-power query: receiver `receiver` (an index into team_pos) of
+ * states[state] is to receive the ball at `target`. */
+typedef struct pps_pass_query {
+    int32_t state;
+    int32_t receiver;
+    float target[2];
+} pps_pass_query;
+
+typedef struct pps_pass_power {
+    float v0;        /* kick power (m/s), within [v_lo, v_hi] */
+    float v1;        /* rolling speed after the slide */
+    float t_pass;    /* the ball's travel time: t_recv + buffer */
+    float t_recv;    /* the receiver's arrival at the target (s) */
+    int32_t clamped; /* 1 when v0 was limited to [v_lo, v_hi] */
+    int32_t status;  /* PPS_STATE_OK, or PPS_STATE_INVALID (bad query or
+                        state: the other fields are NaN) */
+} pps_pass_power;
+
+/* Sec. 4.1, Eq. 1-2: the pass takes the receiver's arrival time at the
+ * target (bang-bang model) plus `buffer` seconds (the paper: 0.3); the
+ * rolling speed covers the distance in that time (d = v1 t - a t^2 / 2,
+ * the reading of the garbled Eq. 1; at least sqrt(2 a d), the slowest ball
+ * that still reaches the target) and the kick power is v1 / slide (Eq. 2),
+ * limited to [v_lo, v_hi].  params: slide, v_lo, v_hi, reach_radius
+ * (NULL = pps_dpps_default_params).  states, queries and out are device
+ * memory; enqueued on the context's stream. */
+pps_status pps_pass_powers(pps_ctx* ctx, const pps_dstate* states,
+                           int n_states, const pps_pass_query* queries,
+                           int n_queries, float buffer,
+                           const pps_dparams* params, pps_pass_power* out);
+
+/* One shooting query: a shooter of states[state] at `from`. */
+typedef struct pps_shot_query {
+    int32_t state;
+    float from[2];
+} pps_shot_query;
+
+typedef struct pps_shot {
+    float theta;     /* the open shot angle (rad) */
+    float dir;       /* shot direction: the middle of the largest gap */
+    float t_line;    /* the ball's time to the goal line (+inf: stops short) */
+    float t_opp;     /* first opponent interception on the way (+inf: none) */
+    int32_t shoot;   /* 1: shoot */
+    int32_t status;  /* PPS_STATE_OK or PPS_STATE_INVALID */
+} pps_shot;
+
+/* Sec. 4.4: shoot when the open angle is at least theta_min and the ball,
+ * kicked at v_shot toward the middle of the largest open gap (rolling from
+ * slide * v_shot), reaches the goal line with no opponent getting it first
+ * (by more than tau_delta; opponents searched along the shot with the
+ * state's K samples).  params: slide, tau_delta, robot_radius,
+ * reach_radius.  Device memory; enqueued on the context's stream. */
+pps_status pps_shoot(pps_ctx* ctx, const pps_dstate* states, int n_states,
+                     const pps_shot_query* queries, int n_queries,
+                     float v_shot, float theta_min, const pps_dparams* params,
+                     pps_shot* out);
+
 #ifdef __cplusplus
 }
 #endif

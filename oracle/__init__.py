@@ -272,13 +272,13 @@ class Oracle:
 
     def shoot(self, st: DState, c, v_shot=6.5, slide=5 / 7, theta_min=0.1,
               tau=0.0, robot_radius=0.09, reach=0.0):
-        out = np.empty(5, np.float64)
+        out = np.empty(6, np.float64)
         self.lib.pps_oracle_shoot(st.ref, float(c[0]), float(c[1]),
                                   float(v_shot), float(slide),
                                   float(theta_min), float(tau),
                                   float(robot_radius), float(reach), _ptr(out))
-        return dict(zip(("theta", "dir", "t_line", "t_opp", "shoot"),
-                        out.tolist()))
+        return dict(zip(("theta", "dir", "t_line", "t_opp", "shoot",
+                         "margin"), out.tolist()))
 
     def shot_gap(self, state: State, c, r):
         start = ctypes.c_double()

@@ -587,7 +587,7 @@ void pps_oracle_shoot(const pps_oracle_dpps_state* st, double cx, double cy,
     double dir = g0 + 0.5 * theta;
     double ux = cos(dir), uy = sin(dir);
     double v = slide * v_shot;
-    double t_line = INFINITY, t_opp = INFINITY;
+    double t_line = INFINITY, t_opp = INFINITY, margin = INFINITY;
     int shoot = 0;
     if (theta > 0.0 && ux > 0.0) {
         /* the ball rolls from (cx, cy) to the goal line x = L/2 */
@@ -609,6 +609,7 @@ void pps_oracle_shoot(const pps_oracle_dpps_state* st, double cx, double cy,
                                                           reach);
                     if (tj < T) T = tj;
                 }
+                if (fabs(T - tk) < margin) margin = fabs(T - tk);
                 if (T <= tk) {
                     t_opp = tk;
                     break;
@@ -624,6 +625,7 @@ void pps_oracle_shoot(const pps_oracle_dpps_state* st, double cx, double cy,
     out[2] = t_line;
     out[3] = t_opp;
     out[4] = shoot;
+    out[5] = margin;
 }
 
 int pps_oracle_max_threads(void)

@@ -218,7 +218,8 @@ void pps_oracle_pass_power(const pps_oracle_dpps_state* st, int receiver,
  * out[1] the shot direction (middle of the largest gap), out[2] the ball's
  * time to the goal line (+inf if it stops short), out[3] the first
  * opponent's interception time along the shot (+inf if none), out[4]
- * shoot (0/1). */
+ * shoot (0/1), out[5] the smallest |T - t_ball| over the samples searched
+ * (how far the interception decision was from flipping). */
 void pps_oracle_shoot(const pps_oracle_dpps_state* st, double cx, double cy,
                       double v_shot, double slide, double theta_min,
                       double tau, double robot_radius, double reach,

@@ -376,6 +376,123 @@ __global__ void __launch_bounds__(128) dpps_finalize(const DArgs a) {
     a.counts[s] = 0;
 }
 
+// Sec. 4.1, Eq. 1-2, one thread per query.
+template <int J>
+__global__ void __launch_bounds__(128)
+    pass_power_kernel(const pps_dstate* __restrict__ states, int n_states,
+                      const pps_pass_query* __restrict__ q, int n, float buffer,
+                      const pps_dparams prm, int kmax,
+                      pps_pass_power* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const pps_pass_query qu = q[i];
+    pps_pass_power o;
+    o.v0 = o.v1 = o.t_pass = o.t_recv = CUDART_NAN_F;
+    o.clamped = 0;
+    o.status = PPS_STATE_INVALID;
+    if (qu.state >= 0 && qu.state < n_states) {
+        const pps_dstate& st = states[qu.state];
+        const DStateK sk = derive_dstate<J>(st, prm, kmax);
+        if (sk.valid && qu.receiver >= 0 && qu.receiver < sk.nteam &&
+            finite_(qu.target[0]) && finite_(qu.target[1])) {
+            // the receiver's arrival: the intercept form at the target
+            const float rx = pps::scaled_diff(qu.target[0], st.team_pos[qu.receiver][0], sk.kappa);
+            const float ry = pps::scaled_diff(qu.target[1], st.team_pos[qu.receiver][1], sk.kappa);
+            const float ux = __fmul_rn(st.team_vel[qu.receiver][0], sk.inv_vmax);
+            const float uy = __fmul_rn(st.team_vel[qu.receiver][1], sk.inv_vmax);
+            const float2 z = make_float2(0.f, 0.f);
+            const float nrm =
+                (sk.general
+                     ? pps::sbip_num2<true>(z, z, z, make_float2(rx, rx),
+                                            make_float2(ry, ry), make_float2(ux, ux),
+                                            make_float2(uy, uy), sk.reach)
+                     : pps::sbip_num2<false>(z, z, z, make_float2(rx, rx),
+                                             make_float2(ry, ry), make_float2(ux, ux),
+                                             make_float2(uy, uy), sk.reach))
+                    .x;
+            const float T = __fmul_rn(nrm, sk.t_scale);
+            const float t = __fadd_rn(T, buffer);
+            const float dx = __fsub_rn(qu.target[0], sk.bx);
+            const float dy = __fsub_rn(qu.target[1], sk.by);
+            const float d = __fsqrt_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)));
+            const float half_at2 = __fmul_rn(0.5f * sk.ab, __fmul_rn(t, t));
+            float v1 = t > 0.f ? __fdiv_rn(__fadd_rn(d, half_at2), t) : CUDART_INF_F;
+            const float vmin = __fsqrt_rn(__fmul_rn(sk.two_ab, d));
+            if (v1 < vmin || d < half_at2) v1 = vmin;
+            float v0 = __fdiv_rn(v1, prm.slide);
+            int cl = 0;
+            if (v0 < prm.v_lo) { v0 = prm.v_lo; cl = 1; }
+            if (v0 > prm.v_hi) { v0 = prm.v_hi; cl = 1; }
+            o.v0 = v0;
+            o.v1 = v1;
+            o.t_pass = t;
+            o.t_recv = T;
+            o.clamped = cl;
+            o.status = PPS_STATE_OK;
+        }
+    }
+    out[i] = o;
+}
+
+// Sec. 4.4, one thread per query.
+template <int J>
+__global__ void __launch_bounds__(128)
+    shoot_kernel(const pps_dstate* __restrict__ states, int n_states,
+                 const pps_shot_query* __restrict__ q, int n, float v_shot,
+                 float theta_min, const pps_dparams prm, int kmax,
+                 pps_shot* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const pps_shot_query qu = q[i];
+    pps_shot o;
+    o.theta = o.dir = o.t_line = o.t_opp = CUDART_NAN_F;
+    o.shoot = 0;
+    o.status = PPS_STATE_INVALID;
+    if (qu.state >= 0 && qu.state < n_states && finite_(qu.from[0]) &&
+        finite_(qu.from[1])) {
+        const pps_dstate& st = states[qu.state];
+        DStateK sk = derive_dstate<J>(st, prm, kmax);
+        if (sk.valid) {
+            const float cx = qu.from[0], cy = qu.from[1];
+            float start;
+            const float theta = pps::shot_angle_of<J>(
+                st.opp_pos, sk.nopp, sk.hw, cx < sk.hl, cx, cy,
+                __fsub_rn(sk.hl, cx), prm.robot_radius, &start);
+            const float dir = __fmaf_rn(0.5f, theta, start);
+            float sn, cs;
+            sincosf(dir, &sn, &cs);
+            o.theta = theta;
+            o.dir = dir;
+            o.t_line = o.t_opp = CUDART_INF_F;
+            if (theta > 0.f && cs > 0.f) {
+                Path p;
+                p.ux = cs;
+                p.uy = sn;
+                p.v = __fmul_rn(prm.slide, v_shot);
+                p.S = __fdiv_rn(__fsub_rn(sk.hl, cx), cs);
+                p.stopped = false;
+                const float disc = __fmaf_rn(-sk.two_ab, p.S, __fmul_rn(p.v, p.v));
+                if (disc >= 0.f) {
+                    o.t_line = __fdiv_rn(__fmul_rn(2.f, p.S),
+                                         __fadd_rn(p.v, __fsqrt_rn(disc)));
+                    // the opponents, relative to the shooter
+                    sk.bx = cx;
+                    sk.by = cy;
+                    OppRegs<J> g;
+                    load_group<J>(st.opp_pos, st.opp_vel, sk.nopp, sk, g);
+                    int k, who;
+                    o.t_opp = group_first<J>(sk, g, p, true, k, who);
+                    o.shoot = theta >= theta_min &&
+                              (!(o.t_opp < CUDART_INF_F) ||
+                               __fsub_rn(o.t_opp, o.t_line) > prm.tau_delta);
+                }
+            }
+            o.status = PPS_STATE_OK;
+        }
+    }
+    out[i] = o;
+}
+
 template <int J>
 cudaError_t launch(const DArgs& a, int num_sms, cudaStream_t st) {
     static int occ = 0;
@@ -468,5 +585,76 @@ extern "C" pps_status pps_dpps_search(pps_ctx* ctx, const pps_dstate* states,
         e = pps_ctx_jmax(ctx) == 8 ? launch<8>(a, sms, st) : launch<16>(a, sms, st);
     }
     if (e != cudaSuccess) return pps_ctx_cuda_error(ctx, e, "pps_dpps_search");
+    return PPS_OK;
+}
+
+extern "C" pps_status pps_pass_powers(pps_ctx* ctx, const pps_dstate* states,
+                                      int n_states, const pps_pass_query* queries,
+                                      int n_queries, float buffer,
+                                      const pps_dparams* params,
+                                      pps_pass_power* out) {
+    if (!ctx) return PPS_EINVAL;
+    if (pps_ctx_failed(ctx))
+        return pps_ctx_error(ctx, PPS_ECUDA, "context failed earlier; call pps_reset");
+    if (n_queries == 0) return PPS_OK;
+    if (n_queries < 0 || n_states < 0 || !states || !queries || !out)
+        return pps_ctx_error(ctx, PPS_EINVAL, "pps_pass_powers: bad buffers or counts");
+    pps_dparams p;
+    if (params)
+        p = *params;
+    else
+        pps_dpps_default_params(&p);
+    if (!fin(buffer) || buffer < 0.f || !(p.slide > 0.f) || p.slide > 1.f ||
+        !(p.v_lo > 0.f) || !fin(p.v_hi) || p.v_hi < p.v_lo ||
+        !fin(p.reach_radius) || p.reach_radius < 0.f)
+        return pps_ctx_error(ctx, PPS_EINVAL, "pps_pass_powers: parameter out of range");
+    cudaError_t e = cudaSetDevice(pps_ctx_device(ctx));
+    cudaStream_t st = pps_ctx_stream(ctx);
+    const unsigned grid = (unsigned)((n_queries + 127) / 128);
+    if (e == cudaSuccess) {
+        if (pps_ctx_jmax(ctx) == 8)
+            pass_power_kernel<8><<<grid, 128, 0, st>>>(states, n_states, queries, n_queries,
+                                                       buffer, p, pps_ctx_max_K(ctx), out);
+        else
+            pass_power_kernel<16><<<grid, 128, 0, st>>>(states, n_states, queries, n_queries,
+                                                        buffer, p, pps_ctx_max_K(ctx), out);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return pps_ctx_cuda_error(ctx, e, "pps_pass_powers");
+    return PPS_OK;
+}
+
+extern "C" pps_status pps_shoot(pps_ctx* ctx, const pps_dstate* states, int n_states,
+                                const pps_shot_query* queries, int n_queries,
+                                float v_shot, float theta_min,
+                                const pps_dparams* params, pps_shot* out) {
+    if (!ctx) return PPS_EINVAL;
+    if (pps_ctx_failed(ctx))
+        return pps_ctx_error(ctx, PPS_ECUDA, "context failed earlier; call pps_reset");
+    if (n_queries == 0) return PPS_OK;
+    if (n_queries < 0 || n_states < 0 || !states || !queries || !out)
+        return pps_ctx_error(ctx, PPS_EINVAL, "pps_shoot: bad buffers or counts");
+    pps_dparams p;
+    if (params)
+        p = *params;
+    else
+        pps_dpps_default_params(&p);
+    if (!(v_shot > 0.f) || !fin(v_shot) || !fin(theta_min) || !(p.slide > 0.f) ||
+        p.slide > 1.f || !fin(p.tau_delta) || !fin(p.robot_radius) ||
+        p.robot_radius < 0.f || !fin(p.reach_radius) || p.reach_radius < 0.f)
+        return pps_ctx_error(ctx, PPS_EINVAL, "pps_shoot: parameter out of range");
+    cudaError_t e = cudaSetDevice(pps_ctx_device(ctx));
+    cudaStream_t st = pps_ctx_stream(ctx);
+    const unsigned grid = (unsigned)((n_queries + 127) / 128);
+    if (e == cudaSuccess) {
+        if (pps_ctx_jmax(ctx) == 8)
+            shoot_kernel<8><<<grid, 128, 0, st>>>(states, n_states, queries, n_queries,
+                                                  v_shot, theta_min, p, pps_ctx_max_K(ctx), out);
+        else
+            shoot_kernel<16><<<grid, 128, 0, st>>>(states, n_states, queries, n_queries,
+                                                   v_shot, theta_min, p, pps_ctx_max_K(ctx), out);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return pps_ctx_cuda_error(ctx, e, "pps_shoot");
     return PPS_OK;
 }

@@ -353,7 +353,9 @@ template <int JMAX>
 __device__ __forceinline__ float shot_angle_of(const float (*opp)[2],
                                                int nopp, float hw, bool front,
                                                float cx, float cy, float gx,
-                                               float r) {
+                                               float r,
+                                               float* gap_start = nullptr) {
+    if (gap_start) *gap_start = 0.f;
     if (!front) return 0.f;
     const float lo = atan2f(__fsub_rn(-hw, cy), gx);
     const float hi = atan2f(__fsub_rn(hw, cy), gx);
@@ -408,14 +410,26 @@ __device__ __forceinline__ float shot_angle_of(const float (*opp)[2],
             e[i] = e0;
             e[i + 1] = e1;
         }
-    float best = 0.f, cur = lo;
+    float best = 0.f, cur = lo, start = lo;
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
-        if (s[j] > cur && cur < hi)
-            best = fmaxf(best, __fsub_rn(fminf(s[j], hi), cur));
+        if (s[j] > cur && cur < hi) {
+            const float gap = __fsub_rn(fminf(s[j], hi), cur);
+            if (gap > best) {
+                best = gap;
+                start = cur;
+            }
+        }
         cur = fmaxf(cur, e[j]);
     }
-    if (cur < hi) best = fmaxf(best, __fsub_rn(hi, cur));
+    if (cur < hi) {
+        const float gap = __fsub_rn(hi, cur);
+        if (gap > best) {
+            best = gap;
+            start = cur;
+        }
+    }
+    if (gap_start) *gap_start = start;
     return best;
 }
 

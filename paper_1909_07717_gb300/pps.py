@@ -167,6 +167,14 @@ DBEST_DTYPE = np.dtype([("idx", "<i4"), ("dir", "<i4"), ("pow", "<i4"),
                         ("recv", "<f4", (2,)), ("n_feasible", "<i4"),
                         ("status", "<i4"), ("reserved", "<i4")])
 assert DSTATE_DTYPE.itemsize == 556 and DBEST_DTYPE.itemsize == 48
+PASS_QUERY_DTYPE = np.dtype([("state", "<i4"), ("receiver", "<i4"),
+                             ("target", "<f4", (2,))])
+PASS_POWER_DTYPE = np.dtype([("v0", "<f4"), ("v1", "<f4"), ("t_pass", "<f4"),
+                             ("t_recv", "<f4"), ("clamped", "<i4"),
+                             ("status", "<i4")])
+SHOT_QUERY_DTYPE = np.dtype([("state", "<i4"), ("from", "<f4", (2,))])
+SHOT_DTYPE = np.dtype([("theta", "<f4"), ("dir", "<f4"), ("t_line", "<f4"),
+                       ("t_opp", "<f4"), ("shoot", "<i4"), ("status", "<i4")])
 
 EXPORTS = ("pps_abi_version", "pps_status_string", "pps_last_error",
            "pps_default_params", "pps_grid_from_field", "pps_mask_words",
@@ -181,7 +189,8 @@ EXPORTS = ("pps_abi_version", "pps_status_string", "pps_last_error",
            "pps_net_get_weights", "pps_net_raster", "pps_net_forward_layers",
            "pps_net_forward", "pps_net_grad", "pps_net_train_step",
            "pps_net_labels", "pps_propose", "pps_dpps_default_params",
-           "pps_dpps_mask_words", "pps_dpps_search")
+           "pps_dpps_mask_words", "pps_dpps_search", "pps_pass_powers",
+           "pps_shoot")
 
 
 class PpsError(RuntimeError):
@@ -294,6 +303,12 @@ def lib():
             L.pps_dpps_search.argtypes = [c_void_p, c_void_p, ctypes.c_int,
                                           P(pps_dparams), c_void_p, c_void_p,
                                           c_void_p]
+            L.pps_pass_powers.argtypes = [c_void_p, c_void_p, ctypes.c_int,
+                                          c_void_p, ctypes.c_int, c_float,
+                                          P(pps_dparams), c_void_p]
+            L.pps_shoot.argtypes = [c_void_p, c_void_p, ctypes.c_int, c_void_p,
+                                    ctypes.c_int, c_float, c_float,
+                                    P(pps_dparams), c_void_p]
             if L.pps_abi_version() != PPS_ABI_VERSION:
                 raise RuntimeError("libpps ABI version mismatch")
             _lib = L
@@ -553,6 +568,22 @@ def pps_dpps_search(ctx, states, n_states, params, out_best, out_mask=None,
         ctx, states, n_states,
         ctypes.byref(params) if params is not None else None, out_best,
         out_mask, out_dbg), ctx)
+
+
+def pps_pass_powers(ctx, states, n_states, queries, n_queries, buffer,
+                    params, out):
+    """Device addresses for states, queries and out."""
+    return _check(lib().pps_pass_powers(
+        ctx, states, n_states, queries, n_queries, buffer,
+        ctypes.byref(params) if params is not None else None, out), ctx)
+
+
+def pps_shoot(ctx, states, n_states, queries, n_queries, v_shot, theta_min,
+              params, out):
+    """Device addresses for states, queries and out."""
+    return _check(lib().pps_shoot(
+        ctx, states, n_states, queries, n_queries, v_shot, theta_min,
+        ctypes.byref(params) if params is not None else None, out), ctx)
 
 
 def dparams_from_dict(d: dict | None) -> pps_dparams:

@@ -158,3 +158,78 @@ def test_invalid_states_and_empty_teams(searcher):
     assert best[1]["idx"] == -2 and best[1]["status"] & 1
     assert best[2]["idx"] == -1 and bits[2].sum() == 0
     assert best[0]["status"] == 0
+
+
+def _device(torch, arr):
+    return torch.from_numpy(np.ascontiguousarray(arr).view(np.uint8)
+                            .reshape(-1).copy()).cuda()
+
+
+def test_pass_powers_match_the_oracle(searcher):
+    torch = searcher.torch
+    batch = synth.dpps_states(33, 6, n_team=5, n_opp=5, K=32)
+    rng = np.random.default_rng(4)
+    q = np.zeros(120, pps.PASS_QUERY_DTYPE)
+    q["state"] = rng.integers(0, 6, 120)
+    q["receiver"] = rng.integers(0, 5, 120)
+    q["target"] = rng.uniform([-6, -4.5], [6, 4.5], (120, 2))
+    q["receiver"][0] = 7          # no such receiver
+    q["state"][1] = 9             # no such state
+    states = _device(torch, pps.pack_dstates(batch))
+    qd = _device(torch, q)
+    out = torch.empty(120 * pps.PASS_POWER_DTYPE.itemsize, dtype=torch.uint8,
+                      device="cuda")
+    p = pps.dparams_from_dict(synth.DPPS_PARAMS)
+    pps.pps_pass_powers(searcher.ctx, states.data_ptr(), 6, qd.data_ptr(),
+                        120, 0.3, p, out.data_ptr())
+    torch.cuda.synchronize()
+    g = np.frombuffer(out.cpu().numpy().tobytes(), pps.PASS_POWER_DTYPE)
+    assert g["status"][0] == 1 and g["status"][1] == 1
+    assert np.isnan(g["v0"][0])
+    for i in range(2, 120):
+        st = oracle.dstate_of(batch, int(q["state"][i]))
+        r = oracle.pass_power(st, int(q["receiver"][i]), q["target"][i],
+                              buffer=0.3)
+        assert g["status"][i] == 0
+        assert abs(g["t_recv"][i] - r["t_recv"]) <= 1e-5 * (1 + r["t_recv"])
+        assert abs(g["v1"][i] - r["v1"]) <= 1e-5 * (1 + r["v1"])
+        if abs(r["v0"] - 6.5) > 1e-4 and abs(r["v0"] - 1.0) > 1e-4:
+            assert g["clamped"][i] == r["clamped"]
+        assert abs(g["v0"][i] - r["v0"]) <= 1e-5 * (1 + r["v0"])
+
+
+def test_shooting_decisions_match_the_oracle(searcher):
+    torch = searcher.torch
+    batch = synth.dpps_states(34, 6, n_team=4, n_opp=8, K=32)
+    rng = np.random.default_rng(5)
+    n = 200
+    q = np.zeros(n, pps.SHOT_QUERY_DTYPE)
+    q["state"] = rng.integers(0, 6, n)
+    q["from"] = rng.uniform([-2, -4], [6, 4], (n, 2))
+    states = _device(torch, pps.pack_dstates(batch))
+    qd = _device(torch, q)
+    out = torch.empty(n * pps.SHOT_DTYPE.itemsize, dtype=torch.uint8,
+                      device="cuda")
+    p = pps.dparams_from_dict(synth.DPPS_PARAMS)
+    pps.pps_shoot(searcher.ctx, states.data_ptr(), 6, qd.data_ptr(), n, 5.0,
+                  0.1, p, out.data_ptr())
+    torch.cuda.synchronize()
+    g = np.frombuffer(out.cpu().numpy().tobytes(), pps.SHOT_DTYPE)
+    shots = checked = 0
+    for i in range(n):
+        st = oracle.dstate_of(batch, int(q["state"][i]))
+        r = oracle.shoot(st, q["from"][i], v_shot=5.0, theta_min=0.1)
+        assert g["status"][i] == 0
+        assert abs(g["theta"][i] - r["theta"]) <= 2e-5
+        if r["theta"] > 0:
+            assert abs(g["dir"][i] - r["dir"]) <= 2e-5
+        assert _close(g["t_line"][i], r["t_line"], 1e-5)
+        if r["margin"] <= EPS or abs(r["theta"] - 0.1) <= 1e-5:
+            continue
+        assert _close(g["t_opp"][i], r["t_opp"], 1e-5), (i, g[i], r)
+        if math.isfinite(r["t_opp"]) and abs(r["t_opp"] - r["t_line"]) <= EPS:
+            continue
+        assert g["shoot"][i] == r["shoot"], (i, g[i], r)
+        shots += int(r["shoot"])
+        checked += 1
+    assert checked >= 0.9 * n and 0 < shots < checked
