@@ -33,6 +33,11 @@ PARAMS = ("w_angle", "w_dist", "w_margin", "margin_cap", "tau_safe",
 DPPS_PARAMS = ("vlo", "vhi", "slide", "tau_delta", "delta_cap", "w_time",
                "w_angle", "w_dist", "w_refr", "w_delta", "robot_radius",
                "reach_radius", "min_time")
+# Running-point parameters, in the order of PPS_ORACLE_R_* (pps_oracle.h).
+RUN_PARAMS = ("spacing", "w_goal", "w_ball", "w_angle", "w_guard", "w_avoid",
+              "ball_ref", "angle_lo", "angle_hi", "angle_span", "def_depth",
+              "def_width", "guard_cap", "n_run")
+RUN_CRITERIA = ("goal", "ball", "angle", "guard", "avoid")
 
 
 def build(force: bool = False, src: str = _SRC, out: str = _LIB) -> str:
@@ -89,6 +94,15 @@ def _bind(lib):
     lib.pps_oracle_dpps_search.restype = i
     lib.pps_oracle_dpps_search.argtypes = [i, p, p, p, p, p, p, i, i, i, p,
                                            p, p, p, p, p, p, p, i]
+    lib.pps_oracle_run_point.restype = None
+    lib.pps_oracle_run_point.argtypes = [p, p, d, d, p]
+    lib.pps_oracle_run_zone.restype = i
+    lib.pps_oracle_run_zone.argtypes = [p, d, d]
+    lib.pps_oracle_run_choose.restype = None
+    lib.pps_oracle_run_choose.argtypes = [p, p, i, i, p]
+    lib.pps_oracle_run_search.restype = i
+    lib.pps_oracle_run_search.argtypes = [i, p, p, p, i, p, p, p, p, p, p, p,
+                                          i]
     return lib
 
 
@@ -334,6 +348,66 @@ class Oracle:
         return out
 
 
+    # -- running points (pps_oracle.h, R) --
+    def run_point(self, st: DState, params: dict, p):
+        """Score, zone, the five criteria and candidacy of point p."""
+        prm = np.array([float(params[k]) for k in RUN_PARAMS], np.float64)
+        out = np.empty(8, np.float64)
+        self.lib.pps_oracle_run_point(st.ref, _ptr(prm), float(p[0]),
+                                      float(p[1]), _ptr(out))
+        r = {"score": out[0], "zone": int(out[1]), "candidate": bool(out[7])}
+        r.update(zip(RUN_CRITERIA, out[2:7].tolist()))
+        return r
+
+    def run_zone(self, st: DState, p) -> int:
+        return self.lib.pps_oracle_run_zone(st.ref, float(p[0]), float(p[1]))
+
+    def run_choose(self, best_idx, best_score, avoid, n_run):
+        bi = np.ascontiguousarray(np.asarray(best_idx, np.int64))
+        bs = np.ascontiguousarray(np.asarray(best_score, np.float64))
+        ch = np.empty(4, np.int32)
+        self.lib.pps_oracle_run_choose(_ptr(bi), _ptr(bs), int(avoid),
+                                       int(n_run), _ptr(ch))
+        return ch
+
+    def run_search(self, batch: dict, params: dict, *, pass_points=None,
+                   dense=False, n_threads=0):
+        """Running points of every state of a batch (teammates unused).
+        pass_points: (S, 2) best passing points, NaN for none."""
+        ball = np.asarray(batch["ball"], np.float64)
+        S = ball.shape[0]
+        sc = np.ascontiguousarray(np.stack(
+            [ball[:, 0], ball[:, 1]] + [np.asarray(batch[k], np.float64)
+                                        for k in SCALARS[2:]], axis=1))
+        J = batch["opp_pos"].shape[1]
+        opp = np.zeros((S, J, 4), np.float64)
+        opp[:, :, :2] = batch["opp_pos"]
+        opp[:, :, 2:] = batch["opp_vel"]
+        opp = np.ascontiguousarray(opp)
+        n_opp = np.ascontiguousarray(np.asarray(batch["n_opp"], np.int32))
+        prm = np.array([float(params[k]) for k in RUN_PARAMS], np.float64)
+        pp = None if pass_points is None else np.ascontiguousarray(
+            np.asarray(pass_points, np.float64).reshape(S, 2))
+        out = {"best_idx": np.empty((S, 4), np.int64),
+               "best_score": np.empty((S, 4), np.float64),
+               "chosen": np.empty((S, 4), np.int32),
+               "avoided": np.empty(S, np.int32)}
+        if dense:
+            g = prm[0]
+            L = float(np.asarray(batch["field_len"]).reshape(-1)[0])
+            W = float(np.asarray(batch["field_wid"]).reshape(-1)[0])
+            nx, ny = int(round(0.5 * L / g)) + 1, int(round(W / g)) + 1
+            out["score"] = np.empty((S, ny, nx), np.float64)
+        rc = self.lib.pps_oracle_run_search(
+            S, _ptr(sc), _ptr(n_opp), _ptr(opp), J, _ptr(prm), _ptr(pp),
+            _ptr(out["best_idx"]), _ptr(out["best_score"]),
+            _ptr(out["chosen"]), _ptr(out["avoided"]), _ptr(out.get("score")),
+            int(n_threads))
+        if rc != 0:
+            raise ValueError("oracle rejected the batch")
+        return out
+
+
 class _DState(ctypes.Structure):
     _fields_ = [("sc", ctypes.c_void_p), ("n_team", ctypes.c_int),
                 ("team", ctypes.c_void_p), ("n_opp", ctypes.c_int),
@@ -406,6 +480,7 @@ def __getattr__(name):
                 "min_intercept_many",
                 "margin", "shot_angle", "score", "search", "max_threads",
                 "dpps_path", "dpps_group", "dpps_candidate", "dpps_search",
-                "pass_power", "shoot", "shot_gap"):
+                "pass_power", "shoot", "shot_gap", "run_point", "run_zone",
+                "run_choose", "run_search"):
         return getattr(default(), name)
     raise AttributeError(name)

@@ -628,6 +628,197 @@ void pps_oracle_shoot(const pps_oracle_dpps_state* st, double cx, double cy,
     out[5] = margin;
 }
 
+/* ---- R: running points (Sec. 5.1-5.2) ---- */
+
+/* The point where the segment from p to q first enters the rectangle
+ * [x0, x1] x [y0, y1] (Liang-Barsky); returns 0 if it never does. */
+static int segment_entry(double px, double py, double qx, double qy,
+                         double x0, double x1, double y0, double y1,
+                         double* ex, double* ey)
+{
+    double t0 = 0.0, t1 = 1.0;
+    double dx = qx - px, dy = qy - py;
+    double p_[4] = {-dx, dx, -dy, dy};
+    double q_[4] = {px - x0, x1 - px, py - y0, y1 - py};
+    for (int i = 0; i < 4; ++i) {
+        if (p_[i] == 0.0) {
+            if (q_[i] < 0.0) return 0;
+        } else {
+            double r = q_[i] / p_[i];
+            if (p_[i] < 0.0) {
+                if (r > t1) return 0;
+                if (r > t0) t0 = r;
+            } else {
+                if (r < t0) return 0;
+                if (r < t1) t1 = r;
+            }
+        }
+    }
+    *ex = px + t0 * dx;
+    *ey = py + t0 * dy;
+    return 1;
+}
+
+/* READING: zones I-IV are the attacking half cut at x = L/4 and at the
+ * ball's y, kept within +-W/4 so that no zone closes up.  No bounds check:
+ * the grid's last column may lie a rounding error beyond L/2. */
+static int zone_of(const pps_oracle_dpps_state* st, double px, double py)
+{
+    double L = st->sc[PPS_ORACLE_FIELD_LEN], W = st->sc[PPS_ORACLE_FIELD_WID];
+    double by = st->sc[PPS_ORACLE_BALL_Y];
+    double ys = by < -0.25 * W ? -0.25 * W : (by > 0.25 * W ? 0.25 * W : by);
+    return (px >= 0.25 * L ? 2 : 0) + (py >= ys ? 1 : 0);
+}
+
+int pps_oracle_run_zone(const pps_oracle_dpps_state* st, double px,
+                        double py)
+{
+    double L = st->sc[PPS_ORACLE_FIELD_LEN], W = st->sc[PPS_ORACLE_FIELD_WID];
+    if (!(px >= 0.0 && px <= 0.5 * L && fabs(py) <= 0.5 * W)) return -1;
+    return zone_of(st, px, py);
+}
+
+void pps_oracle_run_point(const pps_oracle_dpps_state* st, const double* prm,
+                          double px, double py, double* out)
+{
+    double L = st->sc[PPS_ORACLE_FIELD_LEN], W = st->sc[PPS_ORACLE_FIELD_WID];
+    double bx = st->sc[PPS_ORACLE_BALL_X], by = st->sc[PPS_ORACLE_BALL_Y];
+    double hw = 0.5 * st->sc[PPS_ORACLE_GOAL_WIDTH];
+    double vmax = st->sc[PPS_ORACLE_VMAX], amax = st->sc[PPS_ORACLE_AMAX];
+    /* the opponent's defence area: x in [L/2 - depth, L/2], |y| <= width/2 */
+    double x0 = 0.5 * L - prm[PPS_ORACLE_R_DEF_DEPTH], x1 = 0.5 * L;
+    double y1 = 0.5 * prm[PPS_ORACLE_R_DEF_WIDTH], y0 = -y1;
+    /* 1. distance to the opponent's goal, a cost */
+    double gx = x1 - px, gy = -py;
+    double x_goal = sqrt(gx * gx + gy * gy) / sqrt(L * L + W * W);
+    /* 2. distance to the ball: being too close is bad (READING: the credit
+     * grows with the distance up to ball_ref) */
+    double db = sqrt((px - bx) * (px - bx) + (py - by) * (py - by));
+    double ref = prm[PPS_ORACLE_R_BALL_REF];
+    double x_ball = (db < ref ? db : ref) / ref;
+    /* 3. angle to the goal: the best chance lies in a range of angles off
+     * the goal axis, not at 0 (READING: full credit in [lo, hi], falling
+     * linearly to 0 over span on either side) */
+    double alpha = fabs(atan2(gy, gx));
+    double lo = prm[PPS_ORACLE_R_ANGLE_LO], hi = prm[PPS_ORACLE_R_ANGLE_HI];
+    double off = alpha < lo ? lo - alpha : (alpha > hi ? alpha - hi : 0.0);
+    double f = off / prm[PPS_ORACLE_R_ANGLE_SPAN];
+    double x_angle = 1.0 - (f > 1.0 ? 1.0 : f);
+    /* 4. the opponent guards' time: P and Q are where the lines from p to
+     * the two goal posts enter the defence area; the guards are the
+     * opponents inside it (READING: the time to each of P and Q is the
+     * fastest guard's, capped; no guard or no entry scores the cap) */
+    double cap = prm[PPS_ORACLE_R_GUARD_CAP];
+    double tsum = 0.0;
+    for (int side = 0; side < 2; ++side) {
+        double ex, ey, T = cap;
+        if (segment_entry(px, py, x1, side ? hw : -hw, x0, x1, y0, y1, &ex,
+                          &ey)) {
+            for (int j = 0; j < st->n_opp; ++j) {
+                const double* o = st->opp + 4 * j;
+                if (o[0] < x0 || o[0] > x1 || o[1] < y0 || o[1] > y1) continue;
+                double t = pps_oracle_intercept_time(o[0], o[1], o[2], o[3], ex,
+                                                     ey, vmax, amax, 0.0);
+                if (t < T) T = t;
+            }
+        }
+        tsum += T;
+    }
+    double x_guard = tsum / (2.0 * cap);
+    /* 5. avoid the opponent's defence: a cost when some opponent is nearer
+     * the ball than p, so it would reach the ball first */
+    double x_avoid = 0.0;
+    for (int j = 0; j < st->n_opp; ++j) {
+        const double* o = st->opp + 4 * j;
+        double dj = sqrt((o[0] - bx) * (o[0] - bx) + (o[1] - by) * (o[1] - by));
+        if (dj < db) x_avoid = 1.0;
+    }
+    /* READING: attackers may not stand inside the opponent's defence area,
+     * so its interior holds no candidate */
+    int cand = !(px > x0 && py > y0 && py < y1);
+    out[0] = cand ? -prm[PPS_ORACLE_R_W_GOAL] * x_goal
+                        + prm[PPS_ORACLE_R_W_BALL] * x_ball
+                        + prm[PPS_ORACLE_R_W_ANGLE] * x_angle
+                        + prm[PPS_ORACLE_R_W_GUARD] * x_guard
+                        - prm[PPS_ORACLE_R_W_AVOID] * x_avoid
+                  : -INFINITY;
+    out[1] = zone_of(st, px, py);
+    out[2] = x_goal;
+    out[3] = x_ball;
+    out[4] = x_angle;
+    out[5] = x_guard;
+    out[6] = x_avoid;
+    out[7] = cand;
+}
+
+void pps_oracle_run_choose(const int64_t* best_idx, const double* best_score,
+                           int avoid, int n_run, int* chosen)
+{
+    int k = 0;
+    for (int z = 0; z < 4; ++z) chosen[z] = -1;
+    /* the front pair (III, IV) first, then I, II */
+    for (int pair = 1; pair >= 0; --pair) {
+        int a = 2 * pair, b = 2 * pair + 1;
+        int first = best_score[b] > best_score[a] ? b : a;
+        int order[2] = {first, first == a ? b : a};
+        for (int t = 0; t < 2; ++t) {
+            int z = order[t];
+            if (k < n_run && best_idx[z] >= 0 && z != avoid) chosen[k++] = z;
+        }
+    }
+}
+
+int pps_oracle_run_search(int S, const double* sc, const int* n_opp,
+                          const double* opp, int jstride, const double* prm,
+                          const double* pass, int64_t* best_idx,
+                          double* best_score, int* chosen, int* avoided,
+                          double* score, int n_threads)
+{
+    double g = prm[PPS_ORACLE_R_SPACING];
+    if (S < 0 || !(g > 0.0)) return -1;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int s = 0; s < S; ++s) {
+        pps_oracle_dpps_state st;
+        st.sc = sc + (int64_t)s * PPS_ORACLE_NSCALAR;
+        st.n_team = 0;
+        st.team = NULL;
+        st.n_opp = n_opp[s];
+        st.opp = opp + (int64_t)s * jstride * 4;
+        st.K = 1;
+        double L = st.sc[PPS_ORACLE_FIELD_LEN], W = st.sc[PPS_ORACLE_FIELD_WID];
+        int nx = (int)lround(0.5 * L / g) + 1, ny = (int)lround(W / g) + 1;
+        int64_t* bi = best_idx + 4 * s;
+        double* bs = best_score + 4 * s;
+        for (int z = 0; z < 4; ++z) {
+            bi[z] = -1;
+            bs[z] = -INFINITY;
+        }
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                double out[8];
+                pps_oracle_run_point(&st, prm, i * g, -0.5 * W + j * g, out);
+                int64_t idx = (int64_t)j * nx + i;
+                int z = (int)out[1];
+                if (score) score[(int64_t)s * nx * ny + idx] = out[0];
+                if (out[7] != 0.0 && (bi[z] < 0 || out[0] > bs[z])) {
+                    bi[z] = idx;
+                    bs[z] = out[0];
+                }
+            }
+        int av = -1;
+        if (pass && !isnan(pass[2 * s]) && !isnan(pass[2 * s + 1]))
+            av = pps_oracle_run_zone(&st, pass[2 * s], pass[2 * s + 1]);
+        avoided[s] = av;
+        pps_oracle_run_choose(bi, bs, av, (int)prm[PPS_ORACLE_R_N_RUN],
+                              chosen + 4 * s);
+    }
+    (void)n_threads;
+    return 0;
+}
+
 int pps_oracle_max_threads(void)
 {
 #ifdef _OPENMP

@@ -229,6 +229,61 @@ void pps_oracle_shoot(const pps_oracle_dpps_state* st, double cx, double cy,
 double pps_oracle_shot_gap(const pps_oracle_state* st, double cx, double cy,
                            double r, double* start);
 
+/* ---- R: running points (Sec. 5.1-5.2) ----
+ * The attacking half is rasterised (x = i g, i = 0..round(L/2/g);
+ * y = -W/2 + j g, j = 0..round(W/g)) and split into four zones: I, II
+ * behind x = L/4, III, IV in front of it, each pair split at the ball's y
+ * (kept within +-W/4, so the zones move with the ball).  Every grid point
+ * outside the opponent's defence area is scored by the weighted sum of the
+ * five criteria of Sec. 5.2 (Eq. 4); the best point of each zone is the
+ * zone's running point.  Parameters, PPS_ORACLE_R_NPARAM doubles: */
+enum {
+    PPS_ORACLE_R_SPACING = 0,
+    PPS_ORACLE_R_W_GOAL = 1,     /* weight of |goal - p| / diagonal (a cost) */
+    PPS_ORACLE_R_W_BALL = 2,     /* weight of min(|p - b|, ball_ref) / ball_ref */
+    PPS_ORACLE_R_W_ANGLE = 3,    /* weight of the angle-to-goal credit */
+    PPS_ORACLE_R_W_GUARD = 4,    /* weight of the guards' time to P and Q */
+    PPS_ORACLE_R_W_AVOID = 5,    /* weight of the defence-avoidance cost */
+    PPS_ORACLE_R_BALL_REF = 6,   /* m */
+    PPS_ORACLE_R_ANGLE_LO = 7,   /* rad: full credit for angles in [lo, hi] */
+    PPS_ORACLE_R_ANGLE_HI = 8,
+    PPS_ORACLE_R_ANGLE_SPAN = 9, /* rad: the credit falls to 0 over this span */
+    PPS_ORACLE_R_DEF_DEPTH = 10, /* defence area depth (m) */
+    PPS_ORACLE_R_DEF_WIDTH = 11, /* defence area width (m) */
+    PPS_ORACLE_R_GUARD_CAP = 12, /* s: cap of each guard time */
+    PPS_ORACLE_R_N_RUN = 13,     /* supporters to place, 0..4 */
+    PPS_ORACLE_R_NPARAM = 14
+};
+
+/* The point (px, py) of state st (its ball and opponents; teammates
+ * unused): out[0] score (-inf inside the defence area), out[1] zone 0..3
+ * (I..IV), out[2..6] the criteria (goal distance, ball, angle, guard,
+ * avoid), out[7] 1 if a candidate (outside the defence area). */
+void pps_oracle_run_point(const pps_oracle_dpps_state* st, const double* prm,
+                          double px, double py, double* out);
+
+/* Zone of a point of the attacking half (-1 outside it). */
+int pps_oracle_run_zone(const pps_oracle_dpps_state* st, double px,
+                        double py);
+
+/* Sec. 5.1's choice of zones for n_run supporters: zones without a point
+ * and the zone `avoid` (the best passing point's, -1 none) are left out;
+ * zones III and IV come before I and II, each pair by score (the lower
+ * zone first on ties).  chosen[0..3]: zones in that order, -1 after the
+ * last. */
+void pps_oracle_run_choose(const int64_t* best_idx, const double* best_score,
+                           int avoid, int n_run, int* chosen);
+
+/* All states: per state and zone the best grid index j * nx + i (-1 if the
+ * zone holds no candidate; the lowest index on ties) and score, the chosen
+ * zones and the avoided zone.  pass: S x 2 best passing points (NaN: none)
+ * or NULL.  score: optional dense scores, S x ny x nx. */
+int pps_oracle_run_search(int S, const double* sc, const int* n_opp,
+                          const double* opp, int jstride, const double* prm,
+                          const double* pass, int64_t* best_idx,
+                          double* best_score, int* chosen, int* avoided,
+                          double* score, int n_threads);
+
 int pps_oracle_max_threads(void);
 
 #ifdef __cplusplus

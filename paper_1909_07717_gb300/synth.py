@@ -196,6 +196,47 @@ def dpps_oracle_params(p: dict = DPPS_PARAMS) -> dict:
             "reach_radius": p["reach_radius"], "min_time": 0.0}
 
 
+# Running points (Sec. 5.1-5.2).  The paper gives no weights and no
+# criterion constants; these defaults are the build's: the 0.1 m raster the
+# paper names, weights 1, full distance credit from 2 m off the ball, full
+# angle credit 0.25-0.75 rad off the goal axis (falling to 0 over 0.5 rad),
+# the 2019 SSL division-A defence area (1.2 m deep, 2.4 m wide), guard times
+# capped at 2 s, four supporters.
+RUN_SEED = 6
+RUN_STATES = 4096
+RUN_PARAMS = {"spacing": 0.1, "w_goal": 1.0, "w_ball": 1.0, "w_angle": 1.0,
+              "w_guard": 1.0, "w_avoid": 1.0, "ball_ref": 2.0,
+              "angle_lo": 0.25, "angle_hi": 0.75, "angle_span": 0.5,
+              "def_depth": 1.2, "def_width": 2.4, "guard_cap": 2.0,
+              "n_run": 4}
+
+
+def run_states(seed: int, n_states: int, *, n_opp: int = 16,
+               def_depth: float = 1.2, def_width: float = 2.4) -> dict:
+    """States for the running-point search: as ``dpps_states``, but the
+    first opponent is a goalkeeper, placed uniformly inside the defence area
+    of the goal at +L/2, and in half the states (drawn) the second opponent
+    is a second guard placed the same way."""
+    b = dpps_states(seed, n_states, n_team=0, n_opp=n_opp, K=1)
+    rng = np.random.Generator(np.random.PCG64(seed + 1000))
+    L = b["field_len"].astype(np.float64)
+    for j in range(min(2, n_opp)):
+        x = 0.5 * L - rng.uniform(0.0, def_depth, n_states)
+        y = rng.uniform(-0.5 * def_width, 0.5 * def_width, n_states)
+        take = np.ones(n_states, bool) if j == 0 else \
+            rng.uniform(size=n_states) < 0.5
+        b["opp_pos"][take, j, 0] = x[take]
+        b["opp_pos"][take, j, 1] = y[take]
+    return b
+
+
+def run_oracle_params(p: dict = RUN_PARAMS) -> dict:
+    """The running-point parameters as the CUDA path holds them (float32),
+    promoted for the oracle."""
+    return {k: (float(np.float32(v)) if k != "n_run" else int(v))
+            for k, v in p.items()}
+
+
 def uneven_batch(seed: int, n_states: int, *,
                  spacings=(0.025, 0.05, 0.1), k_range=(32, 128),
                  speed_range=(2.0, 6.5), decel_range=(0.3, 0.7),

@@ -16,6 +16,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_pins as pins
+from tests import test_oracle_run as run_pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "pps_oracle.c")
 
@@ -82,8 +83,50 @@ CHECKS = [pins.check_hand_ball, pins.check_hand_intercept,
           pins.check_intercept_monotone]
 
 
-def _caught(orc):
-    for chk in CHECKS:
+# Running points (Sec. 5.1-5.2), checked by the running-point pins.
+RUN_MUTANTS = [
+    ("run: zone cut at L/2", "return (px >= 0.25 * L ? 2 : 0) + (py >= ys ? 1 : 0);",
+     "return (px >= 0.5 * L ? 2 : 0) + (py >= ys ? 1 : 0);"),
+    ("run: zone ignores the ball", "double ys = by < -0.25 * W ? -0.25 * W : (by > 0.25 * W ? 0.25 * W : by);",
+     "double ys = 0.0;"),
+    ("run: zone clamp dropped", "double ys = by < -0.25 * W ? -0.25 * W : (by > 0.25 * W ? 0.25 * W : by);",
+     "double ys = by;"),
+    ("run: goal distance over L", "double x_goal = sqrt(gx * gx + gy * gy) / sqrt(L * L + W * W);",
+     "double x_goal = sqrt(gx * gx + gy * gy) / L;"),
+    ("run: ball credit uncapped", "double x_ball = (db < ref ? db : ref) / ref;",
+     "double x_ball = db / ref;"),
+    ("run: angle band low side dropped", "double off = alpha < lo ? lo - alpha : (alpha > hi ? alpha - hi : 0.0);",
+     "double off = alpha > hi ? alpha - hi : 0.0;"),
+    ("run: angle credit not clamped", "double x_angle = 1.0 - (f > 1.0 ? 1.0 : f);",
+     "double x_angle = 1.0 - f;"),
+    ("run: both lines to one post", "side ? hw : -hw", "hw"),
+    ("run: guards outside the area", "if (o[0] < x0 || o[0] > x1 || o[1] < y0 || o[1] > y1) continue;",
+     ";"),
+    ("run: slowest guard", "if (t < T) T = t;\n            }\n        }\n        tsum += T;",
+     "if (t > T || T == cap) T = t;\n            }\n        }\n        tsum += T;"),
+    ("run: guard cap not applied", "double ex, ey, T = cap;", "double ex, ey, T = 1e300;"),
+    ("run: entry at the far side", "*ex = px + t0 * dx;\n    *ey = py + t0 * dy;",
+     "*ex = px + t1 * dx;\n    *ey = py + t1 * dy;"),
+    ("run: avoid comparison flipped", "if (dj < db) x_avoid = 1.0;",
+     "if (dj > db) x_avoid = 1.0;"),
+    ("run: avoid sign", "- prm[PPS_ORACLE_R_W_AVOID] * x_avoid",
+     "+ prm[PPS_ORACLE_R_W_AVOID] * x_avoid"),
+    ("run: goal sign", "cand ? -prm[PPS_ORACLE_R_W_GOAL] * x_goal",
+     "cand ? prm[PPS_ORACLE_R_W_GOAL] * x_goal"),
+    ("run: defence area kept", "int cand = !(px > x0 && py > y0 && py < y1);",
+     "int cand = 1;"),
+    ("run: ties to the larger index", "if (out[7] != 0.0 && (bi[z] < 0 || out[0] > bs[z])) {",
+     "if (out[7] != 0.0 && (bi[z] < 0 || out[0] >= bs[z])) {"),
+    ("run: back pair first", "for (int pair = 1; pair >= 0; --pair) {",
+     "for (int pair = 0; pair <= 1; ++pair) {"),
+    ("run: pass zone not avoided", "best_idx[z] >= 0 && z != avoid", "best_idx[z] >= 0"),
+    ("run: grid y from 0", "pps_oracle_run_point(&st, prm, i * g, -0.5 * W + j * g, out);",
+     "pps_oracle_run_point(&st, prm, i * g, j * g, out);"),
+]
+
+
+def _caught(orc, checks=None):
+    for chk in checks or CHECKS:
         try:
             chk(orc)
         except (AssertionError, ValueError, ZeroDivisionError, OverflowError):
@@ -103,4 +146,19 @@ def test_mutant_is_caught(tmp_path, name, orig, mut):
     lib = oracle.build(force=True, src=bad,
                        out=os.path.join(tmp_path, "libmutant.so"))
     caught = _caught(oracle.Oracle(lib))
+    assert caught is not None, f"no pin caught mutant: {name}"
+
+
+@pytest.mark.parametrize("name,orig,mut", RUN_MUTANTS,
+                         ids=[m[0] for m in RUN_MUTANTS])
+def test_running_point_mutant_is_caught(tmp_path, name, orig, mut):
+    text = open(SRC).read()
+    assert text.count(orig) >= 1, f"mutation site missing: {orig!r}"
+    bad = os.path.join(tmp_path, "pps_oracle.c")
+    with open(bad, "w") as f:
+        f.write(text.replace(orig, mut, 1))
+    shutil.copy(os.path.join(os.path.dirname(SRC), "pps_oracle.h"), tmp_path)
+    lib = oracle.build(force=True, src=bad,
+                       out=os.path.join(tmp_path, "libmutant.so"))
+    caught = _caught(oracle.Oracle(lib), run_pins.CHECKS)
     assert caught is not None, f"no pin caught mutant: {name}"
