@@ -799,7 +799,12 @@ int pps_oracle_run_search(int S, const double* sc, const int* n_opp,
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
                 double out[8];
-                pps_oracle_run_point(&st, prm, i * g, -0.5 * W + j * g, out);
+                /* READING: the raster spans the attacking half exactly;
+                 * its last column lies on the goal line and its last row
+                 * on the touch line, whatever the rounding of i g */
+                double px = fmin(i * g, 0.5 * L);
+                double py = fmin(-0.5 * W + j * g, 0.5 * W);
+                pps_oracle_run_point(&st, prm, px, py, out);
                 int64_t idx = (int64_t)j * nx + i;
                 int z = (int)out[1];
                 if (score) score[(int64_t)s * nx * ny + idx] = out[0];

@@ -230,8 +230,8 @@ double pps_oracle_shot_gap(const pps_oracle_state* st, double cx, double cy,
                            double r, double* start);
 
 /* ---- R: running points (Sec. 5.1-5.2) ----
- * The attacking half is rasterised (x = i g, i = 0..round(L/2/g);
- * y = -W/2 + j g, j = 0..round(W/g)) and split into four zones: I, II
+ * The attacking half is rasterised (x = min(i g, L/2), i = 0..round(L/2/g);
+ * y = min(-W/2 + j g, W/2), j = 0..round(W/g)) and split into four zones: I, II
  * behind x = L/4, III, IV in front of it, each pair split at the ball's y
  * (kept within +-W/4, so the zones move with the ball).  Every grid point
  * outside the opponent's defence area is scored by the weighted sum of the

@@ -120,8 +120,8 @@ RUN_MUTANTS = [
     ("run: back pair first", "for (int pair = 1; pair >= 0; --pair) {",
      "for (int pair = 0; pair <= 1; ++pair) {"),
     ("run: pass zone not avoided", "best_idx[z] >= 0 && z != avoid", "best_idx[z] >= 0"),
-    ("run: grid y from 0", "pps_oracle_run_point(&st, prm, i * g, -0.5 * W + j * g, out);",
-     "pps_oracle_run_point(&st, prm, i * g, j * g, out);"),
+    ("run: grid y from 0", "double py = fmin(-0.5 * W + j * g, 0.5 * W);",
+     "double py = fmin(j * g, 0.5 * W);"),
 ]
 
 

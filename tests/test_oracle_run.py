@@ -167,8 +167,8 @@ def _zones_here(batch, s, nx, ny, g):
     W = float(batch["field_wid"][s])
     by = float(batch["ball"][s][1])
     ys = min(max(by, -W / 4), W / 4)
-    x = np.arange(nx) * g
-    y = -W / 2 + np.arange(ny) * g
+    x = np.minimum(np.arange(nx) * g, L / 2)
+    y = np.minimum(-W / 2 + np.arange(ny) * g, W / 2)
     X, Y = np.meshgrid(x, y)
     return (X >= L / 4) * 2 + (Y >= ys)
 
@@ -204,6 +204,28 @@ def check_ties_go_to_the_lowest_index(orc):
         for q in range(4):
             assert r["best_idx"][s, q] == np.where(z == q)[0][0]
             assert r["best_score"][s, q] == 0.0
+
+
+def check_raster_ends_on_the_goal_and_touch_lines(orc):
+    """With g = 0.1 as a float (0.100000001...), 60 g overshoots 6 m: the
+    last column still lies on the goal line, where a point's lines to the
+    posts run along the defence area's back edge and enter it at its
+    corner, (6, +-1.2)."""
+    batch = synth.run_states(15, 1)
+    batch["opp_pos"][0, 0] = (6.0, 1.2)      # a guard at rest on the corner
+    batch["opp_vel"][0, 0] = (0.0, 0.0)
+    batch["opp_pos"][0, 1] = (-6.0, 0.0)     # the second: out of the area
+    prm = synth.run_oracle_params()
+    r = orc.run_search(batch, prm, dense=True)
+    st = oracle.dstate_of(batch, 0)
+    top = orc.run_point(st, prm, (6.0, 4.5))
+    assert r["score"][0, -1, -1] == top["score"]
+    # both lines run down the goal line and enter at the corner, where the
+    # guard stands: no time to either P or Q
+    assert top["guard"] < 1e-6
+    # one step in from the goal line the lines enter through the side
+    # y = 1.2 left of the corner, and the guard needs time
+    assert orc.run_point(st, prm, (5.9, 4.5))["guard"] > 1e-2
 
 
 def check_zone_choice_hand_cases(orc):
@@ -263,6 +285,7 @@ CHECKS = [
     check_score_is_the_weighted_sum_with_costs_signed,
     check_best_per_zone_is_the_argmax_of_the_dense_scores,
     check_ties_go_to_the_lowest_index,
+    check_raster_ends_on_the_goal_and_touch_lines,
     check_zone_choice_hand_cases,
     check_pass_point_zone_is_avoided,
     check_mirror_symmetry,
