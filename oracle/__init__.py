@@ -97,7 +97,7 @@ def _bind(lib):
     lib.pps_oracle_run_point.restype = None
     lib.pps_oracle_run_point.argtypes = [p, p, d, d, p]
     lib.pps_oracle_run_zone.restype = i
-    lib.pps_oracle_run_zone.argtypes = [p, d, d]
+    lib.pps_oracle_run_zone.argtypes = [p, p, d, d]
     lib.pps_oracle_run_choose.restype = None
     lib.pps_oracle_run_choose.argtypes = [p, p, i, i, p]
     lib.pps_oracle_run_search.restype = i
@@ -359,8 +359,14 @@ class Oracle:
         r.update(zip(RUN_CRITERIA, out[2:7].tolist()))
         return r
 
-    def run_zone(self, st: DState, p) -> int:
-        return self.lib.pps_oracle_run_zone(st.ref, float(p[0]), float(p[1]))
+    def run_zone(self, st: DState, p, params: dict | None = None) -> int:
+        """Zone 0..3 of point p, -1 outside the attacking half; the edge
+        tolerance comes from params' spacing (default 0.1 m)."""
+        params = params or {"spacing": 0.1}
+        prm = np.zeros(len(RUN_PARAMS), np.float64)
+        prm[0] = float(params["spacing"])
+        return self.lib.pps_oracle_run_zone(st.ref, _ptr(prm), float(p[0]),
+                                            float(p[1]))
 
     def run_choose(self, best_idx, best_score, avoid, n_run):
         bi = np.ascontiguousarray(np.asarray(best_idx, np.int64))

@@ -660,22 +660,33 @@ static int segment_entry(double px, double py, double qx, double qy,
 }
 
 /* READING: zones I-IV are the attacking half cut at x = L/4 and at the
- * ball's y, kept within +-W/4 so that no zone closes up.  No bounds check:
- * the grid's last column may lie a rounding error beyond L/2. */
-static int zone_of(const pps_oracle_dpps_state* st, double px, double py)
+ * ball's y, kept within +-W/4 so that no zone closes up.  A point within
+ * tol of a cut counts as on it (and so in front of it or above it).  No
+ * bounds check: the grid's last column may lie a rounding error beyond
+ * L/2. */
+static int zone_of(const pps_oracle_dpps_state* st, double px, double py,
+                   double tol)
 {
     double L = st->sc[PPS_ORACLE_FIELD_LEN], W = st->sc[PPS_ORACLE_FIELD_WID];
     double by = st->sc[PPS_ORACLE_BALL_Y];
     double ys = by < -0.25 * W ? -0.25 * W : (by > 0.25 * W ? 0.25 * W : by);
-    return (px >= 0.25 * L ? 2 : 0) + (py >= ys ? 1 : 0);
+    return (px >= 0.25 * L - tol ? 2 : 0) + (py >= ys - tol ? 1 : 0);
 }
 
-int pps_oracle_run_zone(const pps_oracle_dpps_state* st, double px,
-                        double py)
+/* READING: the cuts and the defence area's edges fall on grid lines at the
+ * decimal spacings the paper rasterises with (0.1 m), where the rounding of
+ * i g must not decide; a point within g / 1024 of one counts as on it. */
+static double edge_tol(const double* prm)
+{
+    return prm[PPS_ORACLE_R_SPACING] / 1024.0;
+}
+
+int pps_oracle_run_zone(const pps_oracle_dpps_state* st, const double* prm,
+                        double px, double py)
 {
     double L = st->sc[PPS_ORACLE_FIELD_LEN], W = st->sc[PPS_ORACLE_FIELD_WID];
     if (!(px >= 0.0 && px <= 0.5 * L && fabs(py) <= 0.5 * W)) return -1;
-    return zone_of(st, px, py);
+    return zone_of(st, px, py, edge_tol(prm));
 }
 
 void pps_oracle_run_point(const pps_oracle_dpps_state* st, const double* prm,
@@ -734,15 +745,17 @@ void pps_oracle_run_point(const pps_oracle_dpps_state* st, const double* prm,
         if (dj < db) x_avoid = 1.0;
     }
     /* READING: attackers may not stand inside the opponent's defence area,
-     * so its interior holds no candidate */
-    int cand = !(px > x0 && py > y0 && py < y1);
+     * so its interior holds no candidate; its edge (within the tolerance)
+     * does */
+    double tol = edge_tol(prm);
+    int cand = !(px > x0 + tol && py > y0 + tol && py < y1 - tol);
     out[0] = cand ? -prm[PPS_ORACLE_R_W_GOAL] * x_goal
                         + prm[PPS_ORACLE_R_W_BALL] * x_ball
                         + prm[PPS_ORACLE_R_W_ANGLE] * x_angle
                         + prm[PPS_ORACLE_R_W_GUARD] * x_guard
                         - prm[PPS_ORACLE_R_W_AVOID] * x_avoid
                   : -INFINITY;
-    out[1] = zone_of(st, px, py);
+    out[1] = zone_of(st, px, py, tol);
     out[2] = x_goal;
     out[3] = x_ball;
     out[4] = x_angle;
@@ -815,7 +828,7 @@ int pps_oracle_run_search(int S, const double* sc, const int* n_opp,
             }
         int av = -1;
         if (pass && !isnan(pass[2 * s]) && !isnan(pass[2 * s + 1]))
-            av = pps_oracle_run_zone(&st, pass[2 * s], pass[2 * s + 1]);
+            av = pps_oracle_run_zone(&st, prm, pass[2 * s], pass[2 * s + 1]);
         avoided[s] = av;
         pps_oracle_run_choose(bi, bs, av, (int)prm[PPS_ORACLE_R_N_RUN],
                               chosen + 4 * s);

@@ -233,8 +233,10 @@ double pps_oracle_shot_gap(const pps_oracle_state* st, double cx, double cy,
  * The attacking half is rasterised (x = min(i g, L/2), i = 0..round(L/2/g);
  * y = min(-W/2 + j g, W/2), j = 0..round(W/g)) and split into four zones: I, II
  * behind x = L/4, III, IV in front of it, each pair split at the ball's y
- * (kept within +-W/4, so the zones move with the ball).  Every grid point
- * outside the opponent's defence area is scored by the weighted sum of the
+ * (kept within +-W/4, so the zones move with the ball).  A point within
+ * spacing / 1024 of a cut or of the defence area's edge counts as on it.
+ * Every grid point outside the opponent's defence area (its edge included)
+ * is scored by the weighted sum of the
  * five criteria of Sec. 5.2 (Eq. 4); the best point of each zone is the
  * zone's running point.  Parameters, PPS_ORACLE_R_NPARAM doubles: */
 enum {
@@ -262,9 +264,10 @@ enum {
 void pps_oracle_run_point(const pps_oracle_dpps_state* st, const double* prm,
                           double px, double py, double* out);
 
-/* Zone of a point of the attacking half (-1 outside it). */
-int pps_oracle_run_zone(const pps_oracle_dpps_state* st, double px,
-                        double py);
+/* Zone of a point of the attacking half (-1 outside it); the cuts take the
+ * edge tolerance spacing / 1024 of prm. */
+int pps_oracle_run_zone(const pps_oracle_dpps_state* st, const double* prm,
+                        double px, double py);
 
 /* Sec. 5.1's choice of zones for n_run supporters: zones without a point
  * and the zone `avoid` (the best passing point's, -1 none) are left out;

@@ -85,8 +85,10 @@ CHECKS = [pins.check_hand_ball, pins.check_hand_intercept,
 
 # Running points (Sec. 5.1-5.2), checked by the running-point pins.
 RUN_MUTANTS = [
-    ("run: zone cut at L/2", "return (px >= 0.25 * L ? 2 : 0) + (py >= ys ? 1 : 0);",
-     "return (px >= 0.5 * L ? 2 : 0) + (py >= ys ? 1 : 0);"),
+    ("run: zone cut at L/2", "return (px >= 0.25 * L - tol ? 2 : 0) + (py >= ys - tol ? 1 : 0);",
+     "return (px >= 0.5 * L - tol ? 2 : 0) + (py >= ys - tol ? 1 : 0);"),
+    ("run: no edge tolerance", "return prm[PPS_ORACLE_R_SPACING] / 1024.0;",
+     "return 0.0;"),
     ("run: zone ignores the ball", "double ys = by < -0.25 * W ? -0.25 * W : (by > 0.25 * W ? 0.25 * W : by);",
      "double ys = 0.0;"),
     ("run: zone clamp dropped", "double ys = by < -0.25 * W ? -0.25 * W : (by > 0.25 * W ? 0.25 * W : by);",
@@ -113,7 +115,7 @@ RUN_MUTANTS = [
      "+ prm[PPS_ORACLE_R_W_AVOID] * x_avoid"),
     ("run: goal sign", "cand ? -prm[PPS_ORACLE_R_W_GOAL] * x_goal",
      "cand ? prm[PPS_ORACLE_R_W_GOAL] * x_goal"),
-    ("run: defence area kept", "int cand = !(px > x0 && py > y0 && py < y1);",
+    ("run: defence area kept", "int cand = !(px > x0 + tol && py > y0 + tol && py < y1 - tol);",
      "int cand = 1;"),
     ("run: ties to the larger index", "if (out[7] != 0.0 && (bi[z] < 0 || out[0] > bs[z])) {",
      "if (out[7] != 0.0 && (bi[z] < 0 || out[0] >= bs[z])) {"),

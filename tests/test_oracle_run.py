@@ -228,6 +228,27 @@ def check_raster_ends_on_the_goal_and_touch_lines(orc):
     assert orc.run_point(st, prm, (5.9, 4.5))["guard"] > 1e-2
 
 
+def check_edges_take_a_tolerance_of_g_over_1024(orc):
+    """A point within g / 1024 (about 1e-4 m at 0.1 m) of the defence
+    area's edge or of a zone cut counts as on it, so grid points on those
+    lines do not depend on the rounding of i g."""
+    st = _st()
+    assert orc.run_point(st, PRM, (4.8 + 5e-5, 0.0))["candidate"]
+    assert not orc.run_point(st, PRM, (4.8 + 2e-4, 0.0))["candidate"]
+    assert orc.run_point(st, PRM, (5.5, 1.2 - 5e-5))["candidate"]
+    assert not orc.run_point(st, PRM, (5.5, 1.2 - 2e-4))["candidate"]
+    assert orc.run_zone(st, (3.0 - 5e-5, 1.0), PRM) == 3
+    assert orc.run_zone(st, (3.0 - 2e-4, 1.0), PRM) == 1
+    assert orc.run_zone(st, (1.0, -5e-5), PRM) == 1
+    assert orc.run_zone(st, (1.0, -2e-4), PRM) == 0
+    # on the float grid, column 48 (48 g = 4.80000007 with g the float
+    # nearest 0.1) is on the area's front edge: a candidate at y = 0
+    batch = synth.run_states(16, 1)
+    r = orc.run_search(batch, synth.run_oracle_params(), dense=True)
+    assert np.isfinite(r["score"][0, 45, 48])
+    assert np.isinf(r["score"][0, 45, 49])
+
+
 def check_zone_choice_hand_cases(orc):
     idx = [10, 20, 30, 40]
     sc = [0.5, 0.9, 1.0, 1.2]
@@ -286,6 +307,7 @@ CHECKS = [
     check_best_per_zone_is_the_argmax_of_the_dense_scores,
     check_ties_go_to_the_lowest_index,
     check_raster_ends_on_the_goal_and_touch_lines,
+    check_edges_take_a_tolerance_of_g_over_1024,
     check_zone_choice_hand_cases,
     check_pass_point_zone_is_avoided,
     check_mirror_symmetry,
