@@ -385,6 +385,8 @@ def run_pps(args):
             line["proposal"] = _proposal(args, dev, stream)
         if world == 1 and not args.no_dpps:
             line["dpps"] = _dpps(args, dev, stream)
+        if world == 1 and not args.no_run:
+            line["run_points"] = _run_points(args, dev, stream)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
@@ -575,6 +577,72 @@ def _dpps(args, dev, stream):
             "ok": bool(np.all(b["status"] == 0))}
 
 
+def _run_points(args, dev, stream):
+    """Running points (Sec. 5.1-5.2): the attacking half of a 12 x 9 m field
+    at 0.1 m (61 x 91 points), every point scored by the five criteria, the
+    best point of each of the four zones and the supporters' zones, for
+    4096 states with 16 opponents (one or two guards); timed like the main
+    step, with and without the dense score output.  The oracle's rate on the
+    host cores (512 states) beside it."""
+    import torch
+    from paper_1909_07717_gb300 import pps, synth
+    S = args.states or synth.RUN_STATES
+    prm = pps.rparams_from_dict(synth.RUN_PARAMS)
+    batch = synth.run_states(synth.RUN_SEED, S)
+    nx, ny = pps.pps_run_grid(12.0, 9.0, prm.spacing)
+    searcher = pps.Searcher(max_states=S, max_opp=16, device=dev.index,
+                            stream=stream)
+    rec = torch.from_numpy(pps.pack_dstates(batch).view(np.uint8).copy()).to(dev)
+    out = torch.empty(S * pps.RBEST_DTYPE.itemsize, dtype=torch.uint8,
+                      device=dev)
+    dense = torch.empty((S, nx * ny), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed(with_dense):
+        def run():
+            pps.pps_run_points(searcher.ctx, rec.data_ptr(), S, prm,
+                               out.data_ptr(), None,
+                               dense.data_ptr() if with_dense else None,
+                               nx * ny if with_dense else 0)
+        for _ in range(2):
+            run()
+        steps = max(3, min(args.steps, 5))
+        ev = [(torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            run()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / steps
+
+    ms = timed(False)
+    ms_dense = timed(True)
+    r = np.frombuffer(out.cpu().numpy().tobytes(), pps.RBEST_DTYPE)
+    searcher.close()
+    pts = S * nx * ny
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        sub = {k: (v[:512] if isinstance(v, np.ndarray) else v)
+               for k, v in batch.items()}
+        t0 = time.perf_counter()
+        oracle.run_search(sub, synth.run_oracle_params())
+        dt = time.perf_counter() - t0
+        cpu = {"points_per_s": 512 * nx * ny / dt, "states_per_s": 512 / dt,
+               "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "first 512 states of the workload"}
+    return {"workload": (f"run_{S}x{nx}x{ny}: 12x9 m attacking half at "
+                         f"0.1 m, 16 opponents (seed {synth.RUN_SEED})"),
+            "unit": "points/s", "value": pts / (ms / 1e3), "ms_per_run": ms,
+            "states_per_s": S / (ms / 1e3),
+            "ms_per_run_dense": ms_dense,
+            "dense_gbs": S * nx * ny * 4 / (ms_dense / 1e3) / 1e9,
+            "cpu_baseline": cpu,
+            "ok": bool(np.all(r["status"] == 0))}
+
+
 def _serving(dev, seconds=2.0):
     """The serving loop: 512 simulated matches at 60 Hz (12x9 or 9x6 fields,
     6-11 opponents, 0.05 m grid, 4 speeds, K = 32) replayed in real time
@@ -623,6 +691,8 @@ def main():
                     help="skip the learned-proposal comparison")
     ap.add_argument("--no-dpps", action="store_true",
                     help="skip the direction x power search")
+    ap.add_argument("--no-run", action="store_true",
+                    help="skip the running-point search")
     ap.add_argument("--states", type=int, default=0,
                     help="states per GPU (default: the workload's 4096); "
                          "smaller only for profiling captures")

@@ -729,6 +729,88 @@ pps_status pps_shoot(pps_ctx* ctx, const pps_dstate* states, int n_states,
                      float v_shot, float theta_min, const pps_dparams* params,
                      pps_shot* out);
 
+/* ---- Running points (Sec. 5.1-5.2) ----------------------------------------
+ *
+ * The attacking half of each state's field (the goal at x = +L/2) is
+ * rasterised at `spacing` g: x = min(i g, L/2), i = 0..nx-1,
+ * nx = round(L/2/g) + 1; y = min(-W/2 + j g, W/2), j = 0..ny-1,
+ * ny = round(W/g) + 1 (rounding to nearest, ties to even, in float), so
+ * the last column lies on the goal line and the last row on the touch
+ * line.  Four zones (Sec. 5.1): I and II behind
+ * x = L/4, III and IV in front of it, each pair split at the ball's y kept
+ * within +-W/4 (I and III below the cut, II and IV on or above it; both
+ * cuts inclusive upward), so the zones move with the ball.  Points inside
+ * the opponent's defence area (x > L/2 - def_depth, |y| < def_width/2) are
+ * no candidates.  A point within g / 1024 of a cut or of the area's edge
+ * counts as on it (so grid lines that fall on them do not depend on the
+ * rounding of i g).  Every other point p gets the weighted sum of Eq. 4 over
+ * the five criteria of Sec. 5.2:
+ *   - w_goal  * |goal - p| / sqrt(L^2 + W^2)           (closer is better)
+ *   + w_ball  * min(|p - ball|, ball_ref) / ball_ref   (not too close)
+ *   + w_angle * a(alpha)   alpha = |angle of goal - p off the x axis|;
+ *                          a = 1 in [angle_lo, angle_hi], falling linearly
+ *                          to 0 over angle_span on either side
+ *   + w_guard * (T_P + T_Q) / (2 guard_cap)
+ *                          P, Q: where the lines from p to the two goal
+ *                          posts enter the defence area; T: the fastest
+ *                          guard's arrival (guards: the opponents inside
+ *                          the area; the bang-bang intercept time of the
+ *                          pass search, reach 0), capped at guard_cap, and
+ *                          guard_cap when no guard or no entry
+ *   - w_avoid * [some opponent is nearer the ball than p]
+ * The best point of each zone (the lowest j * nx + i on ties) is the
+ * zone's running point.  Then the zones are chosen for n_run supporters:
+ * zones without a candidate and the zone holding the best passing point
+ * are left out; III and IV come before I and II, each pair by score (the
+ * lower zone first on ties). */
+typedef struct pps_rparams {
+    float spacing;                          /* grid spacing g (m), > 0 */
+    float w_goal, w_ball, w_angle, w_guard, w_avoid;  /* Eq. 4 weights */
+    float ball_ref;                         /* m, > 0 */
+    float angle_lo, angle_hi, angle_span;   /* rad: 0 <= lo <= hi, span > 0 */
+    float def_depth, def_width;             /* defence area (m), > 0 */
+    float guard_cap;                        /* s, > 0 */
+    int32_t n_run;                          /* supporters, 0..4 */
+} pps_rparams;
+
+typedef struct pps_rbest {
+    int32_t idx[4];       /* zones I..IV: grid index j * nx + i of the best
+                             point; -1: no candidate in the zone */
+    float score[4];       /* -inf when idx < 0 */
+    float point[4][2];    /* (x, y) of the point (m); NaN when idx < 0 */
+    int32_t chosen[4];    /* zones (0..3 = I..IV) for the supporters, in
+                             order; -1 after the last */
+    int32_t avoided;      /* zone of the best passing point; -1: none */
+    int32_t nx, ny;       /* the state's grid */
+    int32_t status;       /* PPS_STATE_OK or PPS_STATE_INVALID */
+} pps_rbest;
+
+/* Defaults: g = 0.1 m, weights 1, ball_ref 2 m, angles 0.25..0.75 rad with
+ * span 0.5 rad, defence area 1.2 m x 2.4 m, guard_cap 2 s, n_run 4. */
+pps_status pps_run_default_params(pps_rparams* out);
+
+/* The grid of a field at spacing g, as the kernel forms it; PPS_EINVAL
+ * for non-positive or non-finite sizes or a side above 32768 points. */
+pps_status pps_run_grid(float field_len, float field_wid, float spacing,
+                        int* nx, int* ny);
+
+/* Running points of n_states states (their ball and opponents; receivers
+ * and K unused).  pass: NULL, or n_states records of pps_dpps_search over
+ * the same states, whose receive point (idx >= 0) names the zone to avoid.
+ * out: n_states records.  out_scores: NULL, or n_states x score_stride
+ * floats; state s writes its nx * ny scores (row j, column i at
+ * s * score_stride + j * nx + i; -inf inside the defence area).  A state
+ * that fails validation (non-finite ball or robot, non-positive field or
+ * robot limits, n_opp outside 0..PPS_MAX_OPP, a grid side above 32768, or
+ * nx * ny above score_stride when out_scores is given) gets
+ * PPS_STATE_INVALID and idx -1.  Device memory, enqueued on the context's
+ * stream; PPS_EINVAL for a NULL buffer, n_states < 0 or out-of-range
+ * parameters. */
+pps_status pps_run_points(pps_ctx* ctx, const pps_dstate* states,
+                          int n_states, const pps_rparams* params,
+                          const pps_dbest* pass, pps_rbest* out,
+                          float* out_scores, size_t score_stride);
+
 #ifdef __cplusplus
 }
 #endif

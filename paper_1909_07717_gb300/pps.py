@@ -176,6 +176,24 @@ SHOT_QUERY_DTYPE = np.dtype([("state", "<i4"), ("from", "<f4", (2,))])
 SHOT_DTYPE = np.dtype([("theta", "<f4"), ("dir", "<f4"), ("t_line", "<f4"),
                        ("t_opp", "<f4"), ("shoot", "<i4"), ("status", "<i4")])
 
+
+# running points (pps_run_*)
+class pps_rparams(ctypes.Structure):
+    _fields_ = [("spacing", c_float), ("w_goal", c_float),
+                ("w_ball", c_float), ("w_angle", c_float),
+                ("w_guard", c_float), ("w_avoid", c_float),
+                ("ball_ref", c_float), ("angle_lo", c_float),
+                ("angle_hi", c_float), ("angle_span", c_float),
+                ("def_depth", c_float), ("def_width", c_float),
+                ("guard_cap", c_float), ("n_run", c_int32)]
+
+
+RBEST_DTYPE = np.dtype([("idx", "<i4", (4,)), ("score", "<f4", (4,)),
+                        ("point", "<f4", (4, 2)), ("chosen", "<i4", (4,)),
+                        ("avoided", "<i4"), ("nx", "<i4"), ("ny", "<i4"),
+                        ("status", "<i4")])
+assert RBEST_DTYPE.itemsize == 96 and ctypes.sizeof(pps_rparams) == 56
+
 EXPORTS = ("pps_abi_version", "pps_status_string", "pps_last_error",
            "pps_default_params", "pps_grid_from_field", "pps_mask_words",
            "pps_create", "pps_destroy", "pps_search", "pps_sync", "pps_reset",
@@ -190,7 +208,8 @@ EXPORTS = ("pps_abi_version", "pps_status_string", "pps_last_error",
            "pps_net_forward", "pps_net_grad", "pps_net_train_step",
            "pps_net_labels", "pps_propose", "pps_dpps_default_params",
            "pps_dpps_mask_words", "pps_dpps_search", "pps_pass_powers",
-           "pps_shoot")
+           "pps_shoot", "pps_run_default_params", "pps_run_grid",
+           "pps_run_points")
 
 
 class PpsError(RuntimeError):
@@ -309,6 +328,12 @@ def lib():
             L.pps_shoot.argtypes = [c_void_p, c_void_p, ctypes.c_int, c_void_p,
                                     ctypes.c_int, c_float, c_float,
                                     P(pps_dparams), c_void_p]
+            L.pps_run_default_params.argtypes = [P(pps_rparams)]
+            L.pps_run_grid.argtypes = [c_float, c_float, c_float,
+                                       P(ctypes.c_int), P(ctypes.c_int)]
+            L.pps_run_points.argtypes = [c_void_p, c_void_p, ctypes.c_int,
+                                         P(pps_rparams), c_void_p, c_void_p,
+                                         c_void_p, c_size_t]
             if L.pps_abi_version() != PPS_ABI_VERSION:
                 raise RuntimeError("libpps ABI version mismatch")
             _lib = L
@@ -584,6 +609,36 @@ def pps_shoot(ctx, states, n_states, queries, n_queries, v_shot, theta_min,
     return _check(lib().pps_shoot(
         ctx, states, n_states, queries, n_queries, v_shot, theta_min,
         ctypes.byref(params) if params is not None else None, out), ctx)
+
+
+def pps_run_default_params() -> pps_rparams:
+    p = pps_rparams()
+    _check(lib().pps_run_default_params(ctypes.byref(p)))
+    return p
+
+
+def pps_run_grid(field_len, field_wid, spacing):
+    """(nx, ny) of the running-point grid of a field."""
+    nx, ny = ctypes.c_int(), ctypes.c_int()
+    _check(lib().pps_run_grid(field_len, field_wid, spacing,
+                              ctypes.byref(nx), ctypes.byref(ny)))
+    return nx.value, ny.value
+
+
+def pps_run_points(ctx, states, n_states, params, out, pass_best=None,
+                   out_scores=None, score_stride=0):
+    """Device addresses for states, pass_best, out and out_scores."""
+    return _check(lib().pps_run_points(
+        ctx, states, n_states,
+        ctypes.byref(params) if params is not None else None, pass_best, out,
+        out_scores, score_stride), ctx)
+
+
+def rparams_from_dict(d: dict | None) -> pps_rparams:
+    p = pps_run_default_params()
+    for k, v in (d or {}).items():
+        setattr(p, k, int(v) if k == "n_run" else float(v))
+    return p
 
 
 def dparams_from_dict(d: dict | None) -> pps_dparams:
