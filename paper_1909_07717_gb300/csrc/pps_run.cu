@@ -34,6 +34,14 @@ __device__ __forceinline__ uint32_t ordered(float f) {
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
+// sqrt and 1/x from the SFU's approximations (a few ulp; the scores are
+// compared with the FP64 oracle at 2e-5): sqrt(0) = 0.
+__device__ __forceinline__ float sqrt_a(float x) {
+    return x > 0.f ? __fmul_rn(x, rsqrtf(x)) : 0.f;
+}
+
+__device__ __forceinline__ float rcp_a(float x) { return __fdividef(1.f, x); }
+
 __device__ __forceinline__ float unordered(uint32_t o) {
     return __uint_as_float((o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o);
 }
@@ -43,22 +51,23 @@ __device__ __forceinline__ float unordered(uint32_t o) {
 __device__ __forceinline__ float intercept_time(float ox, float oy, float ux,
                                                 float uy, float px, float py,
                                                 float vmax, float amax,
-                                                float inv_amax) {
+                                                float inv_amax, float inv_vmax) {
     const float dx = __fsub_rn(px, ox), dy = __fsub_rn(py, oy);
-    const float d = __fsqrt_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)));
-    if (d <= 0.f) return 0.f;
-    float w = __fdiv_rn(__fmaf_rn(ux, dx, __fmul_rn(uy, dy)), d);
+    const float d2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
+    if (d2 <= 0.f) return 0.f;
+    const float rd = rsqrtf(d2);
+    const float d = __fmul_rn(d2, rd);
+    float w = __fmul_rn(__fmaf_rn(ux, dx, __fmul_rn(uy, dy)), rd);
     w = fminf(fmaxf(w, -vmax), vmax);
     const float d_top = __fmul_rn(__fmaf_rn(-w, w, __fmul_rn(vmax, vmax)),
                                   __fmul_rn(0.5f, inv_amax));
     if (d <= d_top) {
         // w t + amax t^2 / 2 = d; the cancellation-free root for w >= 0
-        const float r = __fsqrt_rn(__fmaf_rn(w, w, __fmul_rn(2.f * amax, d)));
-        return w >= 0.f ? __fdiv_rn(__fmul_rn(2.f, d), __fadd_rn(w, r))
+        const float r = sqrt_a(__fmaf_rn(w, w, __fmul_rn(2.f * amax, d)));
+        return w >= 0.f ? __fdividef(__fmul_rn(2.f, d), __fadd_rn(w, r))
                         : __fmul_rn(__fsub_rn(r, w), inv_amax);
     }
-    return __fadd_rn(__fmul_rn(__fsub_rn(vmax, w), inv_amax),
-                     __fdiv_rn(__fsub_rn(d, d_top), vmax));
+    return __fmaf_rn(__fsub_rn(vmax, w), inv_amax, __fmul_rn(__fsub_rn(d, d_top), inv_vmax));
 }
 
 struct RShared {
@@ -143,7 +152,7 @@ __device__ void derive(const pps_dstate& st, const RArgs& a, RShared& sh,
     if (lane < 4) sh.key[lane] = 0ull;
 }
 
-__global__ void __launch_bounds__(kTPB) run_kernel(const RArgs a) {
+__global__ void __launch_bounds__(kTPB, 4) run_kernel(const RArgs a) {
     __shared__ RShared sh;
     const pps_rparams& p = a.p;
     for (int s = blockIdx.x; s < a.n_states; s += gridDim.x) {
@@ -173,11 +182,17 @@ __global__ void __launch_bounds__(kTPB) run_kernel(const RArgs a) {
             const float inv_span = __frcp_rn(p.angle_span);
             const float inv_amax = __frcp_rn(st.amax);
             const float inv_2cap = __frcp_rn(__fmul_rn(2.f, p.guard_cap));
-            const float vmax = st.vmax;
+            const float vmax = st.vmax, inv_vmax = __frcp_rn(st.vmax);
             const float dmin2 = sh.dmin2;
-            unsigned long long best[4] = {0ull, 0ull, 0ull, 0ull};
+            // per zone the best score and its first index (a thread meets its
+            // points in increasing idx, so "greater" keeps the first on ties)
+            float bsc[4] = {-CUDART_INF_F, -CUDART_INF_F, -CUDART_INF_F, -CUDART_INF_F};
+            int bid[4] = {-1, -1, -1, -1};
+            // row-major walk: idx = tid, tid + kTPB, ...; (j, i) advanced
+            // incrementally
+            const int step_j = kTPB / nx, step_i = kTPB - step_j * nx;
+            int j = (int)threadIdx.x / nx, i = (int)threadIdx.x - j * nx;
             for (int idx = threadIdx.x; idx < n; idx += kTPB) {
-                const int j = idx / nx, i = idx - j * nx;
                 // the raster ends on the goal line and the touch line
                 const float px = fminf(__fmul_rn((float)i, g), x1);
                 const float py = fminf(__fmaf_rn((float)j, g, y_lo), y_hi);
@@ -187,10 +202,10 @@ __global__ void __launch_bounds__(kTPB) run_kernel(const RArgs a) {
                     // 1. distance to the goal, 2. distance to the ball
                     const float gx = __fsub_rn(x1, px), gy = -py;
                     const float x_goal = __fmul_rn(
-                        __fsqrt_rn(__fmaf_rn(gx, gx, __fmul_rn(gy, gy))), inv_diag);
+                        sqrt_a(__fmaf_rn(gx, gx, __fmul_rn(gy, gy))), inv_diag);
                     const float dbx = __fsub_rn(px, bx), dby = __fsub_rn(py, by);
                     const float db2 = __fmaf_rn(dbx, dbx, __fmul_rn(dby, dby));
-                    const float db = __fsqrt_rn(db2);
+                    const float db = sqrt_a(db2);
                     const float x_ball = __fmul_rn(fminf(db, p.ball_ref), inv_ref);
                     // 3. the angle band
                     const float alpha = fabsf(atan2f(gy, gx));
@@ -198,41 +213,35 @@ __global__ void __launch_bounds__(kTPB) run_kernel(const RArgs a) {
                                       : alpha > p.angle_hi ? __fsub_rn(alpha, p.angle_hi)
                                                            : 0.f;
                     const float x_angle = __fsub_rn(1.f, fminf(__fmul_rn(off, inv_span), 1.f));
-                    // 4. the guards' time to P and Q
+                    // 4. the guards' time to P and Q.  The segment p + t (dx, dy),
+                    // t in [0, 1], enters the area where it is inside both slabs
+                    // (Liang-Barsky); dx = x1 - px >= 0 is the same for both
+                    // posts, so the x slab's interval is shared.
+                    const float dx = gx;
+                    float tx0 = 0.f;
+                    if (dx > 0.f) tx0 = fmaxf(0.f, __fmul_rn(__fsub_rn(x0, px), rcp_a(dx)));
                     float tsum = 0.f;
 #pragma unroll
                     for (int side = 0; side < 2; ++side) {
-                        const float qy = side ? hw : -hw;
-                        const float dx = __fsub_rn(x1, px), dy = __fsub_rn(qy, py);
-                        // Liang-Barsky entry of p + t (dx, dy), t in [0, 1]
-                        float t0 = 0.f, t1 = 1.f;
-                        bool hit = true;
-                        const float pp[4] = {-dx, dx, -dy, dy};
-                        const float qq[4] = {__fsub_rn(px, x0), __fsub_rn(x1, px),
-                                             __fadd_rn(py, y1), __fsub_rn(y1, py)};
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            if (pp[e] == 0.f) {
-                                if (qq[e] < 0.f) hit = false;
-                            } else {
-                                const float r = __fdiv_rn(qq[e], pp[e]);
-                                if (pp[e] < 0.f) {
-                                    if (r > t1) hit = false;
-                                    t0 = fmaxf(t0, r);
-                                } else {
-                                    if (r < t0) hit = false;
-                                    t1 = fminf(t1, r);
-                                }
-                            }
+                        const float dy = __fsub_rn(side ? hw : -hw, py);
+                        float t0 = tx0, t1 = 1.f;
+                        if (dy != 0.f) {
+                            const float rdy = rcp_a(dy);
+                            const float ra = __fmul_rn(__fsub_rn(-y1, py), rdy);
+                            const float rb = __fmul_rn(__fsub_rn(y1, py), rdy);
+                            t0 = fmaxf(t0, fminf(ra, rb));
+                            t1 = fminf(t1, fmaxf(ra, rb));
+                        } else if (py < -y1 || py > y1) {
+                            t1 = -1.f;  // parallel to the y slab and outside it
                         }
                         float T = p.guard_cap;
-                        if (hit) {
+                        if (t0 <= t1) {
                             const float ex = __fmaf_rn(t0, dx, px);
                             const float ey = __fmaf_rn(t0, dy, py);
                             for (int k = 0; k < ng; ++k)
                                 T = fminf(T, intercept_time(sh.gx[k], sh.gy[k], sh.gux[k],
                                                             sh.guy[k], ex, ey, vmax,
-                                                            st.amax, inv_amax));
+                                                            st.amax, inv_amax, inv_vmax));
                         }
                         tsum = __fadd_rn(tsum, T);
                     }
@@ -246,18 +255,27 @@ __global__ void __launch_bounds__(kTPB) run_kernel(const RArgs a) {
                     score = __fmaf_rn(-p.w_avoid, x_avoid, score);
                     score = __fadd_rn(score, 0.f);  // -0 -> +0
                     const int z = zone_of(px, py, quarter_l, ys, tol);
-                    const unsigned long long key =
-                        ((unsigned long long)ordered(score) << 32) |
-                        (unsigned long long)(0xFFFFFFFFu - (uint32_t)idx);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (q == z && key > best[q]) best[q] = key;
+                    for (int q = 0; q < 4; ++q) {
+                        const bool up = (q == z) && (score > bsc[q] || bid[q] < 0);
+                        bsc[q] = up ? score : bsc[q];
+                        bid[q] = up ? idx : bid[q];
+                    }
                 }
                 if (a.scores) a.scores[(long long)s * a.stride + idx] = score;
+                i += step_i;
+                j += step_j;
+                if (i >= nx) {
+                    i -= nx;
+                    ++j;
+                }
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                unsigned long long k = best[q];
+                unsigned long long k =
+                    bid[q] < 0 ? 0ull
+                               : ((unsigned long long)ordered(bsc[q]) << 32) |
+                                     (unsigned long long)(0xFFFFFFFFu - (uint32_t)bid[q]);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     const unsigned long long v = __shfl_xor_sync(0xffffffffu, k, o);
