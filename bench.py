@@ -551,6 +551,43 @@ def _dpps(args, dev, stream):
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in ev) / steps
     b = np.frombuffer(best.cpu().numpy().tobytes(), pps.DBEST_DTYPE)
+    # Sec. 4.1 passing powers and Sec. 4.4 shots: 16 queries per state
+    Q = 16 * S
+    rng = np.random.default_rng(synth.DPPS_SEED)
+    pq = np.zeros(Q, pps.PASS_QUERY_DTYPE)
+    pq["state"] = np.repeat(np.arange(S), 16)
+    pq["receiver"] = np.tile(np.arange(16), S)
+    pq["target"] = rng.uniform([-6, -4.5], [6, 4.5], (Q, 2))
+    sq = np.zeros(Q, pps.SHOT_QUERY_DTYPE)
+    sq["state"] = pq["state"]
+    sq["from"] = rng.uniform([-2, -4.5], [6, 4.5], (Q, 2))
+
+    pqd = torch.from_numpy(pq.view(np.uint8).copy()).to(dev)
+    sqd = torch.from_numpy(sq.view(np.uint8).copy()).to(dev)
+    pout = torch.empty(Q * pps.PASS_POWER_DTYPE.itemsize, dtype=torch.uint8,
+                       device=dev)
+    sout = torch.empty(Q * pps.SHOT_DTYPE.itemsize, dtype=torch.uint8,
+                       device=dev)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        evs = [(torch.cuda.Event(enable_timing=True),
+                torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for e0, e1 in evs:
+            flush.zero_()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return sum(x.elapsed_time(y) for x, y in evs) / steps
+
+    ms_pass = timed(lambda: pps.pps_pass_powers(
+        searcher.ctx, rec.data_ptr(), S, pqd.data_ptr(), Q, 0.3, prm,
+        pout.data_ptr()))
+    ms_shot = timed(lambda: pps.pps_shoot(
+        searcher.ctx, rec.data_ptr(), S, sqd.data_ptr(), Q, 6.5, 0.1, prm,
+        sout.data_ptr()))
     searcher.close()
     robots = int(batch["n_team"][0] + batch["n_opp"][0])
     sbip = S * prm.n_dir * prm.n_pow * robots
@@ -573,6 +610,10 @@ def _dpps(args, dev, stream):
             "sbip_per_decision": prm.n_dir * prm.n_pow * robots,
             "feasible_frac": float(b["n_feasible"].mean()
                                    / (prm.n_dir * prm.n_pow)),
+            "pass_powers": {"queries": Q, "ms": ms_pass,
+                            "queries_per_s": Q / (ms_pass / 1e3)},
+            "shots": {"queries": Q, "ms": ms_shot,
+                      "queries_per_s": Q / (ms_shot / 1e3)},
             "cpu_baseline": cpu,
             "ok": bool(np.all(b["status"] == 0))}
 

@@ -219,3 +219,36 @@ def test_invalid_states_and_arguments(searcher):
             _run(searcher, good, dict(synth.RUN_PARAMS, **bad), dense=False)
     # no states: nothing to do
     pps.pps_run_points(searcher.ctx, 0, 0, None, 0)
+
+
+def test_small_field_fine_grid_and_ragged_opponents(searcher):
+    """9 x 6 m fields at 0.05 m (91 x 121 points), 0-16 opponents (a state
+    with none has no guard and nothing to avoid): each zone's best against
+    the oracle's dense scores."""
+    rng = np.random.default_rng(47)
+    batch = synth.ssl_states(47, 10, field_len=9.0, field_wid=6.0, n_opp=16,
+                             n_team=0, K=1)
+    batch["n_opp"] = rng.integers(0, 17, 10).astype(np.int32)
+    batch["n_opp"][0] = 0
+    batch["opp_pos"][1, 0] = (4.0, 0.3)           # a guard
+    prm = dict(synth.RUN_PARAMS, spacing=0.05)
+    got, dense = _run(searcher, batch, prm)
+    oprm = synth.run_oracle_params(prm)
+    ref = oracle.run_search(batch, oprm, dense=True)
+    ny, nx = ref["score"].shape[1:]
+    assert (nx, ny) == (91, 121)
+    for s in range(10):
+        assert got[s]["status"] == 0 and (got[s]["nx"], got[s]["ny"]) == (nx, ny)
+        r = ref["score"][s].reshape(-1)
+        g = dense[s, :nx * ny]
+        amb = _ambiguous(batch, s, nx, ny, oprm).reshape(-1)
+        fin = ~amb & np.isfinite(r)
+        assert np.max(np.abs(g[fin] - r[fin])) <= TOL, s
+        for q in range(4):
+            gi = int(got[s]["idx"][q])
+            assert gi >= 0
+            if np.isfinite(r[gi]):
+                assert abs(r[gi] - ref["best_score"][s, q]) <= 2 * TOL, (s, q)
+    # no opponent: nothing to avoid and no guard, so those criteria are
+    # constant and every score is below the sum of the weights
+    assert np.all(dense[0, :nx * ny][np.isfinite(dense[0, :nx * ny])] <= 4.0)
