@@ -16,6 +16,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_pins as pins
+from tests import test_oracle_dpps as dpps_pins
 from tests import test_oracle_run as run_pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "pps_oracle.c")
@@ -127,6 +128,48 @@ RUN_MUTANTS = [
 ]
 
 
+# The direction x power search, passing power and shooting (Sec. 4.1-4.4),
+# checked by the pins of the direction x power search.
+DPPS_MUTANTS = [
+    ("dpps: wrong field edge", "if (ux < 0.0) s_out = fmin(s_out, (-hl - bx) / ux);",
+     "if (ux < 0.0) s_out = fmin(s_out, (hl - bx) / ux);"),
+    ("dpps: stop distance missing 2", "double s_stop = v * v / (2.0 * a);",
+     "double s_stop = v * v / a;"),
+    ("dpps: ball at rest at 2v/a", "double tk = last_stop ? v / a : pps_oracle_ball_time(s, v, a);",
+     "double tk = last_stop ? 2.0 * v / a : pps_oracle_ball_time(s, v, a);"),
+    ("dpps: stop sample ignores the robot", "return T <= tk ? tk : T;", "return tk;"),
+    ("dpps: samples start at the ball", "double s = (double)k / (double)K * S;",
+     "double s = (double)(k - 1) / (double)K * S;"),
+    ("dpps: group takes the slowest robot",
+     "            if (t < T) {\n                T = t;\n                w = r;",
+     "            if (t > T || w < 0) {\n                T = t;\n                w = r;"),
+    ("dpps: no slide", "double v = prm[PPS_ORACLE_D_SLIDE] * v0;", "double v = v0;"),
+    ("dpps: power grid over npow", "vlo + (double)j * (vhi - vlo) / (double)(npow - 1)",
+     "vlo + (double)j * (vhi - vlo) / (double)npow"),
+    ("dpps: half circle of directions", "double phi = 2.0 * pi * (double)i / (double)ndir;",
+     "double phi = pi * (double)i / (double)ndir;"),
+    ("dpps: delta sign", "(t_opp - t_team > prm[PPS_ORACLE_D_TAU_DELTA])",
+     "(t_team - t_opp > prm[PPS_ORACLE_D_TAU_DELTA])"),
+    ("dpps: refraction sign", "- prm[PPS_ORACLE_D_W_REFR] * refr / pi",
+     "+ prm[PPS_ORACLE_D_W_REFR] * refr / pi"),
+    ("dpps: delta uncapped", "(delta < cap ? delta : cap)", "delta"),
+    ("dpps: refraction transposed", "double c = (ux * gx + uy * gy) / dg;",
+     "double c = (ux * gx - uy * gy) / dg;"),
+    ("dpps: receive point one sample short", "double s = (double)k_team / (double)st->K * S;",
+     "double s = (double)(k_team - 1) / (double)st->K * S;"),
+    ("pass: Eq. 1 sign", "double v1 = t > 0.0 ? (d + 0.5 * a * t * t) / t : INFINITY;",
+     "double v1 = t > 0.0 ? (d - 0.5 * a * t * t) / t : INFINITY;"),
+    ("pass: Eq. 2 inverted", "double v0 = v1 / slide;", "double v0 = v1 * slide;"),
+    ("pass: buffer dropped", "double t = T + buffer;", "double t = T;"),
+    ("shoot: aims at the gap's edge", "double dir = g0 + 0.5 * theta;",
+     "double dir = g0 + theta;"),
+    ("shoot: no slide", "double v = slide * v_shot;", "double v = v_shot;"),
+    ("shoot: angle not required",
+     "shoot = theta >= theta_min && (t_opp - t_line > tau || isinf(t_opp));",
+     "shoot = (t_opp - t_line > tau || isinf(t_opp));"),
+]
+
+
 def _caught(orc, checks=None):
     for chk in checks or CHECKS:
         try:
@@ -163,4 +206,19 @@ def test_running_point_mutant_is_caught(tmp_path, name, orig, mut):
     lib = oracle.build(force=True, src=bad,
                        out=os.path.join(tmp_path, "libmutant.so"))
     caught = _caught(oracle.Oracle(lib), run_pins.CHECKS)
+    assert caught is not None, f"no pin caught mutant: {name}"
+
+
+@pytest.mark.parametrize("name,orig,mut", DPPS_MUTANTS,
+                         ids=[m[0] for m in DPPS_MUTANTS])
+def test_direction_power_mutant_is_caught(tmp_path, name, orig, mut):
+    text = open(SRC).read()
+    assert text.count(orig) >= 1, f"mutation site missing: {orig!r}"
+    bad = os.path.join(tmp_path, "pps_oracle.c")
+    with open(bad, "w") as f:
+        f.write(text.replace(orig, mut, 1))
+    shutil.copy(os.path.join(os.path.dirname(SRC), "pps_oracle.h"), tmp_path)
+    lib = oracle.build(force=True, src=bad,
+                       out=os.path.join(tmp_path, "libmutant.so"))
+    caught = _caught(oracle.Oracle(lib), dpps_pins.CHECKS)
     assert caught is not None, f"no pin caught mutant: {name}"
