@@ -151,12 +151,13 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-def _cpu_oracle_rate(w, batch, grid_spec, n_states):
-    """Oracle evals/s on the first n_states states, all host cores."""
+def _cpu_oracle_rate(w, batch, grid_spec, n_states, cores=None):
+    """Oracle evals/s on the first n_states states, on `cores` threads (all
+    host cores by default)."""
     import oracle
     from paper_1909_07717_gb300 import synth
     sub = synth.take(batch, list(range(n_states)))
-    cores = oracle.max_threads()
+    cores = cores or oracle.max_threads()
     t0 = time.perf_counter()
     oracle.search(sub, grid_spec, w.speeds, w.params, n_threads=cores)
     dt = time.perf_counter() - t0
@@ -357,10 +358,17 @@ def run_pps(args):
             gs = (float(np.float32(grid.spacing)), grid.nx, grid.ny,
                   float(grid.x0), float(grid.y0))
             r, dt, cores = _cpu_oracle_rate(w, batch, gs, CPU_SAMPLE_STATES)
+            r1, dt1, _ = _cpu_oracle_rate(w, batch, gs, 2, cores=1)
+            # OpenMP keeps the last thread count: give the later oracle
+            # timings all cores again
+            _cpu_oracle_rate(w, batch, gs, 1, cores=cores)
             cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": (f"first {CPU_SAMPLE_STATES} states of the "
                               f"batched workload (seed {w.seed}), full grid, "
-                              f"all speeds; {dt:.1f} s wall")}
+                              f"all speeds; {dt:.1f} s wall"),
+                   "single_thread": {"value": r1, "unit": UNIT, "cores": 1,
+                                     "sample": (f"first 2 states, one "
+                                                f"thread; {dt1:.1f} s wall")}}
         line = {"metric": METRIC, "value": value, "unit": UNIT,
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps,

@@ -70,6 +70,25 @@ def test_host_helpers(lib):
             pps.pps_grid_from_field(*bad)
 
 
+def test_running_point_host_helpers(lib):
+    assert pps.pps_run_grid(12.0, 9.0, 0.1) == (61, 91)
+    assert pps.pps_run_grid(9.0, 6.0, 0.05) == (91, 121)
+    assert pps.pps_run_grid(12.0, 9.0, 0.025) == (241, 361)
+    for bad in [(0.0, 9.0, 0.1), (12.0, 9.0, 0.0), (12.0, float("inf"), 0.1),
+                (12.0, 9.0, 1e-5)]:
+        with pytest.raises(pps.PpsError):
+            pps.pps_run_grid(*bad)
+    p = pps.pps_run_default_params()
+    assert abs(p.spacing - 0.1) < 1e-7 and p.n_run == 4
+    assert (p.w_goal, p.w_ball, p.w_angle, p.w_guard, p.w_avoid) == (1.0,) * 5
+    assert abs(p.def_depth - 1.2) < 1e-6 and abs(p.def_width - 2.4) < 1e-6
+    assert ctypes.sizeof(pps.pps_rparams) == 56
+    assert pps.RBEST_DTYPE.itemsize == 96
+    d = pps.pps_dpps_default_params()
+    assert (d.n_dir, d.n_pow) == (128, 64) and abs(d.slide - 5 / 7) < 1e-7
+    assert pps.pps_dpps_mask_words(d) == 128 * 64 // 32
+
+
 def test_create_without_device_fails_cleanly(lib):
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():
