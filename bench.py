@@ -372,6 +372,7 @@ def run_pps(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT,
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps,
+                "ms_per_step_median": float(np.median(step_ms)),
                 "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": _config(w, grid.nx, grid.ny, world),
