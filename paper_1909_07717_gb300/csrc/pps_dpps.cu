@@ -166,6 +166,12 @@ __device__ __forceinline__ float group_min(float f, float cbx, float cby,
 
 // One lane's candidate pass, fixed by its path: rolling speed v, path
 // length S along (ux, uy), ending by a stop or at the field edge.
+template <int J, bool GEN>
+__device__ __forceinline__ float group_min_val(float f, float cbx, float cby,
+                                               const OppRegs<J>& g, float reach) {
+    return pps::opp_min<J, GEN>(f, cbx, cby, g, reach);
+}
+
 struct Path {
     float ux, uy, v, S;
     bool stopped;
@@ -187,20 +193,29 @@ __device__ __forceinline__ float group_first(const DStateK& sk,
     const float cby = __fmul_rn(sk.kappa, __fmul_rn(p.S, p.uy));
     const float v2 = __fmul_rn(p.v, p.v);
     const float twoaS = __fmul_rn(sk.two_ab, p.S);
+    // The sample loop keeps only the group's minimum; the robot holding it
+    // is found again at the sample the loop stops at.
+    auto holder = [&](float f) {
+        int w;
+        if (sk.general)
+            group_min<J, true>(f, cbx, cby, g, sk.reach, w);
+        else
+            group_min<J, false>(f, cbx, cby, g, sk.reach, w);
+        return w;
+    };
     for (int k = 1; k <= sk.K; ++k) {
         const float f = __fmul_rn((float)k, sk.invK);
-        int w;
-        const float n = sk.general ? group_min<J, true>(f, cbx, cby, g, sk.reach, w)
-                                   : group_min<J, false>(f, cbx, cby, g, sk.reach, w);
+        const float n = sk.general ? group_min_val<J, true>(f, cbx, cby, g, sk.reach)
+                                   : group_min_val<J, false>(f, cbx, cby, g, sk.reach);
         if (p.stopped && k == sk.K) {
             k_out = k;
-            who = w;
+            who = holder(f);
             return fmaxf(__fmul_rn(n, sk.t_scale), __fdiv_rn(p.v, sk.ab));
         }
         const float root = pps::sqrt_ball(fmaxf(__fmaf_rn(-f, twoaS, v2), 0.f));
         if (__fadd_rn(__fmul_rn(n, sk.at_scale), root) <= p.v) {
             k_out = k;
-            who = w;
+            who = holder(f);
             // t_ball(s) = 2 s / (v + sqrt(v^2 - 2 a s))
             return __fdiv_rn(__fmul_rn(2.f, __fmul_rn(f, p.S)), __fadd_rn(p.v, root));
         }
