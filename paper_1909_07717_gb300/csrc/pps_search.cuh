@@ -630,6 +630,9 @@ __device__ __forceinline__ unsigned long long warp_max_u64(
 // EXT instances also honour a.list (search only the listed states), a.skip
 // (states to leave untouched) and write a.dbg_point; the plain instances
 // carry none of these checks in their loop.
+// Longest run of consecutive items a warp takes at once (see search_kernel).
+constexpr long long kMaxRun = 64;
+
 template <int JMAX, int VMAX, bool EXT = false>
 __global__ void __launch_bounds__(search_tpb<JMAX, VMAX>(), 1)
     search_kernel(const SearchArgs a) {
@@ -641,15 +644,29 @@ __global__ void __launch_bounds__(search_tpb<JMAX, VMAX>(), 1)
     const long long n_items =
         (long long)(listed ? *a.list_n : a.n_states) * a.words;
 
-    for (long long item = gw; item < n_items; item += warps) {
+    // Each warp takes runs of R consecutive items (mostly one state), the
+    // runs dealt round-robin; the state's constants and opponents are
+    // derived once per run and state.  R grows with the batch up to kMaxRun
+    // while every warp still gets at least 8 runs, so small batches keep
+    // all warps busy.
+    const long long R = n_items >= warps * 8 * kMaxRun
+                            ? kMaxRun
+                            : (n_items >= warps * 8 ? n_items / (warps * 8) : 1);
+    int cur = -1;
+    StateK sk;
+    OppRegs<JMAX> o;
+    for (long long item = gw * R, j = 0; item < n_items;
+         item = (++j == R) ? (j = 0, item - (R - 1) + warps * R) : item + 1) {
         const int i = (int)(item / a.words);
         const int chunk = (int)(item - (long long)i * a.words);
         const int s = listed ? a.list[i] : i;
         if (EXT && a.skip && a.skip[s]) continue;
         const pps_state& st = a.states[s];
-        const StateK sk = derive_state(st, a.prm, JMAX, a.kmax);
-        OppRegs<JMAX> o;
-        load_opps<JMAX>(st, sk, o);
+        if (s != cur) {
+            sk = derive_state(st, a.prm, JMAX, a.kmax);
+            load_opps<JMAX>(st, sk, o);
+            cur = s;
+        }
 
         const int p = chunk * 32 + lane;
         const bool active = p < a.P;
