@@ -27,6 +27,7 @@ namespace {
 using pps::OppRegs;
 
 constexpr int kTPB = 512;
+constexpr long long kMaxRun = 64;
 
 struct DArgs {
     const pps_dstate* states;
@@ -311,14 +312,25 @@ __global__ void __launch_bounds__(kTPB) dpps_kernel(const DArgs a) {
     const long long gw = (long long)blockIdx.x * (kTPB / 32) + (threadIdx.x >> 5);
     const long long per_state = (long long)a.prm.n_dir * a.chunks;
     const long long n_items = (long long)a.n_states * per_state;
-    for (long long item = gw; item < n_items; item += warps) {
+    // runs of R consecutive items (mostly one state), dealt round-robin, as
+    // in the receive-point search; the state's constants once per run
+    const long long R = n_items >= warps * 8 * kMaxRun
+                            ? kMaxRun
+                            : (n_items >= warps * 8 ? n_items / (warps * 8) : 1);
+    int cur = -1;
+    DStateK sk;
+    for (long long item = gw * R, j = 0; item < n_items;
+         item = (++j == R) ? (j = 0, item - (R - 1) + warps * R) : item + 1) {
         const int s = (int)(item / per_state);
         const int rem = (int)(item - (long long)s * per_state);
         const int dir = rem / a.chunks, chunk = rem - dir * a.chunks;
         const int pw = chunk * 32 + lane;
         const bool active = pw < a.prm.n_pow;
         const pps_dstate& st = a.states[s];
-        const DStateK sk = derive_dstate<J>(st, a.prm, a.kmax);
+        if (s != cur) {
+            sk = derive_dstate<J>(st, a.prm, a.kmax);
+            cur = s;
+        }
         DRes r;
         dpps_eval<J>(st, sk, a.prm, dir, active ? pw : 0, active, r);
         const bool f = active && r.feas;
