@@ -36,6 +36,15 @@
  *            mouth's angular interval not covered by any opponent disc.
  *  Sec. 1 / Sec. 4.3  The best pass is the highest score; READING: ties go
  *            to the smallest candidate index.
+ *
+ * Further sections, each with its readings beside the code:
+ *  D   Sec. 4.2 as the paper parameterises it: directions x kick powers
+ *      from the ball holder, teammates and opponents searched along every
+ *      ball path (the 5/7 slide of Sec. 4.1 applied), Sec. 4.3's features.
+ *  D2  Sec. 4.1, Eq. 1-2: the kick power for a receiver and a target.
+ *  D3  Sec. 4.4: the shooting decision.
+ *  R   Sec. 5.1-5.2: running points -- four ball-dependent zones over the
+ *      attacking half, the five criteria of Eq. 4, the supporters' zones.
  */
 #include "pps_oracle.h"
 
