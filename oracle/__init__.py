@@ -1,4 +1,5 @@
-"""FP64 CPU oracle for the passing-point search (ZJUNlict 2019, Sec. 4.1-4.4).
+"""FP64 CPU oracle for the passing-point search (ZJUNlict 2019, Sec. 4.1-4.4)
+and the running points (Sec. 5.1-5.2).
 
 TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` are the only code allowed to import this

@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY, like the rest of ``oracle/``: the tests use it to
 check the GPU rasteriser, convolutions, loss and gradients.  It shares no
 code with the CUDA path.
 
-Definitions (the proposal of the build; the paper has no network):
+Definitions (the learned proposal; the paper has no network):
   * map: the 12 x 9 m field rasterised at 0.2 m, H = 46 rows (y) by W = 61
     columns (x); pixel (y, x) is centred at c = ((x - 30) / 5, (y - 22.5) / 5);
   * 8 input channels per pixel, with opponents o_j, ball b, goal centre

@@ -1,7 +1,8 @@
 /*
  * pps_oracle.h -- plain FP64 CPU oracle for the passing-point search of the
  * ZJUNlict 2019 team description paper (Sec. 4.1 ball model, Sec. 4.2
- * SBIP-based dynamic passing-point search, Sec. 4.3 value-based best pass).
+ * SBIP-based dynamic passing-point search, Sec. 4.3 value-based best pass,
+ * Sec. 4.4 shooting, Sec. 5.1-5.2 running points).
  *
  * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
  * baseline leg of the benchmark may load this library.  It shares no code,
