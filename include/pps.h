@@ -61,7 +61,7 @@ typedef int pps_status;
 #define PPS_ENOMEM 2   /* device memory or the context's budget ran out */
 #define PPS_ECUDA 3    /* a CUDA call failed; the context needs pps_reset */
 #define PPS_ETIMEOUT 4 /* a bounded device wait gave up */
-#define PPS_ENOTIMPL 5 /* not available in this build */
+#define PPS_ENOTIMPL 5 /* not available in this library */
 
 /* pps_search flag: every buffer argument is device memory (e.g. a torch
  * CUDA tensor's data pointer).  Without it they are host memory; the
@@ -164,7 +164,7 @@ typedef struct pps_ctx_desc {
 
 typedef struct pps_ctx pps_ctx;
 
-/* Library ABI version (PPS_ABI_VERSION of the build). */
+/* Library ABI version (the PPS_ABI_VERSION it was compiled with). */
 int pps_abi_version(void);
 
 /* Human-readable name of a status code (static storage). */
