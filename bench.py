@@ -23,6 +23,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -64,15 +65,24 @@ def _peaks():
         return {}
 
 
+def _code_only(text: str) -> str:
+    """C/C++ source without comments and with whitespace runs collapsed, so
+    that a comment edit does not count as a change of the kernel."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def _kernel_src_digest():
-    """Digest of the sources the timed search kernel is built from."""
+    """Digest of the code (comments aside) the timed search kernel is built
+    from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1909_07717_gb300", "csrc")
     for path in (os.path.join(csrc, "pps_search.cuh"),
                  os.path.join(csrc, "pps_lib.cu"),
                  os.path.join(ROOT, "include", "pps.h")):
-        with open(path, "rb") as f:
-            h.update(os.path.basename(path).encode() + f.read())
+        with open(path) as f:
+            h.update((os.path.basename(path) + _code_only(f.read())).encode())
     return h.hexdigest()[:16]
 
 
