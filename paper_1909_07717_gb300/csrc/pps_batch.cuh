@@ -6,8 +6,10 @@
 // items are (state, 32 consecutive grid points) as in the single-grid
 // search, numbered through a per-bucket prefix sum of each state's item
 // count, so states of very different grid sizes share one persistent launch.
-// Every warp walks the item range round-robin and finds its state by binary
-// search in the prefix sum.  The per-point arithmetic is eval_point, the same
+// The launch is persistent: every warp takes the next few items from an
+// atomic counter (a work queue over the item range, so that warps whose
+// items were cheap -- short pass lines, small K -- take more of them) and
+// finds each item's state by binary search in the prefix sum.  The per-point arithmetic is eval_point, the same
 // device code the single-grid search runs.
 #pragma once
 
@@ -29,7 +31,12 @@ struct BatchArgs {
     uint32_t* mask;               // may be null
     unsigned long long* keys;     // per state of the plan
     int* counts;                  // per state of the plan
+    unsigned long long* next;     // the launch's work-queue counter: 0 when
+                                  // it starts, left 0 by the finalize kernel
 };
+
+// Items a warp takes from the work queue at a time.
+constexpr unsigned long long kQueueRun = 4;
 
 // A job's grid in the form the kernels use; speeds padded with the last one.
 struct JobView {
@@ -68,13 +75,11 @@ __device__ __forceinline__ int find_bucket_slot(const long long* start, int n,
     return lo;
 }
 
-template <int JMAX, int VMAX, int TPB>
-__global__ void __launch_bounds__(TPB) batch_search_kernel(const BatchArgs a) {
-    const int lane = threadIdx.x & 31;
-    const long long warps = (long long)gridDim.x * (TPB / 32);
-    const long long gw = (long long)blockIdx.x * (TPB / 32) + (threadIdx.x >> 5);
-
-    for (long long item = gw; item < a.n_items; item += warps) {
+// One work item: 32 consecutive grid points of one state (all lanes).
+template <int JMAX, int VMAX>
+__device__ __forceinline__ void batch_item(const BatchArgs& a, long long item,
+                                           int lane) {
+    {
         const int b = find_bucket_slot(a.item_start, a.n_bucket, item);
         const int s = __ldg(a.bucket_states + b);
         const int chunk = (int)(item - __ldg(a.item_start + b));
@@ -123,11 +128,33 @@ __global__ void __launch_bounds__(TPB) batch_search_kernel(const BatchArgs a) {
     }
 }
 
+template <int JMAX, int VMAX, int TPB>
+__global__ void __launch_bounds__(TPB) batch_search_kernel(const BatchArgs a) {
+    const int lane = threadIdx.x & 31;
+    // several items a fetch only when there are many per warp: a small
+    // launch (a serving batch) spreads its items one per warp
+    const long long warps = (long long)gridDim.x * (TPB / 32);
+    const unsigned long long run =
+        a.n_items >= warps * 16 ? kQueueRun : 1ull;
+    for (;;) {
+        unsigned long long q = 0ull;
+        if (lane == 0) q = atomicAdd(a.next, run);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if (q >= (unsigned long long)a.n_items) break;
+        const long long end = (long long)(q + run) < a.n_items
+                                  ? (long long)(q + run)
+                                  : a.n_items;
+        for (long long item = (long long)q; item < end; ++item)
+            batch_item<JMAX, VMAX>(a, item, lane);
+    }
+}
+
 // One thread per state of the bucket: decode the key, re-evaluate the
 // winning point for its margin and check that the score reproduces.
 template <int JMAX, int VMAX>
 __global__ void __launch_bounds__(128) batch_finalize_kernel(const BatchArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *a.next = 0ull;  // the queue is empty again for the next launch
     if (i >= a.n_bucket) return;
     const int s = a.bucket_states[i];
     const pps_state& st = a.states[s];

@@ -63,8 +63,9 @@ struct pps_plan {
     long long* d_mask_off = nullptr;
     unsigned long long* d_keys = nullptr;
     int* d_counts = nullptr;
+    unsigned long long* d_next = nullptr;  // one work-queue counter per group
     size_t b_jobs = 0, b_states = 0, b_start = 0, b_mask = 0, b_keys = 0,
-           b_counts = 0;
+           b_counts = 0, b_next = 0;
     // autotuning and graph replay
     bool tuned = false;
     cudaStream_t cap_stream = nullptr;
@@ -215,7 +216,11 @@ extern "C" pps_status pps_plan_create(pps_ctx* ctx, const pps_job* jobs,
                                         (size_t)n_states, "plan keys")) !=
             PPS_OK ||
         (s = upload<int>(pl, &pl->d_counts, &pl->b_counts, nullptr,
-                         (size_t)n_states, "plan counts")) != PPS_OK) {
+                         (size_t)n_states, "plan counts")) != PPS_OK ||
+        (s = upload<unsigned long long>(
+             pl, &pl->d_next, &pl->b_next,
+             std::vector<unsigned long long>(pl->groups.size(), 0ull).data(),
+             pl->groups.size(), "plan queues")) != PPS_OK) {
         pps_plan_destroy(pl);
         return s;
     }
@@ -264,6 +269,7 @@ pps::BatchArgs group_args(const pps_plan* pl, const Group& g,
     a.mask = mask;
     a.keys = pl->d_keys;
     a.counts = pl->d_counts;
+    a.next = pl->d_next + (&g - pl->groups.data());
     return a;
 }
 
@@ -293,6 +299,7 @@ cudaError_t enqueue_all(const pps_plan* pl, const pps_state* states,
                         pps_best* best, uint32_t* mask, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(pl->d_keys, 0, pl->b_keys, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(pl->d_counts, 0, pl->b_counts, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pl->d_next, 0, pl->b_next, st);
     for (const Group& g : pl->groups) {
         if (e != cudaSuccess) break;
         e = launch_group(pl, group_args(pl, g, states, best, mask), g, g.tpb,
@@ -429,6 +436,7 @@ extern "C" void pps_plan_destroy(pps_plan* pl) {
     pps_ctx_free(ctx, pl->d_mask_off, pl->b_mask);
     pps_ctx_free(ctx, pl->d_keys, pl->b_keys);
     pps_ctx_free(ctx, pl->d_counts, pl->b_counts);
+    pps_ctx_free(ctx, pl->d_next, pl->b_next);
     cudaGetLastError();
     delete pl;
 }

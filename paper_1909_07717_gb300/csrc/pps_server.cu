@@ -44,6 +44,8 @@ int64_t now_ns() {
 
 int opp_slots(int m) { return m <= 6 ? 6 : m <= 8 ? 8 : m <= 12 ? 12 : 16; }
 int speed_slots(int n) { return n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : 8; }
+// (opponent slots, speed slots) pairs: at most this many groups a launch
+constexpr int kMaxGroups = 16;
 
 struct Request {
     uint64_t ticket = 0;
@@ -72,6 +74,8 @@ struct Slot {
     pps_best* h_best = nullptr;
     unsigned long long* d_keys = nullptr;  // cleared by the finalize kernels
     int* d_counts = nullptr;
+    unsigned long long* d_next = nullptr;  // a work-queue counter per group,
+                                           // left 0 by the finalize kernels
     uint32_t* d_mask = nullptr;
     uint32_t* h_mask = nullptr;
     // this batch's sections in the packed buffer
@@ -113,7 +117,7 @@ pps_status fail(pps_status s, const char* msg, cudaError_t e = cudaSuccess) {
 void free_slot(Slot& s) {
     if (s.stream) cudaStreamSynchronize(s.stream);
     for (void* p : {(void*)s.d_in, (void*)s.d_best, (void*)s.d_keys,
-                    (void*)s.d_counts, (void*)s.d_mask})
+                    (void*)s.d_counts, (void*)s.d_next, (void*)s.d_mask})
         if (p) cudaFree(p);
     for (void* p : {(void*)s.h_in, (void*)s.h_best, (void*)s.h_mask})
         if (p) cudaFreeHost(p);
@@ -168,6 +172,10 @@ cudaError_t alloc_slot(Slot& s, int max_batch, long long mask_words) {
     if (e == cudaSuccess)
         e = cudaMemset(s.d_keys, 0, sizeof(unsigned long long) * n);
     if (e == cudaSuccess) e = cudaMemset(s.d_counts, 0, sizeof(int) * n);
+    if (e == cudaSuccess)
+        e = cudaMalloc((void**)&s.d_next, sizeof(unsigned long long) * kMaxGroups);
+    if (e == cudaSuccess)
+        e = cudaMemset(s.d_next, 0, sizeof(unsigned long long) * kMaxGroups);
     if (e == cudaSuccess && mask_words > 0)
         e = both(&s.d_mask, &s.h_mask, (size_t)mask_words);
     return e;
@@ -337,6 +345,7 @@ cudaError_t launch_batch(pps_server* srv, Slot& s) {
         a.mask = masks ? s.d_mask : nullptr;
         a.keys = s.d_keys;
         a.counts = s.d_counts;
+        a.next = s.d_next + (&g - groups.data());
         int occ = 1;
         switch (g.j) {
             case 6: occ = pps::batch_occupancy_j6(g.v, kTpb); break;
