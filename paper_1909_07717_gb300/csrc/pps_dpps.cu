@@ -289,10 +289,15 @@ __device__ __forceinline__ void dpps_eval(const pps_dstate& st,
                                                   r.rx < sk.hl, r.rx, r.ry, gx,
                                                   prm.robot_radius);
         const float dg = __fsqrt_rn(__fmaf_rn(gx, gx, __fmul_rn(r.ry, r.ry)));
+        // the turn from the pass direction u to the shot direction g - r,
+        // as atan2(|u x (g - r)|, u . (g - r)): the same angle as the acos
+        // of the normalised dot product, without its loss of precision
+        // when the two directions nearly agree
         float refr = 0.f;
         if (dg > 0.f) {
-            const float c = __fdiv_rn(__fmaf_rn(p.ux, gx, __fmul_rn(p.uy, -r.ry)), dg);
-            refr = acosf(fminf(fmaxf(c, -1.f), 1.f));
+            const float dot = __fmaf_rn(p.ux, gx, __fmul_rn(p.uy, -r.ry));
+            const float crs = __fmaf_rn(p.ux, -r.ry, -__fmul_rn(p.uy, gx));
+            refr = atan2f(fabsf(crs), dot);
         }
         const float delta = __fsub_rn(r.t_opp, r.t_team);
         const float inv_pi = 0.318309886183790672f;

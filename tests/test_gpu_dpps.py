@@ -233,3 +233,78 @@ def test_shooting_decisions_match_the_oracle(searcher):
         shots += int(r["shoot"])
         checked += 1
     assert checked >= 0.9 * n and 0 < shots < checked
+
+
+@pytest.mark.parametrize("over", [
+    dict(tau_delta=0.1, reach_radius=0.05),        # threshold, general path
+    dict(slide=1.0, delta_cap=0.5, w_refr=2.0, w_dist=0.5, v_lo=2.0,
+         v_hi=5.0),
+])
+def test_candidates_match_the_oracle_with_other_parameters(searcher, over):
+    prm = dict(synth.DPPS_PARAMS, n_dir=16, n_pow=32, **over)
+    batch = synth.dpps_states(35, 3, n_team=5, n_opp=6, K=24)
+    best, bits, dbg = _run(searcher, batch, prm)
+    checked = total = 0
+    for s in range(3):
+        ref = _oracle_candidates(batch, prm, s)
+        for i in range(prm["n_dir"]):
+            for j in range(prm["n_pow"]):
+                c = ref[i][j]
+                idx = i * prm["n_pow"] + j
+                g_tt, g_to, g_sc = dbg[s, idx]
+                total += 1
+                if c["m_team"] <= EPS:
+                    continue
+                assert _close(g_tt, c["t_team"], 1e-5), (s, i, j)
+                if math.isinf(c["t_team"]):
+                    assert bits[s, idx] == 0
+                    checked += 1
+                    continue
+                if c["m_opp"] <= EPS:
+                    continue
+                assert _close(g_to, c["t_opp"], 1e-5), (s, i, j)
+                if abs(c["t_opp"] - c["t_team"] - prm["tau_delta"]) <= EPS:
+                    continue
+                assert bits[s, idx] == int(c["feasible"]), (s, i, j)
+                if c["feasible"]:
+                    assert abs(g_sc - c["score"]) <= 1e-4, (s, i, j, g_sc, c)
+                checked += 1
+        fe = [c["score"] for row in ref for c in row if c["feasible"]]
+        if fe:
+            assert abs(float(best[s]["score"]) - max(fe)) <= 2e-4
+        else:
+            assert best[s]["idx"] == -1
+    assert checked >= 0.8 * total, (checked, total)
+
+
+def test_pass_powers_with_other_limits(searcher):
+    """No buffer, no slide and a narrower kick range (more clamping)."""
+    torch = searcher.torch
+    batch = synth.dpps_states(36, 4, n_team=4, n_opp=4, K=16)
+    rng = np.random.default_rng(6)
+    q = np.zeros(80, pps.PASS_QUERY_DTYPE)
+    q["state"] = rng.integers(0, 4, 80)
+    q["receiver"] = rng.integers(0, 4, 80)
+    q["target"] = rng.uniform([-6, -4.5], [6, 4.5], (80, 2))
+    states = _device(torch, pps.pack_dstates(batch))
+    qd = _device(torch, q)
+    out = torch.empty(80 * pps.PASS_POWER_DTYPE.itemsize, dtype=torch.uint8,
+                      device="cuda")
+    p = pps.dparams_from_dict(dict(synth.DPPS_PARAMS, slide=1.0, v_lo=2.0,
+                                   v_hi=5.0))
+    pps.pps_pass_powers(searcher.ctx, states.data_ptr(), 4, qd.data_ptr(), 80,
+                        0.0, p, out.data_ptr())
+    torch.cuda.synchronize()
+    g = np.frombuffer(out.cpu().numpy().tobytes(), pps.PASS_POWER_DTYPE)
+    clamped = 0
+    for i in range(80):
+        st = oracle.dstate_of(batch, int(q["state"][i]))
+        r = oracle.pass_power(st, int(q["receiver"][i]), q["target"][i],
+                              buffer=0.0, slide=1.0, v_lo=2.0, v_hi=5.0)
+        assert g["status"][i] == 0
+        assert abs(g["v1"][i] - r["v1"]) <= 1e-5 * (1 + r["v1"])
+        assert abs(g["v0"][i] - r["v0"]) <= 1e-5 * (1 + r["v0"])
+        if abs(r["v0"] - 5.0) > 1e-4 and abs(r["v0"] - 2.0) > 1e-4:
+            assert g["clamped"][i] == r["clamped"]
+        clamped += int(r["clamped"])
+    assert clamped > 0

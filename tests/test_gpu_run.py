@@ -252,3 +252,28 @@ def test_small_field_fine_grid_and_ragged_opponents(searcher):
     # no opponent: nothing to avoid and no guard, so those criteria are
     # constant and every score is below the sum of the weights
     assert np.all(dense[0, :nx * ny][np.isfinite(dense[0, :nx * ny])] <= 4.0)
+
+
+def test_other_weights_band_and_area(searcher):
+    """Other criterion weights, an angle band from 0, a smaller defence area
+    and two supporters: dense scores and zone bests against the oracle."""
+    prm = dict(synth.RUN_PARAMS, w_goal=2.0, w_ball=0.5, w_angle=1.5,
+               w_guard=0.7, w_avoid=3.0, ball_ref=1.5, angle_lo=0.0,
+               angle_hi=0.4, angle_span=0.8, def_depth=1.0, def_width=2.0,
+               guard_cap=1.5, n_run=2)
+    batch = synth.run_states(48, 6, def_depth=1.0, def_width=2.0)
+    oprm = synth.run_oracle_params(prm)
+    got, dense = _run(searcher, batch, prm)
+    ref = oracle.run_search(batch, oprm, dense=True)
+    ny, nx = ref["score"].shape[1:]
+    for s in range(6):
+        r = ref["score"][s].reshape(-1)
+        g = dense[s, :nx * ny]
+        amb = _ambiguous(batch, s, nx, ny, oprm).reshape(-1)
+        fin = ~amb & np.isfinite(r)
+        assert np.max(np.abs(g[fin] - r[fin])) <= 2 * TOL, s
+        for q in range(4):
+            gi = int(got[s]["idx"][q])
+            if np.isfinite(r[gi]):
+                assert abs(r[gi] - ref["best_score"][s, q]) <= 4 * TOL, (s, q)
+        assert sum(z >= 0 for z in got[s]["chosen"]) == 2
