@@ -570,6 +570,7 @@ extern "C" pps_status pps_dpps_search(pps_ctx* ctx, const pps_dstate* states,
                                       int n_states, const pps_dparams* params,
                                       pps_dbest* out_best, uint32_t* out_mask,
                                       float* out_dbg) {
+    PPS_RANGE("pps_dpps_search");
     if (!ctx) return PPS_EINVAL;
     if (pps_ctx_failed(ctx))
         return pps_ctx_error(ctx, PPS_ECUDA, "context failed earlier; call pps_reset");
@@ -625,6 +626,7 @@ extern "C" pps_status pps_pass_powers(pps_ctx* ctx, const pps_dstate* states,
                                       int n_queries, float buffer,
                                       const pps_dparams* params,
                                       pps_pass_power* out) {
+    PPS_RANGE("pps_pass_powers");
     if (!ctx) return PPS_EINVAL;
     if (pps_ctx_failed(ctx))
         return pps_ctx_error(ctx, PPS_ECUDA, "context failed earlier; call pps_reset");
@@ -660,6 +662,7 @@ extern "C" pps_status pps_shoot(pps_ctx* ctx, const pps_dstate* states, int n_st
                                 const pps_shot_query* queries, int n_queries,
                                 float v_shot, float theta_min,
                                 const pps_dparams* params, pps_shot* out) {
+    PPS_RANGE("pps_shoot");
     if (!ctx) return PPS_EINVAL;
     if (pps_ctx_failed(ctx))
         return pps_ctx_error(ctx, PPS_ECUDA, "context failed earlier; call pps_reset");

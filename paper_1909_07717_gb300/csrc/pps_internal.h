@@ -4,9 +4,20 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stddef.h>
 
 #include "pps.h"
+
+// An NVTX range over the host side of an entry point (enqueueing its
+// work), for timelines in external profilers; free when none is attached.
+struct PpsRange {
+    explicit PpsRange(const char* name) { nvtxRangePushA(name); }
+    ~PpsRange() { nvtxRangePop(); }
+    PpsRange(const PpsRange&) = delete;
+    PpsRange& operator=(const PpsRange&) = delete;
+};
+#define PPS_RANGE(name) PpsRange pps_range_(name)
 
 int pps_ctx_device(const pps_ctx* ctx);
 cudaStream_t pps_ctx_stream(const pps_ctx* ctx);

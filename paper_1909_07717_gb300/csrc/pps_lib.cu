@@ -353,6 +353,7 @@ pps_status pps_search(pps_ctx* ctx, const pps_state* states, int n_states,
                       const pps_params* params, pps_best* out_best,
                       uint32_t* out_mask, const pps_debug_out* dbg,
                       unsigned flags) {
+    PPS_RANGE("pps_search");
     if (!ctx) return PPS_EINVAL;
     ctx->err[0] = 0;
     if (ctx->failed) {

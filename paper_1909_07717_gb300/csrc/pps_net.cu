@@ -422,6 +422,7 @@ pps_status forward_to(pps_net* nt, const pps_state* states, int n, float* out,
 
 extern "C" pps_status pps_net_forward(pps_net* nt, const pps_state* states,
                                       int n, float* out) {
+    PPS_RANGE("pps_net_forward");
     return forward_to(nt, states, n, out, false, "pps_net_forward");
 }
 
@@ -462,6 +463,7 @@ extern "C" pps_status pps_net_grad(pps_net* nt, const pps_state* states,
 extern "C" pps_status pps_net_train_step(pps_net* nt, const pps_state* states,
                                          const float* labels, int n, float lr,
                                          float* loss) {
+    PPS_RANGE("pps_net_train_step");
     pps_status s = check_batch(nt, states, n);
     if (s != PPS_OK) return s;
     if (!labels || !(lr > 0.f) || !std::isfinite(lr))

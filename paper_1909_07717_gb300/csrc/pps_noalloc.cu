@@ -19,6 +19,7 @@
 #include <mutex>
 
 #include "pps.h"
+#include "pps_internal.h"
 #include "pps_search.cuh"
 
 // Defined in pps_lib.cu: the thread's message buffer read by
@@ -113,6 +114,7 @@ extern "C" pps_status pps_search_noalloc(
     int device, void* stream, int max_opp, const pps_state* states,
     int n_states, const pps_grid* grid, const float* speeds, int n_speeds,
     const pps_params* params, pps_best* out_best, uint32_t* out_mask) {
+    PPS_RANGE("pps_search_noalloc");
     pps_thread_error_buffer()[0] = 0;
     if (device < 0 || device >= kMaxDevices)
         return fail(PPS_EINVAL, "pps_search_noalloc: device %d outside 0..%d",

@@ -394,6 +394,7 @@ pps_status capture(pps_plan* pl, const pps_state* states, pps_best* best,
 
 extern "C" pps_status pps_plan_run(pps_plan* pl, const pps_state* states,
                                    pps_best* out_best, uint32_t* out_mask) {
+    PPS_RANGE("pps_plan_run");
     if (!pl) return PPS_EINVAL;
     pps_ctx* ctx = pl->ctx;
     if (pps_ctx_failed(ctx))

@@ -170,6 +170,7 @@ extern "C" pps_status pps_propose(pps_ctx* ctx, pps_net* net,
                                   int n_speeds, const pps_params* params,
                                   int topk, unsigned flags, pps_best* out_best,
                                   int32_t* out_cells) {
+    PPS_RANGE("pps_propose");
     if (!ctx || !net) return PPS_EINVAL;
     if (pps_ctx_failed(ctx))
         return pps_ctx_error(ctx, PPS_ECUDA, "context failed earlier; call pps_reset");

@@ -378,6 +378,7 @@ extern "C" pps_status pps_run_points(pps_ctx* ctx, const pps_dstate* states,
                                      int n_states, const pps_rparams* params,
                                      const pps_dbest* pass, pps_rbest* out,
                                      float* out_scores, size_t score_stride) {
+    PPS_RANGE("pps_run_points");
     if (!ctx) return PPS_EINVAL;
     if (pps_ctx_failed(ctx))
         return pps_ctx_error(ctx, PPS_ECUDA, "context failed earlier; call pps_reset");
