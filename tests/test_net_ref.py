@@ -3,13 +3,16 @@
 The convolution is checked against a loop written straight from its
 definition, the analytic gradients against central finite differences of
 the loss, the rasteriser against closed forms, and the bfloat16 rounding
-against values fixed by the format.
+against values fixed by the format.  Each check takes the reference module,
+so the mutant tests can run them against copies with planted mistakes.
 """
 from __future__ import annotations
 
 import math
 
 import numpy as np
+
+import pytest
 
 from oracle import net_ref
 
@@ -32,12 +35,12 @@ def _conv_loops(x, Wl, bl):
     return out
 
 
-def test_conv_matches_its_definition():
+def check_conv_matches_its_definition(ref):
     rng = np.random.default_rng(1)
     x = rng.normal(size=(2, 5, 4, 3))
     Wl = rng.normal(size=(3, 3, 2, 3))
     bl = rng.normal(size=2)
-    assert np.allclose(net_ref.conv(x, Wl, bl), _conv_loops(x, Wl, bl),
+    assert np.allclose(ref.conv(x, Wl, bl), _conv_loops(x, Wl, bl),
                        atol=1e-12)
 
 
@@ -46,12 +49,12 @@ def _tiny_layers(rng, chans=(3, 4, 4, 1)):
             for ci, co in zip(chans[:-1], chans[1:])]
 
 
-def test_gradients_match_finite_differences():
+def check_gradients_match_finite_differences(ref):
     rng = np.random.default_rng(2)
     layers = _tiny_layers(rng)
     x = rng.normal(size=(2, 5, 6, 3))
     labels = rng.normal(size=(2, 5, 6))
-    loss, grads = net_ref.loss_and_grads(x, labels, layers, round_grads=False)
+    loss, grads = ref.loss_and_grads(x, labels, layers, round_grads=False)
     h = 1e-6
     for li, (Wl, bl) in enumerate(layers):
         for idx in [(0, 0, 0, 0), (1, 2, 1, 2), (2, 1, Wl.shape[2] - 1, 0)]:
@@ -60,10 +63,10 @@ def test_gradients_match_finite_differences():
             Wp[idx] += h
             Wm = Wl.copy()
             Wm[idx] -= h
-            lp = net_ref.loss_and_grads(
+            lp = ref.loss_and_grads(
                 x, labels, layers[:li] + [(Wp, bl)] + layers[li + 1:],
                 round_grads=False)[0]
-            lm = net_ref.loss_and_grads(
+            lm = ref.loss_and_grads(
                 x, labels, layers[:li] + [(Wm, bl)] + layers[li + 1:],
                 round_grads=False)[0]
             num = (lp - lm) / (2 * h)
@@ -72,67 +75,67 @@ def test_gradients_match_finite_differences():
         bp[0] += h
         bm = bl.copy()
         bm[0] -= h
-        num = (net_ref.loss_and_grads(x, labels, layers[:li] + [(Wl, bp)]
+        num = (ref.loss_and_grads(x, labels, layers[:li] + [(Wl, bp)]
                                       + layers[li + 1:], round_grads=False)[0]
-               - net_ref.loss_and_grads(x, labels, layers[:li] + [(Wl, bm)]
+               - ref.loss_and_grads(x, labels, layers[:li] + [(Wl, bm)]
                                         + layers[li + 1:],
                                         round_grads=False)[0]) / (2 * h)
         assert abs(grads[li][1][0] - num) <= 1e-6 * max(1, abs(num))
 
 
-def test_focused_loss_gradients_match_finite_differences():
+def check_focused_loss_gradients_match_finite_differences(ref):
     rng = np.random.default_rng(6)
     layers = _tiny_layers(rng)
     x = rng.normal(size=(2, 5, 6, 3))
     labels = rng.normal(size=(2, 5, 6))
     kw = dict(round_grads=False, top_band=0.8, low_weight=0.25,
               under_weight=3.0)
-    _, out = net_ref.forward(x, layers, round_acts=False)
-    w = net_ref.loss_weights(out, labels, 0.8, 0.25)
+    _, out = ref.forward(x, layers, round_acts=False)
+    w = ref.loss_weights(out, labels, 0.8, 0.25)
     assert (w == 1).any() and (w == 0.25).any()
-    _, grads = net_ref.loss_and_grads(x, labels, layers, **kw)
+    _, grads = ref.loss_and_grads(x, labels, layers, **kw)
     h = 1e-6
     Wl, bl = layers[1]
     for idx in [(0, 0, 0, 0), (1, 2, 3, 1)]:
         Wp, Wm = Wl.copy(), Wl.copy()
         Wp[idx] += h
         Wm[idx] -= h
-        lp = net_ref.loss_and_grads(x, labels, [layers[0], (Wp, bl)]
+        lp = ref.loss_and_grads(x, labels, [layers[0], (Wp, bl)]
                                     + layers[2:], **kw)[0]
-        lm = net_ref.loss_and_grads(x, labels, [layers[0], (Wm, bl)]
+        lm = ref.loss_and_grads(x, labels, [layers[0], (Wm, bl)]
                                     + layers[2:], **kw)[0]
         num = (lp - lm) / (2 * h)
         assert abs(grads[1][0][idx] - num) <= 1e-6 * max(1, abs(num))
 
 
-def test_loss_weights():
+def check_loss_weights(ref):
     labels = np.array([[[0.0, 1.0, 0.1, 0.5]]])
     out = np.array([[[0.9, 0.0, 0.2, 0.0]]])
     # best label 1.0, band 0.2: pixels reaching 0.8 by label or output
-    w = net_ref.loss_weights(out, labels, 0.2, 0.1)
+    w = ref.loss_weights(out, labels, 0.2, 0.1)
     assert np.array_equal(w, [[[1.0, 1.0, 0.1, 0.1]]])
     # under-predictions (pixels 1 and 3) cost under_weight times more
-    w = net_ref.loss_weights(out, labels, 0.2, 0.1, 4.0)
+    w = ref.loss_weights(out, labels, 0.2, 0.1, 4.0)
     assert np.array_equal(w, [[[1.0, 4.0, 0.1, 0.4]]])
     # a low weight of 1 is the plain mean squared error for any band
     rng = np.random.default_rng(7)
     layers = _tiny_layers(rng)
     x = rng.normal(size=(1, 4, 4, 3))
     lab = rng.normal(size=(1, 4, 4))
-    a = net_ref.loss_and_grads(x, lab, layers, False, 0.3, 1.0)
-    b = net_ref.loss_and_grads(x, lab, layers, False)
+    a = ref.loss_and_grads(x, lab, layers, False, 0.3, 1.0)
+    b = ref.loss_and_grads(x, lab, layers, False)
     assert a[0] == b[0]
-    assert np.array_equal(net_ref.flatten(a[1]), net_ref.flatten(b[1]))
+    assert np.array_equal(ref.flatten(a[1]), ref.flatten(b[1]))
 
 
-def test_input_gradient_is_the_adjoint_of_conv():
+def check_input_gradient_is_the_adjoint_of_conv(ref):
     """<conv(x) - b, g> == <x, conv_grad_input(g)> for every x, g."""
     rng = np.random.default_rng(3)
     x = rng.normal(size=(1, 4, 5, 3))
     g = rng.normal(size=(1, 4, 5, 2))
     Wl = rng.normal(size=(3, 3, 2, 3))
-    lhs = np.sum((net_ref.conv(x, Wl, np.zeros(2))) * g)
-    rhs = np.sum(x * net_ref.conv_grad_input(g, Wl))
+    lhs = np.sum((ref.conv(x, Wl, np.zeros(2))) * g)
+    rhs = np.sum(x * ref.conv_grad_input(g, Wl))
     assert math.isclose(lhs, rhs, rel_tol=1e-12)
 
 
@@ -157,10 +160,10 @@ def _open_mouth(q):
             - math.atan2(-0.9 - q[1], 6.0 - q[0])) / math.pi
 
 
-def test_raster_closed_forms():
-    bf = net_ref.bf16
+def check_raster_closed_forms(ref):
+    bf = ref.bf16
     # density: an opponent on the centre of pixel (20, 40), c = (2, -0.5)
-    m = net_ref.raster(_state([(2.0, -0.5)], [(0.0, 0.0)]))
+    m = ref.raster(_state([(2.0, -0.5)], [(0.0, 0.0)]))
     assert m.shape == (46, 61, 8)
     assert m[20, 40, 0] == 1.0
     assert m[20, 41, 0] == bf(math.exp(-0.04 / 0.18))
@@ -186,12 +189,12 @@ def test_raster_closed_forms():
                 continue
             want = max(want, min(t_opp(k / 16 * D) - t_ball(k / 16 * D, v)
                                  for k in range(1, 17)))
-    on_ball = net_ref.raster(_state([(0.0, 0.0)], [(0.0, 0.0)]))
+    on_ball = ref.raster(_state([(0.0, 0.0)], [(0.0, 0.0)]))
     assert on_ball[20, 40, 3] == bf(min(max(want, -2.0), 1.0))
 
     # no opponents: every pass is feasible with margin > 1, so the coarse
     # score is the angle and distance terms plus the capped margin 1
-    e = net_ref.raster(_state([], []))
+    e = ref.raster(_state([], []))
     assert np.all(e[..., 0] == 0)
     assert np.all(e[..., 3] == 1.0)
     qs = _sub_points(0, 22)
@@ -205,15 +208,15 @@ def test_raster_closed_forms():
     assert e[0, 0, 6] == -1.0 and e[0, 60, 6] == 1.0
     assert e[0, 0, 7] == -1.0 and e[45, 0, 7] == 1.0
     # a 1 m/s kick stops after 1 m: far cells get the floors
-    slow = net_ref.raster(_state([], []), speeds=(1.0,))
+    slow = ref.raster(_state([], []), speeds=(1.0,))
     assert slow[22, 60, 3] == -2.0 and slow[22, 60, 1] == bf(-1.2)
     assert slow[22, 30, 3] == 1.0
 
 
-def test_bf16_rounding():
+def check_bf16_rounding(ref):
     v = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 2 ** -7, 1.0 + 3 * 2 ** -8,
                   -2.5, 0.0, 65504.0])
-    r = net_ref.bf16(v)
+    r = ref.bf16(v)
     assert r[0] == 1.0
     assert r[1] == 1.0                       # tie to even
     assert r[2] == 1.0 + 2 ** -7             # representable
@@ -222,17 +225,35 @@ def test_bf16_rounding():
     assert r[6] == 65536.0
 
 
-def test_zero_network_is_the_coarse_score():
+def check_zero_network_is_the_coarse_score(ref):
     """The output adds the input's coarse-score channel to the last
     convolution: with zero weights the prediction is that channel."""
     rng = np.random.default_rng(5)
-    x = net_ref.bf16(rng.normal(size=(2, 46, 61, 8)))
-    _, out = net_ref.forward(x, net_ref.unflatten(np.zeros(net_ref.n_params())))
+    x = ref.bf16(rng.normal(size=(2, 46, 61, 8)))
+    _, out = ref.forward(x, ref.unflatten(np.zeros(ref.n_params())))
     assert np.array_equal(out, x[..., 1])
 
 
-def test_parameter_layout():
-    assert net_ref.n_params() == 21121
+def check_parameter_layout(ref):
+    assert ref.n_params() == 21121
     rng = np.random.default_rng(4)
-    w = rng.normal(size=net_ref.n_params())
-    assert np.array_equal(net_ref.flatten(net_ref.unflatten(w)), w)
+    w = rng.normal(size=ref.n_params())
+    assert np.array_equal(ref.flatten(ref.unflatten(w)), w)
+
+
+CHECKS = [
+    check_conv_matches_its_definition,
+    check_gradients_match_finite_differences,
+    check_focused_loss_gradients_match_finite_differences,
+    check_loss_weights,
+    check_input_gradient_is_the_adjoint_of_conv,
+    check_raster_closed_forms,
+    check_bf16_rounding,
+    check_zero_network_is_the_coarse_score,
+    check_parameter_layout,
+]
+
+
+@pytest.mark.parametrize("chk", CHECKS, ids=[c.__name__[6:] for c in CHECKS])
+def test_pin(chk):
+    chk(net_ref)
