@@ -33,8 +33,25 @@ def _nvcc() -> str:
     return cand if os.path.exists(cand) else "nvcc"
 
 
+# Sources compiled more than once, each time with its own defines: the
+# batched-plan kernels, once per opponent-slot count.
+VARIANTS = {"pps_batch_inst.cu": [("j%d" % j, ["-DPPS_BATCH_J=%d" % j])
+                                  for j in (6, 8, 12, 16)]}
+
+
 def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+
+
+def _units():
+    """(source, object name, extra flags) of every compilation."""
+    out = []
+    for src in _sources():
+        base = os.path.basename(src)
+        for tag, flags in VARIANTS.get(base, [("", [])]):
+            name = base + ("." + tag if tag else "") + ".o"
+            out.append((src, name, flags))
+    return out
 
 
 def _deps():
@@ -55,11 +72,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     os.makedirs(OBJ_DIR, exist_ok=True)
     nvcc = _nvcc()
-    srcs = _sources()
+    units = _units()
 
-    def compile_one(src):
-        obj = os.path.join(OBJ_DIR, os.path.basename(src) + ".o")
-        cmd = [nvcc] + NVCC_FLAGS + ["-c", src, "-o", obj]
+    def compile_one(unit):
+        src, name, extra = unit
+        obj = os.path.join(OBJ_DIR, name)
+        cmd = [nvcc] + NVCC_FLAGS + extra + ["-c", src, "-o", obj]
         if verbose:
             cmd += ["-Xptxas", "-v"]
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -69,8 +87,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=max(1, len(srcs))) as ex:
-        objs = list(ex.map(compile_one, srcs))
+    with cf.ThreadPoolExecutor(max_workers=max(1, len(units))) as ex:
+        objs = list(ex.map(compile_one, units))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -527,13 +527,7 @@ __global__ void __launch_bounds__(128)
 
 template <int J>
 cudaError_t launch(const DArgs& a, int num_sms, cudaStream_t st) {
-    static int occ = 0;
-    if (!occ) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dpps_kernel<J>,
-                                                          kTPB, 0) != cudaSuccess)
-            return cudaGetLastError();
-        if (occ < 1) occ = 1;
-    }
+    const int occ = pps_occupancy((const void*)dpps_kernel<J>, kTPB, 0);
     const long long items = (long long)a.n_states * a.prm.n_dir * a.chunks;
     long long grid = (items + kTPB / 32 - 1) / (kTPB / 32);
     if (grid > (long long)num_sms * occ) grid = (long long)num_sms * occ;

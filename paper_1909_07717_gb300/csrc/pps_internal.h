@@ -38,6 +38,12 @@ void pps_ctx_scratch(pps_ctx* ctx, unsigned long long** keys, int** counts);
 int pps_ctx_max_states(const pps_ctx* ctx);
 int pps_ctx_jmax(const pps_ctx* ctx);
 
+// CTAs per SM of kernel `func` at `tpb` threads and `smem` bytes of dynamic
+// shared memory on the calling thread's current device (at least 1).
+// Cached per (device, kernel, CTA size, shared memory) under a lock, so
+// concurrent callers and several devices each get their own figure.
+int pps_occupancy(const void* func, int tpb, size_t smem);
+
 // Network internals for the proposal path (pps_net.cu): the fallback's
 // per-state skip flags, the list of states to re-search and its length.
 struct pps_net_scratch {

@@ -10,7 +10,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 
 #include "pps.h"
 #include "pps_internal.h"
@@ -122,13 +125,8 @@ pps_status check_state(pps_ctx* ctx, const pps_state& s, int i) {
 
 template <int J, int V, bool EXT>
 cudaError_t launch(const pps::SearchArgs& a, int num_sms, cudaStream_t st) {
-    static int occ = 0;  // CTAs per SM of this instance (per process)
-    if (occ == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &occ, pps::search_kernel<J, V, EXT>, pps::search_tpb<J, V>(), 0);
-        if (e != cudaSuccess) return e;
-        if (occ < 1) occ = 1;
-    }
+    const int occ = pps_occupancy((const void*)pps::search_kernel<J, V, EXT>,
+                                  pps::search_tpb<J, V>(), 0);
     // One warp per work item of 32 points; no more CTAs than items need.
     const long long items = (long long)a.n_states * a.words;
     long long grid = (long long)num_sms * occ;
@@ -156,13 +154,35 @@ cudaError_t launch_v(const pps::SearchArgs& a, int num_sms, cudaStream_t st) {
 
 template <int J, int V>
 int occupancy_of() {
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ, pps::search_kernel<J, V>, pps::search_tpb<J, V>(), 0);
-    return occ;
+    return pps_occupancy((const void*)pps::search_kernel<J, V>,
+                         pps::search_tpb<J, V>(), 0);
 }
 
+std::mutex g_occ_mu;
+std::map<std::tuple<int, const void*, int, size_t>, int> g_occ;
+
 }  // namespace
+
+int pps_occupancy(const void* func, int tpb, size_t smem) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    const auto key = std::make_tuple(dev, func, tpb, smem);
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    auto it = g_occ.find(key);
+    if (it != g_occ.end()) return it->second;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, func, tpb, smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 1;  // not cached: the next call asks again
+    }
+    if (occ < 1) occ = 1;
+    g_occ.emplace(key, occ);
+    return occ;
+}
 
 // The calling thread's error buffer behind pps_last_error(NULL), shared with
 // the no-allocation entry point in pps_noalloc.cu.

@@ -9,6 +9,9 @@
 // Host code cannot use the array's name as a device address (it names a
 // host-side shadow), so the first call on each device, with that device
 // current, asks the runtime for the device address once and caches it.
+// That first call also loads every kernel instance the entry point can
+// launch, so that a later call never loads code (which lazy module loading
+// would otherwise do at an instance's first launch).
 
 #include <cuda_runtime.h>
 
@@ -37,9 +40,20 @@ constexpr size_t kScratchBytes = kKeyBytes + sizeof(int) * kMaxStates;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
+// The kernel instances this entry point launches: 8 or 16 opponent slots x
+// 1, 2, 4 or 8 speed slots.
+constexpr int kInstances = 8;
+int instance_of(int J, int V) {
+    return (J == 8 ? 0 : 4) + (V <= 1 ? 0 : V <= 2 ? 1 : V <= 4 ? 2 : 3);
+}
+
 std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices];  // device address of g_scratch per device
-int g_num_sms[kMaxDevices];
+struct DeviceSetup {
+    void* scratch = nullptr;  // device address of g_scratch on this device
+    int num_sms = 0;
+    int occ[kInstances] = {};  // CTAs per SM of each search-kernel instance
+};
+DeviceSetup g_dev[kMaxDevices];
 
 pps_status fail(pps_status s, const char* fmt, ...) {
     va_list ap;
@@ -49,47 +63,68 @@ pps_status fail(pps_status s, const char* fmt, ...) {
     return s;
 }
 
+// Load one instance's search and finalize kernels onto the current device
+// (cudaFuncGetAttributes forces the module load that lazy loading would
+// otherwise do at the first launch) and record its occupancy.
+template <int J, int V>
+cudaError_t load_instance(int* occ) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, pps::search_kernel<J, V>);
+    if (e == cudaSuccess)
+        e = cudaFuncGetAttributes(&fa, pps::finalize_kernel<J, V>);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            occ, pps::search_kernel<J, V>, pps::search_tpb<J, V>(), 0);
+    if (*occ < 1) *occ = 1;
+    return e;
+}
+
+template <int J>
+cudaError_t load_instances(int* occ) {
+    cudaError_t e = load_instance<J, 1>(occ + instance_of(J, 1));
+    if (e == cudaSuccess) e = load_instance<J, 2>(occ + instance_of(J, 2));
+    if (e == cudaSuccess) e = load_instance<J, 4>(occ + instance_of(J, 4));
+    if (e == cudaSuccess) e = load_instance<J, 8>(occ + instance_of(J, 8));
+    return e;
+}
+
 // Once per device, with that device current: resolve the scratch array's
-// device address (and the SM count for the persistent grid).
-pps_status setup(int device, void** scratch, int* num_sms) {
+// device address, the SM count, and load every kernel instance with its
+// occupancy, so that no later call on the device loads code.
+pps_status setup(int device, const DeviceSetup** out) {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[device]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess || !p) {
+    DeviceSetup& d = g_dev[device];
+    if (!d.scratch) {
+        DeviceSetup n;
+        cudaError_t e = cudaGetSymbolAddress(&n.scratch, g_scratch);
+        if (e != cudaSuccess || !n.scratch) {
             cudaGetLastError();
             return fail(PPS_ECUDA,
                         "pps_search_noalloc: cudaGetSymbolAddress on device "
                         "%d: %s", device, cudaGetErrorString(e));
         }
-        int sms = 0;
-        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount,
+        e = cudaDeviceGetAttribute(&n.num_sms, cudaDevAttrMultiProcessorCount,
                                    device);
+        if (e == cudaSuccess) e = load_instances<8>(n.occ);
+        if (e == cudaSuccess) e = load_instances<16>(n.occ);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(PPS_ECUDA, "pps_search_noalloc: device %d: %s",
                         device, cudaGetErrorString(e));
         }
-        g_num_sms[device] = sms;
-        g_scratch_addr[device] = p;
+        d = n;
     }
-    *scratch = g_scratch_addr[device];
-    *num_sms = g_num_sms[device];
+    *out = &d;
     return PPS_OK;
 }
 
 template <int J, int V>
-cudaError_t launch(const pps::SearchArgs& a, int num_sms, cudaStream_t st) {
-    static int occ = 0;
-    if (occ == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &occ, pps::search_kernel<J, V>, pps::search_tpb<J, V>(), 0);
-        if (e != cudaSuccess) return e;
-        if (occ < 1) occ = 1;
-    }
+cudaError_t launch(const pps::SearchArgs& a, const DeviceSetup& dv,
+                   cudaStream_t st) {
+    const int occ = dv.occ[instance_of(J, V)];
     // One warp per work item of 32 points; no more CTAs than items need.
     const long long items = (long long)a.n_states * a.words;
-    long long grid = (long long)num_sms * occ;
+    long long grid = (long long)dv.num_sms * occ;
     constexpr int tpb = pps::search_tpb<J, V>();
     const long long need = (items + tpb / 32 - 1) / (tpb / 32);
     if (grid > need) grid = need;
@@ -99,11 +134,12 @@ cudaError_t launch(const pps::SearchArgs& a, int num_sms, cudaStream_t st) {
 }
 
 template <int J>
-cudaError_t launch_v(const pps::SearchArgs& a, int num_sms, cudaStream_t st) {
-    if (a.V <= 1) return launch<J, 1>(a, num_sms, st);
-    if (a.V <= 2) return launch<J, 2>(a, num_sms, st);
-    if (a.V <= 4) return launch<J, 4>(a, num_sms, st);
-    return launch<J, 8>(a, num_sms, st);
+cudaError_t launch_v(const pps::SearchArgs& a, const DeviceSetup& dv,
+                     cudaStream_t st) {
+    if (a.V <= 1) return launch<J, 1>(a, dv, st);
+    if (a.V <= 2) return launch<J, 2>(a, dv, st);
+    if (a.V <= 4) return launch<J, 4>(a, dv, st);
+    return launch<J, 8>(a, dv, st);
 }
 
 bool finite_pos(float x) { return std::isfinite(x) && x > 0.f; }
@@ -169,10 +205,10 @@ extern "C" pps_status pps_search_noalloc(
         return fail(PPS_ECUDA, "pps_search_noalloc: cudaSetDevice(%d): %s",
                     device, cudaGetErrorString(e));
     }
-    void* scratch = nullptr;
-    int num_sms = 0;
-    pps_status s = setup(device, &scratch, &num_sms);
+    const DeviceSetup* dv = nullptr;
+    pps_status s = setup(device, &dv);
     if (s != PPS_OK) return s;
+    void* scratch = dv->scratch;
 
     cudaStream_t st = (cudaStream_t)stream;
     pps::SearchArgs a;
@@ -206,8 +242,8 @@ extern "C" pps_status pps_search_noalloc(
     if (e == cudaSuccess)
         e = cudaMemsetAsync(a.counts, 0, sizeof(int) * n_states, st);
     if (e == cudaSuccess)
-        e = max_opp <= 8 ? launch_v<8>(a, num_sms, st)
-                         : launch_v<16>(a, num_sms, st);
+        e = max_opp <= 8 ? launch_v<8>(a, *dv, st)
+                         : launch_v<16>(a, *dv, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(PPS_ECUDA, "pps_search_noalloc: launch: %s",

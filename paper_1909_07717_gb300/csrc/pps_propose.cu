@@ -108,13 +108,8 @@ __global__ void fallback_list_kernel(const pps_best* __restrict__ best, int n,
 
 template <int J, int V>
 int occupancy() {
-    static int occ = 0;
-    if (!occ) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &occ, refine_kernel<J, V>, pps::search_tpb<J, V>(), 0);
-        if (occ < 1) occ = 1;
-    }
-    return occ;
+    return pps_occupancy((const void*)refine_kernel<J, V>,
+                         pps::search_tpb<J, V>(), 0);
 }
 
 template <int J, int V>

@@ -412,17 +412,11 @@ extern "C" pps_status pps_run_points(pps_ctx* ctx, const pps_dstate* states,
     a.scores = out_scores;
     a.stride = out_scores ? (long long)score_stride : 0;
     if (e == cudaSuccess) {
-        static int occ = 0;
-        if (!occ) {
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, run_kernel, kTPB, 0);
-            if (occ < 1) occ = 1;
-        }
-        if (e == cudaSuccess) {
-            long long grid = (long long)pps_ctx_num_sms(ctx) * occ;
-            if (grid > n_states) grid = n_states;
-            run_kernel<<<(unsigned)grid, kTPB, 0, pps_ctx_stream(ctx)>>>(a);
-            e = cudaGetLastError();
-        }
+        const int occ = pps_occupancy((const void*)run_kernel, kTPB, 0);
+        long long grid = (long long)pps_ctx_num_sms(ctx) * occ;
+        if (grid > n_states) grid = n_states;
+        run_kernel<<<(unsigned)grid, kTPB, 0, pps_ctx_stream(ctx)>>>(a);
+        e = cudaGetLastError();
     }
     if (e != cudaSuccess) return pps_ctx_cuda_error(ctx, e, "pps_run_points");
     return PPS_OK;
