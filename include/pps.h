@@ -257,15 +257,20 @@ pps_status pps_reset(pps_ctx* ctx);
  *   max_opp   1..16: <= 8 runs the 8-slot kernel; states with more
  *             opponents than the kernel's slots are marked invalid
  *   states, out_best, out_mask: DEVICE memory, as pps_search with
- *             PPS_DEVICE_PTRS (out_mask may be NULL); results are identical
- *             to pps_search's for the same inputs
+ *             PPS_DEVICE_PTRS (out_mask may be NULL); the records and mask
+ *             are byte for byte those of pps_search on a context with the
+ *             same opponent slots (max_opp <= 8 on both, or > 8 on both)
+ *             for states whose K is within that context's max_K (this entry
+ *             point accepts K up to PPS_MAX_K)
  *   grid, speeds, params: host memory, as pps_search
  * Returns EINVAL for n_states > PPS_NOALLOC_MAX_STATES or any argument
  * pps_search would reject (message in pps_last_error(NULL)), ECUDA on a
  * device error.  Enqueues the work on `stream` and returns without waiting.
  *
  * The first call on each device resolves the array's device address
- * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * (cudaGetSymbolAddress, with that device current) and caches it, and loads
+ * every kernel instance this entry point can launch (8 or 16 opponent slots
+ * x 1, 2, 4 or 8 speed slots) so that no later call loads code; make that
  * first call before any stream capture.  Every call on a device shares the
  * one array and clears the slots it uses before the search, so calls that
  * overlap on the GPU (concurrent streams, or several host threads) race on
@@ -530,12 +535,25 @@ pps_status pps_net_forward(pps_net* net, const pps_state* states, int n,
 pps_status pps_net_forward_layers(pps_net* net, const pps_state* states,
                                   int n, float* out);
 
+/* The prediction from a given input map instead of states: map[n][46][61][8]
+ * bfloat16 bit patterns (device; the layout pps_net_raster writes).
+ * layers = 0 runs the tcgen05 pass of pps_net_forward, layers != 0 the
+ * layer-by-layer pass of pps_net_forward_layers.  For training or checking
+ * the network on maps computed elsewhere. */
+pps_status pps_net_forward_map(pps_net* net, const uint16_t* map, int n,
+                               int layers, float* out);
+
 /* The loss (pps_net_set_loss) of the prediction against labels[n][46][61]
  * (device) and its gradient with respect to the weights (grads:
  * PPS_NET_PARAMS floats, host, or NULL).  Waits for the result. */
 pps_status pps_net_grad(pps_net* net, const pps_state* states,
                         const float* labels, int n, float* grads,
                         float* loss);
+
+/* pps_net_grad from a given input map (device, as pps_net_forward_map). */
+pps_status pps_net_grad_map(pps_net* net, const uint16_t* map,
+                            const float* labels, int n, float* grads,
+                            float* loss);
 
 /* One Adam step (lr, beta 0.9/0.999) on a batch; *loss (host, may be NULL:
  * then the call does not wait) gets the batch's loss before the step. */

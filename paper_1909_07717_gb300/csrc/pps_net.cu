@@ -83,15 +83,34 @@ cudaError_t cast_weights(pps_net* nt) {
     return cudaGetLastError();
 }
 
-// Forward pass of n states into nt->out.  keep: layer by layer on mma.sync,
-// keeping every activation for the backward pass (training); otherwise the
-// tcgen05 kernel, which keeps them on the SM.
-cudaError_t forward(pps_net* nt, const pps_state* states, int n, bool keep,
-                    bool withhold = false) {
+// The input map of n states into nt->a0: rasterised from the states, or
+// (states NULL) copied from a caller's map[n][46][61][8] bf16 into the
+// 16-channel rows the kernels read (channels 8..15 zero).
+cudaError_t load_input(pps_net* nt, const pps_state* states,
+                       const uint16_t* map, int n) {
+    const long long P = (long long)n * NPIX;
+    cudaStream_t st = nt->stream;
+    if (states) {
+        raster_kernel<<<blocks(P, 128), 128, 0, st>>>(states, n, nt->cfg,
+                                                      nt->a0);
+        return cudaGetLastError();
+    }
+    cudaError_t e = cudaMemsetAsync(nt->a0, 0, sizeof(__nv_bfloat16) * P * C0, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(nt->a0, C0 * sizeof(uint16_t), map,
+                              8 * sizeof(uint16_t), 8 * sizeof(uint16_t), P,
+                              cudaMemcpyDeviceToDevice, st);
+    return e;
+}
+
+// Forward pass of the map in nt->a0 into nt->out.  keep: layer by layer on
+// mma.sync, keeping every activation for the backward pass (training);
+// otherwise the tcgen05 kernel, which keeps them on the SM.
+cudaError_t forward_loaded(pps_net* nt, int n, bool keep,
+                           bool withhold = false) {
     const long long P = (long long)n * NPIX;
     const unsigned g = blocks(P, 64);
     cudaStream_t st = nt->stream;
-    raster_kernel<<<blocks(P, 128), 128, 0, st>>>(states, n, nt->cfg, nt->a0);
     if (!keep) {
         cudaError_t e = cudaFuncSetAttribute(
             tcf::tc_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -115,6 +134,13 @@ cudaError_t forward(pps_net* nt, const pps_state* states, int n, bool keep,
     conv_kernel<CH, CO, kOutput><<<g, 128, 0, st>>>(
         nt->a3, nt->Wf + wf_off(3), nt->w + bias_off(3), P, nt->out, nt->a0);
     return cudaGetLastError();
+}
+
+// Forward pass of n states (or, states NULL, of a caller's input map).
+cudaError_t forward(pps_net* nt, const pps_state* states, int n, bool keep,
+                    bool withhold = false, const uint16_t* map = nullptr) {
+    cudaError_t e = load_input(nt, states, map, n);
+    return e == cudaSuccess ? forward_loaded(nt, n, keep, withhold) : e;
 }
 
 // Gradients of the mean squared error into nt->grad (accumulated).
@@ -407,12 +433,13 @@ extern "C" pps_status pps_net_raster(pps_net* nt, const pps_state* states,
 
 namespace {
 pps_status forward_to(pps_net* nt, const pps_state* states, int n, float* out,
-                      bool keep, const char* who) {
-    pps_status s = check_batch(nt, states, n);
+                      bool keep, const char* who,
+                      const uint16_t* map = nullptr) {
+    pps_status s = check_batch(nt, states ? (const void*)states : map, n);
     if (s != PPS_OK) return s;
     if (!out) return PPS_EINVAL;
     cudaSetDevice(nt->device);
-    cudaError_t e = forward(nt, states, n, keep);
+    cudaError_t e = forward(nt, states, n, keep, false, map);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out, nt->out, sizeof(float) * (size_t)n * NPIX,
                             cudaMemcpyDeviceToDevice, nt->stream);
@@ -432,16 +459,24 @@ extern "C" pps_status pps_net_forward_layers(pps_net* nt,
     return forward_to(nt, states, n, out, true, "pps_net_forward_layers");
 }
 
-extern "C" pps_status pps_net_grad(pps_net* nt, const pps_state* states,
-                                   const float* labels, int n, float* grads,
-                                   float* loss) {
-    pps_status s = check_batch(nt, states, n);
+extern "C" pps_status pps_net_forward_map(pps_net* nt, const uint16_t* map,
+                                          int n, int layers, float* out) {
+    if (!map) return PPS_EINVAL;
+    return forward_to(nt, nullptr, n, out, layers != 0, "pps_net_forward_map",
+                      map);
+}
+
+namespace {
+pps_status grad_of(pps_net* nt, const pps_state* states, const uint16_t* map,
+                   const float* labels, int n, float* grads, float* loss,
+                   const char* who) {
+    pps_status s = check_batch(nt, states ? (const void*)states : map, n);
     if (s != PPS_OK) return s;
     if (!labels) return PPS_EINVAL;
     cudaSetDevice(nt->device);
     cudaError_t e = cudaMemsetAsync(nt->grad, 0, sizeof(float) * kPadParams,
                                     nt->stream);
-    if (e == cudaSuccess) e = forward(nt, states, n, true);
+    if (e == cudaSuccess) e = forward(nt, states, n, true, false, map);
     if (e == cudaSuccess) e = backward(nt, labels, n);
     std::vector<float> pad(kPadParams);
     float l = 0.f;
@@ -454,10 +489,26 @@ extern "C" pps_status pps_net_grad(pps_net* nt, const pps_state* states,
     if (e == cudaSuccess) e = cudaStreamSynchronize(nt->stream);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(nt->grad, 0, sizeof(float) * kPadParams, nt->stream);
-    if (e != cudaSuccess) return fail(PPS_ECUDA, "pps_net_grad", e);
+    if (e != cudaSuccess) return fail(PPS_ECUDA, who, e);
     if (grads) from_padded(pad, grads);
     if (loss) *loss = l;
     return PPS_OK;
+}
+}  // namespace
+
+extern "C" pps_status pps_net_grad(pps_net* nt, const pps_state* states,
+                                   const float* labels, int n, float* grads,
+                                   float* loss) {
+    if (!states) return PPS_EINVAL;
+    return grad_of(nt, states, nullptr, labels, n, grads, loss, "pps_net_grad");
+}
+
+extern "C" pps_status pps_net_grad_map(pps_net* nt, const uint16_t* map,
+                                       const float* labels, int n,
+                                       float* grads, float* loss) {
+    if (!map) return PPS_EINVAL;
+    return grad_of(nt, nullptr, map, labels, n, grads, loss,
+                   "pps_net_grad_map");
 }
 
 extern "C" pps_status pps_net_train_step(pps_net* nt, const pps_state* states,

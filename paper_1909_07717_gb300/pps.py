@@ -205,7 +205,8 @@ EXPORTS = ("pps_abi_version", "pps_status_string", "pps_last_error",
            "pps_net_set_features", "pps_net_set_loss", "pps_net_set_weights",
            "pps_net_sync", "pps_net_selftest_timeout",
            "pps_net_get_weights", "pps_net_raster", "pps_net_forward_layers",
-           "pps_net_forward", "pps_net_grad", "pps_net_train_step",
+           "pps_net_forward", "pps_net_forward_map", "pps_net_grad",
+           "pps_net_grad_map", "pps_net_train_step",
            "pps_net_labels", "pps_propose", "pps_dpps_default_params",
            "pps_dpps_mask_words", "pps_dpps_search", "pps_pass_powers",
            "pps_shoot", "pps_run_default_params", "pps_run_grid",
@@ -303,9 +304,15 @@ def lib():
                                           c_void_p]
             L.pps_net_forward_layers.argtypes = [c_void_p, c_void_p,
                                                  ctypes.c_int, c_void_p]
+            L.pps_net_forward_map.argtypes = [c_void_p, c_void_p,
+                                              ctypes.c_int, ctypes.c_int,
+                                              c_void_p]
             L.pps_net_grad.argtypes = [c_void_p, c_void_p, c_void_p,
                                        ctypes.c_int, c_void_p,
                                        P(ctypes.c_float)]
+            L.pps_net_grad_map.argtypes = [c_void_p, c_void_p, c_void_p,
+                                           ctypes.c_int, c_void_p,
+                                           P(ctypes.c_float)]
             L.pps_net_train_step.argtypes = [c_void_p, c_void_p, c_void_p,
                                              ctypes.c_int, ctypes.c_float,
                                              P(ctypes.c_float)]
@@ -546,11 +553,24 @@ def pps_net_forward_layers(net, states, n, out) -> int:
     return _check(lib().pps_net_forward_layers(net, states, n, out))
 
 
+def pps_net_forward_map(net, maps, n, layers, out) -> int:
+    """Device addresses: maps (n x 46 x 61 x 8 bf16 bits), out."""
+    return _check(lib().pps_net_forward_map(net, maps, n, int(layers), out))
+
+
 def pps_net_grad(net, states, labels, n):
     g = np.zeros(PPS_NET_PARAMS, np.float32)
     loss = ctypes.c_float()
     _check(lib().pps_net_grad(net, states, labels, n, g.ctypes.data,
                               ctypes.byref(loss)))
+    return loss.value, g
+
+
+def pps_net_grad_map(net, maps, labels, n):
+    g = np.zeros(PPS_NET_PARAMS, np.float32)
+    loss = ctypes.c_float()
+    _check(lib().pps_net_grad_map(net, maps, labels, n, g.ctypes.data,
+                                  ctypes.byref(loss)))
     return loss.value, g
 
 

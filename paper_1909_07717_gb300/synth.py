@@ -366,3 +366,65 @@ def serving_matches(seed: int, n_matches: int, n_frames: int, *,
 # 6-11 opponents, grid 0.05 m, 4 kick speeds (K = 32 samples per pass).
 SERVING_SEED = 4
 SERVING_MATCHES = 512
+
+
+# Input maps of the proposal network (46 x 61 pixels x 8 channels), drawn
+# directly instead of rasterised from states, for checking the network's
+# kernels on the same input on both sides.  Each channel is uniform over
+# the range the rasteriser's channel takes on a 12 x 9 m field (opponent
+# density, coarse score with a share of cells at the floor, ball distance,
+# margin, shot angle / pi, goal distance, x and y); the low 16 bits of every
+# float32 are cleared, so each value is exactly a bfloat16 (returned as its
+# 16-bit pattern).
+NET_MAP_RANGES = ((0.0, 2.0), (-1.1, 1.5), (0.0, 1.0), (-2.0, 1.0),
+                  (0.0, 0.35), (0.0, 1.0), (-1.0, 1.0), (-1.0, 1.0))
+NET_MAP_FLOOR = -1.2      # the coarse score where no pass is feasible
+NET_MAP_FLOOR_SHARE = 0.3
+
+
+def net_maps(seed: int, n: int, h: int = 46, w: int = 61,
+             integer: bool = False) -> np.ndarray:
+    """n seeded input maps, uint16 bfloat16 patterns of shape (n, h, w, 8).
+    integer: every value an integer in 0..3 instead (with integer weights
+    the network's sums are then exact in float32 and bfloat16)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if integer:
+        x = rng.integers(0, 4, size=(n, h, w, 8)).astype(np.float32)
+        return (x.view(np.uint32) >> 16).astype(np.uint16)
+    lo = np.array([r[0] for r in NET_MAP_RANGES])
+    hi = np.array([r[1] for r in NET_MAP_RANGES])
+    x = rng.uniform(lo, hi, size=(n, h, w, 8)).astype(np.float32)
+    floor = rng.uniform(size=(n, h, w)) < NET_MAP_FLOOR_SHARE
+    x[..., 1] = np.where(floor, np.float32(NET_MAP_FLOOR), x[..., 1])
+    return (x.view(np.uint32) >> 16).astype(np.uint16)
+
+
+NET_LAYERS = ((8, 32), (32, 32), (32, 32), (32, 1))   # (inputs, outputs)
+
+
+def net_int_weights(seed: int, nonzero: int = 3) -> np.ndarray:
+    """Integer weights for the proposal network, flat in the library's
+    layout (per layer W[3][3][cout][cin], then bias[cout]): each output
+    channel of a hidden layer takes `nonzero` taps of weight +-1 -- the
+    first on input channel (c mod cin) through a permutation, so that every
+    input channel feeds some output, the others at random -- the rest 0;
+    the output channel takes one +-1 tap on every input channel; biases are
+    integers in -1..1.  On integer input maps every sum stays a small
+    integer."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for ci, co in NET_LAYERS:
+        W = np.zeros((9, co, ci), np.float32)
+        perm = rng.permutation(max(ci, co))
+        for c in range(co):
+            if co == 1:
+                taps = rng.integers(0, 9, size=ci)
+                W[taps, c, np.arange(ci)] = rng.choice([-1.0, 1.0], size=ci)
+                continue
+            first = perm[c] % ci
+            rest = rng.choice(9 * ci, size=nonzero - 1, replace=False)
+            W[rng.integers(0, 9), c, first] = rng.choice([-1.0, 1.0])
+            W[rest // ci, c, rest % ci] = rng.choice([-1.0, 1.0],
+                                                     size=nonzero - 1)
+        out += [W.reshape(-1), rng.integers(-1, 2, size=co).astype(np.float32)]
+    return np.concatenate(out)

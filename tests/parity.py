@@ -7,8 +7,13 @@ Tolerances (FP32 GPU against the FP64 oracle on identical FP32 inputs):
     within 1e-5 m of min_pass_dist;
   * intercept times T_k: |dT| <= 1e-5 s + 2 * cond_k, where
     cond_k = |grad_p T_k| * 2e-6 m is how far T_k moves when the sample
-    point moves by the rounding of FP32 coordinates on a 12 m field
-    (well-conditioned samples, the vast majority, get the plain 1e-5 s);
+    point moves by the rounding of FP32 coordinates on a 12 m field;
+    well-conditioned samples (|grad_p T_k| <= 2 s/m: the allowance would be
+    at most 8e-6 s) are held to the plain 1e-5 s, and at most 5 % of a
+    state's samples (of states with at least 1000) may be outside that
+    class (a sample within a metre or two of an opponent moving across the
+    line, where the intercept time changes fast with the point; 0.3-3.2 %
+    of the samples of the dense parity cases);
   * margins (reachable passes outside the reach band):
     |dm| <= 1e-5 s + 2 * max_k (cond_k + bcond_k), where bcond_k is the
     first-order change of the ball time t(s_k) when v^2 and s_k carry FP32
@@ -29,6 +34,8 @@ TOL_T = 1e-5        # s
 TOL_MASK = 1e-3     # s
 TOL_REACH = 1e-4    # relative to v^2
 TOL_SCORE = 1e-5    # relative, floor 1
+WELLCOND_GRAD = 2.0       # s/m: samples held to the plain TOL_T
+MAX_ILLCOND_FRAC = 0.05   # most samples of a state outside that class
 
 
 def grid_spec(grid):
@@ -136,15 +143,23 @@ def check_state_dense(gpu, orc, batch, s, grid, speeds, params, Tcond=None):
         err = np.where(both_inf, 0.0, np.abs(Tg - To))
         tol = TOL_T + 2 * Tcond
         bad = err > tol
-        # well-conditioned: |grad T| <= 1 s/m (a sample metres away from
-        # every opponent that could reach it first)
-        wc = Tcond <= DELTA_P
+        # well-conditioned: |grad T| <= WELLCOND_GRAD (a sample away from
+        # any opponent moving across the line that could reach it first)
+        wc = Tcond <= WELLCOND_GRAD * DELTA_P
         stats["T_max_err_wellcond"] = float(err[wc].max(initial=0))
         stats["T_max_err"] = float(err.max(initial=0))
         stats["T_frac_wellcond"] = float(np.mean(wc))
         assert not bad.any(), (
             f"state {s}: {bad.sum()} T_k outside tolerance, worst "
             f"{err[bad].max():.3g} s at cond {Tcond[bad][np.argmax(err[bad])]:.3g}")
+        assert stats["T_max_err_wellcond"] <= TOL_T, (
+            f"state {s}: well-conditioned T_k off by "
+            f"{stats['T_max_err_wellcond']:.3g} s")
+        # (a share is only meaningful over many samples: tiny grids aside)
+        assert wc.size < 1000 or \
+            1.0 - stats["T_frac_wellcond"] <= MAX_ILLCOND_FRAC, (
+                f"state {s}: {1 - stats['T_frac_wellcond']:.3f} of the "
+                f"samples need the conditioning allowance")
     # ---- bands
     _, cx, cy = sample_points(st, grid, 1)
     D = np.hypot(cx - st.sc[0], cy - st.sc[1])
@@ -155,6 +170,7 @@ def check_state_dense(gpu, orc, batch, s, grid, speeds, params, Tcond=None):
                | (reach_gap <= TOL_REACH)
                | (np.abs(D - params["min_pass_dist"]) <= 1e-5)[None, :])
     stats["mask_band_frac"] = float(in_band.mean())
+    stats["mask_band_count"] = int(in_band.sum())
     diff = (mask[s] != feas_o) & ~in_band
     assert not diff.any(), f"state {s}: {diff.sum()} mask bits differ"
     # ---- margins
