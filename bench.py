@@ -46,6 +46,9 @@ REF_SAMPLE_STATES = 16       # oracle sample per step of --impl reference
 #   per ball evaluation (state, point, sample, speed):          3 FP32 + 1 MUFU
 OPS_INTERACTION, MUFU_INTERACTION = 14, 2
 OPS_BALL, MUFU_BALL = 3, 1
+# The plan's per-unit estimate made before the kernel existed: about 20 FP32
+# lane-ops per interaction and 8 per ball evaluation (reported beside).
+SURVEY_OPS_INTERACTION, SURVEY_OPS_BALL = 20, 8
 FP32_LANES_PER_SM = 128
 MUFU_LANES_PER_SM = 32   # ncu: XU pipe peak ~1 warp-instr/clk/SM on GB300
 
@@ -102,6 +105,46 @@ def _profiled_traffic(digest):
     except (OSError, KeyError, ValueError):
         pass
     return None
+
+
+def _profile_kv(name):
+    """The machine-readable "key: value" lines of a committed ncu summary."""
+    kv = {}
+    try:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+    except OSError:
+        pass
+    return kv
+
+
+def _alu_peak(nsm):
+    """FP32 lane-ops/s: SMs x 128 FP32 lanes x the maximum SM clock."""
+    sm_max = float(_peaks().get("sm_max_mhz", 2070.0))
+    return nsm * FP32_LANES_PER_SM * sm_max * 1e6, sm_max
+
+
+def _alu_roofline(ops, seconds, nsm, per_unit, units):
+    peak, sm_max = _alu_peak(nsm)
+    return {"bound": "alu", "achieved": ops / seconds / 1e12,
+            "peak": peak / 1e12, "unit": "Tops/s (FP32 lane-ops)",
+            "frac": ops / seconds / peak, "traffic": None,
+            "ops_per_launch": ops, "per_unit": per_unit, "units": units,
+            "peak_basis": (f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                           f"{sm_max:.0f} MHz (max SM clock)")}
+
+
+def _oracle_pool_rate(jobs, threads):
+    """Run oracle searches (callables) on `threads` host threads at once
+    (each single-threaded; the calls release the interpreter); seconds."""
+    import concurrent.futures as cf
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(lambda f: f(), jobs))
+    return time.perf_counter() - t0
 
 
 class ClockSampler:
@@ -352,6 +395,15 @@ def run_pps(args):
         peak_ops = nsm * FP32_LANES_PER_SM * sm_max * 1e6
         peak_mufu = nsm * MUFU_LANES_PER_SM * sm_max * 1e6
         digest = _kernel_src_digest()
+        ops_survey = (SURVEY_OPS_INTERACTION * interactions
+                      + SURVEY_OPS_BALL * ball_evals)
+        prof = _profile_kv("search_kernel_batched.txt")
+        ncu = None
+        if "fma_pipe_active" in prof:
+            ncu = {"fma_pipe_active": float(prof["fma_pipe_active"]),
+                   "xu_pipe_active": float(prof["xu_pipe_active"]),
+                   "source": "profiles/search_kernel_batched.txt",
+                   "current_kernel": prof.get("kernel_source_digest") == digest}
         roof = {"bound": "alu", "achieved": ops / t_launch / 1e12,
                 "peak": peak_ops / 1e12, "unit": "Tops/s (FP32 lane-ops)",
                 "frac": ops / t_launch / peak_ops,
@@ -359,6 +411,21 @@ def run_pps(args):
                 "peak_basis": (f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                f"{sm_max:.0f} MHz (max SM clock)"),
                 "ops_per_launch": ops,
+                "per_unit": (f"{OPS_INTERACTION} FP32 lane-ops per opponent "
+                             f"interaction, {OPS_BALL} per ball evaluation "
+                             "(the kernel's own arithmetic)"),
+                "survey_count": {
+                    "per_unit": (f"{SURVEY_OPS_INTERACTION} per interaction, "
+                                 f"{SURVEY_OPS_BALL} per ball evaluation "
+                                 "(the plan's estimate before the kernel)"),
+                    "ops_per_launch": ops_survey,
+                    "achieved": ops_survey / t_launch / 1e12,
+                    "frac": ops_survey / t_launch / peak_ops},
+                "ncu": ncu,
+                "target": ("at least 0.5 of the FP32 pipe: judged on ncu's "
+                           "FMA-pipe active fraction (ncu.fma_pipe_active); "
+                           "frac and survey_count.frac bracket it by the two "
+                           "op counts"),
                 "xu": {"achieved": mufu / t_launch / 1e12,
                        "peak": peak_mufu / 1e12, "unit": "T MUFU ops/s",
                        "frac": mufu / t_launch / peak_mufu},
@@ -399,7 +466,7 @@ def run_pps(args):
         if world == 1 and not args.no_uneven:
             line["uneven"] = _uneven(args, dev, stream)
         if world == 1 and not args.no_serving:
-            line["serving"] = _serving(dev)
+            line["serving"] = _serving(dev, no_cpu=args.no_cpu_baseline)
         if world == 1 and not args.no_proposal:
             line["proposal"] = _proposal(args, dev, stream)
         if world == 1 and not args.no_dpps:
@@ -451,14 +518,57 @@ def _uneven(args, dev, stream):
     groups = [{"opp_slots": g.opp_slots, "speed_slots": g.speed_slots,
                "states": g.n_states, "cta_threads": g.cta_threads,
                "items": g.n_items} for g in plan.groups()]
+    P = np.array([jobs[i].grid.nx * jobs[i].grid.ny for i in range(S)],
+                 np.float64)
+    V = np.array([jobs[i].n_speeds for i in range(S)], np.float64)
+    K = batch["K"].astype(np.float64)
+    J = batch["n_opp"].astype(np.float64)
+    inter, ball = float((P * K * J).sum()), float((P * K * V).sum())
+    props = torch.cuda.get_device_properties(dev)
+    roof = _alu_roofline(OPS_INTERACTION * inter + OPS_BALL * ball, ms / 1e3,
+                         props.multi_processor_count,
+                         f"{OPS_INTERACTION} per opponent interaction "
+                         f"(state x point x sample x opponent), {OPS_BALL} "
+                         "per ball evaluation (state x point x sample x "
+                         "speed), as the single-grid kernel",
+                         {"interactions": inter, "ball_evaluations": ball})
+    roof["scope"] = "every group's kernels of one graph replay"
     out = {"workload": (f"uneven_{S}: 12x9/11v11 + 9x6/6v6, grids "
                         "0.025-0.1 m, 1-8 speeds, K 32-128 (seed 2)"),
            "value": evals / (ms / 1e3), "unit": UNIT, "ms_per_run": ms,
            "states_per_s": S / (ms / 1e3), "first_run_s": first_s,
            "graph": True, "autotuned": True, "groups": groups,
+           "roofline": roof,
            "ok": bool(np.all(best["status"] == 0))}
     plan.close()
     searcher.close()
+    if not args.no_cpu_baseline:
+        # the oracle on 48 states spread over the batch, each on its own
+        # grid, one state per host thread at a time
+        import oracle
+        pick = list(range(0, S, max(1, S // 48)))[:48]
+        cores = oracle.max_threads()
+        calls, n_evals = [], 0.0
+
+        def call(i):
+            g = jobs[i].grid
+            gs = (float(np.float32(g.spacing)), g.nx, g.ny,
+                  float(np.float32(g.x0)), float(np.float32(g.y0)))
+            sp = [float(jobs[i].speeds[v]) for v in range(jobs[i].n_speeds)]
+            sub = synth.take(batch, [i])
+            return lambda: oracle.search(sub, gs, sp, synth.DEFAULT_PARAMS,
+                                         n_threads=1)
+        for i in pick:
+            calls.append(call(i))
+            n_evals += P[i] * V[i] * J[i]
+        dt = _oracle_pool_rate(calls, cores)
+        oracle.search(synth.take(batch, [0]), (0.5, 2, 2, -6.0, -4.5), [3.0],
+                      synth.DEFAULT_PARAMS, n_threads=cores)
+        out["cpu_baseline"] = {"value": n_evals / dt, "unit": UNIT,
+                               "cores": cores, "kind": "oracle",
+                               "sample": (f"{len(pick)} states spread over the "
+                                          f"batch, each on its own grid, one "
+                                          f"per host thread; {dt:.1f} s wall")}
     return out
 
 
@@ -499,6 +609,16 @@ def _proposal(args, dev, stream):
     ms_plain = timed(lambda: pr.exact(st, S, w.speeds, out=exo), steps)
     ms_prop = timed(lambda: pr.run(st, S, w.speeds, out=pro), steps)
     ms_pred = timed(lambda: pr.net.forward(st, S), steps)
+    # the stages on their own: the rasteriser (pps_net_raster, which also
+    # copies the map out), the tcgen05 network on that map
+    # (pps_net_forward_map, which first copies it into the network's
+    # 16-channel input)
+    maps = torch.empty((S, 46, 61, 8), dtype=torch.int16, device=dev)
+    net_out = torch.empty((S, 46, 61), dtype=torch.float32, device=dev)
+    ms_raster = timed(lambda: pps.pps_net_raster(pr.net.net, st.data_ptr(), S,
+                                                 maps.data_ptr()), steps)
+    ms_network = timed(lambda: pps.pps_net_forward_map(
+        pr.net.net, maps.data_ptr(), S, 0, net_out.data_ptr()), steps)
     ex = pps.unpack_best(exo["best"].cpu().numpy())
     pb = pps.unpack_best(pro[0].cpu().numpy())
     nofb = pps.unpack_best(pr.run(st, S, w.speeds, fallback=False)[0]
@@ -520,7 +640,57 @@ def _proposal(args, dev, stream):
                                        10, flush_l2=False)}
     pr.close()
     ok = agreement(pb, ex)
+    props = torch.cuda.get_device_properties(dev)
+    nsm = props.multi_processor_count
+    # network: algorithmic FLOPs of the four 3x3 convolutions on the
+    # unpadded channels, no band halo: 2 x 9 x (8x32 + 32x32 + 32x32 + 32x1)
+    # per pixel
+    flop_px = 2 * 9 * (8 * 32 + 32 * 32 + 32 * 32 + 32 * 1)
+    flops = S * 46 * 61 * flop_px
+    peak_tc = float(_peaks().get("bf16_tflops", 1920.3)) * 1e12
+    net_roof = {"bound": "tensor", "achieved": flops / (ms_network / 1e3) / 1e12,
+                "peak": peak_tc / 1e12, "unit": "TFLOP/s (bf16, FP32 accumulate)",
+                "frac": flops / (ms_network / 1e3) / peak_tc, "traffic": None,
+                "per_unit": f"{flop_px} FLOP per map pixel (unpadded channels, "
+                            "no halo)", "flops_per_launch": flops,
+                "peak_basis": "measured bf16 cuBLAS burst (MEASURED_PEAKS.json)",
+                "ms": ms_network,
+                "note": "time includes copying the map into the network's "
+                        "16-channel input"}
+    # rasteriser: per pixel 4 sub-points x 16 pass-line samples x (8
+    # opponent slots x 14 + 4 speeds x 3) FP32 lane-ops of the search's
+    # arithmetic (shot angles and the other channels not counted)
+    ops_px = 4 * 16 * (8 * OPS_INTERACTION + 4 * OPS_BALL)
+    raster_roof = _alu_roofline(S * 46 * 61 * ops_px, ms_raster / 1e3, nsm,
+                                f"{ops_px} FP32 lane-ops per map pixel (4 "
+                                "sub-points x 16 samples x (8 opponent slots "
+                                "x 14 + 4 speeds x 3)); shot angles and the "
+                                "other channels not counted",
+                                {"pixels": S * 46 * 61})
+    raster_roof["ms"] = ms_raster
+    roofline = {"network": net_roof, "raster": raster_roof,
+                "refine_topk_finalize_ms": ms_prop - ms_pred,
+                "shares_of_the_call": {
+                    "raster": ms_raster / ms_prop,
+                    "network": ms_network / ms_prop,
+                    "top-k, refinement, finalize":
+                        (ms_prop - ms_pred) / ms_prop}}
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        g = pps.fine_grid_12x9()
+        gs = (float(np.float32(g.spacing)), g.nx, g.ny, float(g.x0),
+              float(g.y0))
+        t0 = time.perf_counter()
+        oracle.search(synth.take(batch, list(range(4))), gs, w.speeds,
+                      w.params)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 4 / dt, "unit": "states/s",
+               "cores": oracle.max_threads(), "kind": "oracle",
+               "sample": f"the first 4 states, full 0.025 m grid; {dt:.1f} s "
+                         "wall (the plain search: the proposal's judge)"}
     return {"workload": f"{w.name} (seed {w.seed}, held out of training)",
+            "roofline": roofline, "cpu_baseline": cpu,
             "topk": TOPK, "ms_plain": ms_plain, "ms_proposal": ms_prop,
             "ms_predict": ms_pred,
             "plain_states_per_s": S / (ms_plain / 1e3),
@@ -607,7 +777,31 @@ def _dpps(args, dev, stream):
     ms_shot = timed(lambda: pps.pps_shoot(
         searcher.ctx, rec.data_ptr(), S, sqd.data_ptr(), Q, 6.5, 0.1, prm,
         sout.data_ptr()))
+    # Algorithmic work: per candidate the teammates' search runs sample by
+    # sample up to the first interception (all K when none) and then,
+    # for a pass a teammate gets, the opponents' search likewise; a sample is
+    # 16 robot interactions and one ball term, plus one sample more for the
+    # group that stops (the holder is found again there).  The samples are
+    # counted from the debug times of the first 256 states (untimed run).
+    sub_n = min(S, 256)
+    C = prm.n_dir * prm.n_pow
+    dbg = torch.empty((sub_n, C, 3), dtype=torch.float32, device=dev)
+    best2 = torch.empty(sub_n * 48, dtype=torch.uint8, device=dev)
+    pps.pps_dpps_search(searcher.ctx, rec.data_ptr(), sub_n, prm,
+                        best2.data_ptr(), None, dbg.data_ptr())
+    torch.cuda.synchronize()
+    dd = dbg.cpu().numpy().astype(np.float64)
     searcher.close()
+    samples = _dpps_samples(batch, synth.DPPS_PARAMS, dd)
+    per_sample_ops = 16 * OPS_INTERACTION + OPS_BALL
+    ops = samples / sub_n * S * per_sample_ops
+    props = torch.cuda.get_device_properties(dev)
+    roof = _alu_roofline(ops, ms / 1e3, props.multi_processor_count,
+                         f"{per_sample_ops} FP32 lane-ops per searched sample "
+                         f"(16 robots x {OPS_INTERACTION} + a ball term of "
+                         f"{OPS_BALL}); samples per decision counted from "
+                         "the first 256 states' interception times",
+                         {"samples_per_decision": samples / sub_n})
     robots = int(batch["n_team"][0] + batch["n_opp"][0])
     sbip = S * prm.n_dir * prm.n_pow * robots
     cpu = None
@@ -633,8 +827,47 @@ def _dpps(args, dev, stream):
                             "queries_per_s": Q / (ms_pass / 1e3)},
             "shots": {"queries": Q, "ms": ms_shot,
                       "queries_per_s": Q / (ms_shot / 1e3)},
-            "cpu_baseline": cpu,
+            "cpu_baseline": cpu, "roofline": roof,
             "ok": bool(np.all(b["status"] == 0))}
+
+
+def _dpps_samples(batch, p, dbg):
+    """Samples searched by the direction x power kernel for the states of
+    dbg (n, n_dir * n_pow, 3: t_team, t_opp, score): for each group, the
+    sample of its first interception recovered from the ball's time there
+    (all K samples when none), plus the holder's one."""
+    n = dbg.shape[0]
+    nd, npw = p["n_dir"], p["n_pow"]
+    phi = 2 * np.pi * np.arange(nd) / nd
+    ux, uy = np.cos(phi)[:, None], np.sin(phi)[:, None]
+    v0 = p["v_lo"] + np.arange(npw) * (p["v_hi"] - p["v_lo"]) / max(npw - 1, 1)
+    v = p["slide"] * v0[None, :]
+    total = 0.0
+    for s in range(n):
+        a = float(batch["ball_decel"][s])
+        bx, by = (float(x) for x in batch["ball"][s])
+        hl, hw = batch["field_len"][s] / 2, batch["field_wid"][s] / 2
+        K = int(batch["K"][s])
+        with np.errstate(divide="ignore", invalid="ignore"):
+            edge = np.minimum.reduce([
+                np.where(ux > 0, (hl - bx) / ux, np.inf),
+                np.where(ux < 0, (-hl - bx) / ux, np.inf),
+                np.where(uy > 0, (hw - by) / uy, np.inf),
+                np.where(uy < 0, (-hw - by) / uy, np.inf)])
+        S = np.minimum(v * v / (2 * a), np.maximum(edge, 0.0))
+
+        def k_of(t):
+            tt = np.where(np.isfinite(t), np.minimum(t, v / a), 0.0)
+            dist = v * tt - 0.5 * a * tt * tt
+            with np.errstate(divide="ignore", invalid="ignore"):
+                k = np.clip(np.round(dist / S * K), 1, K)
+            return np.where(np.isfinite(t), k + 1, K)   # + the holder's
+
+        tt = dbg[s, :, 0].reshape(nd, npw)
+        to = dbg[s, :, 1].reshape(nd, npw)
+        got = np.isfinite(tt)
+        total += float(k_of(tt).sum() + np.where(got, k_of(to), 0).sum())
+    return total
 
 
 def _run_points(args, dev, stream):
@@ -693,8 +926,27 @@ def _run_points(args, dev, stream):
         cpu = {"points_per_s": 512 * nx * ny / dt, "states_per_s": 512 / dt,
                "cores": os.cpu_count(), "kind": "oracle",
                "sample": "first 512 states of the workload"}
+    # issue-bound: warp instructions per point from the committed ncu
+    # summary, against one warp instruction per scheduler and clock
+    prof = _profile_kv("run_kernel_4096.txt")
+    roof = None
+    if "warp_instructions_per_32_points" in prof:
+        props = torch.cuda.get_device_properties(dev)
+        nsm = props.multi_processor_count
+        sm_max = float(_peaks().get("sm_max_mhz", 2070.0))
+        ipp = float(prof["warp_instructions_per_32_points"]) / 32
+        peak = nsm * 4 * sm_max * 1e6
+        ach = pts * ipp / (ms / 1e3)
+        roof = {"bound": "issue", "achieved": ach / 1e12, "peak": peak / 1e12,
+                "unit": "T warp-instructions/s", "frac": ach / peak,
+                "traffic": None,
+                "per_unit": f"{ipp * 32:.1f} warp instructions per 32 points "
+                            "(ncu, profiles/run_kernel_4096.txt)",
+                "peak_basis": f"{nsm} SMs x 4 schedulers x {sm_max:.0f} MHz",
+                "ncu_issue_active": float(prof.get("issue_active", "nan"))}
     return {"workload": (f"run_{S}x{nx}x{ny}: 12x9 m attacking half at "
                          f"0.1 m, 16 opponents (seed {synth.RUN_SEED})"),
+            "roofline": roof,
             "unit": "points/s", "value": pts / (ms / 1e3), "ms_per_run": ms,
             "states_per_s": S / (ms / 1e3),
             "ms_per_run_dense": ms_dense,
@@ -703,30 +955,47 @@ def _run_points(args, dev, stream):
             "ok": bool(np.all(r["status"] == 0))}
 
 
-def _serving(dev, seconds=2.0):
+def _serving(dev, seconds=2.0, no_cpu=False):
     """The serving loop: 512 simulated matches at 60 Hz (12x9 or 9x6 fields,
     6-11 opponents, 0.05 m grid, 4 speeds, K = 32) replayed in real time
-    through a pps_server (4 streams, continuous batching, 128 MiB mask pool);
-    frame latency is arrival -> result on the host."""
+    through a pps_server (4 streams, continuous batching), once in each
+    mode: exact (every frame on its full grid, 128 MiB mask pool) and
+    proposal (the serving network ranks the map cells, the exact search
+    refines the best 256 and searches the full grid of a frame whose cells
+    hold no feasible pass).  Frame latency is arrival -> result on the
+    host.  The default mode is the one with the lower p99 at this load; the
+    proposal's agreement with the exact results of the same frames is
+    reported beside it."""
     from paper_1909_07717_gb300 import pps, synth
+    from paper_1909_07717_gb300.proposal import TOPK, agreement
     hz = 60.0
     M, F = synth.SERVING_MATCHES, int(seconds * hz)
     frames = synth.serving_matches(synth.SERVING_SEED, M, F)
     rec = pps.pack_states(frames)
     jobs = pps.match_jobs(frames)
-    desc = pps.pps_server_desc(dev.index, 4, 512, 65536, 128 << 20, 16, 50,
-                               pps.params_from_dict(synth.DEFAULT_PARAMS))
-    srv = pps.pps_server_create(desc)
-    try:
-        # warm-up: one match's frames back to back
-        pps.pps_server_replay(srv, rec[:F], jobs, 1, F, 1e4)
-        res = np.zeros(M * F, pps.RESULT_DTYPE)
-        st = pps.pps_server_replay(srv, rec, jobs, M, F, hz, res)
-    finally:
-        pps.pps_server_destroy(srv)
-    d = st.as_dict()
-    return {"workload": (f"serving_{M}x60Hz: 12x9/9x6, 6-11 opp, grid 0.05 m,"
-                         " 4 speeds, K 32 (seed 4)"),
+    weights = np.ascontiguousarray(pps.load_net_weights(pps.SERVING_WEIGHTS),
+                                   np.float32)
+    prm = pps.params_from_dict(synth.DEFAULT_PARAMS)
+    modes, results = {}, {}
+    for mode in ("exact", "proposal"):
+        if mode == "exact":
+            desc = pps.pps_server_desc(dev.index, 4, 512, 65536, 128 << 20,
+                                       16, 50, prm)
+        else:
+            desc = pps.pps_server_desc(dev.index, 4, 512, 65536, 0, 16, 50,
+                                       prm, pps.PPS_SERVE_PROPOSAL, TOPK,
+                                       weights.ctypes.data)
+        srv = pps.pps_server_create(desc)
+        try:
+            # warm-up: one match's frames back to back
+            pps.pps_server_replay(srv, rec[:F], jobs, 1, F, 1e4)
+            res = np.zeros(M * F, pps.RESULT_DTYPE)
+            st = pps.pps_server_replay(srv, rec, jobs, M, F, hz, res)
+        finally:
+            pps.pps_server_destroy(srv)
+        d = st.as_dict()
+        results[mode] = res
+        modes[mode] = {
             "frames": int(d["completed"]), "p50_us": d["p50_us"],
             "p99_us": d["p99_us"], "max_us": d["max_us"],
             "mean_us": d["mean_us"], "states_per_s": d["states_per_s"],
@@ -734,6 +1003,39 @@ def _serving(dev, seconds=2.0):
             "queue_p50_us": float(np.percentile(res["queue_ns"], 50) / 1e3),
             "queue_p99_us": float(np.percentile(res["queue_ns"], 99) / 1e3),
             "ok": bool(np.all(res["status"] == 0))}
+    ok = agreement(results["proposal"]["best"], results["exact"]["best"])
+    modes["proposal"]["agree_2pct"] = float(ok.mean())
+    modes["proposal"]["topk"] = TOPK
+    default = min(modes, key=lambda m: modes[m]["p99_us"])
+    out = {"workload": (f"serving_{M}x60Hz: 12x9/9x6, 6-11 opp, grid 0.05 m,"
+                        " 4 speeds, K 32 (seed 4)"),
+           "default_mode": default, "modes": modes}
+    out.update({k: modes[default][k] for k in
+                ("frames", "p50_us", "p99_us", "max_us", "mean_us",
+                 "states_per_s", "mean_batch", "ok")})
+    if not no_cpu:
+        # the oracle's full-grid search of a sample of the frames, each on
+        # its own grid, on all host cores
+        import oracle
+        flat = {k: v for k, v in frames.items() if isinstance(v, np.ndarray)}
+        pick = list(range(0, M * F, (M * F) // 8))[:8]
+        t0 = time.perf_counter()
+        for i in pick:
+            sub = synth.take(flat, [i])
+            g = pps.pps_grid_from_field(float(flat["field_len"][i]),
+                                        float(flat["field_wid"][i]),
+                                        float(flat["spacing"][i]))
+            gs = (float(np.float32(g.spacing)), g.nx, g.ny, float(g.x0),
+                  float(g.y0))
+            oracle.search(sub, gs, [float(x) for x in
+                                    flat["speeds"][i][:int(flat["n_speeds"][i])]],
+                          synth.DEFAULT_PARAMS)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": len(pick) / dt, "unit": "frames/s",
+                               "cores": oracle.max_threads(), "kind": "oracle",
+                               "sample": f"{len(pick)} frames of the replay, "
+                                         f"full grids; {dt:.1f} s wall"}
+    return out
 
 
 def main():

@@ -369,6 +369,15 @@ pps_status pps_plan_groups(const pps_plan* plan, pps_plan_group* out, int cap,
 
 typedef struct pps_server pps_server;
 
+/* Serving modes (pps_server_desc.mode). */
+#define PPS_SERVE_EXACT 0    /* every frame on its full grid (pps_search) */
+#define PPS_SERVE_PROPOSAL 1 /* every frame through the learned proposal
+                                (pps_propose_jobs with the fallback): the
+                                network ranks the map cells, the exact search
+                                refines the topk best and searches the full
+                                grid of a frame whose cells hold no feasible
+                                pass; best records only (no masks) */
+
 typedef struct pps_server_desc {
     int32_t device;
     int32_t n_streams;        /* batches in flight at once, 1..8 */
@@ -376,12 +385,21 @@ typedef struct pps_server_desc {
     int32_t max_queue;        /* pending requests before submit refuses
                                  (PPS_ENOMEM), >= max_batch */
     size_t pool_bytes;        /* device memory for masks of in-flight
-                                 requests (admission budget); 0 = masks off */
+                                 requests (admission budget); 0 = masks off
+                                 (and always off in the proposal mode) */
     int32_t max_opp;          /* most opponents of any request (<= 16) */
     int32_t max_wait_us;      /* with a launch already in flight, gather
                                  queued requests for up to this long before
                                  launching them (0 = launch at once) */
     pps_params params;        /* value-function parameters of every search */
+    int32_t mode;             /* PPS_SERVE_EXACT or PPS_SERVE_PROPOSAL */
+    int32_t topk;             /* proposal: map cells refined per frame,
+                                 1..2806 */
+    const float* net_weights; /* proposal: PPS_NET_PARAMS floats (host,
+                                 copied at creation; one network per stream,
+                                 its activations sized for max_batch frames);
+                                 every request's grid must then lie on the
+                                 map's cell lattice (see pps_propose_jobs) */
 } pps_server_desc;
 
 /* Per-request completion record. */
@@ -517,7 +535,8 @@ pps_status pps_net_selftest_timeout(pps_net* net, const pps_state* states,
 pps_status pps_net_set_weights(pps_net* net, const float* w);
 pps_status pps_net_get_weights(pps_net* net, float* w);
 
-/* The input map: out[n][46][61][8] bfloat16 bit patterns (device). */
+/* The input map: out[n][46][61][8] bfloat16 bit patterns (device, 16-byte
+ * aligned). */
 pps_status pps_net_raster(pps_net* net, const pps_state* states, int n,
                           uint16_t* out);
 
@@ -536,7 +555,8 @@ pps_status pps_net_forward_layers(pps_net* net, const pps_state* states,
                                   int n, float* out);
 
 /* The prediction from a given input map instead of states: map[n][46][61][8]
- * bfloat16 bit patterns (device; the layout pps_net_raster writes).
+ * bfloat16 bit patterns (device, 16-byte aligned; the layout pps_net_raster
+ * writes).
  * layers = 0 runs the tcgen05 pass of pps_net_forward, layers != 0 the
  * layer-by-layer pass of pps_net_forward_layers.  For training or checking
  * the network on maps computed elsewhere. */
@@ -568,6 +588,15 @@ pps_status pps_net_train_step(pps_net* net, const pps_state* states,
 pps_status pps_net_labels(pps_net* net, const float* point_best, int n,
                           float floor_value, float* labels);
 
+/* pps_net_labels for any fine grid on the map's cell lattice: the grid of
+ * a field of at most 12 x 9 m centred on the origin (pps_grid_from_field)
+ * at a spacing of 0.2 / m m, m = 1, 2, 4 or 8; pixel (cx, cy) then holds
+ * the m x m fine points nearest its centre (-6 + 0.2 cx, -4.5 + 0.2 cy)
+ * and a pixel without points gets floor_value.  EINVAL for another grid. */
+pps_status pps_net_labels_grid(pps_net* net, const float* point_best, int n,
+                               const pps_grid* fine, float floor_value,
+                               float* labels);
+
 /* pps_propose flags. */
 #define PPS_PROPOSE_FALLBACK 1u /* states whose top-k cells hold no feasible
                                    pass are searched on the full grid */
@@ -598,6 +627,26 @@ pps_status pps_propose(pps_ctx* ctx, pps_net* net, const pps_state* states,
                        int n, const pps_grid* fine_grid, const float* speeds,
                        int n_speeds, const pps_params* params, int topk,
                        unsigned flags, pps_best* out_best, int32_t* out_cells);
+
+/* The proposal path for states that each have their own field and grid:
+ * jobs[i] (device, one pps_job per state) gives state i's receive grid and
+ * kick speeds.  Every grid must have the same spacing `spacing` = 0.2 / m
+ * (0.2, 0.1, 0.05 or 0.025 m) and lie on the map's cell lattice (the grid
+ * pps_grid_from_field gives for a field of at most 12 x 9 m), so that map
+ * pixel (cx, cy) holds its m x m nearest points; a state whose job does not
+ * (another spacing, more than max_speeds speeds) gets PPS_STATE_INVALID.
+ * The map of a smaller field is the same 46 x 61 map (the field in its
+ * middle); pixels whose cell holds no point of the grid rank last in the
+ * top-k.  The exact refinement runs on the topk cells' points with the
+ * job's speeds; PPS_PROPOSE_FALLBACK searches a state whose cells hold no
+ * feasible pass on its full grid.  Opponent slots follow the context's
+ * max_opp (8, 12 or 16).  states, jobs, out_best and out_cells (n x topk,
+ * or NULL) are device memory; limits, streams and pruning as pps_propose. */
+pps_status pps_propose_jobs(pps_ctx* ctx, pps_net* net,
+                            const pps_state* states, const pps_job* jobs,
+                            int n, float spacing, int max_speeds,
+                            const pps_params* params, int topk, unsigned flags,
+                            pps_best* out_best, int32_t* out_cells);
 
 /* Number of SMs and the CTAs per SM the search kernel runs with (for
  * benchmarks and the autotuner); EINVAL on NULL. */

@@ -37,6 +37,7 @@ pps_status pps_ctx_cuda_error(pps_ctx* ctx, cudaError_t e, const char* what);
 void pps_ctx_scratch(pps_ctx* ctx, unsigned long long** keys, int** counts);
 int pps_ctx_max_states(const pps_ctx* ctx);
 int pps_ctx_jmax(const pps_ctx* ctx);
+int pps_ctx_max_opp(const pps_ctx* ctx);
 
 // CTAs per SM of kernel `func` at `tpb` threads and `smem` bytes of dynamic
 // shared memory on the calling thread's current device (at least 1).
@@ -54,5 +55,29 @@ struct pps_net_scratch {
 cudaError_t pps_net_predict(pps_net* net, const pps_state* states, int n,
                             cudaStream_t* st, float** scores, int** cells,
                             pps_net_scratch* scratch);
-cudaError_t pps_net_topk(pps_net* net, int n, int k, int* cells);
+// Top-k map pixels per state into cells[n][k]; with jobs (device, one per
+// state), pixels whose cell holds no point of the state's grid rank last.
+cudaError_t pps_net_topk(pps_net* net, int n, int k, int* cells,
+                         const pps_job* jobs = nullptr);
 int pps_net_max_batch(const pps_net* net);
+
+// The proposal for states with their own jobs (pps_propose_jobs), for the
+// library's own callers (the serving loop) as well: every buffer is device
+// memory; keys and counts are n entries of scratch, left zeroed.
+struct PpsProposeJobs {
+    const pps_state* states;
+    const pps_job* jobs;
+    int n;
+    int jslots;  // opponent slots: 8, 12 or 16
+    int vslots;  // speed slots: 1, 2, 4 or 8 (larger n_speeds: invalid)
+    int m;       // fine points per map pixel side (0.2 m / spacing)
+    int topk, kmax, num_sms;
+    bool fallback, prune;
+    pps_params prm;
+    pps_best* best;
+    int* out_cells;  // n x topk, or null (the network's own buffer)
+    unsigned long long* keys;
+    int* counts;
+};
+cudaError_t pps_propose_jobs_enqueue(pps_net* net, const PpsProposeJobs& p,
+                                     cudaStream_t st);

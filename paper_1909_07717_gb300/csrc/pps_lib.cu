@@ -199,6 +199,7 @@ void pps_ctx_scratch(pps_ctx* ctx, unsigned long long** keys, int** counts) {
 }
 int pps_ctx_max_states(const pps_ctx* ctx) { return ctx->max_states; }
 int pps_ctx_jmax(const pps_ctx* ctx) { return ctx->jmax; }
+int pps_ctx_max_opp(const pps_ctx* ctx) { return ctx->max_opp; }
 
 pps_status pps_ctx_alloc(pps_ctx* ctx, void** p, size_t bytes,
                          const char* what) {

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -95,12 +96,11 @@ cudaError_t load_input(pps_net* nt, const pps_state* states,
                                                       nt->a0);
         return cudaGetLastError();
     }
-    cudaError_t e = cudaMemsetAsync(nt->a0, 0, sizeof(__nv_bfloat16) * P * C0, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpy2DAsync(nt->a0, C0 * sizeof(uint16_t), map,
-                              8 * sizeof(uint16_t), 8 * sizeof(uint16_t), P,
-                              cudaMemcpyDeviceToDevice, st);
-    return e;
+    if ((reinterpret_cast<uintptr_t>(map) & 15) != 0)
+        return cudaErrorMisalignedAddress;  // maps are read 16 bytes a pixel
+    widen_map_kernel<<<blocks(P, 256), 256, 0, st>>>(
+        reinterpret_cast<const uint4*>(map), P, reinterpret_cast<uint4*>(nt->a0));
+    return cudaGetLastError();
 }
 
 // Forward pass of the map in nt->a0 into nt->out.  keep: layer by layer on
@@ -230,14 +230,16 @@ cudaError_t pps_net_predict(pps_net* nt, const pps_state* states, int n,
 
 int pps_net_max_batch(const pps_net* nt) { return nt->max_batch; }
 
-cudaError_t pps_net_topk(pps_net* nt, int n, int k, int* cells) {
+cudaError_t pps_net_topk(pps_net* nt, int n, int k, int* cells,
+                         const pps_job* jobs) {
     int p2 = 1;
     while (p2 < k) p2 <<= 1;
     const size_t smem = sizeof(unsigned long long) * (size_t)(NPIX + p2);
     cudaError_t e = cudaFuncSetAttribute(
         topk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    topk_kernel<<<n, kTopkThreads, smem, nt->stream>>>(nt->out, k, p2, cells);
+    topk_kernel<<<n, kTopkThreads, smem, nt->stream>>>(nt->out, k, p2, cells,
+                                                       jobs);
     return cudaGetLastError();
 }
 
@@ -423,11 +425,11 @@ extern "C" pps_status pps_net_raster(pps_net* nt, const pps_state* states,
     const long long P = (long long)n * NPIX;
     raster_kernel<<<blocks(P, 128), 128, 0, nt->stream>>>(states, n, nt->cfg,
                                                           nt->a0);
+    if ((reinterpret_cast<uintptr_t>(out) & 15) != 0)
+        return fail(PPS_EINVAL, "pps_net_raster: out must be 16-byte aligned");
+    narrow_map_kernel<<<blocks(P, 256), 256, 0, nt->stream>>>(
+        reinterpret_cast<const uint4*>(nt->a0), P, reinterpret_cast<uint4*>(out));
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess)
-        e = cudaMemcpy2DAsync(out, 8 * sizeof(uint16_t), nt->a0,
-                              C0 * sizeof(uint16_t), 8 * sizeof(uint16_t), P,
-                              cudaMemcpyDeviceToDevice, nt->stream);
     return e == cudaSuccess ? PPS_OK : fail(PPS_ECUDA, "pps_net_raster", e);
 }
 
@@ -461,7 +463,9 @@ extern "C" pps_status pps_net_forward_layers(pps_net* nt,
 
 extern "C" pps_status pps_net_forward_map(pps_net* nt, const uint16_t* map,
                                           int n, int layers, float* out) {
-    if (!map) return PPS_EINVAL;
+    if (!map || (reinterpret_cast<uintptr_t>(map) & 15) != 0)
+        return fail(PPS_EINVAL, "pps_net_forward_map: map must be a 16-byte "
+                                "aligned device pointer");
     return forward_to(nt, nullptr, n, out, layers != 0, "pps_net_forward_map",
                       map);
 }
@@ -506,7 +510,9 @@ extern "C" pps_status pps_net_grad(pps_net* nt, const pps_state* states,
 extern "C" pps_status pps_net_grad_map(pps_net* nt, const uint16_t* map,
                                        const float* labels, int n,
                                        float* grads, float* loss) {
-    if (!map) return PPS_EINVAL;
+    if (!map || (reinterpret_cast<uintptr_t>(map) & 15) != 0)
+        return fail(PPS_EINVAL, "pps_net_grad_map: map must be a 16-byte "
+                                "aligned device pointer");
     return grad_of(nt, nullptr, map, labels, n, grads, loss,
                    "pps_net_grad_map");
 }
@@ -541,14 +547,28 @@ extern "C" pps_status pps_net_train_step(pps_net* nt, const pps_state* states,
     return e == cudaSuccess ? PPS_OK : fail(PPS_ECUDA, "pps_net_train_step", e);
 }
 
-extern "C" pps_status pps_net_labels(pps_net* nt, const float* point_best,
-                                     int n, float floor_value, float* labels) {
+extern "C" pps_status pps_net_labels_grid(pps_net* nt,
+                                          const float* point_best, int n,
+                                          const pps_grid* fine,
+                                          float floor_value, float* labels) {
     pps_status s = check_batch(nt, point_best, n);
     if (s != PPS_OK) return s;
-    if (!labels || !std::isfinite(floor_value)) return PPS_EINVAL;
+    if (!labels || !fine || !std::isfinite(floor_value)) return PPS_EINVAL;
+    const CellLattice cl = cell_lattice(*fine);
+    if (!cl.ok)
+        return fail(PPS_EINVAL, "pps_net_labels_grid: the grid is not on the "
+                                "map's cell lattice");
     cudaSetDevice(nt->device);
     cell_label_kernel<<<blocks((long long)n * NPIX, 256), 256, 0, nt->stream>>>(
-        point_best, n, 481, 361, floor_value, labels);
+        point_best, n, fine->nx, fine->ny, cl.m, cl.ox, cl.oy, floor_value,
+        labels);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PPS_OK : fail(PPS_ECUDA, "pps_net_labels", e);
+}
+
+extern "C" pps_status pps_net_labels(pps_net* nt, const float* point_best,
+                                     int n, float floor_value, float* labels) {
+    pps_grid fine;
+    pps_grid_from_field(12.f, 9.f, 0.025f, &fine);
+    return pps_net_labels_grid(nt, point_best, n, &fine, floor_value, labels);
 }

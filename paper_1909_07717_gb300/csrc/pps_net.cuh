@@ -16,6 +16,7 @@
 #include <stdint.h>
 
 #include "pps.h"
+#include "pps_cells.cuh"
 #include "pps_search.cuh"
 
 namespace pps {
@@ -194,6 +195,24 @@ __global__ void __launch_bounds__(128, 8)
     uint4* op = reinterpret_cast<uint4*>(out + i * C0);
     op[0] = lo;
     op[1] = hi;
+}
+
+// Input maps between the caller's 8-channel layout and the kernels'
+// 16-channel rows (channels 8..15 zero): one thread per pixel, 16 bytes in,
+// 32 out (or 32 in, 16 out).
+__global__ void widen_map_kernel(const uint4* __restrict__ in8, long long n_pix,
+                                 uint4* __restrict__ out16) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_pix) return;
+    out16[2 * i] = in8[i];
+    out16[2 * i + 1] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+__global__ void narrow_map_kernel(const uint4* __restrict__ in16,
+                                  long long n_pix, uint4* __restrict__ out8) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_pix) return;
+    out8[i] = in16[2 * i];
 }
 
 // --------------------------------------------------------- convolution
@@ -488,26 +507,27 @@ __global__ void cast_kernel(const float* __restrict__ w,
 }
 
 // Labels: per map pixel, the best exact score of the fine grid points of
-// its cell (the 8 x 8 fine points nearest the pixel centre), floored.
+// its cell (cell_lattice), floored; cells without points get the floor.
 __global__ void cell_label_kernel(const float* __restrict__ point_best,
-                                  int n, int fnx, int fny, float floor_v,
+                                  int n, int fnx, int fny, int m, int ox,
+                                  int oy, float floor_v,
                                   float* __restrict__ labels) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)n * NPIX) return;
     const int s = (int)(i / NPIX), q = (int)(i - (long long)s * NPIX);
     const int cy = q / W, cx = q - cy * W;
     const float* pb = point_best + (long long)s * fnx * fny;
-    float m = floor_v;
-    for (int dy = 0; dy < 8; ++dy) {
-        const int fy = 8 * cy - 4 + dy;
+    float best = floor_v;
+    for (int dy = 0; dy < m; ++dy) {
+        const int fy = m * cy + oy + dy;
         if (fy < 0 || fy >= fny) continue;
-        for (int dx = 0; dx < 8; ++dx) {
-            const int fx = 8 * cx - 4 + dx;
+        for (int dx = 0; dx < m; ++dx) {
+            const int fx = m * cx + ox + dx;
             if (fx < 0 || fx >= fnx) continue;
-            m = fmaxf(m, pb[(long long)fy * fnx + fx]);
+            best = fmaxf(best, pb[(long long)fy * fnx + fx]);
         }
     }
-    labels[i] = m;
+    labels[i] = best;
 }
 
 // Top-k map pixels of every state (one CTA per state), best first; equal
@@ -523,9 +543,13 @@ __device__ __forceinline__ unsigned long long topk_key(const float* sc, int i) {
     return ((unsigned long long)u << 32) | (uint32_t)(~(uint32_t)i);
 }
 
+// With jobs, a pixel whose cell holds no point of the state's grid (a field
+// smaller than the map's 12 x 9 m) ranks below every pixel that does: its
+// key keeps only ~pixel, so it is taken only when k exceeds the cells that
+// hold points.
 __global__ void __launch_bounds__(kTopkThreads)
     topk_kernel(const float* __restrict__ scores, int k, int p2,
-                int* __restrict__ cells) {
+                int* __restrict__ cells, const pps_job* __restrict__ jobs) {
     extern __shared__ __align__(16) unsigned long long tk[];
     unsigned long long* key = tk;         // NPIX keys
     unsigned long long* sel = tk + NPIX;  // p2 selected keys
@@ -536,7 +560,18 @@ __global__ void __launch_bounds__(kTopkThreads)
     const int s = blockIdx.x, t = threadIdx.x;
     const int lane = t & 31, warp = t >> 5;
     const float* sc = scores + (long long)s * NPIX;
-    for (int i = t; i < NPIX; i += blockDim.x) key[i] = topk_key(sc, i);
+    if (jobs) {
+        const pps_grid g = jobs[s].grid;
+        const CellLattice cl = cell_lattice(g);
+        for (int i = t; i < NPIX; i += blockDim.x) {
+            const int cy = i / W, cx = i - cy * W;
+            key[i] = cl.ok && cell_on_grid(cl, g, cx, cy)
+                         ? topk_key(sc, i)
+                         : (unsigned long long)(~(uint32_t)i);
+        }
+    } else {
+        for (int i = t; i < NPIX; i += blockDim.x) key[i] = topk_key(sc, i);
+    }
     if (t == 0) {
         s_prefix = 0ull;
         s_need = k;

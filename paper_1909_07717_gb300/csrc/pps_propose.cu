@@ -11,6 +11,7 @@
 
 #include "pps.h"
 #include "pps_internal.h"
+#include "pps_cells.cuh"
 #include "pps_search.cuh"
 
 char* pps_thread_error_buffer();
@@ -157,7 +158,311 @@ cudaError_t run_v(const pps::SearchArgs& a, const int* cells, int topk,
 
 bool finite_pos(float x) { return std::isfinite(x) && x > 0.f; }
 
+// ------------------------------------------------ per-state fields and grids
+// The proposal for states that each carry a job (grid and speeds), all
+// grids of one spacing 0.2 / m on the map's cell lattice (cell_lattice):
+// fields up to 12 x 9 m.  A state's work is its topk cells' m x m fine
+// points, cut into items of 32 consecutive (cell rank, point) slots, so a
+// cell of 64 points is two items and a cell of 16 points half of one.
+// Items run rank-major: item q of every state before item q + 1 of any.
+using pps::net::CellLattice;
+using pps::net::cell_lattice;
+
+struct JobsArgs {
+    const pps_state* states;
+    const pps_job* jobs;
+    int n, kmax, m, vmax, topk, items_per_state;
+    pps_params prm;
+    const int* cells;  // n x topk map pixels, best first
+    pps_best* best;
+    unsigned long long* keys;
+    int* counts;
+    const int* list;    // fallback: the states to search on their full grid
+    const int* list_n;
+};
+
+// A job's grid, speeds and cell lattice; valid = the state's grid has the
+// call's spacing and lies on the lattice.
+struct JobCells {
+    pps::ItemGrid gr;
+    int nx, ny, P, ox, oy;
+    float sp[PPS_MAX_SPEEDS], sp2[PPS_MAX_SPEEDS];
+    bool ok;
+};
+
+__device__ __forceinline__ void load_job_cells(const pps_job& j, int m,
+                                               int vmax, JobCells& c) {
+    const CellLattice cl = cell_lattice(j.grid);
+    c.gr.g = j.grid.spacing;
+    c.gr.x0 = j.grid.x0;
+    c.gr.y0 = j.grid.y0;
+    c.gr.V = j.n_speeds;
+    c.nx = j.grid.nx;
+    c.ny = j.grid.ny;
+    c.P = c.nx * c.ny;
+    c.ox = cl.ox;
+    c.oy = cl.oy;
+    c.ok = cl.ok && cl.m == m && j.n_speeds >= 1 && j.n_speeds <= vmax;
+    const int nv = c.ok ? j.n_speeds : 1;
+#pragma unroll
+    for (int v = 0; v < PPS_MAX_SPEEDS; ++v) {
+        const float x = j.speeds[v < nv ? v : nv - 1];
+        c.sp[v] = x;
+        c.sp2[v] = __fmul_rn(x, x);
+    }
+}
+
+template <int JMAX, int VMAX>
+__device__ __forceinline__ void reduce_item(const JobsArgs& a, int s,
+                                            int lane, bool active, int p,
+                                            int P, int V,
+                                            const pps::PointResult<JMAX, VMAX>& r) {
+    int cnt = 0;
+    unsigned long long key = 0ull;
+#pragma unroll
+    for (int v = 0; v < VMAX; ++v) {
+        const bool f = active && v < V && r.feas[v];
+        cnt += f;
+        if (f) {
+            const uint32_t idx = (uint32_t)(v * P + p);
+            const unsigned long long k2 =
+                ((unsigned long long)pps::order_bits(r.score[v]) << 32) |
+                (unsigned long long)(~idx);
+            key = k2 > key ? k2 : key;
+        }
+    }
+    key = pps::warp_max_u64(key);
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if (lane == 0) {
+        if (key) atomicMax(a.keys + s, key);
+        if (cnt) atomicAdd(a.counts + s, cnt);
+    }
+}
+
+template <int JMAX, int VMAX>
+__global__ void __launch_bounds__(pps::search_tpb<JMAX, VMAX>(), 1)
+    refine_jobs_kernel(const JobsArgs a, bool prune) {
+    constexpr int kWarps = pps::search_tpb<JMAX, VMAX>() / 32;
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * kWarps;
+    const long long gw = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const long long n_items = (long long)a.n * a.items_per_state;
+    const int m2 = a.m * a.m;
+    for (long long item = gw; item < n_items; item += warps) {
+        const int q = (int)(item / a.n);
+        const int s = (int)(item - (long long)q * a.n);
+        JobCells jc;
+        load_job_cells(a.jobs[s], a.m, a.vmax, jc);
+        const int slot = q * 32 + lane;
+        const int rank = slot / m2, within = slot - rank * m2;
+        bool active = jc.ok && rank < a.topk;
+        int ix = 0, iy = 0;
+        if (active) {
+            const int cell = a.cells[(long long)s * a.topk + rank];
+            const int cy = cell / kMapW, cx = cell - cy * kMapW;
+            const int wy = within / a.m;
+            ix = a.m * cx + jc.ox + (within - wy * a.m);
+            iy = a.m * cy + jc.oy + wy;
+            active = ix >= 0 && ix < jc.nx && iy >= 0 && iy < jc.ny;
+        }
+        if (__ballot_sync(0xffffffffu, active) == 0u) continue;
+        if (!active) ix = iy = 0;
+        const pps_state& st = a.states[s];
+        const pps::StateK sk = pps::derive_state(st, a.prm, JMAX, a.kmax);
+        pps::OppRegs<JMAX> o;
+        pps::load_opps<JMAX>(st, sk, o);
+        if (prune) {
+            const unsigned long long cur =
+                __shfl_sync(0xffffffffu, __ldcg(a.keys + s), 0);
+            if (cur) {
+                const float b =
+                    active ? pps::score_bound<JMAX, VMAX>(a.prm, jc.gr, jc.sp,
+                                                          jc.sp2, sk, o, ix, iy)
+                           : -CUDART_INF_F;
+                const uint32_t bk =
+                    __reduce_max_sync(0xffffffffu, pps::order_bits(b));
+                if (bk < (uint32_t)(cur >> 32)) continue;
+            }
+        }
+        pps::PointResult<JMAX, VMAX> res;
+        pps::eval_point<JMAX, VMAX, false>(a.prm, jc.gr, jc.sp, jc.sp2, st, sk,
+                                           o, ix, iy, nullptr, res);
+        reduce_item<JMAX, VMAX>(a, s, lane, active, iy * jc.nx + ix, jc.P,
+                                jc.gr.V, res);
+    }
+}
+
+// Fallback: the listed states on their full grids.  A CTA takes a listed
+// state at a time and its warps share that state's 32-point items.
+template <int JMAX, int VMAX>
+__global__ void __launch_bounds__(pps::search_tpb<JMAX, VMAX>(), 1)
+    fallback_jobs_kernel(const JobsArgs a) {
+    constexpr int kWarps = pps::search_tpb<JMAX, VMAX>() / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nl = *a.list_n;
+    for (int li = blockIdx.x; li < nl; li += gridDim.x) {
+        const int s = a.list[li];
+        JobCells jc;
+        load_job_cells(a.jobs[s], a.m, a.vmax, jc);
+        if (!jc.ok) continue;
+        const pps_state& st = a.states[s];
+        const pps::StateK sk = pps::derive_state(st, a.prm, JMAX, a.kmax);
+        pps::OppRegs<JMAX> o;
+        pps::load_opps<JMAX>(st, sk, o);
+        const int words = (jc.P + 31) / 32;
+        for (int chunk = warp; chunk < words; chunk += kWarps) {
+            const int p = chunk * 32 + lane;
+            const bool active = p < jc.P;
+            const int pc = active ? p : jc.P - 1;
+            const int iy = pc / jc.nx, ix = pc - iy * jc.nx;
+            pps::PointResult<JMAX, VMAX> res;
+            pps::eval_point<JMAX, VMAX, false>(a.prm, jc.gr, jc.sp, jc.sp2, st,
+                                               sk, o, ix, iy, nullptr, res);
+            reduce_item<JMAX, VMAX>(a, s, lane, active, p, jc.P, jc.gr.V, res);
+        }
+    }
+}
+
+// Per state (or, with a list, per listed state): decode the key,
+// re-evaluate the winner for its margin and check that the score
+// reproduces; clears the state's key and count for the next call.  A state
+// whose job does not fit the call (another spacing, off the lattice, bad
+// speeds) is invalid.
+template <int JMAX, int VMAX>
+__global__ void __launch_bounds__(128) jobs_finalize_kernel(const JobsArgs a,
+                                                            bool listed) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (listed ? *a.list_n : a.n)) return;
+    const int s = listed ? a.list[i] : i;
+    const pps_state& st = a.states[s];
+    JobCells jc;
+    load_job_cells(a.jobs[s], a.m, a.vmax, jc);
+    pps::StateK sk = pps::derive_state(st, a.prm, JMAX, a.kmax);
+    sk.valid = sk.valid && jc.ok;
+    pps_best b;
+    b.n_feasible = a.counts[s];
+    b.status = sk.valid ? PPS_STATE_OK : PPS_STATE_INVALID;
+    const unsigned long long key = a.keys[s];
+    if (!sk.valid || key == 0ull) {
+        b.idx = sk.valid ? -1 : -2;
+        b.ix = b.iy = b.speed_idx = -1;
+        b.score = -CUDART_INF_F;
+        b.margin = -CUDART_INF_F;
+        b.n_feasible = sk.valid ? b.n_feasible : 0;
+    } else {
+        const uint32_t idx = ~(uint32_t)(key & 0xffffffffull);
+        const int v = (int)(idx / (uint32_t)jc.P);
+        const int p = (int)(idx - (uint32_t)v * (uint32_t)jc.P);
+        b.idx = (int)idx;
+        b.speed_idx = v;
+        b.iy = p / jc.nx;
+        b.ix = p - b.iy * jc.nx;
+        b.score = pps::order_bits_inv((uint32_t)(key >> 32));
+        pps::OppRegs<JMAX> o;
+        pps::load_opps<JMAX>(st, sk, o);
+        pps::PointResult<JMAX, VMAX> r;
+        pps::eval_point<JMAX, VMAX, false>(a.prm, jc.gr, jc.sp, jc.sp2, st, sk,
+                                           o, b.ix, b.iy, nullptr, r);
+        float mg = 0.f, sc = 0.f;
+        bool f = false;
+#pragma unroll
+        for (int w = 0; w < VMAX; ++w)
+            if (w == v) {
+                mg = r.margin[w];
+                sc = r.score[w];
+                f = r.feas[w];
+            }
+        b.margin = mg;
+        if (!f || __float_as_uint(sc) != __float_as_uint(b.score))
+            b.status |= PPS_STATE_INCONSISTENT;
+    }
+    a.best[s] = b;
+    a.keys[s] = 0ull;
+    a.counts[s] = 0;
+}
+
+template <int J, int V>
+cudaError_t run_jobs(JobsArgs a, bool fallback, bool prune,
+                     const pps_net_scratch& ns, int num_sms, cudaStream_t st) {
+    constexpr int tpb = pps::search_tpb<J, V>();
+    cudaError_t e = cudaMemsetAsync(a.keys, 0, sizeof(unsigned long long) * a.n, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.counts, 0, sizeof(int) * a.n, st);
+    if (e != cudaSuccess) return e;
+    const long long cap =
+        (long long)num_sms *
+        pps_occupancy((const void*)refine_jobs_kernel<J, V>, tpb, 0);
+    const long long items = (long long)a.n * a.items_per_state;
+    long long grid = (items + tpb / 32 - 1) / (tpb / 32);
+    if (grid > cap) grid = cap;
+    refine_jobs_kernel<J, V><<<(unsigned)grid, tpb, 0, st>>>(a, prune);
+    jobs_finalize_kernel<J, V><<<(a.n + 127) / 128, 128, 0, st>>>(a, false);
+    if (!fallback) return cudaGetLastError();
+    e = cudaMemsetAsync(ns.list_n, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    fallback_list_kernel<<<(a.n + 127) / 128, 128, 0, st>>>(
+        a.best, a.n, ns.skip, ns.list, ns.list_n);
+    a.list = ns.list;
+    a.list_n = ns.list_n;
+    // the finalize left every key and count at zero
+    fallback_jobs_kernel<J, V><<<(unsigned)num_sms, tpb, 0, st>>>(a);
+    jobs_finalize_kernel<J, V><<<(a.n + 127) / 128, 128, 0, st>>>(a, true);
+    return cudaGetLastError();
+}
+
+template <int J>
+cudaError_t run_jobs_v(const JobsArgs& a, int vslots, bool fb, bool pr,
+                       const pps_net_scratch& ns, int sms, cudaStream_t st) {
+    if (vslots <= 1) return run_jobs<J, 1>(a, fb, pr, ns, sms, st);
+    if (vslots <= 2) return run_jobs<J, 2>(a, fb, pr, ns, sms, st);
+    if (vslots <= 4) return run_jobs<J, 4>(a, fb, pr, ns, sms, st);
+    return run_jobs<J, 8>(a, fb, pr, ns, sms, st);
+}
+
 }  // namespace
+
+// Library-internal: the per-job proposal of n states (device states and
+// jobs) on the network's stream, which must be `st` or ordered before it by
+// the caller: prediction, top-k (off-grid cells last), refinement and the
+// optional fallback.
+cudaError_t pps_propose_jobs_enqueue(pps_net* net, const PpsProposeJobs& p,
+                                     cudaStream_t st) {
+    cudaStream_t nst = nullptr;
+    float* scores = nullptr;
+    int* cells = nullptr;
+    pps_net_scratch ns{};
+    cudaError_t e = pps_net_predict(net, p.states, p.n, &nst, &scores, &cells, &ns);
+    if (p.out_cells) cells = p.out_cells;
+    if (e == cudaSuccess) e = pps_net_topk(net, p.n, p.topk, cells, p.jobs);
+    if (e == cudaSuccess && nst != st) {
+        cudaEvent_t ev;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev, nst);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
+        cudaEventDestroy(ev);
+    }
+    if (e != cudaSuccess) return e;
+    JobsArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.states = p.states;
+    a.jobs = p.jobs;
+    a.n = p.n;
+    a.kmax = p.kmax;
+    a.m = p.m;
+    a.vmax = p.vslots;
+    a.topk = p.topk;
+    a.items_per_state = (p.topk * p.m * p.m + 31) / 32;
+    a.prm = p.prm;
+    a.cells = cells;
+    a.best = p.best;
+    a.keys = p.keys;
+    a.counts = p.counts;
+    const bool prune = p.prune && p.prm.w_angle >= 0.f && p.prm.w_margin >= 0.f;
+    if (p.jslots <= 8)
+        return run_jobs_v<8>(a, p.vslots, p.fallback, prune, ns, p.num_sms, st);
+    if (p.jslots <= 12)
+        return run_jobs_v<12>(a, p.vslots, p.fallback, prune, ns, p.num_sms, st);
+    return run_jobs_v<16>(a, p.vslots, p.fallback, prune, ns, p.num_sms, st);
+}
 
 extern "C" pps_status pps_propose(pps_ctx* ctx, pps_net* net,
                                   const pps_state* states, int n,
@@ -247,5 +552,70 @@ extern "C" pps_status pps_propose(pps_ctx* ctx, pps_net* net,
             ? run_v<8>(a, cells, topk, fb, prune, ns, sms, st)
             : run_v<16>(a, cells, topk, fb, prune, ns, sms, st);
     if (e != cudaSuccess) return pps_ctx_cuda_error(ctx, e, "pps_propose: refine");
+    return PPS_OK;
+}
+
+extern "C" pps_status pps_propose_jobs(pps_ctx* ctx, pps_net* net,
+                                       const pps_state* states,
+                                       const pps_job* jobs, int n,
+                                       float spacing, int max_speeds,
+                                       const pps_params* params, int topk,
+                                       unsigned flags, pps_best* out_best,
+                                       int32_t* out_cells) {
+    PPS_RANGE("pps_propose_jobs");
+    if (!ctx || !net) return PPS_EINVAL;
+    if (pps_ctx_failed(ctx))
+        return pps_ctx_error(ctx, PPS_ECUDA, "context failed earlier; call pps_reset");
+    if (!states || !jobs || !out_best || n < 1 || n > pps_ctx_max_states(ctx) ||
+        n > pps_net_max_batch(net))
+        return pps_ctx_error(ctx, PPS_EINVAL,
+                             "pps_propose_jobs: n outside 1..min(max_states, "
+                             "max_batch), or a NULL buffer");
+    pps_grid probe{spacing, 1, 1, -6.f, -4.5f};
+    const CellLattice cl = cell_lattice(probe);
+    if (!cl.ok)
+        return pps_ctx_error(ctx, PPS_EINVAL,
+                             "pps_propose_jobs: spacing must be 0.2, 0.1, "
+                             "0.05 or 0.025 m");
+    if (max_speeds < 1 || max_speeds > PPS_MAX_SPEEDS)
+        return pps_ctx_error(ctx, PPS_EINVAL, "pps_propose_jobs: max_speeds "
+                                              "outside 1..8");
+    if (topk < 1 || topk > kMapPix)
+        return pps_ctx_error(ctx, PPS_EINVAL, "pps_propose_jobs: topk outside 1..2806");
+    if (flags & ~(PPS_PROPOSE_FALLBACK | PPS_PROPOSE_NO_PRUNE))
+        return pps_ctx_error(ctx, PPS_EINVAL, "pps_propose_jobs: unknown flags");
+    pps_params prm;
+    if (params)
+        prm = *params;
+    else
+        pps_default_params(&prm);
+    const float pv[] = {prm.w_angle, prm.w_dist, prm.w_margin, prm.margin_cap,
+                        prm.tau_safe, prm.robot_radius, prm.reach_radius,
+                        prm.min_pass_dist};
+    for (float x : pv)
+        if (!std::isfinite(x))
+            return pps_ctx_error(ctx, PPS_EINVAL, "pps_propose_jobs: params must be finite");
+    cudaError_t e = cudaSetDevice(pps_ctx_device(ctx));
+    PpsProposeJobs p;
+    std::memset(&p, 0, sizeof p);
+    p.states = states;
+    p.jobs = jobs;
+    p.n = n;
+    const int mo = pps_ctx_max_opp(ctx);
+    p.jslots = mo <= 8 ? 8 : mo <= 12 ? 12 : 16;
+    p.vslots = max_speeds;
+    p.m = cl.m;
+    p.topk = topk;
+    p.kmax = pps_ctx_max_K(ctx);
+    p.fallback = flags & PPS_PROPOSE_FALLBACK;
+    p.prune = !(flags & PPS_PROPOSE_NO_PRUNE);
+    p.prm = prm;
+    p.best = out_best;
+    p.out_cells = out_cells;
+    pps_ctx_scratch(ctx, &p.keys, &p.counts);
+    p.num_sms = pps_ctx_num_sms(ctx);
+    if (e == cudaSuccess)
+        e = pps_propose_jobs_enqueue(net, p, pps_ctx_stream(ctx));
+    if (e != cudaSuccess) return pps_ctx_cuda_error(ctx, e, "pps_propose_jobs");
     return PPS_OK;
 }

@@ -31,6 +31,8 @@
 
 #include "pps.h"
 #include "pps_batch.cuh"
+#include "pps_cells.cuh"
+#include "pps_internal.h"
 
 char* pps_thread_error_buffer();
 
@@ -78,6 +80,7 @@ struct Slot {
                                            // left 0 by the finalize kernels
     uint32_t* d_mask = nullptr;
     uint32_t* h_mask = nullptr;
+    pps_net* net = nullptr;  // proposal mode: this slot's network
     // this batch's sections in the packed buffer
     size_t o_states = 0, o_jobs = 0, o_bucket = 0, o_start = 0, o_moff = 0;
     bool busy = false;
@@ -121,6 +124,7 @@ void free_slot(Slot& s) {
         if (p) cudaFree(p);
     for (void* p : {(void*)s.h_in, (void*)s.h_best, (void*)s.h_mask})
         if (p) cudaFreeHost(p);
+    if (s.net) pps_net_destroy(s.net);
     if (s.done) cudaEventDestroy(s.done);
     if (s.stream) cudaStreamDestroy(s.stream);
     s = Slot();
@@ -233,11 +237,20 @@ extern "C" pps_status pps_server_create(const pps_server_desc* desc,
     if (p.robot_radius < 0.f || p.reach_radius < 0.f || p.min_pass_dist < 0.f)
         return fail(PPS_EINVAL, "pps_server_create: radii and min_pass_dist "
                                 "must be >= 0");
+    const bool proposal = desc->mode == PPS_SERVE_PROPOSAL;
+    if (desc->mode != PPS_SERVE_EXACT && !proposal)
+        return fail(PPS_EINVAL, "pps_server_create: unknown mode");
+    if (proposal && (!desc->net_weights || desc->topk < 1 ||
+                     desc->topk > PPS_NET_H * PPS_NET_W))
+        return fail(PPS_EINVAL, "pps_server_create: the proposal mode needs "
+                                "net_weights and topk in 1..2806");
     pps_server* srv = new (std::nothrow) pps_server();
     if (!srv) return PPS_ENOMEM;
     srv->d = *desc;
+    srv->d.net_weights = nullptr;  // copied into each slot's network
     srv->mask_words_per_slot =
-        (long long)(desc->pool_bytes / 4 / (size_t)desc->n_streams);
+        proposal ? 0
+                 : (long long)(desc->pool_bytes / 4 / (size_t)desc->n_streams);
     cudaError_t e = cudaSetDevice(desc->device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&srv->num_sms,
@@ -246,10 +259,18 @@ extern "C" pps_status pps_server_create(const pps_server_desc* desc,
     for (Slot& s : srv->slots)
         if (e == cudaSuccess)
             e = alloc_slot(s, desc->max_batch, srv->mask_words_per_slot);
-    if (e != cudaSuccess) {
+    pps_status ns = PPS_OK;
+    for (Slot& s : srv->slots) {
+        if (e != cudaSuccess || ns != PPS_OK || !proposal) break;
+        ns = pps_net_create(desc->device, s.stream, desc->max_batch, &s.net);
+        if (ns == PPS_OK) ns = pps_net_set_weights(s.net, desc->net_weights);
+    }
+    if (e != cudaSuccess || ns != PPS_OK) {
         cudaGetLastError();
         for (Slot& s : srv->slots) free_slot(s);
         delete srv;
+        if (ns != PPS_OK)
+            return fail(ns, "pps_server_create: the slots' networks");
         return fail(e == cudaErrorMemoryAllocation ? PPS_ENOMEM : PPS_ECUDA,
                     "pps_server_create", e);
     }
@@ -274,9 +295,57 @@ extern "C" void pps_server_destroy(pps_server* srv) {
 
 namespace {
 
-// Copy a batch in, launch its kernel-instance groups, copy the results out
-// and record the slot's event (all on the slot's stream).
+// Proposal mode: the batch's requests ordered by their grids' cell size m
+// (one pps_propose_jobs call per m), then each group enqueued.
+void order_by_cells(Slot& s) {
+    std::stable_sort(s.reqs.begin(), s.reqs.end(),
+                     [](const Request& a, const Request& b) {
+                         return pps::net::cell_lattice(a.job.grid).m <
+                                pps::net::cell_lattice(b.job.grid).m;
+                     });
+}
+
+cudaError_t launch_proposal(pps_server* srv, Slot& s, cudaStream_t st) {
+    const int n = (int)s.reqs.size();
+    int i0 = 0;
+    cudaError_t e = cudaSuccess;
+    while (i0 < n && e == cudaSuccess) {
+        const int m = pps::net::cell_lattice(s.reqs[i0].job.grid).m;
+        int i1 = i0, J = 8, V = 1;
+        while (i1 < n && pps::net::cell_lattice(s.reqs[i1].job.grid).m == m) {
+            J = std::max(J, opp_slots(s.reqs[i1].job.max_opp));
+            V = std::max(V, speed_slots(s.reqs[i1].job.n_speeds));
+            ++i1;
+        }
+        PpsProposeJobs p;
+        std::memset(&p, 0, sizeof p);
+        p.states = (const pps_state*)(s.d_in + s.o_states) + i0;
+        p.jobs = (const pps_job*)(s.d_in + s.o_jobs) + i0;
+        p.n = i1 - i0;
+        p.jslots = J;
+        p.vslots = V;
+        p.m = m;
+        p.topk = srv->d.topk;
+        p.kmax = PPS_MAX_K;
+        p.num_sms = srv->num_sms;
+        p.fallback = true;
+        p.prune = true;
+        p.prm = srv->d.params;
+        p.best = s.d_best + i0;
+        p.keys = s.d_keys + i0;
+        p.counts = s.d_counts + i0;
+        e = pps_propose_jobs_enqueue(s.net, p, st);
+        i0 = i1;
+    }
+    return e;
+}
+
+// Copy a batch in, launch its kernel-instance groups (or, in the proposal
+// mode, its proposal calls), copy the results out and record the slot's
+// event (all on the slot's stream).
 cudaError_t launch_batch(pps_server* srv, Slot& s) {
+    const bool proposal = srv->d.mode == PPS_SERVE_PROPOSAL;
+    if (proposal) order_by_cells(s);
     const int n = (int)s.reqs.size();
     const size_t total = layout(n, &s.o_states, &s.o_jobs, &s.o_bucket,
                                 &s.o_start, &s.o_moff);
@@ -328,8 +397,9 @@ cudaError_t launch_batch(pps_server* srv, Slot& s) {
                                     cudaMemcpyHostToDevice, st);
     const bool masks = srv->mask_words_per_slot > 0;
     constexpr int kTpb = 128;  // small batches: spread the items thinly
+    if (proposal && e == cudaSuccess) e = launch_proposal(srv, s, st);
     for (const G& g : groups) {
-        if (e != cudaSuccess) break;
+        if (e != cudaSuccess || proposal) break;
         pps::BatchArgs a;
         std::memset(&a, 0, sizeof a);
         a.states = (const pps_state*)(s.d_in + s.o_states);
@@ -476,6 +546,11 @@ pps_status submit_at(pps_server* srv, const pps_state* state,
         return fail(PPS_EINVAL, "pps_server_submit: NULL argument");
     if (!job_ok(*job, srv->d.max_opp) || !state_ok(*state, *job))
         return fail(PPS_EINVAL, "pps_server_submit: bad state or job");
+    if (srv->d.mode == PPS_SERVE_PROPOSAL &&
+        !pps::net::cell_lattice(job->grid).ok)
+        return fail(PPS_EINVAL, "pps_server_submit: the proposal mode serves "
+                                "grids on the map's cell lattice (a field of "
+                                "at most 12 x 9 m at 0.2 / m m)");
     Request r;
     r.st = *state;
     r.job = *job;

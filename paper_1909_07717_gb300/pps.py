@@ -99,7 +99,13 @@ class pps_server_desc(ctypes.Structure):
     _fields_ = [("device", c_int32), ("n_streams", c_int32),
                 ("max_batch", c_int32), ("max_queue", c_int32),
                 ("pool_bytes", c_size_t), ("max_opp", c_int32),
-                ("max_wait_us", c_int32), ("params", pps_params)]
+                ("max_wait_us", c_int32), ("params", pps_params),
+                ("mode", c_int32), ("topk", c_int32),
+                ("net_weights", c_void_p)]
+
+
+PPS_SERVE_EXACT = 0
+PPS_SERVE_PROPOSAL = 1
 
 
 class pps_server_result(ctypes.Structure):
@@ -207,7 +213,8 @@ EXPORTS = ("pps_abi_version", "pps_status_string", "pps_last_error",
            "pps_net_get_weights", "pps_net_raster", "pps_net_forward_layers",
            "pps_net_forward", "pps_net_forward_map", "pps_net_grad",
            "pps_net_grad_map", "pps_net_train_step",
-           "pps_net_labels", "pps_propose", "pps_dpps_default_params",
+           "pps_net_labels", "pps_net_labels_grid", "pps_propose",
+           "pps_propose_jobs", "pps_dpps_default_params",
            "pps_dpps_mask_words", "pps_dpps_search", "pps_pass_powers",
            "pps_shoot", "pps_run_default_params", "pps_run_grid",
            "pps_run_points")
@@ -318,6 +325,14 @@ def lib():
                                              P(ctypes.c_float)]
             L.pps_net_labels.argtypes = [c_void_p, c_void_p, ctypes.c_int,
                                          ctypes.c_float, c_void_p]
+            L.pps_net_labels_grid.argtypes = [c_void_p, c_void_p, ctypes.c_int,
+                                              P(pps_grid), ctypes.c_float,
+                                              c_void_p]
+            L.pps_propose_jobs.argtypes = [c_void_p, c_void_p, c_void_p,
+                                           c_void_p, ctypes.c_int, c_float,
+                                           ctypes.c_int, P(pps_params),
+                                           ctypes.c_int, ctypes.c_uint,
+                                           c_void_p, c_void_p]
             L.pps_propose.argtypes = [c_void_p, c_void_p, c_void_p,
                                       ctypes.c_int, P(pps_grid), c_void_p,
                                       ctypes.c_int, P(pps_params),
@@ -586,6 +601,22 @@ def pps_net_labels(net, point_best, n, floor_value, labels) -> int:
                                        labels))
 
 
+def pps_net_labels_grid(net, point_best, n, fine_grid, floor_value,
+                        labels) -> int:
+    return _check(lib().pps_net_labels_grid(net, point_best, n,
+                                            ctypes.byref(fine_grid),
+                                            floor_value, labels))
+
+
+def pps_propose_jobs(ctx, net, states, jobs, n, spacing, max_speeds, params,
+                     topk, flags, out_best, out_cells=None) -> int:
+    """Device addresses for states, jobs, out_best, out_cells."""
+    return _check(lib().pps_propose_jobs(
+        ctx, net, states, jobs, n, spacing, max_speeds,
+        ctypes.byref(params) if params is not None else None, topk, flags,
+        out_best, out_cells), ctx)
+
+
 def pps_propose(ctx, net, states, n, fine_grid, speeds, params, topk, flags,
                 out_best, out_cells=None) -> int:
     """Device addresses for states, out_best, out_cells; speeds host."""
@@ -851,6 +882,27 @@ def jobs_from_batch(batch: dict):
     return jobs
 
 
+def jobs_to_bytes(jobs) -> np.ndarray:
+    """The raw bytes of a ctypes array of pps_job (for a device copy)."""
+    return np.frombuffer(bytes(jobs), np.uint8).copy()
+
+
+def field_jobs(batch: dict, spacing: float, speeds) -> "ctypes.Array":
+    """One pps_job per state of a batch: its own field's grid at `spacing`
+    (pps_grid_from_field) and the shared kick speeds."""
+    S = batch["ball"].shape[0]
+    jobs = (pps_job * S)()
+    for i in range(S):
+        jobs[i].grid = pps_grid_from_field(float(batch["field_len"][i]),
+                                           float(batch["field_wid"][i]),
+                                           spacing)
+        jobs[i].n_speeds = len(speeds)
+        for v, x in enumerate(speeds):
+            jobs[i].speeds[v] = float(x)
+        jobs[i].max_opp = int(batch["n_opp"][i])
+    return jobs
+
+
 class Plan:
     """A batched plan on a Searcher's context, with device output buffers."""
 
@@ -953,6 +1005,8 @@ WEIGHTS_DIR = os.path.join(PKG, "weights")
 # Weights trained by paper_1909_07717_gb300.train_proposal on exact labels
 # of 12 x 9 m, 8-opponent states (kick speeds 2, 3.5, 5, 6.5 m/s, K = 64).
 PROPOSAL_WEIGHTS = os.path.join(WEIGHTS_DIR, "proposal_12x9_v4_K64_J8.bin")
+# the serving workload's network: 12 x 9 and 9 x 6 m fields at 0.05 m
+SERVING_WEIGHTS = os.path.join(WEIGHTS_DIR, "proposal_serving_g0.05_K32.bin")
 _WMAGIC = b"PPSNET\x00\x01"
 
 

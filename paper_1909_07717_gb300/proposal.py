@@ -79,3 +79,71 @@ def agreement(prop: np.ndarray, exact: np.ndarray, rel=REL_TOL) -> np.ndarray:
     d = np.abs(prop["score"].astype(np.float64) - exact["score"])
     ok[both] = d[both] <= rel * np.abs(exact["score"][both].astype(np.float64))
     return ok
+
+
+# The serving workload's proposal: 12 x 9 and 9 x 6 m fields at 0.05 m,
+# 6-11 opponents, K = 32, the same four speeds.
+SERVING_SPACING = 0.05
+
+
+class JobsProposal:
+    """pps_propose_jobs on a context and network sized for ``max_states``
+    states that each carry their own field (grid on the map's lattice)."""
+
+    def __init__(self, max_states, weights, spacing=SERVING_SPACING,
+                 max_opp=16, device=0, stream=None):
+        self.searcher = pps.Searcher(max_states, max_opp=max_opp,
+                                     device=device, stream=stream)
+        self.net = pps.Net(device, stream, max_batch=max_states,
+                           weights=weights)
+        self.torch = self.searcher.torch
+        self.spacing = spacing
+        self.max_states = max_states
+
+    def jobs_to_device(self, jobs):
+        return self.torch.from_numpy(pps.jobs_to_bytes(jobs)).to(
+            self.searcher.device)
+
+    def alloc(self, n, topk=TOPK):
+        t = self.torch
+        return (t.empty(n * 32, dtype=t.uint8, device=self.searcher.device),
+                t.empty((n, topk), dtype=t.int32, device=self.searcher.device))
+
+    def run(self, states_dev, jobs_dev, n, speeds=SPEEDS, params=None,
+            topk=TOPK, fallback=True, prune=True, out=None):
+        """Enqueue the proposal search; returns (best bytes, cells)."""
+        best, cells = out if out is not None else self.alloc(n, topk)
+        prm = params if isinstance(params, pps.pps_params) else \
+            pps.params_from_dict(params)
+        pps.pps_propose_jobs(self.searcher.ctx, self.net.net,
+                             states_dev.data_ptr(), jobs_dev.data_ptr(), n,
+                             self.spacing, len(speeds), prm, topk,
+                             (pps.PPS_PROPOSE_FALLBACK if fallback else 0)
+                             | (0 if prune else pps.PPS_PROPOSE_NO_PRUNE),
+                             best.data_ptr(), cells.data_ptr())
+        return best, cells
+
+    def close(self):
+        self.net.close()
+        self.searcher.close()
+
+
+def exact_per_field(searcher, batch, spacing=SERVING_SPACING, speeds=SPEEDS,
+                    params=None):
+    """The plain full-grid search of every state of a batch on its own
+    field's grid (one pps_search per field size); host pps_best records."""
+    torch = searcher.torch
+    S = batch["ball"].shape[0]
+    out = np.zeros(S, pps.BEST_DTYPE)
+    fields = sorted({(float(a), float(b)) for a, b in
+                     zip(batch["field_len"], batch["field_wid"])})
+    for L, W in fields:
+        idx = np.flatnonzero((batch["field_len"] == L)
+                             & (batch["field_wid"] == W))
+        sub = {k: np.ascontiguousarray(v[idx]) for k, v in batch.items()}
+        grid = pps.pps_grid_from_field(L, W, spacing)
+        o = searcher.search(searcher.states_to_device(sub), len(idx), grid,
+                            speeds, params, mask=False)
+        torch.cuda.synchronize()
+        out[idx] = pps.unpack_best(o["best"].cpu().numpy())
+    return out

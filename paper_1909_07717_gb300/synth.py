@@ -428,3 +428,26 @@ def net_int_weights(seed: int, nonzero: int = 3) -> np.ndarray:
                                                      size=nonzero - 1)
         out += [W.reshape(-1), rng.integers(-1, 2, size=co).astype(np.float32)]
     return np.concatenate(out)
+
+
+def serving_states(seed: int, n_states: int, *, K: int = 32,
+                   vmax: float = 3.25, amax: float = 3.0,
+                   ball_decel: float = 0.5) -> dict:
+    """Independent states shaped like the serving frames: half on a 12 x 9 m
+    field and half on a 9 x 6 m one (interleaved), 6-11 opponents each
+    (uniform), positions uniform over the field, speeds uniform in
+    [0, vmax], K samples.  Opponent slots past n_opp hold drawn values the
+    search ignores."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for L, W in ((12.0, 9.0), (9.0, 6.0)):
+        n = (n_states + (L == 12.0)) // 2
+        b = _draw(rng, n, L, W, None, 11, 16, 8, K, ball_decel, vmax, amax,
+                  False)
+        b["n_opp"] = rng.integers(6, 12, n).astype(np.int32)
+        parts.append(b)
+    big, small = parts
+    order = np.empty(n_states, np.int64)
+    order[0::2] = np.arange(big["ball"].shape[0])
+    order[1::2] = big["ball"].shape[0] + np.arange(small["ball"].shape[0])
+    return take(concat([big, small]), order)

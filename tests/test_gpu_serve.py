@@ -175,3 +175,122 @@ def test_bad_requests_are_refused(torch):
         assert e.value.status == pps.PPS_ETIMEOUT
     finally:
         pps.pps_server_destroy(srv)
+
+
+# ------------------------------------------------------------ proposal mode
+BEST_FIELDS = ("idx", "ix", "iy", "speed_idx", "score", "margin", "status")
+
+
+def _proposal_server(weights, streams=4, max_batch=256, topk=256,
+                     wait_us=50):
+    w = np.ascontiguousarray(weights, np.float32)
+    d = pps.pps_server_desc(0, streams, max_batch, 16384, 0, 16, wait_us,
+                            pps.params_from_dict(PARAMS),
+                            pps.PPS_SERVE_PROPOSAL, topk, w.ctypes.data)
+    return pps.pps_server_create(d)   # the weights are copied
+
+
+def _best_fields(best):
+    return [best[f].tobytes() for f in BEST_FIELDS]
+
+
+def _propose_direct(torch, frames, jobs, weights, topk=256):
+    """The same frames through pps_propose_jobs (with the fallback)."""
+    from paper_1909_07717_gb300.proposal import JobsProposal
+    S = frames["ball"].shape[0]
+    pr = JobsProposal(S, weights)
+    try:
+        st = pr.searcher.states_to_device(
+            {k: v for k, v in frames.items() if isinstance(v, np.ndarray)})
+        b, _ = pr.run(st, pr.jobs_to_device(jobs), S, topk=topk)
+        torch.cuda.synchronize()
+        return pps.unpack_best(b.cpu().numpy())
+    finally:
+        pr.close()
+
+
+def test_proposal_alone_equals_in_the_mix(torch):
+    """Proposal mode: a frame alone, in a mix of 128 frames of 16 matches
+    and alone again gets the same best pass, and every frame the one
+    pps_propose_jobs gives it (fields, grids and speeds of its own)."""
+    frames = synth.serving_matches(405, 16, 8)
+    rec = pps.pack_states(frames)
+    jobs = pps.jobs_from_batch(frames)
+    S = rec.shape[0]
+    w = pps.load_net_weights(pps.SERVING_WEIGHTS)
+    srv = _proposal_server(w)
+    try:
+        def one(i):
+            t = pps.pps_server_submit(srv, rec[i:i + 1].ctypes.data,
+                                      pps.ctypes.addressof(jobs[i]))
+            return pps.pps_server_wait(srv, t, -1)
+        alone = one(5)
+        assert alone.batch_size == 1
+        tickets = [pps.pps_server_submit(srv, rec[i:i + 1].ctypes.data,
+                                         pps.ctypes.addressof(jobs[i]))
+                   for i in range(S)]
+        mixed = [pps.pps_server_wait(srv, t, -1) for t in tickets]
+        again = one(5)
+    finally:
+        pps.pps_server_destroy(srv)
+    assert max(r.batch_size for r in mixed) > 1, "no batching happened"
+    got = np.frombuffer(b"".join(bytes(r.best) for r in mixed),
+                        pps.BEST_DTYPE)
+    a = np.frombuffer(bytes(alone.best), pps.BEST_DTYPE)
+    b = np.frombuffer(bytes(again.best), pps.BEST_DTYPE)
+    assert _best_fields(a) == _best_fields(got[5:6]) == _best_fields(b)
+    assert np.all(got["status"] == 0)
+    ref = _propose_direct(torch, frames, jobs, w)
+    assert _best_fields(got) == _best_fields(ref)
+
+
+def test_proposal_replay_agrees_with_the_exact_search(torch):
+    """60 Hz replay of 32 matches in the proposal mode: every frame served,
+    each result what pps_propose_jobs gives, never above the exact best,
+    and within 2 % of it on at least 99 % of the frames."""
+    from paper_1909_07717_gb300.proposal import agreement
+    M, F = 32, 30
+    frames = synth.serving_matches(406, M, F)
+    rec = pps.pack_states(frames)
+    jobs_m = pps.match_jobs(frames)
+    w = pps.load_net_weights(pps.SERVING_WEIGHTS)
+    srv = _proposal_server(w)
+    try:
+        res = np.zeros(M * F, pps.RESULT_DTYPE)
+        st = pps.pps_server_replay(srv, rec, jobs_m, M, F, 60.0, res)
+    finally:
+        pps.pps_server_destroy(srv)
+    assert st.completed == M * F and np.all(res["status"] == 0)
+    jobs = pps.jobs_from_batch(frames)
+    got = res["best"]
+    assert _best_fields(got) == _best_fields(
+        _propose_direct(torch, frames, jobs, w))
+    ex, _, _ = _reference(torch, frames, jobs)
+    found = got["idx"] >= 0
+    assert np.all(got["score"][found] <= ex["score"][found])
+    ok = agreement(got, ex)
+    assert ok.mean() >= 0.99, ok.mean()
+
+
+def test_proposal_mode_refuses_what_it_cannot_serve(torch):
+    frames = synth.serving_matches(407, 2, 1)
+    rec = pps.pack_states(frames)
+    jobs = pps.jobs_from_batch(frames)
+    d = pps.pps_server_desc(0, 1, 8, 64, 0, 16, 0,
+                            pps.params_from_dict(PARAMS),
+                            pps.PPS_SERVE_PROPOSAL, 256, None)
+    with pytest.raises(pps.PpsError) as e:
+        pps.pps_server_create(d)
+    assert e.value.status == pps.PPS_EINVAL
+    srv = _proposal_server(pps.init_weights(1), streams=1, max_batch=8)
+    try:
+        jobs[0].grid.x0 += 0.01          # off the map's cell lattice
+        with pytest.raises(pps.PpsError) as e:
+            pps.pps_server_submit(srv, rec[0:1].ctypes.data,
+                                  pps.ctypes.addressof(jobs[0]))
+        assert e.value.status == pps.PPS_EINVAL
+        t = pps.pps_server_submit(srv, rec[1:2].ctypes.data,
+                                  pps.ctypes.addressof(jobs[1]))
+        assert pps.pps_server_wait(srv, t, -1).status == 0
+    finally:
+        pps.pps_server_destroy(srv)
