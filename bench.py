@@ -473,6 +473,8 @@ def run_pps(args):
             line["dpps"] = _dpps(args, dev, stream)
         if world == 1 and not args.no_run:
             line["run_points"] = _run_points(args, dev, stream)
+        if world == 1 and not args.no_training:
+            line["training"] = _training(args, dev, stream)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
@@ -955,6 +957,63 @@ def _run_points(args, dev, stream):
             "ok": bool(np.all(r["status"] == 0))}
 
 
+def _training(args, dev, stream):
+    """One training step of the proposal network (pps_net_train_step: the
+    rasteriser, the forward pass keeping every activation, the loss, the
+    backward pass -- input and weight gradients of the four convolutions --
+    and the Adam update) on batches of 256 states of the 12 x 9 m workload
+    with exact labels, as train_proposal.py runs it; the forward pass of the
+    same batch through the training kernels (pps_net_forward_layers) and
+    through the tcgen05 inference kernel beside it."""
+    import torch
+    from paper_1909_07717_gb300 import pps, synth
+    B = 256
+    batch = synth.ssl_states(100_000, B, K=64)
+    net = pps.Net(dev.index, stream, max_batch=B,
+                  weights=pps.init_weights(0, zero_output=True))
+    rec = torch.from_numpy(pps.pack_states(batch).view(np.uint8).copy()).to(dev)
+    rng = np.random.default_rng(0)
+    lab = torch.from_numpy(rng.normal(0.3, 0.4, (B, 46, 61))
+                           .astype(np.float32)).to(dev)
+    out = torch.empty((B, 46, 61), dtype=torch.float32, device=dev)
+    steps = 20
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = (torch.cuda.Event(enable_timing=True),
+                  torch.cuda.Event(enable_timing=True))
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    step = lambda: pps.pps_net_train_step(  # noqa: E731
+        net.net, rec.data_ptr(), lab.data_ptr(), B, 1e-4, want_loss=False)
+    pps.pps_net_set_train_kernels(net.net, pps.PPS_NET_TRAIN_MMA_SYNC)
+    ms_step_mma = timed(step)
+    pps.pps_net_set_train_kernels(net.net, pps.PPS_NET_TRAIN_TCGEN05)
+    ms_step = timed(step)
+    pps.pps_net_sync(net.net)
+    ms_fwd_layers = timed(lambda: pps.pps_net_forward_layers(
+        net.net, rec.data_ptr(), B, out.data_ptr()))
+    ms_fwd_tc = timed(lambda: pps.pps_net_forward(net.net, rec.data_ptr(), B,
+                                                  out.data_ptr()))
+    net.close()
+    return {"workload": f"train_step_{B}: 12x9 m, 8 v 8, K 64 features",
+            "batch": B, "kernels": "tcgen05", "ms_per_step": ms_step,
+            "states_per_s": B / (ms_step / 1e3),
+            "ms_per_step_mma_sync": ms_step_mma,
+            "speedup_over_mma_sync": ms_step_mma / ms_step,
+            "ms_forward_training_kernels": ms_fwd_layers,
+            "ms_forward_tcgen05": ms_fwd_tc,
+            "note": "steps back to back with no L2 flush, as training runs "
+                    "them"}
+
+
 def _serving(dev, seconds=2.0, no_cpu=False):
     """The serving loop: 512 simulated matches at 60 Hz (12x9 or 9x6 fields,
     6-11 opponents, 0.05 m grid, 4 speeds, K = 32) replayed in real time
@@ -1055,6 +1114,8 @@ def main():
                     help="skip the direction x power search")
     ap.add_argument("--no-run", action="store_true",
                     help="skip the running-point search")
+    ap.add_argument("--no-training", action="store_true",
+                    help="skip the proposal network's training step")
     ap.add_argument("--states", type=int, default=0,
                     help="states per GPU (default: the workload's 4096); "
                          "smaller only for profiling captures")

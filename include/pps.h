@@ -481,8 +481,9 @@ pps_status pps_server_get_stats(pps_server* srv, pps_server_stats* out);
  * points of that pixel's cell, as channel 1 plus a learned correction:
  * 4 layers of 3x3 convolutions
  * (8 -> 32 -> 32 -> 32 -> 1, ReLU between), bfloat16 weights and
- * activations with float32 accumulation, all on the tensor cores, trained
- * on the GPU with the library's own forward and backward kernels (Adam). */
+ * activations with float32 accumulation, all on the tensor cores (tcgen05),
+ * trained on the GPU with the library's own forward and backward kernels
+ * (Adam). */
 
 #define PPS_NET_H 46
 #define PPS_NET_W 61
@@ -547,10 +548,10 @@ pps_status pps_net_raster(pps_net* net, const pps_state* states, int n,
 pps_status pps_net_forward(pps_net* net, const pps_state* states, int n,
                            float* out);
 
-/* The same prediction computed layer by layer on mma.sync, as training does
- * (every activation written to device memory for the backward pass).  It
- * differs from pps_net_forward only by FP32 summation order (and the
- * bfloat16 roundings that order can flip). */
+/* The same prediction computed layer by layer on mma.sync (every activation
+ * written to device memory), the forward pass of the PPS_NET_TRAIN_MMA_SYNC
+ * training kernels.  It differs from pps_net_forward only by FP32 summation
+ * order (and the bfloat16 roundings that order can flip). */
 pps_status pps_net_forward_layers(pps_net* net, const pps_state* states,
                                   int n, float* out);
 
@@ -574,6 +575,19 @@ pps_status pps_net_grad(pps_net* net, const pps_state* states,
 pps_status pps_net_grad_map(pps_net* net, const uint16_t* map,
                             const float* labels, int n, float* grads,
                             float* loss);
+
+/* The kernels pps_net_grad and pps_net_train_step run on.
+ *   PPS_NET_TRAIN_TCGEN05 (the default): the forward pass is the fused
+ *     tcgen05 kernel of pps_net_forward, writing the hidden activations; the
+ *     input gradients are tcgen05 convolutions; the weight and bias
+ *     gradients a tcgen05 product over the batch's pixels, summed per CTA
+ *     and then over the CTAs in a fixed order (the same gradient every run).
+ *   PPS_NET_TRAIN_MMA_SYNC: the layer-by-layer mma.sync kernels (forward,
+ *     input gradients, weight gradients with atomic sums).
+ * EINVAL for another kind. */
+#define PPS_NET_TRAIN_TCGEN05 0
+#define PPS_NET_TRAIN_MMA_SYNC 1
+pps_status pps_net_set_train_kernels(pps_net* net, int kind);
 
 /* One Adam step (lr, beta 0.9/0.999) on a batch; *loss (host, may be NULL:
  * then the call does not wait) gets the batch's loss before the step. */

@@ -15,6 +15,7 @@
 #include "pps_internal.h"
 #include "pps_net.cuh"
 #include "pps_net_tc.cuh"
+#include "pps_net_tc_train.cuh"
 
 using namespace pps::net;
 char* pps_thread_error_buffer();
@@ -37,6 +38,8 @@ struct pps_net {
     int* list_n = nullptr; // proposal scratch: their number
     float* smax = nullptr; // training scratch: max_batch best labels
     int* err = nullptr;    // set by a kernel whose bounded wait ran out
+    float* wpart = nullptr;  // weight-gradient partial sums, one row per CTA
+    int train_kind = PPS_NET_TRAIN_TCGEN05;
     RasterCfg cfg{};       // speeds and parameters of the input features
     float top_band = 3.0e38f, low_w = 1.f, under_w = 1.f;  // the loss
 };
@@ -103,15 +106,16 @@ cudaError_t load_input(pps_net* nt, const pps_state* states,
     return cudaGetLastError();
 }
 
-// Forward pass of the map in nt->a0 into nt->out.  keep: layer by layer on
-// mma.sync, keeping every activation for the backward pass (training);
-// otherwise the tcgen05 kernel, which keeps them on the SM.
-cudaError_t forward_loaded(pps_net* nt, int n, bool keep,
+// Forward pass of the map in nt->a0 into nt->out.  layers: layer by layer
+// on mma.sync, every activation written to device memory; otherwise the
+// fused tcgen05 kernel, which keeps the activations on the SM -- or, with
+// keep (training), also writes them for the backward pass.
+cudaError_t forward_loaded(pps_net* nt, int n, bool layers, bool keep = false,
                            bool withhold = false) {
     const long long P = (long long)n * NPIX;
     const unsigned g = blocks(P, 64);
     cudaStream_t st = nt->stream;
-    if (!keep) {
+    if (!layers) {
         cudaError_t e = cudaFuncSetAttribute(
             tcf::tc_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
             (int)tcf::kSmemBytes);
@@ -122,7 +126,8 @@ cudaError_t forward_loaded(pps_net* nt, int n, bool keep,
         tcf::tc_forward_kernel<<<grid, tcf::kThreads, tcf::kSmemBytes, st>>>(
             nt->a0, n, nt->Wf, nt->w, nt->out, wf_off(1), wf_off(2), wf_off(3),
             bias_off(0), bias_off(1), bias_off(2), bias_off(3), nt->err,
-            withhold ? 1 : 0);
+            withhold ? 1 : 0, keep ? nt->a1 : nullptr, keep ? nt->a2 : nullptr,
+            keep ? nt->a3 : nullptr);
         return cudaGetLastError();
     }
     conv_kernel<C0, CH, kHidden><<<g, 128, 0, st>>>(
@@ -137,10 +142,76 @@ cudaError_t forward_loaded(pps_net* nt, int n, bool keep,
 }
 
 // Forward pass of n states (or, states NULL, of a caller's input map).
-cudaError_t forward(pps_net* nt, const pps_state* states, int n, bool keep,
+cudaError_t forward(pps_net* nt, const pps_state* states, int n, bool layers,
                     bool withhold = false, const uint16_t* map = nullptr) {
     cudaError_t e = load_input(nt, states, map, n);
-    return e == cudaSuccess ? forward_loaded(nt, n, keep, withhold) : e;
+    return e == cudaSuccess ? forward_loaded(nt, n, layers, false, withhold) : e;
+}
+
+// The forward pass of a training step: every activation kept for the
+// backward pass, by the kernels of the network's training kind.
+cudaError_t forward_train(pps_net* nt, const pps_state* states, int n,
+                          const uint16_t* map = nullptr) {
+    cudaError_t e = load_input(nt, states, map, n);
+    if (e != cudaSuccess) return e;
+    return nt->train_kind == PPS_NET_TRAIN_TCGEN05
+               ? forward_loaded(nt, n, false, true)
+               : forward_loaded(nt, n, true);
+}
+
+// The tcgen05 training products of one layer: weight and bias gradients of
+// layer l from g (its output gradient) and x (its input), accumulated into
+// nt->grad; and, for l > 0, the masked input gradient g_in.
+template <int CIN, int COUT>
+cudaError_t wgrad_tc(pps_net* nt, int l, const __nv_bfloat16* g,
+                     const __nv_bfloat16* x, int n) {
+    using S = tct::WgradShape<CIN, COUT>;
+    cudaError_t e = cudaFuncSetAttribute(
+        tct::wgrad_tc_kernel<CIN, COUT>,
+        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem);
+    if (e != cudaSuccess) return e;
+    const long long nb = (long long)n * (H / 2);
+    const int grid = (int)(nb < nt->num_sms ? nb : nt->num_sms);
+    tct::wgrad_tc_kernel<CIN, COUT><<<grid, tct::kThreads, S::kSmem,
+                                      nt->stream>>>(g, x, n, nt->wpart,
+                                                    nt->err);
+    constexpr int kAll = 9 * COUT * CIN + COUT;
+    tct::wgrad_reduce_kernel<CIN, COUT><<<blocks(kAll, 256), 256, 0,
+                                          nt->stream>>>(
+        nt->wpart, grid, nt->grad + layer_off(l), nt->grad + bias_off(l));
+    return cudaGetLastError();
+}
+
+template <int CIN, int COUT>
+cudaError_t bconv_tc(pps_net* nt, const __nv_bfloat16* g,
+                     const __nv_bfloat16* Wt, const __nv_bfloat16* aux,
+                     __nv_bfloat16* out, int n) {
+    using S = tct::BconvShape<CIN, COUT>;
+    cudaError_t e = cudaFuncSetAttribute(
+        tct::bconv_tc_kernel<CIN, COUT>,
+        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem);
+    if (e != cudaSuccess) return e;
+    const long long units = (long long)n * tct::kBands;
+    const int grid = (int)(units < nt->num_sms ? units : nt->num_sms);
+    tct::bconv_tc_kernel<CIN, COUT><<<grid, tct::kThreads, S::kSmem,
+                                      nt->stream>>>(g, n, Wt, aux, out,
+                                                    nt->err);
+    return cudaGetLastError();
+}
+
+// The backward pass on tcgen05 (the loss gradient g4 already written).
+cudaError_t backward_tc(pps_net* nt, int n) {
+    cudaError_t e = wgrad_tc<CH, CO>(nt, 3, nt->g4, nt->a3, n);
+    if (e == cudaSuccess)
+        e = bconv_tc<CO, CH>(nt, nt->g4, nt->WT + wf_off(3), nt->a3, nt->g3, n);
+    if (e == cudaSuccess) e = wgrad_tc<CH, CH>(nt, 2, nt->g3, nt->a2, n);
+    if (e == cudaSuccess)
+        e = bconv_tc<CH, CH>(nt, nt->g3, nt->WT + wf_off(2), nt->a2, nt->g2, n);
+    if (e == cudaSuccess) e = wgrad_tc<CH, CH>(nt, 1, nt->g2, nt->a1, n);
+    if (e == cudaSuccess)
+        e = bconv_tc<CH, CH>(nt, nt->g2, nt->WT + wf_off(1), nt->a1, nt->g1, n);
+    if (e == cudaSuccess) e = wgrad_tc<C0, CH>(nt, 0, nt->g1, nt->a0, n);
+    return e;
 }
 
 // Gradients of the mean squared error into nt->grad (accumulated).
@@ -157,6 +228,10 @@ cudaError_t backward(pps_net* nt, const float* labels, int n) {
                                                 1.f / (float)P, nt->top_band,
                                                 nt->low_w, nt->under_w, nt->g4,
                                                 nt->loss);
+    if (nt->train_kind == PPS_NET_TRAIN_TCGEN05) {
+        e = cudaGetLastError();
+        return e == cudaSuccess ? backward_tc(nt, n) : e;
+    }
     // layer 4 (32 -> 1)
     wgrad_kernel<CH, CO><<<gw, 288, 0, st>>>(nt->g4, nt->a3, P, chunk,
                                               nt->grad + layer_off(3));
@@ -286,6 +361,8 @@ extern "C" pps_status pps_net_create(int device, void* stream, int max_batch,
     al(&nt->list, sizeof(int) * (size_t)max_batch);
     al(&nt->list_n, sizeof(int));
     al(&nt->err, sizeof(int));
+    al(&nt->wpart, sizeof(float) * (size_t)(nt->num_sms > 0 ? nt->num_sms : 1) *
+                       (9 * CH * CH + CH));
     if (e != cudaSuccess) {
         cudaGetLastError();
         pps_net_destroy(nt);
@@ -306,7 +383,7 @@ extern "C" void pps_net_destroy(pps_net* nt) {
                     (void*)nt->g3, (void*)nt->g4, (void*)nt->out,
                     (void*)nt->loss, (void*)nt->cells, (void*)nt->skip,
                     (void*)nt->smax, (void*)nt->list, (void*)nt->list_n,
-                    (void*)nt->err})
+                    (void*)nt->err, (void*)nt->wpart})
         if (p) cudaFree(p);
     cudaGetLastError();
     delete nt;
@@ -480,7 +557,7 @@ pps_status grad_of(pps_net* nt, const pps_state* states, const uint16_t* map,
     cudaSetDevice(nt->device);
     cudaError_t e = cudaMemsetAsync(nt->grad, 0, sizeof(float) * kPadParams,
                                     nt->stream);
-    if (e == cudaSuccess) e = forward(nt, states, n, true, false, map);
+    if (e == cudaSuccess) e = forward_train(nt, states, n, map);
     if (e == cudaSuccess) e = backward(nt, labels, n);
     std::vector<float> pad(kPadParams);
     float l = 0.f;
@@ -526,7 +603,7 @@ extern "C" pps_status pps_net_train_step(pps_net* nt, const pps_state* states,
     if (!labels || !(lr > 0.f) || !std::isfinite(lr))
         return fail(PPS_EINVAL, "pps_net_train_step: labels and lr > 0");
     cudaSetDevice(nt->device);
-    cudaError_t e = forward(nt, states, n, true);
+    cudaError_t e = forward_train(nt, states, n);
     if (e == cudaSuccess) e = backward(nt, labels, n);
     ++nt->step;
     const float b1 = 0.9f, b2 = 0.999f;
@@ -571,4 +648,11 @@ extern "C" pps_status pps_net_labels(pps_net* nt, const float* point_best,
     pps_grid fine;
     pps_grid_from_field(12.f, 9.f, 0.025f, &fine);
     return pps_net_labels_grid(nt, point_best, n, &fine, floor_value, labels);
+}
+
+extern "C" pps_status pps_net_set_train_kernels(pps_net* nt, int kind) {
+    if (!nt || (kind != PPS_NET_TRAIN_TCGEN05 && kind != PPS_NET_TRAIN_MMA_SYNC))
+        return fail(PPS_EINVAL, "pps_net_set_train_kernels: unknown kind");
+    nt->train_kind = kind;
+    return PPS_OK;
 }

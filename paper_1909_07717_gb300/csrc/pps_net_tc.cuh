@@ -5,7 +5,8 @@
 // descriptors; D = FP32 accumulators in tensor memory), the bias / ReLU /
 // bfloat16 epilogue read back with tcgen05.ld.  Activations never leave the
 // SM; the next band's input rows stream in with cp.async while layers 2-4
-// run.
+// run.  For training the kernel also writes the hidden activations of each
+// band's own rows to device memory.
 //
 // Layouts (all K-major, no swizzle: 8-row x 16-byte core matrices):
 //   activations: one plane per 8 channels; a plane is a run of 16-byte
@@ -120,11 +121,16 @@ __device__ __forceinline__ void issue(uint32_t tmem, const uint8_t* in,
 // Hidden-layer epilogue: bias, ReLU, bf16, into the next buffer (zero
 // outside the map and in columns 61..63).  A warp serves one lane quarter
 // of a tile as soon as that tile's accumulators are complete.
+// With act (training), the band's own rows y0 .. y0 + kBand - 1 of the
+// activations also go to act[s][y][x][32] in device memory for the
+// backward pass (the halo rows are other bands' own rows).
 __device__ __forceinline__ bool epi_hidden(uint32_t tmem, int ntiles,
                                            const float* __restrict__ bias,
                                            int y_first, uint8_t* out,
                                            int slots_out, uint32_t bars,
-                                           uint32_t phases, uint32_t polls) {
+                                           uint32_t phases, uint32_t polls,
+                                           __nv_bfloat16* __restrict__ act,
+                                           int s, int y0) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int q = warp & 3;
     bool ok = true;
@@ -136,6 +142,10 @@ __device__ __forceinline__ bool epi_hidden(uint32_t tmem, int ntiles,
         const int r = 32 * q + lane, row = 2 * j + (r >> 6), col = r & 63;
         const int Y = y_first + row;
         const bool in_map = Y >= 0 && Y < H && col < W;
+        const bool own = act && in_map && Y >= y0 && Y < y0 + kBand;
+        uint4* ga = own ? reinterpret_cast<uint4*>(
+                              act + ((long long)s * NPIX + Y * W + col) * CH)
+                        : nullptr;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             uint4 o;
@@ -148,6 +158,7 @@ __device__ __forceinline__ bool epi_hidden(uint32_t tmem, int ntiles,
                               : 0u;
             }
             reinterpret_cast<uint4*>(out)[k * slots_out + kLead + row * kRow + col] = o;
+            if (own) ga[k] = o;
         }
     }
     return ok;
@@ -158,7 +169,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                       const __nv_bfloat16* __restrict__ Wf,
                       const float* __restrict__ w32, float* __restrict__ out,
                       int wf1, int wf2, int wf3, int b0, int b1, int b2, int b3,
-                      int* __restrict__ err, int withhold) {
+                      int* __restrict__ err, int withhold,
+                      __nv_bfloat16* __restrict__ act1,
+                      __nv_bfloat16* __restrict__ act2,
+                      __nv_bfloat16* __restrict__ act3) {
     extern __shared__ __align__(128) uint8_t smem[];
     uint8_t* bin = smem;
     uint8_t* ba = smem + kOffA;
@@ -225,14 +239,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                       t4 = kBand / 2;
         if (!start_layer([&] { issue<C0, CH>(tmem, bin, kSlotsIn, smem + kOffW0, t1, bars); }))
             break;
-        end_layer(t1, epi_hidden(tmem, t1, w32 + b0, y0 - 3, ba, kSlotsA, bars, phases, polls));
+        end_layer(t1, epi_hidden(tmem, t1, w32 + b0, y0 - 3, ba, kSlotsA, bars,
+                                 phases, polls, act1, s, y0));
         if (!start_layer([&] { issue<CH, CH>(tmem, ba, kSlotsA, smem + kOffW1, t2, bars); }))
             break;
         if (u + gridDim.x < units) prefetch(a0, u + gridDim.x, bin);
-        end_layer(t2, epi_hidden(tmem, t2, w32 + b1, y0 - 2, bb, kSlotsB, bars, phases, polls));
+        end_layer(t2, epi_hidden(tmem, t2, w32 + b1, y0 - 2, bb, kSlotsB, bars,
+                                 phases, polls, act2, s, y0));
         if (!start_layer([&] { issue<CH, CH>(tmem, bb, kSlotsB, smem + kOffW2, t3, bars); }))
             break;
-        end_layer(t3, epi_hidden(tmem, t3, w32 + b2, y0 - 1, ba, kSlotsA, bars, phases, polls));
+        end_layer(t3, epi_hidden(tmem, t3, w32 + b2, y0 - 1, ba, kSlotsA, bars,
+                                 phases, polls, act3, s, y0));
         // layer 4: A -> the output map (+ the coarse-score input channel)
         if (!start_layer([&] { issue<CH, kNOut>(tmem, ba, kSlotsA, smem + kOffW3, t4, bars); }))
             break;

@@ -212,7 +212,8 @@ EXPORTS = ("pps_abi_version", "pps_status_string", "pps_last_error",
            "pps_net_sync", "pps_net_selftest_timeout",
            "pps_net_get_weights", "pps_net_raster", "pps_net_forward_layers",
            "pps_net_forward", "pps_net_forward_map", "pps_net_grad",
-           "pps_net_grad_map", "pps_net_train_step",
+           "pps_net_grad_map", "pps_net_set_train_kernels",
+           "pps_net_train_step",
            "pps_net_labels", "pps_net_labels_grid", "pps_propose",
            "pps_propose_jobs", "pps_dpps_default_params",
            "pps_dpps_mask_words", "pps_dpps_search", "pps_pass_powers",
@@ -320,6 +321,7 @@ def lib():
             L.pps_net_grad_map.argtypes = [c_void_p, c_void_p, c_void_p,
                                            ctypes.c_int, c_void_p,
                                            P(ctypes.c_float)]
+            L.pps_net_set_train_kernels.argtypes = [c_void_p, ctypes.c_int]
             L.pps_net_train_step.argtypes = [c_void_p, c_void_p, c_void_p,
                                              ctypes.c_int, ctypes.c_float,
                                              P(ctypes.c_float)]
@@ -587,6 +589,14 @@ def pps_net_grad_map(net, maps, labels, n):
     _check(lib().pps_net_grad_map(net, maps, labels, n, g.ctypes.data,
                                   ctypes.byref(loss)))
     return loss.value, g
+
+
+PPS_NET_TRAIN_TCGEN05 = 0
+PPS_NET_TRAIN_MMA_SYNC = 1
+
+
+def pps_net_set_train_kernels(net, kind) -> int:
+    return _check(lib().pps_net_set_train_kernels(net, int(kind)))
 
 
 def pps_net_train_step(net, states, labels, n, lr, want_loss=True):

@@ -149,14 +149,18 @@ def test_forward_real_network_within_bounds(torch):
         net.close()
 
 
+TRAIN_KINDS = [0, 1]   # PPS_NET_TRAIN_TCGEN05, PPS_NET_TRAIN_MMA_SYNC
+
+
+@pytest.mark.parametrize("kind", TRAIN_KINDS)
 @pytest.mark.parametrize("band,low,under", [(np.inf, 1.0, 1.0),
                                             (0.4, 0.1, 3.0)])
-def test_gradients_match_reference(torch, band, low, under):
+def test_gradients_match_reference(torch, band, low, under, kind):
     """Every weight and bias gradient element of pps_net_grad_map against
     the FP64 reference on an integer-valued network (exact forward pass),
     within the element-wise bound net_bounds derives from the float32 sums
-    and bfloat16 roundings of the backward pass; the bound is a small
-    fraction of each gradient."""
+    and bfloat16 roundings of the backward pass, for both training kernel
+    kinds; the bound is a small fraction of each gradient."""
     n = 4
     bits = synth.net_maps(604, n, integer=True)
     w = synth.net_int_weights(605)
@@ -168,10 +172,17 @@ def test_gradients_match_reference(torch, band, low, under):
         top_band=band, low_weight=low, under_weight=under, exact=True)
     net = pps.Net(max_batch=n, weights=w)
     try:
+        pps.pps_net_set_train_kernels(net.net, kind)
         pps.pps_net_set_loss(net.net, band, low, under)
         d = _maps_to_device(torch, bits)
         lab = torch.from_numpy(labels).cuda()
         loss, g = pps.pps_net_grad_map(net.net, d.data_ptr(), lab.data_ptr(), n)
+        assert pps.pps_net_sync(net.net) == pps.PPS_OK
+        if kind == 0:
+            # fixed-order sums: the same gradient bit for bit every run
+            loss2, g2 = pps.pps_net_grad_map(net.net, d.data_ptr(),
+                                             lab.data_ptr(), n)
+            assert g2.tobytes() == g.tobytes()
     finally:
         net.close()
     # the loss: a float32 sum over every pixel
@@ -193,12 +204,14 @@ def test_gradients_match_reference(torch, band, low, under):
     print(f"largest error / bound {worst:.3f}")
 
 
-def test_training_reduces_the_loss(torch):
+@pytest.mark.parametrize("kind", TRAIN_KINDS)
+def test_training_reduces_the_loss(torch, kind):
     """Adam steps on one batch: the network learns to reproduce a map
     (the ball-proximity channel) it is given as input."""
     batch = synth.ssl_states(504, 16, K=64)
     net = pps.Net(max_batch=16, weights=pps.init_weights(10))
     try:
+        pps.pps_net_set_train_kernels(net.net, kind)
         dev, x = _gpu_raster(torch, net, batch)
         lab = torch.from_numpy(x[..., 3].astype(np.float32)).cuda()
         losses = [pps.pps_net_train_step(net.net, dev.data_ptr(),
