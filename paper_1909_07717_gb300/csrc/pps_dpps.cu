@@ -236,7 +236,9 @@ template <int J>
 __device__ __forceinline__ void dpps_eval(const pps_dstate& st,
                                           const DStateK& sk,
                                           const pps_dparams& prm, int dir,
-                                          int pw, bool active, DRes& r) {
+                                          int pw, bool active,
+                                          const OppRegs<J>& team,
+                                          const OppRegs<J>& opp, DRes& r) {
     Path p;
     float sn, cs;
     sincospif(__fdiv_rn(2.f * (float)dir, (float)prm.n_dir), &sn, &cs);
@@ -264,17 +266,11 @@ __device__ __forceinline__ void dpps_eval(const pps_dstate& st,
     r.score = -CUDART_INF_F;
     r.t_opp = CUDART_INF_F;
     r.rx = r.ry = 0.f;
-    {
-        OppRegs<J> g;
-        load_group<J>(st.team_pos, st.team_vel, sk.nteam, sk, g);
-        r.t_team = group_first<J>(sk, g, p, active && sk.valid, r.k_team, r.recv);
-    }
+    r.t_team = group_first<J>(sk, team, p, active && sk.valid, r.k_team, r.recv);
     const bool got = r.t_team < CUDART_INF_F;
     {
-        OppRegs<J> g;
-        load_group<J>(st.opp_pos, st.opp_vel, sk.nopp, sk, g);
         int k_opp, who;
-        r.t_opp = group_first<J>(sk, g, p, got, k_opp, who);
+        r.t_opp = group_first<J>(sk, opp, p, got, k_opp, who);
     }
     // Sec. 4.3: safe when the first opponent comes more than tau later
     r.feas = got && __fsub_rn(r.t_opp, r.t_team) > prm.tau_delta;
@@ -311,7 +307,7 @@ __device__ __forceinline__ void dpps_eval(const pps_dstate& st,
 }
 
 template <int J>
-__global__ void __launch_bounds__(kTPB) dpps_kernel(const DArgs a) {
+__global__ void __launch_bounds__(kTPB, 2) dpps_kernel(const DArgs a) {
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (kTPB / 32);
     const long long gw = (long long)blockIdx.x * (kTPB / 32) + (threadIdx.x >> 5);
@@ -322,6 +318,12 @@ __global__ void __launch_bounds__(kTPB) dpps_kernel(const DArgs a) {
     const long long R = n_items >= warps * 8 * kMaxRun
                             ? kMaxRun
                             : (n_items >= warps * 8 ? n_items / (warps * 8) : 1);
+    // the warp's state's two robot groups, in shared memory: every lane
+    // reads the same robot at the same time (a broadcast), and the groups
+    // need no registers
+    __shared__ OppRegs<J> groups[kTPB / 32][2];
+    OppRegs<J>& team = groups[threadIdx.x >> 5][0];
+    OppRegs<J>& opp = groups[threadIdx.x >> 5][1];
     int cur = -1;
     DStateK sk;
     for (long long item = gw * R, j = 0; item < n_items;
@@ -335,9 +337,15 @@ __global__ void __launch_bounds__(kTPB) dpps_kernel(const DArgs a) {
         if (s != cur) {
             sk = derive_dstate<J>(st, a.prm, a.kmax);
             cur = s;
+            __syncwarp();
+            if (lane == 0) {
+                load_group<J>(st.team_pos, st.team_vel, sk.nteam, sk, team);
+                load_group<J>(st.opp_pos, st.opp_vel, sk.nopp, sk, opp);
+            }
+            __syncwarp();
         }
         DRes r;
-        dpps_eval<J>(st, sk, a.prm, dir, active ? pw : 0, active, r);
+        dpps_eval<J>(st, sk, a.prm, dir, active ? pw : 0, active, team, opp, r);
         const bool f = active && r.feas;
         const uint32_t idx = (uint32_t)(dir * a.prm.n_pow + pw);
         if (a.dbg && active) {
@@ -393,7 +401,10 @@ __global__ void __launch_bounds__(128) dpps_finalize(const DArgs a) {
         b.pow = (int)(idx - (uint32_t)b.dir * (uint32_t)a.prm.n_pow);
         b.score = pps::order_bits_inv((uint32_t)(key >> 32));
         DRes r;
-        dpps_eval<J>(st, sk, a.prm, b.dir, b.pow, true, r);
+        OppRegs<J> team, opp;
+        load_group<J>(st.team_pos, st.team_vel, sk.nteam, sk, team);
+        load_group<J>(st.opp_pos, st.opp_vel, sk.nopp, sk, opp);
+        dpps_eval<J>(st, sk, a.prm, b.dir, b.pow, true, team, opp, r);
         b.receiver = r.recv;
         b.t_team = r.t_team;
         b.t_opp = r.t_opp;

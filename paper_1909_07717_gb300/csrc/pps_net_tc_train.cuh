@@ -68,13 +68,18 @@ __device__ __forceinline__ uint4 load8(const __nv_bfloat16* __restrict__ t,
 }
 
 // ------------------------------------------------------ weight gradient
+// Core matrices sit kCm = 144 bytes apart along K (128 of data, 16 of
+// padding): a warp's threads each write one core matrix's eight 16-byte
+// rows at once, and the padding spreads those writes over all banks.
+constexpr int kCm = 144;
+
 template <int CIN, int COUT>
 struct WgradShape {
     static constexpr int N = CIN + 16;           // + the ones column group
     static constexpr int kAChunks = 16;          // 128 slots / 8
     static constexpr int kXChunks = 32;          // 4 rows x 64 slots / 8
-    static constexpr int kABytes = 16 * kAChunks * 128;     // 128 rows
-    static constexpr int kXBytes = (N / 8) * kXChunks * 128;
+    static constexpr int kABytes = 16 * kAChunks * kCm;     // 128 rows
+    static constexpr int kXBytes = (N / 8) * kXChunks * kCm;
     static constexpr int kStage = kABytes + kXBytes;
     static constexpr int kOffBar = 2 * kStage;
     static constexpr int kOffTmem = kOffBar + 16;
@@ -113,7 +118,7 @@ __device__ __forceinline__ void wgrad_stage(const __nv_bfloat16* __restrict__ g,
                 const int row = ok ? q / kRow : 0, col = ok ? q % kRow : W;
                 in[i] = load8<COUT>(g, s, y0 + row, col, cg);
             }
-            dst = A + ((dxi * kCg + cg) * S::kAChunks + c) * 128;
+            dst = A + ((dxi * kCg + cg) * S::kAChunks + c) * kCm;
         } else if (t < kATasks + kXTasks) {
             // X^T[ci][q], q = -64 + 8 c + i: rows y0 - 1 .. y0 + 2
             const int u = t - kATasks;
@@ -123,7 +128,7 @@ __device__ __forceinline__ void wgrad_stage(const __nv_bfloat16* __restrict__ g,
                 const int q = 8 * c + i;  // 0 .. 255 = row y0 - 1 + q / 64
                 in[i] = load8<CIN>(x, s, y0 - 1 + q / kRow, q % kRow, cg);
             }
-            dst = X + (cg * S::kXChunks + c) * 128;
+            dst = X + (cg * S::kXChunks + c) * kCm;
         } else {
             // the ones group: row CIN is 1 at real pixels, the rest 0
             const int c = t - kATasks - kXTasks;
@@ -138,7 +143,7 @@ __device__ __forceinline__ void wgrad_stage(const __nv_bfloat16* __restrict__ g,
                 const uint32_t hi = rowok && c1 < W ? 0x3F80u : 0u;
                 w[j] = lo | (hi << 16);
             }
-            uint4* d = reinterpret_cast<uint4*>(X + (kXg * S::kXChunks + c) * 128);
+            uint4* d = reinterpret_cast<uint4*>(X + (kXg * S::kXChunks + c) * kCm);
             d[0] = make_uint4(w[0], w[1], w[2], w[3]);
 #pragma unroll
             for (int k = 1; k < 8; ++k) d[k] = make_uint4(0u, 0u, 0u, 0u);
@@ -197,17 +202,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncthreads();
         if (threadIdx.x == 0) {
             tc::fence_after_sync();
-            const uint64_t a0 = tc::desc_kmajor(tc::smem_u32(base), 128,
-                                                S::kAChunks * 128);
+            const uint64_t a0 = tc::desc_kmajor(tc::smem_u32(base), kCm,
+                                                S::kAChunks * kCm);
             const uint64_t x0 = tc::desc_kmajor(tc::smem_u32(base + S::kABytes),
-                                                128, S::kXChunks * 128);
+                                                kCm, S::kXChunks * kCm);
+            constexpr int u = kCm / 16;   // a chunk in 16-byte units
 #pragma unroll
             for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
                 for (int ks = 0; ks < 8; ++ks) {
-                    // 16-byte units: two chunks of 128 bytes per K step
-                    const uint64_t a = a0 + (uint64_t)(ks * 16);
-                    const uint64_t xb = x0 + (uint64_t)((8 + 8 * dy + 2 * ks) * 8);
+                    // two chunks per K step of 16
+                    const uint64_t a = a0 + (uint64_t)(2 * ks * u);
+                    const uint64_t xb = x0 + (uint64_t)((8 + 8 * dy + 2 * ks) * u);
                     tc::mma_bf16(tmem + (uint32_t)((dy + 1) * S::N), a, xb, idesc,
                                  (first && ks == 0) ? 0u : 1u);
                 }
