@@ -51,6 +51,7 @@ struct pps_net_scratch {
     int* skip;
     int* list;
     int* list_n;
+    unsigned long long* queue;  // the refinement's work-queue counter
 };
 cudaError_t pps_net_predict(pps_net* net, const pps_state* states, int n,
                             cudaStream_t* st, float** scores, int** cells,

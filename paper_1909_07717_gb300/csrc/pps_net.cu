@@ -36,6 +36,7 @@ struct pps_net {
     int* skip = nullptr;   // proposal scratch: max_batch
     int* list = nullptr;   // proposal scratch: max_batch states to re-search
     int* list_n = nullptr; // proposal scratch: their number
+    unsigned long long* queue = nullptr;  // proposal scratch: work queue
     float* smax = nullptr; // training scratch: max_batch best labels
     int* err = nullptr;    // set by a kernel whose bounded wait ran out
     float* wpart = nullptr;  // weight-gradient partial sums, one row per CTA
@@ -300,6 +301,7 @@ cudaError_t pps_net_predict(pps_net* nt, const pps_state* states, int n,
     scratch->skip = nt->skip;
     scratch->list = nt->list;
     scratch->list_n = nt->list_n;
+    scratch->queue = nt->queue;
     return forward(nt, states, n, false);
 }
 
@@ -360,6 +362,7 @@ extern "C" pps_status pps_net_create(int device, void* stream, int max_batch,
     al(&nt->smax, sizeof(float) * (size_t)max_batch);
     al(&nt->list, sizeof(int) * (size_t)max_batch);
     al(&nt->list_n, sizeof(int));
+    al(&nt->queue, sizeof(unsigned long long));
     al(&nt->err, sizeof(int));
     al(&nt->wpart, sizeof(float) * (size_t)(nt->num_sms > 0 ? nt->num_sms : 1) *
                        (9 * CH * CH + CH));
@@ -383,7 +386,7 @@ extern "C" void pps_net_destroy(pps_net* nt) {
                     (void*)nt->g3, (void*)nt->g4, (void*)nt->out,
                     (void*)nt->loss, (void*)nt->cells, (void*)nt->skip,
                     (void*)nt->smax, (void*)nt->list, (void*)nt->list_n,
-                    (void*)nt->err, (void*)nt->wpart})
+                    (void*)nt->err, (void*)nt->wpart, (void*)nt->queue})
         if (p) cudaFree(p);
     cudaGetLastError();
     delete nt;

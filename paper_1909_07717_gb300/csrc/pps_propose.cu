@@ -28,17 +28,25 @@ constexpr int kFineNx = 481, kFineNy = 361;
 // `prune` an item whose score bound (score_bound: the whole mouth's angle
 // and the last pass-line sample's margin, max over its points) falls below
 // that pass's score is skipped: it cannot hold the best.
+// Items are handed out one at a time from a work-queue counter (zero at
+// launch): pruned items cost a small fraction of evaluated ones, so a
+// static deal would leave most warps idle while a few finish theirs.
+__device__ __forceinline__ long long next_item(unsigned long long* queue,
+                                               int lane) {
+    unsigned long long q = 0ull;
+    if (lane == 0) q = atomicAdd(queue, 1ull);
+    return (long long)__shfl_sync(0xffffffffu, q, 0);
+}
+
 template <int JMAX, int VMAX>
 __global__ void __launch_bounds__(pps::search_tpb<JMAX, VMAX>(), 1)
     refine_kernel(const pps::SearchArgs a, const int* __restrict__ cells,
-                  int topk, bool prune) {
-    constexpr int kWarps = pps::search_tpb<JMAX, VMAX>() / 32;
+                  int topk, bool prune, unsigned long long* queue) {
     const int lane = threadIdx.x & 31;
-    const long long warps = (long long)gridDim.x * kWarps;
-    const long long gw = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const long long n_items = (long long)a.n_states * topk * 2;
     const pps::ItemGrid gr{a.g, a.x0, a.y0, a.V};
-    for (long long item = gw; item < n_items; item += warps) {
+    for (long long item = next_item(queue, lane); item < n_items;
+         item = next_item(queue, lane)) {
         const int r = (int)(item / a.n_states);     // rank x 2 + half
         const int s = (int)(item - (long long)r * a.n_states);
         const int cell = cells[(long long)s * topk + (r >> 1)];
@@ -126,7 +134,10 @@ cudaError_t run(const pps::SearchArgs& base, const int* cells, int topk,
     constexpr int tpb = pps::search_tpb<J, V>();
     long long grid = (items + tpb / 32 - 1) / (tpb / 32);
     if (grid > cap) grid = cap;
-    refine_kernel<J, V><<<(unsigned)grid, tpb, 0, st>>>(a, cells, topk, prune);
+    e = cudaMemsetAsync(ns.queue, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    refine_kernel<J, V><<<(unsigned)grid, tpb, 0, st>>>(a, cells, topk, prune,
+                                                        ns.queue);
     pps::finalize_kernel<J, V><<<(a.n_states + 127) / 128, 128, 0, st>>>(a);
     if (!fallback) return cudaGetLastError();
     e = cudaMemsetAsync(ns.list_n, 0, sizeof(int), st);
@@ -241,14 +252,13 @@ __device__ __forceinline__ void reduce_item(const JobsArgs& a, int s,
 
 template <int JMAX, int VMAX>
 __global__ void __launch_bounds__(pps::search_tpb<JMAX, VMAX>(), 1)
-    refine_jobs_kernel(const JobsArgs a, bool prune) {
-    constexpr int kWarps = pps::search_tpb<JMAX, VMAX>() / 32;
+    refine_jobs_kernel(const JobsArgs a, bool prune,
+                       unsigned long long* queue) {
     const int lane = threadIdx.x & 31;
-    const long long warps = (long long)gridDim.x * kWarps;
-    const long long gw = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const long long n_items = (long long)a.n * a.items_per_state;
     const int m2 = a.m * a.m;
-    for (long long item = gw; item < n_items; item += warps) {
+    for (long long item = next_item(queue, lane); item < n_items;
+         item = next_item(queue, lane)) {
         const int q = (int)(item / a.n);
         const int s = (int)(item - (long long)q * a.n);
         JobCells jc;
@@ -394,7 +404,10 @@ cudaError_t run_jobs(JobsArgs a, bool fallback, bool prune,
     const long long items = (long long)a.n * a.items_per_state;
     long long grid = (items + tpb / 32 - 1) / (tpb / 32);
     if (grid > cap) grid = cap;
-    refine_jobs_kernel<J, V><<<(unsigned)grid, tpb, 0, st>>>(a, prune);
+    e = cudaMemsetAsync(ns.queue, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    refine_jobs_kernel<J, V><<<(unsigned)grid, tpb, 0, st>>>(a, prune,
+                                                             ns.queue);
     jobs_finalize_kernel<J, V><<<(a.n + 127) / 128, 128, 0, st>>>(a, false);
     if (!fallback) return cudaGetLastError();
     e = cudaMemsetAsync(ns.list_n, 0, sizeof(int), st);
