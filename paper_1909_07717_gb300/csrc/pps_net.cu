@@ -117,18 +117,19 @@ cudaError_t forward_loaded(pps_net* nt, int n, bool layers, bool keep = false,
     const unsigned g = blocks(P, 64);
     cudaStream_t st = nt->stream;
     if (!layers) {
+        auto kernel = keep ? tcf::tc_forward_kernel<true>
+                           : tcf::tc_forward_kernel<false>;
         cudaError_t e = cudaFuncSetAttribute(
-            tcf::tc_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
             (int)tcf::kSmemBytes);
         if (e != cudaSuccess) return e;
         const long long units = (long long)n * tcf::kBands;
         const unsigned grid =
             (unsigned)(units < nt->num_sms ? units : nt->num_sms);
-        tcf::tc_forward_kernel<<<grid, tcf::kThreads, tcf::kSmemBytes, st>>>(
+        kernel<<<grid, tcf::kThreads, tcf::kSmemBytes, st>>>(
             nt->a0, n, nt->Wf, nt->w, nt->out, wf_off(1), wf_off(2), wf_off(3),
             bias_off(0), bias_off(1), bias_off(2), bias_off(3), nt->err,
-            withhold ? 1 : 0, keep ? nt->a1 : nullptr, keep ? nt->a2 : nullptr,
-            keep ? nt->a3 : nullptr);
+            withhold ? 1 : 0, nt->a1, nt->a2, nt->a3);
         return cudaGetLastError();
     }
     conv_kernel<C0, CH, kHidden><<<g, 128, 0, st>>>(

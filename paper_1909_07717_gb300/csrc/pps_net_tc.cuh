@@ -124,6 +124,7 @@ __device__ __forceinline__ void issue(uint32_t tmem, const uint8_t* in,
 // With act (training), the band's own rows y0 .. y0 + kBand - 1 of the
 // activations also go to act[s][y][x][32] in device memory for the
 // backward pass (the halo rows are other bands' own rows).
+template <bool KEEP>
 __device__ __forceinline__ bool epi_hidden(uint32_t tmem, int ntiles,
                                            const float* __restrict__ bias,
                                            int y_first, uint8_t* out,
@@ -142,7 +143,7 @@ __device__ __forceinline__ bool epi_hidden(uint32_t tmem, int ntiles,
         const int r = 32 * q + lane, row = 2 * j + (r >> 6), col = r & 63;
         const int Y = y_first + row;
         const bool in_map = Y >= 0 && Y < H && col < W;
-        const bool own = act && in_map && Y >= y0 && Y < y0 + kBand;
+        const bool own = KEEP && in_map && Y >= y0 && Y < y0 + kBand;
         uint4* ga = own ? reinterpret_cast<uint4*>(
                               act + ((long long)s * NPIX + Y * W + col) * CH)
                         : nullptr;
@@ -158,12 +159,15 @@ __device__ __forceinline__ bool epi_hidden(uint32_t tmem, int ntiles,
                               : 0u;
             }
             reinterpret_cast<uint4*>(out)[k * slots_out + kLead + row * kRow + col] = o;
-            if (own) ga[k] = o;
+            if (KEEP && own) ga[k] = o;
         }
     }
     return ok;
 }
 
+// KEEP (training): the hidden activations of each band's own rows also go
+// to act1..act3; the inference instance carries none of that.
+template <bool KEEP>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_forward_kernel(const __nv_bfloat16* __restrict__ a0, int n,
                       const __nv_bfloat16* __restrict__ Wf,
@@ -239,16 +243,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                       t4 = kBand / 2;
         if (!start_layer([&] { issue<C0, CH>(tmem, bin, kSlotsIn, smem + kOffW0, t1, bars); }))
             break;
-        end_layer(t1, epi_hidden(tmem, t1, w32 + b0, y0 - 3, ba, kSlotsA, bars,
+        end_layer(t1, epi_hidden<KEEP>(tmem, t1, w32 + b0, y0 - 3, ba, kSlotsA, bars,
                                  phases, polls, act1, s, y0));
         if (!start_layer([&] { issue<CH, CH>(tmem, ba, kSlotsA, smem + kOffW1, t2, bars); }))
             break;
         if (u + gridDim.x < units) prefetch(a0, u + gridDim.x, bin);
-        end_layer(t2, epi_hidden(tmem, t2, w32 + b1, y0 - 2, bb, kSlotsB, bars,
+        end_layer(t2, epi_hidden<KEEP>(tmem, t2, w32 + b1, y0 - 2, bb, kSlotsB, bars,
                                  phases, polls, act2, s, y0));
         if (!start_layer([&] { issue<CH, CH>(tmem, bb, kSlotsB, smem + kOffW2, t3, bars); }))
             break;
-        end_layer(t3, epi_hidden(tmem, t3, w32 + b2, y0 - 1, ba, kSlotsA, bars,
+        end_layer(t3, epi_hidden<KEEP>(tmem, t3, w32 + b2, y0 - 1, ba, kSlotsA, bars,
                                  phases, polls, act3, s, y0));
         // layer 4: A -> the output map (+ the coarse-score input channel)
         if (!start_layer([&] { issue<CH, kNOut>(tmem, ba, kSlotsA, smem + kOffW3, t4, bars); }))
