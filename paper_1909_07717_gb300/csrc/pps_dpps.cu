@@ -4,11 +4,16 @@
 // is searched for the first teammate and the first opponent that can reach
 // it (SBIP, Sec. 4.2), and feasible candidates get the Sec. 4.3 score.
 //
-// One warp per (state, direction, 32 powers), one lane per candidate.  A
-// group's robots sit in registers as pairs (two robots per packed f32x2
-// instruction, the same intercept arithmetic as the receive-point search);
-// the teammates are searched first, the opponents only for candidates a
-// teammate receives.  Each lane stops at its group's first interception.
+// Work items are chunks of 1024 consecutive candidates of one state, taken
+// by warps from a queue.  A warp's lanes are persistent: each lane holds one
+// candidate and takes one ball-path sample per loop trip -- the teammates
+// first, the opponents only if a teammate receives -- and takes the next
+// candidate as soon as its current one ends, so no lane idles while the
+// chunk has candidates left.  Paths are prepared 32 at a time by the whole
+// warp; feasible candidates wait in shared memory and are scored 32 at a
+// time.  The state's two robot groups sit in shared memory as pairs (two
+// robots per packed f32x2 instruction, the same intercept arithmetic as the
+// receive-point search).
 
 #include <cuda_runtime.h>
 
@@ -27,12 +32,15 @@ namespace {
 using pps::OppRegs;
 
 constexpr int kTPB = 512;
-constexpr long long kMaxRun = 64;
+constexpr int kWarps = kTPB / 32;
+constexpr int kChunk = 1024;  // candidates per work item, a multiple of 32
+constexpr int kRing = 64;     // prepared paths a warp holds (a power of 2, > 62)
+constexpr int kPend = 64;     // feasible candidates awaiting a score (> 62)
+constexpr unsigned kFull = 0xffffffffu;
 
 struct DArgs {
     const pps_dstate* states;
     int n_states;
-    int chunks;  // ceil(n_pow / 32)
     int words;   // mask words per state
     int kmax;
     pps_dparams prm;
@@ -41,6 +49,7 @@ struct DArgs {
     float* dbg;      // may be null: t_team, t_opp, score per candidate
     unsigned long long* keys;
     int* counts;
+    unsigned long long* queue;  // work-item counter, zero at launch
 };
 
 // Per-state constants (validity as in derive_state, for both groups).
@@ -230,15 +239,11 @@ struct DRes {
     bool feas;
 };
 
-// Everything for one candidate (dir, pw); shared by the search and the
-// finalize kernels so that both give the same numbers.
-template <int J>
-__device__ __forceinline__ void dpps_eval(const pps_dstate& st,
-                                          const DStateK& sk,
-                                          const pps_dparams& prm, int dir,
-                                          int pw, bool active,
-                                          const OppRegs<J>& team,
-                                          const OppRegs<J>& opp, DRes& r) {
+// The ball's path of candidate (dir, pw): direction 2 pi dir / n_dir,
+// rolling speed slide x the pw-th kick power, length up to its stop or the
+// field edge, whichever comes first.
+__device__ __forceinline__ Path dpps_path(const pps_dstate& st, const DStateK& sk,
+                                          const pps_dparams& prm, int dir, int pw) {
     Path p;
     float sn, cs;
     sincospif(__fdiv_rn(2.f * (float)dir, (float)prm.n_dir), &sn, &cs);
@@ -261,7 +266,60 @@ __device__ __forceinline__ void dpps_eval(const pps_dstate& st,
     s_out = fmaxf(s_out, 0.f);
     p.stopped = s_stop <= s_out;
     p.S = p.stopped ? s_stop : s_out;
+    return p;
+}
 
+// Sec. 4.3 score of a feasible candidate along (ux, uy), received at
+// (rx, ry) at t_team, first reached by an opponent at t_opp.
+template <int J>
+__device__ __forceinline__ float dpps_score(const pps_dstate& st, const DStateK& sk,
+                                            const pps_dparams& prm, float ux,
+                                            float uy, float t_team, float t_opp,
+                                            float rx, float ry) {
+    const float gx = __fsub_rn(sk.hl, rx);
+    const float theta = pps::shot_angle_of<J>(st.opp_pos, sk.nopp, sk.hw,
+                                              rx < sk.hl, rx, ry, gx,
+                                              prm.robot_radius);
+    const float dg = __fsqrt_rn(__fmaf_rn(gx, gx, __fmul_rn(ry, ry)));
+    // the turn from the pass direction u to the shot direction g - r, as
+    // atan2(|u x (g - r)|, u . (g - r)): the same angle as the acos of the
+    // normalised dot product, without its loss of precision when the two
+    // directions nearly agree
+    float refr = 0.f;
+    if (dg > 0.f) {
+        const float dot = __fmaf_rn(ux, gx, __fmul_rn(uy, -ry));
+        const float crs = __fmaf_rn(ux, -ry, -__fmul_rn(uy, gx));
+        refr = atan2f(fabsf(crs), dot);
+    }
+    const float delta = __fsub_rn(t_opp, t_team);
+    const float inv_pi = 0.318309886183790672f;
+    float sc = -__fmul_rn(prm.w_time, t_team);
+    sc = __fadd_rn(sc, __fmul_rn(prm.w_angle, __fmul_rn(theta, inv_pi)));
+    sc = __fsub_rn(sc, __fmul_rn(prm.w_dist, __fmul_rn(dg, sk.inv_diag)));
+    sc = __fsub_rn(sc, __fmul_rn(prm.w_refr, __fmul_rn(refr, inv_pi)));
+    sc = __fadd_rn(sc, __fmul_rn(prm.w_delta, fminf(delta, prm.delta_cap)));
+    return sc;
+}
+
+// The receive point: sample k_team of K along the path.
+__device__ __forceinline__ void receive_point(const DStateK& sk, float ux, float uy,
+                                              float S, int k_team, float& rx,
+                                              float& ry) {
+    const float s = __fmul_rn(__fmul_rn((float)k_team, sk.invK), S);
+    rx = __fmaf_rn(s, ux, sk.bx);
+    ry = __fmaf_rn(s, uy, sk.by);
+}
+
+// Everything for one candidate (dir, pw), one candidate a thread: the
+// finalize kernel's check of the search's best.
+template <int J>
+__device__ __forceinline__ void dpps_eval(const pps_dstate& st,
+                                          const DStateK& sk,
+                                          const pps_dparams& prm, int dir,
+                                          int pw, bool active,
+                                          const OppRegs<J>& team,
+                                          const OppRegs<J>& opp, DRes& r) {
+    const Path p = dpps_path(st, sk, prm, dir, pw);
     r.feas = false;
     r.score = -CUDART_INF_F;
     r.t_opp = CUDART_INF_F;
@@ -274,104 +332,314 @@ __device__ __forceinline__ void dpps_eval(const pps_dstate& st,
     }
     // Sec. 4.3: safe when the first opponent comes more than tau later
     r.feas = got && __fsub_rn(r.t_opp, r.t_team) > prm.tau_delta;
-    if (got) {
-        const float s = __fmul_rn(__fmul_rn((float)r.k_team, sk.invK), p.S);
-        r.rx = __fmaf_rn(s, p.ux, sk.bx);
-        r.ry = __fmaf_rn(s, p.uy, sk.by);
+    if (got) receive_point(sk, p.ux, p.uy, p.S, r.k_team, r.rx, r.ry);
+    if (r.feas)
+        r.score = dpps_score<J>(st, sk, prm, p.ux, p.uy, r.t_team, r.t_opp,
+                                r.rx, r.ry);
+}
+
+// Sample f of the pass (cbx, cby) against a group in shared memory
+// (16-byte aligned), two robot pairs to a 16-byte load: per robot the
+// arithmetic of opp_min, and its minimum tree.
+template <int J, bool GEN>
+__device__ __forceinline__ float group_min_smem(float f, float cbx, float cby,
+                                                const OppRegs<J>& g, float reach) {
+    static_assert(J % 4 == 0, "pairs are read two at a time");
+    const float2 f2 = make_float2(f, f), cx2 = make_float2(cbx, cbx),
+                 cy2 = make_float2(cby, cby);
+    float t[J];
+#pragma unroll
+    for (int i = 0; i < J / 2; i += 2) {
+        const float4 bx = *reinterpret_cast<const float4*>(&g.bx[i]);
+        const float4 by = *reinterpret_cast<const float4*>(&g.by[i]);
+        const float4 ux = *reinterpret_cast<const float4*>(&g.ux[i]);
+        const float4 uy = *reinterpret_cast<const float4*>(&g.uy[i]);
+        float2 r = pps::sbip_num2<GEN>(f2, cx2, cy2, make_float2(bx.x, bx.y),
+                                       make_float2(by.x, by.y), make_float2(ux.x, ux.y),
+                                       make_float2(uy.x, uy.y), reach);
+        t[2 * i] = r.x;
+        t[2 * i + 1] = r.y;
+        r = pps::sbip_num2<GEN>(f2, cx2, cy2, make_float2(bx.z, bx.w),
+                                make_float2(by.z, by.w), make_float2(ux.z, ux.w),
+                                make_float2(uy.z, uy.w), reach);
+        t[2 * i + 2] = r.x;
+        t[2 * i + 3] = r.y;
     }
-    if (r.feas) {
-        const float gx = __fsub_rn(sk.hl, r.rx);
-        const float theta = pps::shot_angle_of<J>(st.opp_pos, sk.nopp, sk.hw,
-                                                  r.rx < sk.hl, r.rx, r.ry, gx,
-                                                  prm.robot_radius);
-        const float dg = __fsqrt_rn(__fmaf_rn(gx, gx, __fmul_rn(r.ry, r.ry)));
-        // the turn from the pass direction u to the shot direction g - r,
-        // as atan2(|u x (g - r)|, u . (g - r)): the same angle as the acos
-        // of the normalised dot product, without its loss of precision
-        // when the two directions nearly agree
-        float refr = 0.f;
-        if (dg > 0.f) {
-            const float dot = __fmaf_rn(p.ux, gx, __fmul_rn(p.uy, -r.ry));
-            const float crs = __fmaf_rn(p.ux, -r.ry, -__fmul_rn(p.uy, gx));
-            refr = atan2f(fabsf(crs), dot);
+#pragma unroll
+    for (int w = 1; w < J; w *= 2)
+#pragma unroll
+        for (int j = 0; j + w < J; j += 2 * w) t[j] = fminf(t[j], t[j + w]);
+    return t[0];
+}
+
+// A warp's shared memory: the state's constants and two robot groups, the
+// prepared paths, each lane's current candidate, the feasible candidates
+// awaiting their score, the lanes' argmax keys and counts, and the chunk's
+// mask words.  What the sample loop reads only when a phase ends lives
+// here rather than in registers.
+template <int J>
+struct __align__(16) WarpSmem {
+    DStateK sk;
+    alignas(16) OppRegs<J> team;
+    float pad[4];  // the opponents 16 bytes further on, so that lanes in the
+                   // two phases read the same robot slot from other banks
+    OppRegs<J> opp;
+    float ring[5][kRing];  // prepared paths: ux, uy, v, S, stopped
+    float cur[10][32];     // the lane's candidate: ux, uy, S, t_team, k_team,
+                           // and its sample terms cbx, cby, v^2, 2 a S, v
+    float pend[7][kPend];  // candidate (bits), t_team, t_opp, rx, ry, ux, uy
+    unsigned long long key[32];
+    int cnt[32];
+    uint32_t mask[kChunk / 32];
+};
+
+// Score the feasible candidate in pending slot `slot` and fold it into the
+// lane's argmax key and count.
+template <int J>
+__device__ __noinline__ void score_pending(const DArgs& a, const pps_dstate& st,
+                                           int s, WarpSmem<J>& w, int slot, int lane) {
+    const uint32_t idx = __float_as_uint(w.pend[0][slot]);
+    const float t_team = w.pend[1][slot], t_opp = w.pend[2][slot];
+    const float sc = dpps_score<J>(st, w.sk, a.prm, w.pend[5][slot], w.pend[6][slot],
+                                   t_team, t_opp, w.pend[3][slot], w.pend[4][slot]);
+    const unsigned long long k =
+        ((unsigned long long)pps::order_bits(sc) << 32) | (unsigned long long)(~idx);
+    if (k > w.key[lane]) w.key[lane] = k;
+    ++w.cnt[lane];
+    if (a.dbg) {
+        float* d = a.dbg + ((long long)s * a.prm.n_dir * a.prm.n_pow + idx) * 3;
+        d[0] = t_team;
+        d[1] = t_opp;
+        d[2] = sc;
+    }
+}
+
+// The path of candidate c into its ring slot.
+template <int J>
+__device__ __noinline__ void prepare_path(const DArgs& a, const pps_dstate& st,
+                                          WarpSmem<J>& w, int c) {
+    const int dir = c / a.prm.n_pow;
+    const Path p = dpps_path(st, w.sk, a.prm, dir, c - dir * a.prm.n_pow);
+    const int slot = c & (kRing - 1);
+    w.ring[0][slot] = p.ux;
+    w.ring[1][slot] = p.uy;
+    w.ring[2][slot] = p.v;
+    w.ring[3][slot] = p.S;
+    w.ring[4][slot] = p.stopped ? 1.f : 0.f;
+}
+
+// Candidates [c0, c1) of state s (c0 a multiple of kChunk) with persistent
+// lanes, two samples a loop trip.  Per lane and phase the samples k = 1..K
+// are taken in order and the phase ends at the first interception, exactly
+// as group_first does: the same arithmetic on the same values, so every
+// time and score equals the one-candidate-a-thread evaluation bit for bit
+// (a trip's second sample is discarded when the first ends the phase).
+template <int J, bool GEN>
+__device__ __forceinline__ void run_chunk(const DArgs& a, const pps_dstate& st, int s,
+                                          int c0, int c1, WarpSmem<J>& w, int lane) {
+    const DStateK& sk = w.sk;
+    const unsigned lt = (1u << lane) - 1u;
+    w.mask[lane] = 0u;  // kChunk / 32 == 32 words, one a lane
+    w.key[lane] = 0ull;
+    w.cnt[lane] = 0;
+    __syncwarp();
+    // prepared paths wait in ring slot c mod kRing (c0 is a multiple of
+    // kRing, and at most 63 candidates are ever prepared and not taken)
+    int next = c0;   // first candidate not yet prepared
+    int taken = c0;  // first prepared candidate not yet handed out
+    int npend = 0;
+    int cand = -1, k = 0;
+    bool opp = false, stopped = false;
+    for (;;) {
+        const unsigned need = __ballot_sync(kFull, cand < 0);
+        if (need) {
+            const int want = __popc(need);
+            if (next - taken < want && next < c1) {
+                // the next (up to) 32 paths, one a lane; at most 31 are
+                // waiting, so the ring's 64 slots never overrun
+                __syncwarp();
+                if (next + lane < c1) prepare_path<J>(a, st, w, next + lane);
+                next = min(next + 32, c1);
+                __syncwarp();
+            }
+            const int r = __popc(need & lt);
+            if (cand < 0 && taken + r < next) {
+                const int slot = (taken + r) & (kRing - 1);
+                const float ux = w.ring[0][slot], uy = w.ring[1][slot];
+                const float S = w.ring[3][slot];
+                const float v = w.ring[2][slot];
+                stopped = w.ring[4][slot] != 0.f;
+                w.cur[0][lane] = ux;
+                w.cur[1][lane] = uy;
+                w.cur[2][lane] = S;
+                w.cur[5][lane] = __fmul_rn(sk.kappa, __fmul_rn(S, ux));
+                w.cur[6][lane] = __fmul_rn(sk.kappa, __fmul_rn(S, uy));
+                w.cur[7][lane] = __fmul_rn(v, v);
+                w.cur[8][lane] = __fmul_rn(sk.two_ab, S);
+                w.cur[9][lane] = v;
+                cand = taken + r;
+                opp = false;
+                k = 1;
+            }
+            taken += min(want, next - taken);
         }
-        const float delta = __fsub_rn(r.t_opp, r.t_team);
-        const float inv_pi = 0.318309886183790672f;
-        float sc = -__fmul_rn(prm.w_time, r.t_team);
-        sc = __fadd_rn(sc, __fmul_rn(prm.w_angle, __fmul_rn(theta, inv_pi)));
-        sc = __fsub_rn(sc, __fmul_rn(prm.w_dist, __fmul_rn(dg, sk.inv_diag)));
-        sc = __fsub_rn(sc, __fmul_rn(prm.w_refr, __fmul_rn(refr, inv_pi)));
-        sc = __fadd_rn(sc, __fmul_rn(prm.w_delta, fminf(delta, prm.delta_cap)));
-        r.score = sc;
+        if (__all_sync(kFull, cand < 0)) break;
+
+        // samples k and k + 1 of the lane's current phase: the first of
+        // them (up to K) at which the group gets the ball ends the phase
+        bool done = false, feas = false;
+        float t_opp = CUDART_INF_F;
+        if (cand >= 0) {
+            const OppRegs<J>& g = opp ? w.opp : w.team;
+            const float cbx = w.cur[5][lane], cby = w.cur[6][lane], v2 = w.cur[7][lane],
+                        twoaS = w.cur[8][lane], v = w.cur[9][lane];
+            const float f0 = __fmul_rn((float)k, sk.invK);
+            const float f1 = __fmul_rn((float)(k + 1), sk.invK);
+            const float n0 = group_min_smem<J, GEN>(f0, cbx, cby, g, sk.reach);
+            const float n1 = group_min_smem<J, GEN>(f1, cbx, cby, g, sk.reach);
+            int kk = k;
+            float f = f0, n = n0;
+            bool end = k == sk.K;
+            // at the stop the group always gets the ball
+            bool stop = stopped && end;
+            float root = pps::sqrt_ball(fmaxf(__fmaf_rn(-f0, twoaS, v2), 0.f));
+            bool hit = stop || __fadd_rn(__fmul_rn(n0, sk.at_scale), root) <= v;
+            if (!hit && !end) {
+                kk = k + 1;
+                f = f1;
+                n = n1;
+                end = kk == sk.K;
+                stop = stopped && end;
+                root = pps::sqrt_ball(fmaxf(__fmaf_rn(-f1, twoaS, v2), 0.f));
+                hit = stop || __fadd_rn(__fmul_rn(n1, sk.at_scale), root) <= v;
+            }
+            float t = CUDART_INF_F;
+            if (stop)
+                t = fmaxf(__fmul_rn(n, sk.t_scale), __fdiv_rn(v, sk.ab));
+            else if (hit)
+                // t_ball(s) = 2 s / (v + sqrt(v^2 - 2 a s))
+                t = __fdiv_rn(__fmul_rn(2.f, __fmul_rn(f, w.cur[2][lane])),
+                              __fadd_rn(v, root));
+            end = end || hit;
+            if (end && !opp && t < CUDART_INF_F) {
+                // a teammate receives: search the opponents from sample 1
+                w.cur[3][lane] = t;
+                w.cur[4][lane] = __int_as_float(kk);
+                opp = true;
+                k = 1;
+            } else if (end) {
+                done = true;
+                if (!opp) {
+                    w.cur[3][lane] = CUDART_INF_F;
+                } else {
+                    t_opp = t;
+                    // Sec. 4.3: safe when the first opponent comes more
+                    // than tau later
+                    feas = __fsub_rn(t_opp, w.cur[3][lane]) > a.prm.tau_delta;
+                }
+            } else {
+                k += 2;
+            }
+        }
+        const unsigned fm = __ballot_sync(kFull, feas);
+        if (feas) {
+            const int slot = npend + __popc(fm & lt);
+            const float ux = w.cur[0][lane], uy = w.cur[1][lane];
+            float rx, ry;
+            receive_point(sk, ux, uy, w.cur[2][lane], __float_as_int(w.cur[4][lane]),
+                          rx, ry);
+            w.pend[0][slot] = __uint_as_float((uint32_t)cand);
+            w.pend[1][slot] = w.cur[3][lane];
+            w.pend[2][slot] = t_opp;
+            w.pend[3][slot] = rx;
+            w.pend[4][slot] = ry;
+            w.pend[5][slot] = ux;
+            w.pend[6][slot] = uy;
+            atomicOr(&w.mask[(cand & (kChunk - 1)) >> 5], 1u << (cand & 31));
+        } else if (done && a.dbg) {
+            float* d = a.dbg + ((long long)s * a.prm.n_dir * a.prm.n_pow + cand) * 3;
+            d[0] = w.cur[3][lane];
+            d[1] = t_opp;
+            d[2] = -CUDART_INF_F;
+        }
+        if (done) cand = -1;
+        npend += __popc(fm);
+        if (npend >= 32) {
+            // a full warp of scores (at most 31 stay behind, so the 64
+            // pending slots never overrun)
+            __syncwarp();
+            npend -= 32;
+            score_pending<J>(a, st, s, w, npend + lane, lane);
+            __syncwarp();
+        }
+    }
+    __syncwarp();
+    if (lane < npend) score_pending<J>(a, st, s, w, lane, lane);
+    if (a.mask) {
+        const int c = c0 + 32 * lane;
+        if (c < c1) a.mask[(long long)s * a.words + (c >> 5)] = w.mask[lane];
+    }
+    const unsigned long long key = pps::warp_max_u64(w.key[lane]);
+    const int cnt = __reduce_add_sync(kFull, w.cnt[lane]);
+    if (lane == 0) {
+        if (key) atomicMax(a.keys + s, key);
+        if (cnt) atomicAdd(a.counts + s, cnt);
+    }
+    __syncwarp();
+}
+
+// An invalid state: no candidate is feasible; its mask words are zero.
+__device__ __forceinline__ void invalid_chunk(const DArgs& a, int s, long long P,
+                                              int c0, int c1, int lane) {
+    if (a.dbg)
+        for (int c = c0 + lane; c < c1; c += 32) {
+            float* d = a.dbg + ((long long)s * P + c) * 3;
+            d[0] = CUDART_INF_F;
+            d[1] = CUDART_INF_F;
+            d[2] = -CUDART_INF_F;
+        }
+    if (a.mask) {
+        const int c = c0 + 32 * lane;
+        if (c < c1) a.mask[(long long)s * a.words + (c >> 5)] = 0u;
     }
 }
 
 template <int J>
 __global__ void __launch_bounds__(kTPB, 2) dpps_kernel(const DArgs a) {
+    extern __shared__ __align__(16) unsigned char dpps_smem[];
+    WarpSmem<J>& w = reinterpret_cast<WarpSmem<J>*>(dpps_smem)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
-    const long long warps = (long long)gridDim.x * (kTPB / 32);
-    const long long gw = (long long)blockIdx.x * (kTPB / 32) + (threadIdx.x >> 5);
-    const long long per_state = (long long)a.prm.n_dir * a.chunks;
-    const long long n_items = (long long)a.n_states * per_state;
-    // runs of R consecutive items (mostly one state), dealt round-robin, as
-    // in the receive-point search; the state's constants once per run
-    const long long R = n_items >= warps * 8 * kMaxRun
-                            ? kMaxRun
-                            : (n_items >= warps * 8 ? n_items / (warps * 8) : 1);
-    // the warp's state's two robot groups, in shared memory: every lane
-    // reads the same robot at the same time (a broadcast), and the groups
-    // need no registers
-    __shared__ OppRegs<J> groups[kTPB / 32][2];
-    OppRegs<J>& team = groups[threadIdx.x >> 5][0];
-    OppRegs<J>& opp = groups[threadIdx.x >> 5][1];
+    const long long P = (long long)a.prm.n_dir * a.prm.n_pow;
+    const long long per_state = (P + kChunk - 1) / kChunk;
+    const unsigned long long n_items = (unsigned long long)a.n_states * per_state;
     int cur = -1;
-    DStateK sk;
-    for (long long item = gw * R, j = 0; item < n_items;
-         item = (++j == R) ? (j = 0, item - (R - 1) + warps * R) : item + 1) {
-        const int s = (int)(item / per_state);
-        const int rem = (int)(item - (long long)s * per_state);
-        const int dir = rem / a.chunks, chunk = rem - dir * a.chunks;
-        const int pw = chunk * 32 + lane;
-        const bool active = pw < a.prm.n_pow;
+    const DStateK& sk = w.sk;
+    for (;;) {
+        unsigned long long item = 0ull;
+        if (lane == 0) item = atomicAdd(a.queue, 1ull);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= n_items) break;
+        const int s = (int)(item / (unsigned long long)per_state);
+        const int c0 = (int)(item - (unsigned long long)s * per_state) * kChunk;
+        const int c1 = (int)min((long long)c0 + kChunk, P);
         const pps_dstate& st = a.states[s];
         if (s != cur) {
-            sk = derive_dstate<J>(st, a.prm, a.kmax);
             cur = s;
             __syncwarp();
             if (lane == 0) {
-                load_group<J>(st.team_pos, st.team_vel, sk.nteam, sk, team);
-                load_group<J>(st.opp_pos, st.opp_vel, sk.nopp, sk, opp);
+                const DStateK d = derive_dstate<J>(st, a.prm, a.kmax);
+                w.sk = d;
+                load_group<J>(st.team_pos, st.team_vel, d.nteam, d, w.team);
+                load_group<J>(st.opp_pos, st.opp_vel, d.nopp, d, w.opp);
             }
             __syncwarp();
         }
-        DRes r;
-        dpps_eval<J>(st, sk, a.prm, dir, active ? pw : 0, active, team, opp, r);
-        const bool f = active && r.feas;
-        const uint32_t idx = (uint32_t)(dir * a.prm.n_pow + pw);
-        if (a.dbg && active) {
-            float* d = a.dbg + ((long long)s * a.prm.n_dir * a.prm.n_pow + idx) * 3;
-            d[0] = r.t_team;
-            d[1] = r.t_opp;
-            d[2] = r.score;
-        }
-        if (a.mask) {
-            if ((a.prm.n_pow & 31) == 0) {
-                const uint32_t word = __ballot_sync(0xffffffffu, f);
-                if (lane == 0) a.mask[(long long)s * a.words + idx / 32] = word;
-            } else if (f) {
-                atomicOr(a.mask + (long long)s * a.words + idx / 32, 1u << (idx & 31));
-            }
-        }
-        unsigned long long key = 0ull;
-        if (f)
-            key = ((unsigned long long)pps::order_bits(r.score) << 32) |
-                  (unsigned long long)(~idx);
-        key = pps::warp_max_u64(key);
-        const int cnt = __reduce_add_sync(0xffffffffu, f ? 1 : 0);
-        if (lane == 0) {
-            if (key) atomicMax(a.keys + s, key);
-            if (cnt) atomicAdd(a.counts + s, cnt);
-        }
+        if (!sk.valid)
+            invalid_chunk(a, s, P, c0, c1, lane);
+        else if (sk.general)
+            run_chunk<J, true>(a, st, s, c0, c1, w, lane);
+        else
+            run_chunk<J, false>(a, st, s, c0, c1, w, lane);
     }
 }
 
@@ -538,11 +806,18 @@ __global__ void __launch_bounds__(128)
 
 template <int J>
 cudaError_t launch(const DArgs& a, int num_sms, cudaStream_t st) {
-    const int occ = pps_occupancy((const void*)dpps_kernel<J>, kTPB, 0);
-    const long long items = (long long)a.n_states * a.prm.n_dir * a.chunks;
-    long long grid = (items + kTPB / 32 - 1) / (kTPB / 32);
+    const size_t smem = sizeof(WarpSmem<J>) * kWarps;
+    cudaError_t e = cudaFuncSetAttribute(
+        dpps_kernel<J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int occ = pps_occupancy((const void*)dpps_kernel<J>, kTPB, smem);
+    const long long P = (long long)a.prm.n_dir * a.prm.n_pow;
+    const long long items = (long long)a.n_states * ((P + kChunk - 1) / kChunk);
+    long long grid = (items + kWarps - 1) / kWarps;
     if (grid > (long long)num_sms * occ) grid = (long long)num_sms * occ;
-    dpps_kernel<J><<<(unsigned)grid, kTPB, 0, st>>>(a);
+    e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    dpps_kernel<J><<<(unsigned)grid, kTPB, smem, st>>>(a);
     dpps_finalize<J><<<(a.n_states + 127) / 128, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
@@ -604,7 +879,6 @@ extern "C" pps_status pps_dpps_search(pps_ctx* ctx, const pps_dstate* states,
     std::memset(&a, 0, sizeof a);
     a.states = states;
     a.n_states = n_states;
-    a.chunks = (p.n_pow + 31) / 32;
     a.words = (int)pps_dpps_mask_words(&p);
     a.kmax = pps_ctx_max_K(ctx);
     a.prm = p;
@@ -612,12 +886,11 @@ extern "C" pps_status pps_dpps_search(pps_ctx* ctx, const pps_dstate* states,
     a.mask = out_mask;
     a.dbg = out_dbg;
     pps_ctx_scratch(ctx, &a.keys, &a.counts);
+    a.queue = pps_ctx_work_counter(ctx);
     cudaStream_t st = pps_ctx_stream(ctx);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(a.keys, 0, sizeof(unsigned long long) * n_states, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.counts, 0, sizeof(int) * n_states, st);
-    if (e == cudaSuccess && out_mask && (p.n_pow & 31) != 0)
-        e = cudaMemsetAsync(out_mask, 0, sizeof(uint32_t) * (size_t)a.words * n_states, st);
     if (e == cudaSuccess) {
         const int sms = pps_ctx_num_sms(ctx);
         e = pps_ctx_jmax(ctx) == 8 ? launch<8>(a, sms, st) : launch<16>(a, sms, st);

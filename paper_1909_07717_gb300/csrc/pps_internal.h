@@ -35,6 +35,8 @@ pps_status pps_ctx_cuda_error(pps_ctx* ctx, cudaError_t e, const char* what);
 
 // Context scratch and limits for the proposal path.
 void pps_ctx_scratch(pps_ctx* ctx, unsigned long long** keys, int** counts);
+// One device word for a kernel's work queue (zero it before the launch).
+unsigned long long* pps_ctx_work_counter(pps_ctx* ctx);
 int pps_ctx_max_states(const pps_ctx* ctx);
 int pps_ctx_jmax(const pps_ctx* ctx);
 int pps_ctx_max_opp(const pps_ctx* ctx);

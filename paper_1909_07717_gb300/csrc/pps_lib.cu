@@ -26,7 +26,8 @@ struct pps_ctx {
     int max_states = 0, max_points = 0, max_speeds = 0, max_K = 0;
     int max_opp = 0, jmax = 8;
     int num_sms = 0;
-    unsigned long long* keys = nullptr;  // scratch, max_states entries
+    unsigned long long* keys = nullptr;  // scratch, max_states entries and
+                                         // a work-queue counter after them
     int* counts = nullptr;               // scratch, max_states entries
     struct Buf {
         void* p = nullptr;
@@ -197,6 +198,10 @@ void pps_ctx_scratch(pps_ctx* ctx, unsigned long long** keys, int** counts) {
     *keys = ctx->keys;
     *counts = ctx->counts;
 }
+
+unsigned long long* pps_ctx_work_counter(pps_ctx* ctx) {
+    return ctx->keys + ctx->max_states;
+}
 int pps_ctx_max_states(const pps_ctx* ctx) { return ctx->max_states; }
 int pps_ctx_jmax(const pps_ctx* ctx) { return ctx->jmax; }
 int pps_ctx_max_opp(const pps_ctx* ctx) { return ctx->max_opp; }
@@ -314,7 +319,7 @@ pps_status pps_create(pps_ctx** out, const pps_ctx_desc* desc) {
         return PPS_ECUDA;
     }
     pps_status s = dev_alloc(ctx, (void**)&ctx->keys,
-                             sizeof(unsigned long long) * ctx->max_states,
+                             sizeof(unsigned long long) * (ctx->max_states + 1),
                              "argmax keys");
     if (s == PPS_OK)
         s = dev_alloc(ctx, (void**)&ctx->counts, sizeof(int) * ctx->max_states,
@@ -333,7 +338,7 @@ void pps_destroy(pps_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
-    dev_free(ctx, ctx->keys, sizeof(unsigned long long) * ctx->max_states);
+    dev_free(ctx, ctx->keys, sizeof(unsigned long long) * (ctx->max_states + 1));
     dev_free(ctx, ctx->counts, sizeof(int) * ctx->max_states);
     for (pps_ctx::Buf* b : {&ctx->st, &ctx->best, &ctx->mask, &ctx->dm,
                             &ctx->ds, &ctx->dT})
