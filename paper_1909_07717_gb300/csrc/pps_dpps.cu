@@ -37,6 +37,7 @@ constexpr int kChunk = 1024;  // candidates per work item, a multiple of 32
 constexpr int kRing = 64;     // prepared paths a warp holds (a power of 2, > 62)
 constexpr int kPend = 64;     // feasible candidates awaiting a score (> 62)
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kSamples = 8;   // ball-path samples a lane takes per loop trip
 
 struct DArgs {
     const pps_dstate* states;
@@ -338,6 +339,18 @@ __device__ __forceinline__ void dpps_eval(const pps_dstate& st,
                                 r.rx, r.ry);
 }
 
+// A 16-byte shared-memory load that stays where it is written: the
+// compiler may not hoist it out of the sample loop (the group would then
+// take 64 registers).
+__device__ __forceinline__ float4 lds4(const void* p) {
+    float4 v;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(a));
+    return v;
+}
+
 // Sample f of the pass (cbx, cby) against a group in shared memory
 // (16-byte aligned), two robot pairs to a 16-byte load: per robot the
 // arithmetic of opp_min, and its minimum tree.
@@ -350,10 +363,10 @@ __device__ __forceinline__ float group_min_smem(float f, float cbx, float cby,
     float t[J];
 #pragma unroll
     for (int i = 0; i < J / 2; i += 2) {
-        const float4 bx = *reinterpret_cast<const float4*>(&g.bx[i]);
-        const float4 by = *reinterpret_cast<const float4*>(&g.by[i]);
-        const float4 ux = *reinterpret_cast<const float4*>(&g.ux[i]);
-        const float4 uy = *reinterpret_cast<const float4*>(&g.uy[i]);
+        const float4 bx = lds4(&g.bx[i]);
+        const float4 by = lds4(&g.by[i]);
+        const float4 ux = lds4(&g.ux[i]);
+        const float4 uy = lds4(&g.uy[i]);
         float2 r = pps::sbip_num2<GEN>(f2, cx2, cy2, make_float2(bx.x, bx.y),
                                        make_float2(by.x, by.y), make_float2(ux.x, ux.y),
                                        make_float2(uy.x, uy.y), reach);
@@ -429,11 +442,12 @@ __device__ __noinline__ void prepare_path(const DArgs& a, const pps_dstate& st,
 }
 
 // Candidates [c0, c1) of state s (c0 a multiple of kChunk) with persistent
-// lanes, two samples a loop trip.  Per lane and phase the samples k = 1..K
+// lanes, kSamples samples a loop trip.  Per lane and phase the samples k = 1..K
 // are taken in order and the phase ends at the first interception, exactly
 // as group_first does: the same arithmetic on the same values, so every
 // time and score equals the one-candidate-a-thread evaluation bit for bit
-// (a trip's second sample is discarded when the first ends the phase).
+// (a trip's later samples are discarded when an earlier one ends the
+// phase).
 template <int J, bool GEN>
 __device__ __forceinline__ void run_chunk(const DArgs& a, const pps_dstate& st, int s,
                                           int c0, int c1, WarpSmem<J>& w, int lane) {
@@ -485,33 +499,29 @@ __device__ __forceinline__ void run_chunk(const DArgs& a, const pps_dstate& st, 
         }
         if (__all_sync(kFull, cand < 0)) break;
 
-        // samples k and k + 1 of the lane's current phase: the first of
-        // them (up to K) at which the group gets the ball ends the phase
+        // samples k .. k + kSamples - 1 of the lane's current phase: the
+        // first of them (up to K) at which the group gets the ball ends the
+        // phase
         bool done = false, feas = false;
         float t_opp = CUDART_INF_F;
         if (cand >= 0) {
             const OppRegs<J>& g = opp ? w.opp : w.team;
             const float cbx = w.cur[5][lane], cby = w.cur[6][lane], v2 = w.cur[7][lane],
                         twoaS = w.cur[8][lane], v = w.cur[9][lane];
-            const float f0 = __fmul_rn((float)k, sk.invK);
-            const float f1 = __fmul_rn((float)(k + 1), sk.invK);
-            const float n0 = group_min_smem<J, GEN>(f0, cbx, cby, g, sk.reach);
-            const float n1 = group_min_smem<J, GEN>(f1, cbx, cby, g, sk.reach);
             int kk = k;
-            float f = f0, n = n0;
-            bool end = k == sk.K;
-            // at the stop the group always gets the ball
-            bool stop = stopped && end;
-            float root = pps::sqrt_ball(fmaxf(__fmaf_rn(-f0, twoaS, v2), 0.f));
-            bool hit = stop || __fadd_rn(__fmul_rn(n0, sk.at_scale), root) <= v;
-            if (!hit && !end) {
-                kk = k + 1;
-                f = f1;
-                n = n1;
+            float f = 0.f, n = 0.f, root = 0.f;
+            bool end = false, stop = false, hit = false;
+#pragma unroll 1
+            for (int j = 0; j < kSamples; ++j) {
+                kk = k + j;
+                f = __fmul_rn((float)kk, sk.invK);
+                n = group_min_smem<J, GEN>(f, cbx, cby, g, sk.reach);
                 end = kk == sk.K;
+                // at the stop the group always gets the ball
                 stop = stopped && end;
-                root = pps::sqrt_ball(fmaxf(__fmaf_rn(-f1, twoaS, v2), 0.f));
-                hit = stop || __fadd_rn(__fmul_rn(n1, sk.at_scale), root) <= v;
+                root = pps::sqrt_ball(fmaxf(__fmaf_rn(-f, twoaS, v2), 0.f));
+                hit = stop || __fadd_rn(__fmul_rn(n, sk.at_scale), root) <= v;
+                if (hit || end) break;
             }
             float t = CUDART_INF_F;
             if (stop)
@@ -538,7 +548,7 @@ __device__ __forceinline__ void run_chunk(const DArgs& a, const pps_dstate& st, 
                     feas = __fsub_rn(t_opp, w.cur[3][lane]) > a.prm.tau_delta;
                 }
             } else {
-                k += 2;
+                k += kSamples;
             }
         }
         const unsigned fm = __ballot_sync(kFull, feas);
