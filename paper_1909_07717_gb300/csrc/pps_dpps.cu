@@ -34,6 +34,8 @@ using pps::OppRegs;
 constexpr int kTPB = 512;
 constexpr int kWarps = kTPB / 32;
 constexpr int kChunk = 1024;  // candidates per work item, a multiple of 32
+constexpr int kSmallChunk = 256;  // the same for the last states: the queue's
+                                  // tail drains in small items
 constexpr int kRing = 64;     // prepared paths a warp holds (a power of 2, > 62)
 constexpr int kPend = 64;     // feasible candidates awaiting a score (> 62)
 constexpr unsigned kFull = 0xffffffffu;
@@ -51,6 +53,7 @@ struct DArgs {
     unsigned long long* keys;
     int* counts;
     unsigned long long* queue;  // work-item counter, zero at launch
+    int s_small;                // states from s_small on: kSmallChunk items
 };
 
 // Per-state constants (validity as in derive_state, for both groups).
@@ -441,7 +444,8 @@ __device__ __noinline__ void prepare_path(const DArgs& a, const pps_dstate& st,
     w.ring[4][slot] = p.stopped ? 1.f : 0.f;
 }
 
-// Candidates [c0, c1) of state s (c0 a multiple of kChunk) with persistent
+// Candidates [c0, c1) of state s (c0 a multiple of 32, c1 - c0 at most
+// kChunk) with persistent
 // lanes, kSamples samples a loop trip.  Per lane and phase the samples k = 1..K
 // are taken in order and the phase ends at the first interception, exactly
 // as group_first does: the same arithmetic on the same values, so every
@@ -457,8 +461,8 @@ __device__ __forceinline__ void run_chunk(const DArgs& a, const pps_dstate& st, 
     w.key[lane] = 0ull;
     w.cnt[lane] = 0;
     __syncwarp();
-    // prepared paths wait in ring slot c mod kRing (c0 is a multiple of
-    // kRing, and at most 63 candidates are ever prepared and not taken)
+    // prepared paths wait in ring slot c mod kRing: the candidates prepared
+    // and not yet taken are at most 63 consecutive ones
     int next = c0;   // first candidate not yet prepared
     int taken = c0;  // first prepared candidate not yet handed out
     int npend = 0;
@@ -565,7 +569,7 @@ __device__ __forceinline__ void run_chunk(const DArgs& a, const pps_dstate& st, 
             w.pend[4][slot] = ry;
             w.pend[5][slot] = ux;
             w.pend[6][slot] = uy;
-            atomicOr(&w.mask[(cand & (kChunk - 1)) >> 5], 1u << (cand & 31));
+            atomicOr(&w.mask[(cand - c0) >> 5], 1u << (cand & 31));
         } else if (done && a.dbg) {
             float* d = a.dbg + ((long long)s * a.prm.n_dir * a.prm.n_pow + cand) * 3;
             d[0] = w.cur[3][lane];
@@ -620,8 +624,11 @@ __global__ void __launch_bounds__(kTPB, 2) dpps_kernel(const DArgs a) {
     WarpSmem<J>& w = reinterpret_cast<WarpSmem<J>*>(dpps_smem)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const long long P = (long long)a.prm.n_dir * a.prm.n_pow;
-    const long long per_state = (P + kChunk - 1) / kChunk;
-    const unsigned long long n_items = (unsigned long long)a.n_states * per_state;
+    const long long big = (P + kChunk - 1) / kChunk;
+    const long long small = (P + kSmallChunk - 1) / kSmallChunk;
+    const unsigned long long n_big = (unsigned long long)a.s_small * big;
+    const unsigned long long n_items =
+        n_big + (unsigned long long)(a.n_states - a.s_small) * small;
     int cur = -1;
     const DStateK& sk = w.sk;
     for (;;) {
@@ -629,9 +636,18 @@ __global__ void __launch_bounds__(kTPB, 2) dpps_kernel(const DArgs a) {
         if (lane == 0) item = atomicAdd(a.queue, 1ull);
         item = __shfl_sync(kFull, item, 0);
         if (item >= n_items) break;
-        const int s = (int)(item / (unsigned long long)per_state);
-        const int c0 = (int)(item - (unsigned long long)s * per_state) * kChunk;
-        const int c1 = (int)min((long long)c0 + kChunk, P);
+        int s, c0, c1;
+        if (item < n_big) {
+            s = (int)(item / (unsigned long long)big);
+            c0 = (int)(item - (unsigned long long)s * big) * kChunk;
+            c1 = (int)min((long long)c0 + kChunk, P);
+        } else {
+            const unsigned long long j = item - n_big;
+            const int q = (int)(j / (unsigned long long)small);
+            s = a.s_small + q;
+            c0 = (int)(j - (unsigned long long)q * small) * kSmallChunk;
+            c1 = (int)min((long long)c0 + kSmallChunk, P);
+        }
         const pps_dstate& st = a.states[s];
         if (s != cur) {
             cur = s;
@@ -815,16 +831,22 @@ __global__ void __launch_bounds__(128)
 }
 
 template <int J>
-cudaError_t launch(const DArgs& a, int num_sms, cudaStream_t st) {
+cudaError_t launch(DArgs a, int num_sms, cudaStream_t st) {
     const size_t smem = sizeof(WarpSmem<J>) * kWarps;
     cudaError_t e = cudaFuncSetAttribute(
         dpps_kernel<J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int occ = pps_occupancy((const void*)dpps_kernel<J>, kTPB, smem);
     const long long P = (long long)a.prm.n_dir * a.prm.n_pow;
-    const long long items = (long long)a.n_states * ((P + kChunk - 1) / kChunk);
+    const long long grid_max = (long long)num_sms * occ;
+    // the last states, about two small items a warp, in small items
+    long long n_small = (2 * grid_max * kWarps * kSmallChunk + P - 1) / P;
+    if (n_small > a.n_states) n_small = a.n_states;
+    a.s_small = a.n_states - (int)n_small;
+    const long long items = (long long)a.s_small * ((P + kChunk - 1) / kChunk) +
+                            n_small * ((P + kSmallChunk - 1) / kSmallChunk);
     long long grid = (items + kWarps - 1) / kWarps;
-    if (grid > (long long)num_sms * occ) grid = (long long)num_sms * occ;
+    if (grid > grid_max) grid = grid_max;
     e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     dpps_kernel<J><<<(unsigned)grid, kTPB, smem, st>>>(a);

@@ -259,6 +259,25 @@ def test_full_size_states_against_the_oracle(searcher):
         assert abs(float(best[s]["score"]) - gc["score"]) <= tg
 
 
+def test_large_and_small_work_items_agree(searcher):
+    """1024 states at the benchmark's shape: the search cuts the first
+    states into work items of 1024 candidates and the last ones into items
+    of 256.  Every state's record and mask bits must not depend on which:
+    the first 64 and the last 64 states, searched again as batches of their
+    own (small items only), give the same bytes."""
+    prm = dict(synth.DPPS_PARAMS)
+    batch = synth.dpps_states(synth.DPPS_SEED + 1, 1024)
+    best, bits, _ = _run(searcher, batch, prm, dbg=False)
+    assert np.all(best["status"] == 0)
+    assert np.array_equal(best["n_feasible"], bits.sum(axis=1))
+    for sl in (slice(0, 64), slice(960, 1024)):
+        sub = {k: (v[sl] if isinstance(v, np.ndarray) else v)
+               for k, v in batch.items()}
+        b2, bits2, _ = _run(searcher, sub, prm, dbg=False)
+        assert b2.tobytes() == best[sl].tobytes()
+        assert np.array_equal(bits2, bits[sl])
+
+
 def test_invalid_states_and_empty_teams(searcher):
     prm = dict(synth.DPPS_PARAMS, n_dir=16, n_pow=32)
     batch = synth.dpps_states(32, 3, n_team=4, n_opp=4, K=16)
