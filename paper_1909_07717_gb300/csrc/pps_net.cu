@@ -2,6 +2,7 @@
 // "Learned proposal"): buffers, the weight layouts, forward, backward and
 // the Adam step, all enqueued on the network's stream.
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -43,6 +44,8 @@ struct pps_net {
     int train_kind = PPS_NET_TRAIN_TCGEN05;
     RasterCfg cfg{};       // speeds and parameters of the input features
     float top_band = 3.0e38f, low_w = 1.f, under_w = 1.f;  // the loss
+    CUtensorMap in_map{};  // a0 as the forward kernel's tensor-memory-
+                           // accelerator source (encoded once, at create)
 };
 
 namespace {
@@ -127,7 +130,7 @@ cudaError_t forward_loaded(pps_net* nt, int n, bool layers, bool keep = false,
         const unsigned grid =
             (unsigned)(units < nt->num_sms ? units : nt->num_sms);
         kernel<<<grid, tcf::kThreads, tcf::kSmemBytes, st>>>(
-            nt->a0, n, nt->Wf, nt->w, nt->out, wf_off(1), wf_off(2), wf_off(3),
+            nt->in_map, nt->a0, n, nt->Wf, nt->w, nt->out, wf_off(1), wf_off(2), wf_off(3),
             bias_off(0), bias_off(1), bias_off(2), bias_off(3), nt->err,
             withhold ? 1 : 0, nt->a1, nt->a2, nt->a3);
         return cudaGetLastError();
@@ -321,6 +324,39 @@ cudaError_t pps_net_topk(pps_net* nt, int n, int k, int* cells,
     return cudaGetLastError();
 }
 
+namespace {
+// The input map a0 ([max_batch][H][W][16 channels] bf16) as a 5-D tiled
+// tensor map: channels 0..7 (16 bytes), the two halves of 8 channels, the
+// W columns, the H rows, the states.  The forward kernel copies one box of
+// 8 channels x 64 columns x its band's input rows a plane; what lies
+// outside the map (columns 61..63, rows above and below) reads as zero.
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                 const cuuint64_t*, const cuuint64_t*,
+                                 const cuuint32_t*, const cuuint32_t*,
+                                 CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+cudaError_t encode_input_map(pps_net* nt) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    const cuuint64_t dims[5] = {8, 2, (cuuint64_t)W, (cuuint64_t)H,
+                                (cuuint64_t)nt->max_batch};
+    const cuuint64_t strides[4] = {16, 2 * 16, (cuuint64_t)W * 32,
+                                   (cuuint64_t)NPIX * 32};
+    const cuuint32_t box[5] = {8, 1, (cuuint32_t)tcf::kRow, (cuuint32_t)tcf::kInRows, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const CUresult r = reinterpret_cast<EncodeTiled>(fn)(
+        &nt->in_map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, nt->a0, dims, strides, box,
+        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+        CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+}  // namespace
+
 extern "C" pps_status pps_net_create(int device, void* stream, int max_batch,
                                      pps_net** out) {
     if (!out) return PPS_EINVAL;
@@ -367,6 +403,7 @@ extern "C" pps_status pps_net_create(int device, void* stream, int max_batch,
     al(&nt->err, sizeof(int));
     al(&nt->wpart, sizeof(float) * (size_t)(nt->num_sms > 0 ? nt->num_sms : 1) *
                        (9 * CH * CH + CH));
+    if (e == cudaSuccess) e = encode_input_map(nt);
     if (e != cudaSuccess) {
         cudaGetLastError();
         pps_net_destroy(nt);
