@@ -519,7 +519,9 @@ def _uneven(args, dev, stream):
                 * int(batch["n_opp"][i]) for i in range(S))
     groups = [{"opp_slots": g.opp_slots, "speed_slots": g.speed_slots,
                "states": g.n_states, "cta_threads": g.cta_threads,
-               "items": g.n_items} for g in plan.groups()]
+               "sample_unroll": g.sample_unroll, "items": g.n_items,
+               "tuned_ms": [round(float(x), 4) for x in g.tuned_ms]}
+              for g in plan.groups()]
     P = np.array([jobs[i].grid.nx * jobs[i].grid.ny for i in range(S)],
                  np.float64)
     V = np.array([jobs[i].n_speeds for i in range(S)], np.float64)

@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define PPS_ABI_VERSION 1
+#define PPS_ABI_VERSION 2
 
 #define PPS_MAX_OPP 16   /* opponents per state (the paper: up to 16 a side) */
 #define PPS_MAX_SPEEDS 8 /* kick speeds per call */
@@ -320,9 +320,13 @@ typedef struct pps_plan_group {
     int32_t speed_slots;  /* 1, 2, 4 or 8 */
     int32_t n_states;
     int32_t cta_threads;  /* CTA size in use */
+    int32_t sample_unroll;  /* samples a register block in use (1 or 2) */
+    int32_t reserved;
     int64_t n_items;      /* (state, 32-point) work items */
-    float tuned_ms[5];    /* autotuner's time per candidate (128, 256, 512,
-                             768, 1024 threads); 0 when not measured */
+    float tuned_ms[7];    /* autotuner's time per candidate (CTA threads,
+                             samples a block): (128, 1), (256, 1), (512, 1),
+                             (768, 1), (1024, 1), (128, 2), (256, 2); 0 when
+                             not measured */
 } pps_plan_group;
 
 /* Build a plan on ctx for n_states (1..2^24) states shaped by jobs (host
@@ -349,7 +353,10 @@ pps_status pps_plan_mask_offsets(const pps_plan* plan, int64_t* offsets);
 pps_status pps_plan_run(pps_plan* plan, const pps_state* states,
                         pps_best* out_best, uint32_t* out_mask);
 
-/* The plan's groups: up to cap entries into out, the count into *n. */
+/* The plan's groups: up to cap entries into out, the count into *n.  The
+ * autotuner (PPS_PLAN_AUTOTUNE) picks each group's CTA size and samples a
+ * register block (the unroll of the sample loop; results are the same bit
+ * for bit either way) from the candidates tuned_ms lists. */
 pps_status pps_plan_groups(const pps_plan* plan, pps_plan_group* out, int cap,
                            int* n);
 

@@ -75,8 +75,9 @@ __device__ __forceinline__ int find_bucket_slot(const long long* start, int n,
     return lo;
 }
 
-// One work item: 32 consecutive grid points of one state (all lanes).
-template <int JMAX, int VMAX>
+// One work item: 32 consecutive grid points of one state (all lanes); KU
+// samples a register block.
+template <int JMAX, int VMAX, int KU>
 __device__ __forceinline__ void batch_item(const BatchArgs& a, long long item,
                                            int lane) {
     {
@@ -96,8 +97,8 @@ __device__ __forceinline__ void batch_item(const BatchArgs& a, long long item,
         const int iy = pc / jv.nx, ix = pc - iy * jv.nx;
 
         PointResult<JMAX, VMAX> r;
-        eval_point<JMAX, VMAX, false>(a.prm, jv.gr, jv.sp, jv.sp2, st, sk, o,
-                                      ix, iy, nullptr, r);
+        eval_point<JMAX, VMAX, false, KU>(a.prm, jv.gr, jv.sp, jv.sp2, st, sk, o,
+                                          ix, iy, nullptr, r);
 
         int cnt = 0;
         unsigned long long key = 0ull;
@@ -128,7 +129,7 @@ __device__ __forceinline__ void batch_item(const BatchArgs& a, long long item,
     }
 }
 
-template <int JMAX, int VMAX, int TPB>
+template <int JMAX, int VMAX, int TPB, int KU>
 __global__ void __launch_bounds__(TPB) batch_search_kernel(const BatchArgs a) {
     const int lane = threadIdx.x & 31;
     // several items a fetch only when there are many per warp: a small
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(TPB) batch_search_kernel(const BatchArgs a) {
                                   ? (long long)(q + run)
                                   : a.n_items;
         for (long long item = (long long)q; item < end; ++item)
-            batch_item<JMAX, VMAX>(a, item, lane);
+            batch_item<JMAX, VMAX, KU>(a, item, lane);
     }
 }
 
@@ -206,10 +207,11 @@ __global__ void __launch_bounds__(128) batch_finalize_kernel(const BatchArgs a) 
 
 // Launch entry points, one translation unit per opponent-slot count
 // (6, 8, 12, 16: the plan picks the smallest that holds a job's opponents).
+// ku: samples a register block (1, or 2 at 128 and 256 threads).
 #define PPS_BATCH_DECLARE(J)                                              \
     cudaError_t batch_launch_j##J(const BatchArgs& a, int vmax, int tpb, \
-                                  int grid, cudaStream_t st);            \
-    int batch_occupancy_j##J(int vmax, int tpb);
+                                  int ku, int grid, cudaStream_t st);    \
+    int batch_occupancy_j##J(int vmax, int tpb, int ku);
 PPS_BATCH_DECLARE(6)
 PPS_BATCH_DECLARE(8)
 PPS_BATCH_DECLARE(12)

@@ -17,14 +17,17 @@
 
 namespace {
 
-constexpr int kNumCand = 5;
-constexpr int kCandidates[kNumCand] = {128, 256, 512, 768, 1024};  // CTA sizes tried
+// Candidates: (CTA size, samples a register block); every CTA size with
+// one sample a block, the two smallest (registers to spare) also with two.
+constexpr int kNumCand = 7;
+constexpr int kCandTpb[kNumCand] = {128, 256, 512, 768, 1024, 128, 256};
+constexpr int kCandKu[kNumCand] = {1, 1, 1, 1, 1, 2, 2};
 constexpr int kMaxDevices = 64;
 
 // Autotuner choices per (device, opponent slots, speed slots), shared by all
 // plans of the process.
 std::mutex g_tune_mu;
-int g_tuned_tpb[kMaxDevices][4][4];  // 0 = not tuned yet
+int g_tuned[kMaxDevices][4][4];  // candidate index + 1; 0 = not tuned yet
 
 // Opponent-slot instances of the plan kernels.
 int opp_slots(int max_opp) {
@@ -39,8 +42,8 @@ struct Group {
     int j = 8, v = 1;
     std::vector<int> states;      // state indices
     long long n_items = 0;
-    int tpb = 512;
-    float tuned_ms[kNumCand] = {0, 0, 0, 0, 0};
+    int tpb = 512, ku = 1;
+    float tuned_ms[kNumCand] = {0, 0, 0, 0, 0, 0, 0};
     long long states_off = 0;     // offset into the plan's bucket_states array
     long long start_off = 0;      // offset into the plan's item_start array
 };
@@ -237,11 +240,13 @@ extern "C" pps_status pps_plan_create(pps_ctx* ctx, const pps_job* jobs,
         std::lock_guard<std::mutex> lk(g_tune_mu);
         bool all = true;
         for (Group& g : pl->groups) {
-            const int t = g_tuned_tpb[dev][slot_of_j(g.j)][slot_of_v(g.v)];
-            if (t)
-                g.tpb = t;
-            else
+            const int t = g_tuned[dev][slot_of_j(g.j)][slot_of_v(g.v)];
+            if (t) {
+                g.tpb = kCandTpb[t - 1];
+                g.ku = kCandKu[t - 1];
+            } else {
                 all = false;
+            }
         }
         pl->tuned = all;
     }
@@ -275,23 +280,23 @@ pps::BatchArgs group_args(const pps_plan* pl, const Group& g,
 
 // Persistent grid: CTAs resident on every SM, no more than the items need.
 cudaError_t launch_group(const pps_plan* pl, const pps::BatchArgs& a,
-                         const Group& g, int tpb, cudaStream_t st) {
+                         const Group& g, int tpb, int ku, cudaStream_t st) {
     int occ = 1;
     switch (g.j) {
-        case 6: occ = pps::batch_occupancy_j6(g.v, tpb); break;
-        case 8: occ = pps::batch_occupancy_j8(g.v, tpb); break;
-        case 12: occ = pps::batch_occupancy_j12(g.v, tpb); break;
-        default: occ = pps::batch_occupancy_j16(g.v, tpb); break;
+        case 6: occ = pps::batch_occupancy_j6(g.v, tpb, ku); break;
+        case 8: occ = pps::batch_occupancy_j8(g.v, tpb, ku); break;
+        case 12: occ = pps::batch_occupancy_j12(g.v, tpb, ku); break;
+        default: occ = pps::batch_occupancy_j16(g.v, tpb, ku); break;
     }
     long long grid = (long long)pps_ctx_num_sms(pl->ctx) * occ;
     const long long need = (a.n_items + tpb / 32 - 1) / (tpb / 32);
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     switch (g.j) {
-        case 6: return pps::batch_launch_j6(a, g.v, tpb, (int)grid, st);
-        case 8: return pps::batch_launch_j8(a, g.v, tpb, (int)grid, st);
-        case 12: return pps::batch_launch_j12(a, g.v, tpb, (int)grid, st);
-        default: return pps::batch_launch_j16(a, g.v, tpb, (int)grid, st);
+        case 6: return pps::batch_launch_j6(a, g.v, tpb, ku, (int)grid, st);
+        case 8: return pps::batch_launch_j8(a, g.v, tpb, ku, (int)grid, st);
+        case 12: return pps::batch_launch_j12(a, g.v, tpb, ku, (int)grid, st);
+        default: return pps::batch_launch_j16(a, g.v, tpb, ku, (int)grid, st);
     }
 }
 
@@ -303,13 +308,14 @@ cudaError_t enqueue_all(const pps_plan* pl, const pps_state* states,
     for (const Group& g : pl->groups) {
         if (e != cudaSuccess) break;
         e = launch_group(pl, group_args(pl, g, states, best, mask), g, g.tpb,
-                         st);
+                         g.ku, st);
     }
     return e;
 }
 
-// Time each candidate CTA size on a prefix of every untuned group's items
-// (enough items to fill the GPU several times over) and keep the fastest.
+// Time each candidate (CTA size, samples a register block) on a prefix of
+// every untuned group's items (enough items to fill the GPU several times
+// over) and keep the fastest.
 pps_status autotune(pps_plan* pl, const pps_state* states, pps_best* best,
                     uint32_t* mask) {
     pps_ctx* ctx = pl->ctx;
@@ -323,21 +329,22 @@ pps_status autotune(pps_plan* pl, const pps_state* states, pps_best* best,
         if (e != cudaSuccess) break;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
-            const int t = g_tuned_tpb[dev][slot_of_j(g.j)][slot_of_v(g.v)];
+            const int t = g_tuned[dev][slot_of_j(g.j)][slot_of_v(g.v)];
             if (t) {
-                g.tpb = t;
+                g.tpb = kCandTpb[t - 1];
+                g.ku = kCandKu[t - 1];
                 continue;
             }
         }
         pps::BatchArgs a = group_args(pl, g, states, best, mask);
         a.n_items = std::min(a.n_items, cap);
         float best_ms = 1e30f;
-        int best_tpb = 512;
+        int best_c = 2;
         for (int c = 0; c < kNumCand && e == cudaSuccess; ++c) {
-            const int tpb = kCandidates[c];
-            e = launch_group(pl, a, g, tpb, st);  // warm-up
+            const int tpb = kCandTpb[c], ku = kCandKu[c];
+            e = launch_group(pl, a, g, tpb, ku, st);  // warm-up
             if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-            if (e == cudaSuccess) e = launch_group(pl, a, g, tpb, st);
+            if (e == cudaSuccess) e = launch_group(pl, a, g, tpb, ku, st);
             if (e == cudaSuccess) e = cudaEventRecord(e1, st);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float ms = 0.f;
@@ -346,13 +353,14 @@ pps_status autotune(pps_plan* pl, const pps_state* states, pps_best* best,
             g.tuned_ms[c] = ms;
             if (ms < best_ms) {
                 best_ms = ms;
-                best_tpb = tpb;
+                best_c = c;
             }
         }
         if (e != cudaSuccess) break;
-        g.tpb = best_tpb;
+        g.tpb = kCandTpb[best_c];
+        g.ku = kCandKu[best_c];
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned_tpb[dev][slot_of_j(g.j)][slot_of_v(g.v)] = best_tpb;
+        g_tuned[dev][slot_of_j(g.j)][slot_of_v(g.v)] = best_c + 1;
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -460,6 +468,7 @@ extern "C" pps_status pps_plan_groups(const pps_plan* pl, pps_plan_group* out,
         out[i].speed_slots = g.v;
         out[i].n_states = (int32_t)g.states.size();
         out[i].cta_threads = g.tpb;
+        out[i].sample_unroll = g.ku;
         out[i].n_items = g.n_items;
         for (int c = 0; c < kNumCand; ++c) out[i].tuned_ms[c] = g.tuned_ms[c];
     }

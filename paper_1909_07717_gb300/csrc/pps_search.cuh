@@ -304,7 +304,7 @@ __device__ __forceinline__ float opp_min(float f, float cbx, float cby,
 
 // A3 + A4 over the K samples of one point.  mv[v] accumulates
 // min_k (a T_k + sqrt(v^2 - 2 a s_k)); Trow (debug) receives T_k.
-template <int JMAX, int VMAX, bool GEN, bool TDBG>
+template <int JMAX, int VMAX, bool GEN, bool TDBG, int KU = kKUnroll>
 __device__ __forceinline__ void sample_loop(const StateK& sk,
                                             const OppRegs<JMAX>& o,
                                             float cbx, float cby,
@@ -321,7 +321,7 @@ __device__ __forceinline__ void sample_loop(const StateK& sk,
     // Float sample counter: exact for K <= 2^24, and keeps integer-to-float
     // conversions out of the loop.
     const float Kf = (float)sk.K;
-#pragma unroll kKUnroll
+#pragma unroll KU
     for (float kf = 1.f; kf <= Kf; kf += 1.f) {
         const float f = __fmul_rn(kf, sk.invK);
         const int k = (int)kf;
@@ -459,7 +459,9 @@ struct ItemGrid {
     int V;
 };
 
-template <int JMAX, int VMAX, bool TDBG>
+// KU: unroll of the sample loop (samples a register block holds); it only
+// replicates the loop body, so every result is the same bit for bit.
+template <int JMAX, int VMAX, bool TDBG, int KU = kKUnroll>
 __device__ __forceinline__ void eval_point(const pps_params& prm,
                                            const ItemGrid& gr,
                                            const float (&sp)[PPS_MAX_SPEEDS],
@@ -487,11 +489,11 @@ __device__ __forceinline__ void eval_point(const pps_params& prm,
 #pragma unroll
     for (int v = 0; v < VMAX; ++v) mv[v] = CUDART_INF_F;
     if (sk.general)
-        sample_loop<JMAX, VMAX, true, TDBG>(sk, o, cbx, cby, twoabD, sp2, mv,
-                                            Trow);
+        sample_loop<JMAX, VMAX, true, TDBG, KU>(sk, o, cbx, cby, twoabD, sp2, mv,
+                                                Trow);
     else
-        sample_loop<JMAX, VMAX, false, TDBG>(sk, o, cbx, cby, twoabD, sp2, mv,
-                                             Trow);
+        sample_loop<JMAX, VMAX, false, TDBG, KU>(sk, o, cbx, cby, twoabD, sp2, mv,
+                                                 Trow);
 
     // A5: the receiver is in front of the goal line iff x0 + ix g < L/2,
     // decided exactly on the FP64 grid coordinate.

@@ -418,19 +418,19 @@ cudaError_t launch_batch(pps_server* srv, Slot& s) {
         a.next = s.d_next + (&g - groups.data());
         int occ = 1;
         switch (g.j) {
-            case 6: occ = pps::batch_occupancy_j6(g.v, kTpb); break;
-            case 8: occ = pps::batch_occupancy_j8(g.v, kTpb); break;
-            case 12: occ = pps::batch_occupancy_j12(g.v, kTpb); break;
-            default: occ = pps::batch_occupancy_j16(g.v, kTpb); break;
+            case 6: occ = pps::batch_occupancy_j6(g.v, kTpb, 1); break;
+            case 8: occ = pps::batch_occupancy_j8(g.v, kTpb, 1); break;
+            case 12: occ = pps::batch_occupancy_j12(g.v, kTpb, 1); break;
+            default: occ = pps::batch_occupancy_j16(g.v, kTpb, 1); break;
         }
         long long grid = (long long)srv->num_sms * occ;
         const long long need = (g.items + kTpb / 32 - 1) / (kTpb / 32);
         grid = std::max(1LL, std::min(grid, need));
         switch (g.j) {
-            case 6: e = pps::batch_launch_j6(a, g.v, kTpb, (int)grid, st); break;
-            case 8: e = pps::batch_launch_j8(a, g.v, kTpb, (int)grid, st); break;
-            case 12: e = pps::batch_launch_j12(a, g.v, kTpb, (int)grid, st); break;
-            default: e = pps::batch_launch_j16(a, g.v, kTpb, (int)grid, st); break;
+            case 6: e = pps::batch_launch_j6(a, g.v, kTpb, 1, (int)grid, st); break;
+            case 8: e = pps::batch_launch_j8(a, g.v, kTpb, 1, (int)grid, st); break;
+            case 12: e = pps::batch_launch_j12(a, g.v, kTpb, 1, (int)grid, st); break;
+            default: e = pps::batch_launch_j16(a, g.v, kTpb, 1, (int)grid, st); break;
         }
     }
     if (e == cudaSuccess)

@@ -23,7 +23,7 @@ import numpy as np
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libpps.so")
 
-PPS_ABI_VERSION = 1
+PPS_ABI_VERSION = 2
 PPS_MAX_OPP = 16
 PPS_MAX_SPEEDS = 8
 PPS_MAX_K = 4096
@@ -92,7 +92,8 @@ class pps_job(ctypes.Structure):
 class pps_plan_group(ctypes.Structure):
     _fields_ = [("opp_slots", c_int32), ("speed_slots", c_int32),
                 ("n_states", c_int32), ("cta_threads", c_int32),
-                ("n_items", ctypes.c_int64), ("tuned_ms", c_float * 5)]
+                ("sample_unroll", c_int32), ("reserved", c_int32),
+                ("n_items", ctypes.c_int64), ("tuned_ms", c_float * 7)]
 
 
 class pps_server_desc(ctypes.Structure):

@@ -45,13 +45,15 @@ def test_record_sizes_match_header(lib):
     assert ctypes.sizeof(pps.pps_best) == 32
     assert ctypes.sizeof(pps.pps_grid) == 20
     assert ctypes.sizeof(pps.pps_params) == 32
+    assert ctypes.sizeof(pps.pps_plan_group) == 64
+    assert pps.pps_plan_group.n_items.offset == 24
     text = open(HEADER).read()
     assert f"#define PPS_MAX_OPP {pps.PPS_MAX_OPP}" in text
     assert f"#define PPS_ABI_VERSION {pps.PPS_ABI_VERSION}" in text
 
 
 def test_host_helpers(lib):
-    assert pps.pps_abi_version() == 1
+    assert pps.pps_abi_version() == pps.PPS_ABI_VERSION == 2
     assert pps.pps_status_string(pps.PPS_EINVAL) == "PPS_EINVAL"
     assert pps.pps_status_string(99) == "PPS_UNKNOWN"
     p = pps.pps_default_params()

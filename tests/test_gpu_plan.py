@@ -172,6 +172,10 @@ def test_uneven_full_size_properties(full_uneven):
     S = synth.UNEVEN_STATES
     assert np.all(best["status"] == 0)
     assert all(g.cta_threads in (128, 256, 512, 768, 1024) for g in groups)
+    # samples a register block: 2 only at the two smallest CTA sizes
+    assert all(g.sample_unroll == 1 or (g.sample_unroll == 2 and
+                                        g.cta_threads in (128, 256))
+               for g in groups)
     has = best["idx"] >= 0
     assert np.all(has == (best["n_feasible"] > 0))
     for s in range(0, S, 97):      # popcounts and best bits, spread over all
