@@ -99,7 +99,7 @@ cudaError_t load_input(pps_net* nt, const pps_state* states,
     const long long P = (long long)n * NPIX;
     cudaStream_t st = nt->stream;
     if (states) {
-        raster_kernel<<<blocks(P, 128), 128, 0, st>>>(states, n, nt->cfg,
+        raster_kernel<<<(unsigned)(n * kRasterCtas), kRasterTpb, 0, st>>>(states, n, nt->cfg,
                                                       nt->a0);
         return cudaGetLastError();
     }
@@ -541,7 +541,7 @@ extern "C" pps_status pps_net_raster(pps_net* nt, const pps_state* states,
     if (!out) return PPS_EINVAL;
     cudaSetDevice(nt->device);
     const long long P = (long long)n * NPIX;
-    raster_kernel<<<blocks(P, 128), 128, 0, nt->stream>>>(states, n, nt->cfg,
+    raster_kernel<<<(unsigned)(n * kRasterCtas), kRasterTpb, 0, nt->stream>>>(states, n, nt->cfg,
                                                           nt->a0);
     if ((reinterpret_cast<uintptr_t>(out) & 15) != 0)
         return fail(PPS_EINVAL, "pps_net_raster: out must be 16-byte aligned");

@@ -74,13 +74,63 @@ constexpr float kSubOff = 0.05f;      // sub-points: the cell's quadrant centres
 // f[0] the coarse score (the value function with the margin of kFeatK
 // samples; kScoreFloor where no speed is feasible), f[1] the margin (best
 // speed, clamped to [-2, 1]), f[2] the open shot angle / pi.
+// The opponents' scaled pairs, read from the CTA's shared copy with 16-byte
+// loads that stay inside the sample loop (two pairs a load; the same
+// arithmetic and minimum tree as opp_min).
+__device__ __forceinline__ float4 lds4(const void* p) {
+    float4 v;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(a));
+    return v;
+}
+
 template <int J, bool GEN>
+__device__ __forceinline__ float opp_min_shared(float f, float cbx, float cby,
+                                                const OppRegs<J>& o, float reach) {
+    static_assert(J % 4 == 0, "pairs are read two at a time");
+    const float2 f2 = make_float2(f, f), cx2 = make_float2(cbx, cbx),
+                 cy2 = make_float2(cby, cby);
+    float t[J];
+#pragma unroll
+    for (int i = 0; i < J / 2; i += 2) {
+        const float4 bx = lds4(&o.bx[i]), by = lds4(&o.by[i]);
+        const float4 ux = lds4(&o.ux[i]), uy = lds4(&o.uy[i]);
+        float2 r = sbip_num2<GEN>(f2, cx2, cy2, make_float2(bx.x, bx.y),
+                                  make_float2(by.x, by.y), make_float2(ux.x, ux.y),
+                                  make_float2(uy.x, uy.y), reach);
+        t[2 * i] = r.x;
+        t[2 * i + 1] = r.y;
+        r = sbip_num2<GEN>(f2, cx2, cy2, make_float2(bx.z, bx.w),
+                           make_float2(by.z, by.w), make_float2(ux.z, ux.w),
+                           make_float2(uy.z, uy.w), reach);
+        t[2 * i + 2] = r.x;
+        t[2 * i + 3] = r.y;
+    }
+#pragma unroll
+    for (int w = 1; w < J; w *= 2)
+#pragma unroll
+        for (int j = 0; j + w < J; j += 2 * w) t[j] = fminf(t[j], t[j + w]);
+    return t[0];
+}
+
+// o: the state's opponents (OppRegs<J> as load_opps fills it), in the CTA's
+// shared memory.
+// VMAX: speed slots (4 or 8; the slots past cfg.V repeat the last speed
+// and are left out of the margin), the ball terms of two speeds a packed
+// f32x2 instruction.
+template <int J, bool GEN, int VMAX>
 __device__ __forceinline__ void cell_features(const pps_state& st,
                                               const StateK& sk,
+                                              const OppRegs<J>& o,
                                               const RasterCfg& cfg, float cx,
                                               float cy, float (&f)[3]) {
-    OppRegs<J> o;
-    load_opps<J>(st, sk, o);
+    constexpr int VP = VMAX / 2;
+    float2 s2[VP];
+#pragma unroll
+    for (int i = 0; i < VP; ++i)
+        s2[i] = make_float2(cfg.sp2[2 * i], cfg.sp2[2 * i + 1]);  // padded already
     const float hw = 0.5f * st.field_wid;
     float mbest = -CUDART_INF_F, tbest = 0.f, sbest = kScoreFloor;
 #pragma unroll 1
@@ -93,23 +143,33 @@ __device__ __forceinline__ void cell_features(const pps_state& st,
         const float D = sqrtf(dx * dx + dy * dy);
         const float cbx = sk.kappa * dx, cby = sk.kappa * dy;
         const float twoabD = sk.two_ab * D;
-        float mv[PPS_MAX_SPEEDS];
+        float2 mv2[VP];
 #pragma unroll
-        for (int v = 0; v < PPS_MAX_SPEEDS; ++v) mv[v] = CUDART_INF_F;
+        for (int i = 0; i < VP; ++i) mv2[i] = make_float2(CUDART_INF_F, CUDART_INF_F);
 #pragma unroll 1
         for (int k = 1; k <= kFeatK; ++k) {
             const float fr = (float)k * (1.f / kFeatK);  // exact: kFeatK = 2^n
-            const float aT = opp_min<J, GEN>(fr, cbx, cby, o, sk.reach) * sk.at_scale;
-            const float nf = -fr * twoabD;
+            const float aT =
+                __fmul_rn(opp_min_shared<J, GEN>(fr, cbx, cby, o, sk.reach), sk.at_scale);
+            const float nf = __fmul_rn(-fr, twoabD);
+            const float2 nf2 = make_float2(nf, nf), aT2 = make_float2(aT, aT);
 #pragma unroll
-            for (int v = 0; v < PPS_MAX_SPEEDS; ++v)
-                if (v < cfg.V)
-                    mv[v] = fminf(mv[v],
-                                  aT + sqrt_ball(fmaxf(cfg.sp2[v] + nf, 0.f)));
+            for (int i = 0; i < VP; ++i) {
+                const float2 a = __fadd2_rn(s2[i], nf2);
+                const float2 t = __fadd2_rn(aT2, make_float2(sqrt_ball(fmaxf(a.x, 0.f)),
+                                                              sqrt_ball(fmaxf(a.y, 0.f))));
+                mv2[i] = make_float2(fminf(mv2[i].x, t.x), fminf(mv2[i].y, t.y));
+            }
+        }
+        float mv[VMAX];
+#pragma unroll
+        for (int i = 0; i < VP; ++i) {
+            mv[2 * i] = mv2[i].x;
+            mv[2 * i + 1] = mv2[i].y;
         }
         float m = -CUDART_INF_F;
 #pragma unroll
-        for (int v = 0; v < PPS_MAX_SPEEDS; ++v) {
+        for (int v = 0; v < VMAX; ++v) {
             if (v >= cfg.V) continue;
             float mm;
             if (cfg.sp2[v] - twoabD < 0.f)
@@ -138,7 +198,7 @@ __device__ __forceinline__ void cell_features(const pps_state& st,
     f[2] = tbest;
 }
 
-// One thread per (state, pixel): the 8 input channels of the pixel centred
+// One thread a (state, pixel): the 8 input channels of the pixel centred
 // at c = ((x - 30) / 5, (y - 22.5) / 5), bf16, written as 16-channel rows
 // (channels 8..15 zero):
 //   0  sum_j exp(-|c - o_j|^2 / (2 0.3^2))      opponent density
@@ -148,18 +208,37 @@ __device__ __forceinline__ void cell_features(const pps_state& st,
 //   4  shot angle of the cell    (f[2])
 //   5  |goal centre - c| / diag
 //   6  c_x / (L / 2),  7  c_y / (W / 2)
-__global__ void __launch_bounds__(128, 8)
+// Every CTA covers pixels of one state (kRasterCtas CTAs a state): one
+// thread derives the state's constants and scales its opponents into
+// shared memory, and the pixels read them from there (broadcasts) instead
+// of each thread deriving them and holding the opponents in registers.
+constexpr int kRasterTpb = 128;
+constexpr int kRasterCtas = (NPIX + kRasterTpb - 1) / kRasterTpb;
+
+__global__ void __launch_bounds__(kRasterTpb, 8)
     raster_kernel(const pps_state* __restrict__ states, int n,
                               const RasterCfg cfg,
                               __nv_bfloat16* __restrict__ out) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)n * NPIX) return;
-    const int s = (int)(i / NPIX), q = (int)(i - (long long)s * NPIX);
-    const int y = q / W, x = q - y * W;
+    __shared__ StateK s_sk;
+    __shared__ __align__(16) unsigned char s_opp[sizeof(OppRegs<PPS_MAX_OPP>)];
+    const int s = (int)(blockIdx.x / kRasterCtas);
+    const int q = (int)(blockIdx.x - (unsigned)s * kRasterCtas) * kRasterTpb + threadIdx.x;
     const pps_state& st = states[s];
+    if (threadIdx.x == 0) {
+        const StateK d = derive_state(st, cfg.prm, PPS_MAX_OPP, PPS_MAX_K);
+        s_sk = d;
+        if (d.nopp <= 8)
+            load_opps<8>(st, d, *reinterpret_cast<OppRegs<8>*>(s_opp));
+        else
+            load_opps<PPS_MAX_OPP>(st, d, *reinterpret_cast<OppRegs<PPS_MAX_OPP>*>(s_opp));
+    }
+    __syncthreads();
+    if (q >= NPIX) return;
+    const long long i = (long long)s * NPIX + q;
+    const int y = q / W, x = q - y * W;
     const float cx = __fdiv_rn((float)(x - 30), 5.f);
     const float cy = __fdiv_rn(__fsub_rn((float)y, 22.5f), 5.f);
-    const StateK sk = derive_state(st, cfg.prm, PPS_MAX_OPP, PPS_MAX_K);
+    const StateK& sk = s_sk;
 
     float dens = 0.f;
     for (int j = 0; j < sk.nopp; ++j) {
@@ -168,12 +247,23 @@ __global__ void __launch_bounds__(128, 8)
     }
     float f[3] = {kScoreFloor, -2.f, 0.f};
     if (sk.valid) {
-        if (sk.nopp <= 8)
-            sk.general ? cell_features<8, true>(st, sk, cfg, cx, cy, f)
-                       : cell_features<8, false>(st, sk, cfg, cx, cy, f);
-        else
-            sk.general ? cell_features<PPS_MAX_OPP, true>(st, sk, cfg, cx, cy, f)
-                       : cell_features<PPS_MAX_OPP, false>(st, sk, cfg, cx, cy, f);
+        const auto& o8 = *reinterpret_cast<const OppRegs<8>*>(s_opp);
+        const auto& o16 = *reinterpret_cast<const OppRegs<PPS_MAX_OPP>*>(s_opp);
+        if (cfg.V <= 4) {
+            if (sk.nopp <= 8)
+                sk.general ? cell_features<8, true, 4>(st, sk, o8, cfg, cx, cy, f)
+                           : cell_features<8, false, 4>(st, sk, o8, cfg, cx, cy, f);
+            else
+                sk.general ? cell_features<PPS_MAX_OPP, true, 4>(st, sk, o16, cfg, cx, cy, f)
+                           : cell_features<PPS_MAX_OPP, false, 4>(st, sk, o16, cfg, cx, cy, f);
+        } else {
+            if (sk.nopp <= 8)
+                sk.general ? cell_features<8, true, 8>(st, sk, o8, cfg, cx, cy, f)
+                           : cell_features<8, false, 8>(st, sk, o8, cfg, cx, cy, f);
+            else
+                sk.general ? cell_features<PPS_MAX_OPP, true, 8>(st, sk, o16, cfg, cx, cy, f)
+                           : cell_features<PPS_MAX_OPP, false, 8>(st, sk, o16, cfg, cx, cy, f);
+        }
     }
     const float dxm = cx - sk.bx, dym = cy - sk.by;
     const float gx = sk.Lh - cx;
