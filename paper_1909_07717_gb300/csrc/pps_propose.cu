@@ -26,8 +26,8 @@ constexpr int kFineNx = 481, kFineNy = 361;
 // run rank-major -- every state's best-ranked cell first -- so that when a
 // lower-ranked item starts, its state usually has a pass already; with
 // `prune` an item whose score bound (score_bound: the whole mouth's angle
-// and the last pass-line sample's margin, max over its points) falls below
-// that pass's score is skipped: it cannot hold the best.
+// and the margin over 4 of the pass-line samples, max over its points)
+// falls below that pass's score is skipped: it cannot hold the best.
 // Items are handed out one at a time from a work-queue counter (zero at
 // launch): pruned items cost a small fraction of evaluated ones, so a
 // static deal would leave most warps idle while a few finish theirs.

@@ -544,7 +544,7 @@ __device__ __forceinline__ void eval_point(const pps_params& prm,
 // as the sample loop computes it).  FP32 rounding is monotone, so the bound
 // needs no slack; it holds when w_angle >= 0 and w_margin >= 0, which the
 // caller checks.
-constexpr int kBoundSamples = 1;
+constexpr int kBoundSamples = 4;
 
 template <int JMAX, int VMAX>
 __device__ __forceinline__ float score_bound(const pps_params& prm,
