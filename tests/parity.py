@@ -140,7 +140,8 @@ def check_state_dense(gpu, orc, batch, s, grid, speeds, params, Tcond=None):
         To = orc["T"][s, :, :K]
         Tg = gpu["T"][s, :, :K].astype(np.float64)
         both_inf = np.isinf(To) & np.isinf(Tg)
-        err = np.where(both_inf, 0.0, np.abs(Tg - To))
+        with np.errstate(invalid="ignore"):   # inf - inf where both are inf
+            err = np.where(both_inf, 0.0, np.abs(Tg - To))
         tol = TOL_T + 2 * Tcond
         bad = err > tol
         # well-conditioned: |grad T| <= WELLCOND_GRAD (a sample away from
@@ -182,7 +183,8 @@ def check_state_dense(gpu, orc, batch, s, grid, speeds, params, Tcond=None):
         cmp = reach_o & ~neg & np.isfinite(m_o)
         tolm = TOL_T + 2 * (Tcond.max(axis=1)[None, :]
                             + ball_condition(sp, a, D, K))
-        err = np.abs(mg - m_o)
+        with np.errstate(invalid="ignore"):   # equal infinities: nan, masked below
+            err = np.abs(mg - m_o)
         bad = cmp & (err > tolm)
         stats["margin_max_err"] = float(err[cmp].max(initial=0))
         assert not bad.any(), (
@@ -200,7 +202,8 @@ def check_state_dense(gpu, orc, batch, s, grid, speeds, params, Tcond=None):
         tols = (TOL_SCORE * np.maximum(1, np.abs(so))
                 + params["w_margin"] * np.where(
                     m_o < params["margin_cap"] + 1e-4, tolm, 0))
-        err = np.abs(sg - so)
+        with np.errstate(invalid="ignore"):   # equal infinities: nan, masked below
+            err = np.abs(sg - so)
         stats["score_max_err"] = float(err[both].max(initial=0))
         bad = both & (err > tols)
         assert not bad.any(), f"state {s}: {bad.sum()} scores differ"
