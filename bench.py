@@ -1019,7 +1019,7 @@ def _training(args, dev, stream):
 def _serving(dev, seconds=2.0, no_cpu=False):
     """The serving loop: 512 simulated matches at 60 Hz (12x9 or 9x6 fields,
     6-11 opponents, 0.05 m grid, 4 speeds, K = 32) replayed in real time
-    through a pps_server (4 streams, continuous batching), once in each
+    through a pps_server (8 streams, continuous batching), once in each
     mode: exact (every frame on its full grid, 128 MiB mask pool) and
     proposal (the serving network ranks the map cells, the exact search
     refines the best 256 and searches the full grid of a frame whose cells
@@ -1039,11 +1039,14 @@ def _serving(dev, seconds=2.0, no_cpu=False):
     prm = pps.params_from_dict(synth.DEFAULT_PARAMS)
     modes, results = {}, {}
     for mode in ("exact", "proposal"):
+        # 8 streams, each launch enqueued as soon as a stream is free (no
+        # gathering window): at this load the lowest latency of the
+        # settings measured (4 or 8 streams x 0, 10, 25, 50 us windows)
         if mode == "exact":
-            desc = pps.pps_server_desc(dev.index, 4, 512, 65536, 128 << 20,
-                                       16, 50, prm)
+            desc = pps.pps_server_desc(dev.index, 8, 512, 65536, 128 << 20,
+                                       16, 0, prm)
         else:
-            desc = pps.pps_server_desc(dev.index, 4, 512, 65536, 0, 16, 50,
+            desc = pps.pps_server_desc(dev.index, 8, 512, 65536, 0, 16, 0,
                                        prm, pps.PPS_SERVE_PROPOSAL, TOPK,
                                        weights.ctypes.data)
         srv = pps.pps_server_create(desc)
