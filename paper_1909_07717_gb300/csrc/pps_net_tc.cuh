@@ -16,10 +16,22 @@
 //     rows of tiles j and j + 1 of layer L, so it is issued as soon as
 //     those two tiles' epilogues are done -- the layers of a band, and
 //     consecutive bands, overlap instead of running behind block barriers;
-//   * 16 epilogue warps, four warpgroups taking the band's 22 tiles in
-//     turn; each group reads its tile's accumulators (each warp its lane
+//   * 16 epilogue warps, four warpgroups taking the band's items in turn;
+//     each group reads its tile's accumulators (each warp its lane
 //     quarter), writes the next layer's input rows into shared memory and
 //     arrives on the tile's "epilogue done" mbarrier.
+//   The one-channel output layer is not a convolution of N = 16 MMAs
+//   (15 wasted columns, 18 MMAs a tile): one pair of MMAs per layer-3
+//   tile gives each pixel its 9 taps' partial sums (taps along N), and the
+//   epilogue adds the 9 partials at the shifted pixels -- 10 MMAs a band
+//   instead of 72.
+//   Buffer reuse between the issuers: a commit tracks its own thread's
+//   MMAs only.  Tile j of a layer waits for tiles j and j + 1 of the layer
+//   below, one of each issuer, so every earlier MMA of both issuers has
+//   completed before its epilogue overwrites a buffer; the next band's
+//   layer-1 tile j waits for one tile only, and the rows its epilogue
+//   overwrites are read by no other issuer's pending MMA (the partials of
+//   tile j read only rows 2j, 2j + 1).
 //   Tensor memory holds two halves of 256 columns, used by layers of
 //   alternating parity, so a layer's accumulators can be written while the
 //   previous layer's are still being read.  Every wait is bounded: a wait
@@ -64,13 +76,23 @@ constexpr int kPairs = 5;  // layer 1: the 9 taps' 8 input channels in K pairs
 constexpr int kOffW1 = kOffW0 + kPairs * 2 * CH * 16;
 constexpr int kOffW2 = kOffW1 + 9 * 4 * CH * 16;
 constexpr int kOffW3 = kOffW2 + 9 * 4 * CH * 16;
-constexpr int kOffBias = kOffW3 + 9 * 4 * kNOut * 16;      // 4 x 32 floats
-constexpr int kOffBar = kOffBias + 4 * CH * 4;
-// mbarriers: accumulators full [layer][tile], epilogue done [layer][tile],
-// input full, input free (both issuers), drain [issuer]
-constexpr int kBarAcc = 0, kBarEpi = 4 * kMaxTiles, kBarInFull = 8 * kMaxTiles,
-              kBarInFree = kBarInFull + 1, kBarDrain = kBarInFree + 1,
-              kNumBars = kBarDrain + 2;
+// Output layer (one channel): B = W3 with the 9 taps along N (16, 7 zero)
+// and the 32 input channels along K; one tile's MMAs give every pixel of
+// two layer-3 rows its 9 tap partials, which the epilogue adds up at the
+// shifted pixels.  The partials of the band's 10 layer-3 rows wait in
+// shared memory, [tap][1 + row x 64 + column] floats (a leading zero slot
+// for column -1 of row 0; columns 61..63 are zero like the activations).
+constexpr int kDSlots = 1 + (kBand + 2) * kRow;
+constexpr int kDStride = (kDSlots + 3) & ~3;
+constexpr int kOffBias = kOffW3 + 4 * kNOut * 16;           // 4 x 32 floats
+constexpr int kOffPart = kOffBias + 4 * CH * 4;             // 9 x kDStride f32
+constexpr int kOffBar = kOffPart + 9 * kDStride * 4;
+// mbarriers: accumulators full [layer][tile], epilogue done [layer][tile]
+// (layer 3 = the output layer's partials), output rows done [tile], input
+// full, input free (both issuers), drain [issuer]
+constexpr int kBarAcc = 0, kBarEpi = 4 * kMaxTiles, kBarOut = 8 * kMaxTiles,
+              kBarInFull = kBarOut + kBand / 2, kBarInFree = kBarInFull + 1,
+              kBarDrain = kBarInFree + 1, kNumBars = kBarDrain + 2;
 constexpr int kOffTmem = kOffBar + 8 * kNumBars;
 constexpr int kOffAbort = kOffTmem + 8;
 constexpr size_t kSmemUsed = kOffAbort + 8;
@@ -116,6 +138,18 @@ __device__ __forceinline__ void stage_l1_pairs(uint8_t* dst, const __nv_bfloat16
         reinterpret_cast<uint4*>(dst)[i] =
             tap < 9 ? reinterpret_cast<const uint4*>(src)[(tap * CH + co) * (C0 / 8)]
                     : make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+// Output-layer weights [tap][co][32 cin] (channel co = 0 used) -> [cin / 8]
+// [n = tap, 16 rows, taps 9..15 zero] x 16 B: B of the partials' MMAs.
+__device__ __forceinline__ void stage_out_taps(uint8_t* dst, const __nv_bfloat16* src,
+                                               int tid, int nthreads) {
+    for (int i = tid; i < (CH / 8) * kNOut; i += nthreads) {
+        const int n = i % kNOut, c = i / kNOut;
+        reinterpret_cast<uint4*>(dst)[i] =
+            n < 9 ? reinterpret_cast<const uint4*>(src)[(n * CO) * (CH / 8) + c]
+                  : make_uint4(0u, 0u, 0u, 0u);
     }
 }
 
@@ -193,6 +227,26 @@ __device__ __forceinline__ void issue_tile_l1(uint32_t d_tmem, const uint8_t* in
     tc::commit(bar);
 }
 
+// The output layer's tap partials of layer-3 tile j (its rows 2j, 2j + 1 of
+// buffer A, unshifted): D[pixel][tap] = sum over the 32 channels of
+// W3[tap][c] act3[pixel][c], K = 32 in two MMAs of N = 16.
+__device__ __forceinline__ void issue_out_taps(uint32_t d_tmem, const uint8_t* a3,
+                                               const uint8_t* w, int j, uint32_t bar) {
+    constexpr uint32_t idesc = tc::idesc_bf16(128, kNOut);
+    const uint64_t a_base = tc::desc_kmajor(tc::smem_u32(a3) + kLead * 16,
+                                            kSlotsA * 16, 128);
+    const uint64_t b_base = tc::desc_kmajor(tc::smem_u32(w), kNOut * 16, 128);
+    const uint32_t a_lo = (uint32_t)a_base + (uint32_t)(2 * j * kRow);
+    const uint32_t a_hi = (uint32_t)(a_base >> 32);
+    const uint32_t b_lo = (uint32_t)b_base, b_hi = (uint32_t)(b_base >> 32);
+#pragma unroll
+    for (int kc = 0; kc < CH / 16; ++kc)
+        tc::mma_bf16(d_tmem, ((uint64_t)a_hi << 32) | (a_lo + (uint32_t)(2 * kc * kSlotsA)),
+                     ((uint64_t)b_hi << 32) | (b_lo + (uint32_t)(2 * kc * kNOut)), idesc,
+                     kc != 0);
+    tc::commit(bar);
+}
+
 // Tiles (two map rows each) of the four layers: every layer's rows shrink
 // by one at each side, down to the band's own rows.
 __host__ __device__ constexpr int tiles_of(int layer) {
@@ -244,19 +298,33 @@ __device__ __forceinline__ void epi_hidden_tile(uint32_t t_acc, const float* bia
     }
 }
 
-// Output-layer epilogue of tile j: channel 0 plus its bias plus the coarse-
-// score input channel (channel 1 of the input map) at the band's own rows.
-__device__ __forceinline__ void epi_out_tile(uint32_t t_acc, float b3,
+// The partials' epilogue of layer-3 tile j, lane quarter q: the 9 tap
+// partials of each of its pixels into shared memory.
+__device__ __forceinline__ void epi_out_taps(uint32_t t_acc, float* part, int j, int q,
+                                             int lane) {
+    float v[16];
+    tc::tmem_ld16(t_acc + ((uint32_t)(32 * q) << 16), v);
+    const int r = 32 * q + lane, slot = 1 + (2 * j + (r >> 6)) * kRow + (r & 63);
+#pragma unroll
+    for (int t = 0; t < 9; ++t) part[t * kDStride + slot] = v[t];
+}
+
+// Output rows 2i, 2i + 1 of the band (layer-3 rows 2i .. 2i + 3): the 9
+// partials at the shifted pixels, plus the bias and the coarse-score input
+// channel (channel 1 of the input map).  One pixel a thread of the group.
+__device__ __forceinline__ void epi_out_rows(const float* part, float b3,
                                              const __nv_bfloat16* __restrict__ a0,
-                                             float* __restrict__ out, int j, int q,
+                                             float* __restrict__ out, int i, int q,
                                              int lane, int s, int y0) {
-    const float v = tc::tmem_ld1(t_acc + ((uint32_t)(32 * q) << 16));
-    const int r = 32 * q + lane, row = 2 * j + (r >> 6), col = r & 63;
+    const int r = 32 * q + lane, row = 2 * i + (r >> 6), col = r & 63;
     const int Y = y0 + row;
-    if (Y < H && col < W) {
-        const long long p = (long long)s * NPIX + Y * W + col;
-        out[p] = v + b3 + __bfloat162float(a0[p * C0 + 1]);
-    }
+    if (Y >= H || col >= W) return;
+    float v = 0.f;
+#pragma unroll
+    for (int t = 0; t < 9; ++t)
+        v += part[t * kDStride + 1 + (row + 1 + t / 3 - 1) * kRow + col + t % 3 - 1];
+    const long long p = (long long)s * NPIX + Y * W + col;
+    out[p] = v + b3 + __bfloat162float(a0[p * C0 + 1]);
 }
 
 // KEEP (training): the hidden activations of each band's own rows also go
@@ -291,7 +359,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     stage_l1_pairs(smem + kOffW0, Wf, threadIdx.x, blockDim.x);
     stage(smem + kOffW1, Wf + wf1, CH, CH, CH, threadIdx.x, blockDim.x);
     stage(smem + kOffW2, Wf + wf2, CH, CH, CH, threadIdx.x, blockDim.x);
-    stage(smem + kOffW3, Wf + wf3, CO, kNOut, CH, threadIdx.x, blockDim.x);
+    stage_out_taps(smem + kOffW3, Wf + wf3, threadIdx.x, blockDim.x);
+    for (int i = threadIdx.x; i < 9 * kDStride; i += blockDim.x)
+        reinterpret_cast<float*>(smem + kOffPart)[i] = 0.f;
     for (int i = threadIdx.x; i < 4 * CH; i += blockDim.x) {
         const int l = i / CH, c = i - l * CH;
         const int off = l == 0 ? b0 : l == 1 ? b1 : l == 2 ? b2 : b3;
@@ -350,10 +420,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!ok) break;
                 tc::commit(bar(kBarInFree));  // the input is read once layer 1 is done
                 // layer 2 into half 1: tile j reads layer-1 tiles j, j + 1 and
-                // takes the columns of the last band's layer-4 tile j
+                // takes the columns of the last band's output partials of
+                // layer-3 tile j
                 for (int j = me; j < tiles_of(1); j += kIssuers) {
                     if (!wait(epi(0, j), par) || !wait(epi(0, j + 1), par)) break;
-                    if (k > 0 && j < tiles_of(3) && !wait(epi(3, j), prev)) break;
+                    if (k > 0 && j < tiles_of(2) && !wait(epi(3, j), prev)) break;
                     tc::fence_after_sync();
                     issue_tile<CH, CH>(tmem + kTmemHalf + j * 32, ba, kSlotsA, smem + kOffW1,
                                        j, bar(acc(1, j)));
@@ -375,12 +446,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                                        bar(acc(2, j)));
                 }
                 if (!ok) break;
-                // layer 4 into half 1 (the columns of this band's layer 2)
-                for (int j = me; j < tiles_of(3); j += kIssuers) {
-                    if (!wait(epi(2, j), par) || !wait(epi(2, j + 1), par)) break;
+                // the output layer's tap partials of layer-3 tile j, into
+                // half 1 (the columns of this band's layer 2)
+                for (int j = me; j < tiles_of(2); j += kIssuers) {
+                    if (!wait(epi(2, j), par)) break;
                     tc::fence_after_sync();
-                    issue_tile<CH, kNOut>(tmem + kTmemHalf + j * 32, ba, kSlotsA,
-                                          smem + kOffW3, j, bar(acc(3, j)));
+                    issue_out_taps(tmem + kTmemHalf + j * 32, ba, smem + kOffW3, j,
+                                   bar(acc(3, j)));
                 }
                 if (!ok) break;
             }
@@ -396,22 +468,44 @@ __global__ void __launch_bounds__(kThreads, 1)
                 atomicExch(err, 1);
         }
     } else {
-        // epilogue warpgroup g takes every fourth of the band's tiles, in
-        // the order the issuer issues them; warp q of the group reads TMEM
-        // lanes 32 q .. 32 q + 31
+        // epilogue warpgroup g takes every fourth of the band's items, in
+        // the order the issuers issue them (three hidden layers' tiles, the
+        // output partials of the layer-3 tiles, the output row pairs);
+        // warp q of the group reads TMEM lanes 32 q .. 32 q + 31
         const int g = warp >> 2, q = warp & 3;
+        float* part = reinterpret_cast<float*>(smem + kOffPart);
         bool ok = true;
         int P = 0, k = 0;
+        auto wt = [&](int b, uint32_t par) {
+            if (ok) ok = tc::mbar_wait_or_abort(bar(b), par, polls, abort);
+            return ok;
+        };
         for (long long u = blockIdx.x; u < units && ok; u += gridDim.x, ++k) {
             const int s = (int)(u / kBands);
             const int y0 = (int)(u - (long long)s * kBands) * kBand;
-            const uint32_t par = (uint32_t)k & 1u;
-            for (int L = 0; L < 4 && ok; ++L) {
-                for (int j = 0; j < tiles_of(L); ++j, ++P) {
+            const uint32_t par = (uint32_t)k & 1u, prev = par ^ 1u;
+            for (int L = 0; L < 5 && ok; ++L) {
+                const int nt = L < 4 ? tiles_of(L < 3 ? L : 2) : tiles_of(3);
+                for (int j = 0; j < nt; ++j, ++P) {
                     if ((P & 3) != g) continue;
-                    ok = tc::mbar_wait_or_abort(bar(kBarAcc + L * kMaxTiles + j), par,
-                                                polls, abort);
-                    if (!ok) break;
+                    if (L == 4) {
+                        // output rows 2j, 2j + 1: partials of layer-3 tiles
+                        // j and j + 1
+                        if (!wt(kBarEpi + 3 * kMaxTiles + j, par) ||
+                            !wt(kBarEpi + 3 * kMaxTiles + j + 1, par))
+                            break;
+                        epi_out_rows(part, bias[3 * CH], a0, out, j, q, lane, s, y0);
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(bar(kBarOut + j));
+                        continue;
+                    }
+                    // the partials of tile j overwrite rows that the last
+                    // band's output rows j - 1 and j read
+                    if (L == 3 && k > 0 &&
+                        ((j >= 1 && j - 1 < tiles_of(3) && !wt(kBarOut + j - 1, prev)) ||
+                         (j < tiles_of(3) && !wt(kBarOut + j, prev))))
+                        break;
+                    if (!wt(kBarAcc + L * kMaxTiles + j, par)) break;
                     tc::fence_after_sync();
                     const uint32_t t_acc = tmem + (uint32_t)(L & 1) * kTmemHalf + j * 32;
                     if (L == 0)
@@ -424,7 +518,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         epi_hidden_tile<KEEP>(t_acc, bias + 2 * CH, y0 - 1, ba, kSlotsA, j,
                                               q, lane, act3, s, y0);
                     else
-                        epi_out_tile(t_acc, bias[3 * CH], a0, out, j, q, lane, s, y0);
+                        epi_out_taps(t_acc, part, j, q, lane);
                     // the rows written are the next layer's MMA operands
                     tc::fence_async_smem();
                     tc::fence_before_sync();
