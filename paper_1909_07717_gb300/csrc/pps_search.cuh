@@ -361,6 +361,7 @@ __device__ __forceinline__ float shot_angle_of(const float (*opp)[2],
     const float hi = atan2f(__fsub_rn(hw, cy), gx);
     float s[JMAX], e[JMAX];
     bool all = false;
+    int blocked = 0;
     const float r2 = __fmul_rn(r, r);
     // Post directions from c: A to the lower post, B to the upper one.
     const float ax = gx, ay = __fsub_rn(-hw, cy), by = __fsub_rn(hw, cy);
@@ -391,6 +392,7 @@ __device__ __forceinline__ float shot_angle_of(const float (*opp)[2],
             const float half = asinf(fminf(__fdiv_rn(r, d), 1.f));
             s[j] = __fsub_rn(phi, half);
             e[j] = __fadd_rn(phi, half);
+            ++blocked;
         }
     }
     if (all) return 0.f;
@@ -398,18 +400,35 @@ __device__ __forceinline__ float shot_angle_of(const float (*opp)[2],
     // unused slots sit at 1e30, last), then sweep: a gap opens wherever the
     // next start lies beyond every end so far.  Each gap is the difference
     // of an end (or lo) and the next start (or hi), as in the definition.
+    // With at most one blocked interval the sorted order is that interval
+    // (if any) followed by the unused slots: it is moved to the front
+    // instead, and the sweep sees the same array.
+    if (blocked >= 2) {
 #pragma unroll
-    for (int round = 0; round < JMAX; ++round)
+        for (int round = 0; round < JMAX; ++round)
 #pragma unroll
-        for (int i = round & 1; i + 1 < JMAX; i += 2) {
-            const bool sw = s[i] > s[i + 1];
-            const float s0 = fminf(s[i], s[i + 1]), s1 = fmaxf(s[i], s[i + 1]);
-            const float e0 = sw ? e[i + 1] : e[i], e1 = sw ? e[i] : e[i + 1];
-            s[i] = s0;
-            s[i + 1] = s1;
-            e[i] = e0;
-            e[i + 1] = e1;
-        }
+            for (int i = round & 1; i + 1 < JMAX; i += 2) {
+                const bool sw = s[i] > s[i + 1];
+                const float s0 = fminf(s[i], s[i + 1]), s1 = fmaxf(s[i], s[i + 1]);
+                const float e0 = sw ? e[i + 1] : e[i], e1 = sw ? e[i] : e[i + 1];
+                s[i] = s0;
+                s[i + 1] = s1;
+                e[i] = e0;
+                e[i + 1] = e1;
+            }
+    } else {
+        float s0 = s[0], e0 = e[0];
+#pragma unroll
+        for (int j = 1; j < JMAX; ++j)
+            if (s[j] < s0) {
+                s0 = s[j];
+                e0 = e[j];
+            }
+        s[0] = s0;
+        e[0] = e0;
+#pragma unroll
+        for (int j = 1; j < JMAX; ++j) s[j] = e[j] = 1e30f;
+    }
     float best = 0.f, cur = lo, start = lo;
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
