@@ -150,12 +150,14 @@ __global__ void __launch_bounds__(TPB) batch_search_kernel(const BatchArgs a) {
     }
 }
 
-// One thread per state of the bucket: decode the key, re-evaluate the
-// winning point for its margin and check that the score reproduces.
+// One warp per state of the bucket (finalize_blocks(n) CTAs of 128): decode
+// the key, re-evaluate the winning point for its margin (the lanes sharing
+// its samples) and check that the score reproduces; lane 0 writes.
 template <int JMAX, int VMAX>
 __global__ void __launch_bounds__(128) batch_finalize_kernel(const BatchArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) *a.next = 0ull;  // the queue is empty again for the next launch
+    const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const bool lead = (threadIdx.x & 31) == 0;
+    if (i == 0 && lead) *a.next = 0ull;  // the queue is empty again for the next launch
     if (i >= a.n_bucket) return;
     const int s = a.bucket_states[i];
     const pps_state& st = a.states[s];
@@ -184,8 +186,8 @@ __global__ void __launch_bounds__(128) batch_finalize_kernel(const BatchArgs a) 
         OppRegs<JMAX> o;
         load_opps<JMAX>(st, sk, o);
         PointResult<JMAX, VMAX> r;
-        eval_point<JMAX, VMAX, false>(a.prm, jv.gr, jv.sp, jv.sp2, st, sk, o,
-                                      b.ix, b.iy, nullptr, r);
+        eval_point<JMAX, VMAX, false, kKUnroll, 32>(a.prm, jv.gr, jv.sp, jv.sp2, st,
+                                                    sk, o, b.ix, b.iy, nullptr, r);
         float m = 0.f, sc = 0.f;
         bool f = false;
 #pragma unroll
@@ -199,6 +201,7 @@ __global__ void __launch_bounds__(128) batch_finalize_kernel(const BatchArgs a) 
         if (!f || __float_as_uint(sc) != __float_as_uint(b.score))
             b.status |= PPS_STATE_INCONSISTENT;
     }
+    if (!lead) return;
     a.best[s] = b;
     // Leave the scratch cleared for the next launch that reuses it.
     a.keys[s] = 0ull;

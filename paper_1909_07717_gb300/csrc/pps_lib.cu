@@ -135,7 +135,7 @@ cudaError_t launch(const pps::SearchArgs& a, int num_sms, cudaStream_t st) {
     const long long need = (items + tpb / 32 - 1) / (tpb / 32);
     if (grid > need) grid = need;
     pps::search_kernel<J, V, EXT><<<(unsigned)grid, tpb, 0, st>>>(a);
-    pps::finalize_kernel<J, V><<<(a.n_states + 127) / 128, 128, 0, st>>>(a);
+    pps::finalize_kernel<J, V><<<pps::finalize_blocks(a.n_states), 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 

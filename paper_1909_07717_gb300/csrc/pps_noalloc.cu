@@ -129,7 +129,7 @@ cudaError_t launch(const pps::SearchArgs& a, const DeviceSetup& dv,
     const long long need = (items + tpb / 32 - 1) / (tpb / 32);
     if (grid > need) grid = need;
     pps::search_kernel<J, V><<<(unsigned)grid, tpb, 0, st>>>(a);
-    pps::finalize_kernel<J, V><<<(a.n_states + 127) / 128, 128, 0, st>>>(a);
+    pps::finalize_kernel<J, V><<<pps::finalize_blocks(a.n_states), 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 

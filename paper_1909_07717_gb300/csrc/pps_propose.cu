@@ -138,7 +138,7 @@ cudaError_t run(const pps::SearchArgs& base, const int* cells, int topk,
     if (e != cudaSuccess) return e;
     refine_kernel<J, V><<<(unsigned)grid, tpb, 0, st>>>(a, cells, topk, prune,
                                                         ns.queue);
-    pps::finalize_kernel<J, V><<<(a.n_states + 127) / 128, 128, 0, st>>>(a);
+    pps::finalize_kernel<J, V><<<pps::finalize_blocks(a.n_states), 128, 0, st>>>(a);
     if (!fallback) return cudaGetLastError();
     e = cudaMemsetAsync(ns.list_n, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
@@ -153,7 +153,7 @@ cudaError_t run(const pps::SearchArgs& base, const int* cells, int topk,
     // one CTA per SM at most: the list is usually empty or short
     pps::search_kernel<J, V, true>
         <<<(unsigned)num_sms, pps::search_tpb<J, V>(), 0, st>>>(a);
-    pps::finalize_kernel<J, V><<<(a.n_states + 127) / 128, 128, 0, st>>>(a);
+    pps::finalize_kernel<J, V><<<pps::finalize_blocks(a.n_states), 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -341,7 +341,8 @@ __global__ void __launch_bounds__(pps::search_tpb<JMAX, VMAX>(), 1)
 template <int JMAX, int VMAX>
 __global__ void __launch_bounds__(128) jobs_finalize_kernel(const JobsArgs a,
                                                             bool listed) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    // one warp per state; the lanes share the re-evaluation's samples
+    const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (i >= (listed ? *a.list_n : a.n)) return;
     const int s = listed ? a.list[i] : i;
     const pps_state& st = a.states[s];
@@ -371,8 +372,8 @@ __global__ void __launch_bounds__(128) jobs_finalize_kernel(const JobsArgs a,
         pps::OppRegs<JMAX> o;
         pps::load_opps<JMAX>(st, sk, o);
         pps::PointResult<JMAX, VMAX> r;
-        pps::eval_point<JMAX, VMAX, false>(a.prm, jc.gr, jc.sp, jc.sp2, st, sk,
-                                           o, b.ix, b.iy, nullptr, r);
+        pps::eval_point<JMAX, VMAX, false, pps::kKUnroll, 32>(
+            a.prm, jc.gr, jc.sp, jc.sp2, st, sk, o, b.ix, b.iy, nullptr, r);
         float mg = 0.f, sc = 0.f;
         bool f = false;
 #pragma unroll
@@ -386,6 +387,7 @@ __global__ void __launch_bounds__(128) jobs_finalize_kernel(const JobsArgs a,
         if (!f || __float_as_uint(sc) != __float_as_uint(b.score))
             b.status |= PPS_STATE_INCONSISTENT;
     }
+    if ((threadIdx.x & 31) != 0) return;
     a.best[s] = b;
     a.keys[s] = 0ull;
     a.counts[s] = 0;
@@ -408,7 +410,7 @@ cudaError_t run_jobs(JobsArgs a, bool fallback, bool prune,
     if (e != cudaSuccess) return e;
     refine_jobs_kernel<J, V><<<(unsigned)grid, tpb, 0, st>>>(a, prune,
                                                              ns.queue);
-    jobs_finalize_kernel<J, V><<<(a.n + 127) / 128, 128, 0, st>>>(a, false);
+    jobs_finalize_kernel<J, V><<<pps::finalize_blocks(a.n), 128, 0, st>>>(a, false);
     if (!fallback) return cudaGetLastError();
     e = cudaMemsetAsync(ns.list_n, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
@@ -418,7 +420,7 @@ cudaError_t run_jobs(JobsArgs a, bool fallback, bool prune,
     a.list_n = ns.list_n;
     // the finalize left every key and count at zero
     fallback_jobs_kernel<J, V><<<(unsigned)num_sms, tpb, 0, st>>>(a);
-    jobs_finalize_kernel<J, V><<<(a.n + 127) / 128, 128, 0, st>>>(a, true);
+    jobs_finalize_kernel<J, V><<<pps::finalize_blocks(a.n), 128, 0, st>>>(a, true);
     return cudaGetLastError();
 }
 

@@ -304,7 +304,9 @@ __device__ __forceinline__ float opp_min(float f, float cbx, float cby,
 
 // A3 + A4 over the K samples of one point.  mv[v] accumulates
 // min_k (a T_k + sqrt(v^2 - 2 a s_k)); Trow (debug) receives T_k.
-template <int JMAX, int VMAX, bool GEN, bool TDBG, int KU = kKUnroll>
+// STRIDE 32: the warp's lanes share one point, lane l taking samples
+// l + 1, l + 33, ... (the caller takes the minimum over the lanes).
+template <int JMAX, int VMAX, bool GEN, bool TDBG, int KU = kKUnroll, int STRIDE = 1>
 __device__ __forceinline__ void sample_loop(const StateK& sk,
                                             const OppRegs<JMAX>& o,
                                             float cbx, float cby,
@@ -321,8 +323,9 @@ __device__ __forceinline__ void sample_loop(const StateK& sk,
     // Float sample counter: exact for K <= 2^24, and keeps integer-to-float
     // conversions out of the loop.
     const float Kf = (float)sk.K;
+    const float k0 = STRIDE == 1 ? 1.f : (float)(1 + (threadIdx.x & 31));
 #pragma unroll KU
-    for (float kf = 1.f; kf <= Kf; kf += 1.f) {
+    for (float kf = k0; kf <= Kf; kf += (float)STRIDE) {
         const float f = __fmul_rn(kf, sk.invK);
         const int k = (int)kf;
         const float n = opp_min<JMAX, GEN>(f, cbx, cby, o, sk.reach);
@@ -480,7 +483,11 @@ struct ItemGrid {
 
 // KU: unroll of the sample loop (samples a register block holds); it only
 // replicates the loop body, so every result is the same bit for bit.
-template <int JMAX, int VMAX, bool TDBG, int KU = kKUnroll>
+// STRIDE 32 (all 32 lanes of a warp on the same point): the lanes split the
+// samples and the minimum over them is taken across the warp -- the same
+// minimum, so the same results bit for bit, in a 32nd of the serial time
+// (the finalize kernels, which re-evaluate one point per state).
+template <int JMAX, int VMAX, bool TDBG, int KU = kKUnroll, int STRIDE = 1>
 __device__ __forceinline__ void eval_point(const pps_params& prm,
                                            const ItemGrid& gr,
                                            const float (&sp)[PPS_MAX_SPEEDS],
@@ -508,11 +515,18 @@ __device__ __forceinline__ void eval_point(const pps_params& prm,
 #pragma unroll
     for (int v = 0; v < VMAX; ++v) mv[v] = CUDART_INF_F;
     if (sk.general)
-        sample_loop<JMAX, VMAX, true, TDBG, KU>(sk, o, cbx, cby, twoabD, sp2, mv,
-                                                Trow);
+        sample_loop<JMAX, VMAX, true, TDBG, KU, STRIDE>(sk, o, cbx, cby, twoabD, sp2,
+                                                        mv, Trow);
     else
-        sample_loop<JMAX, VMAX, false, TDBG, KU>(sk, o, cbx, cby, twoabD, sp2, mv,
-                                                 Trow);
+        sample_loop<JMAX, VMAX, false, TDBG, KU, STRIDE>(sk, o, cbx, cby, twoabD, sp2,
+                                                         mv, Trow);
+    if (STRIDE > 1) {
+#pragma unroll
+        for (int v = 0; v < VMAX; ++v)
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+                mv[v] = fminf(mv[v], __shfl_xor_sync(0xffffffffu, mv[v], off));
+    }
 
     // A5: the receiver is in front of the goal line iff x0 + ix g < L/2,
     // decided exactly on the FP64 grid coordinate.
@@ -748,11 +762,18 @@ __global__ void __launch_bounds__(search_tpb<JMAX, VMAX>(), 1)
     }
 }
 
+// CTAs of 128 threads for the finalize kernels of n states (a warp each).
+__host__ __device__ constexpr unsigned finalize_blocks(long long n) {
+    return (unsigned)((n + 3) / 4);
+}
+
 // Per state: decode the key, re-evaluate the winning point for its margin
-// and check that the score reproduces.
+// and check that the score reproduces.  One warp per state (4 a CTA,
+// finalize_blocks(n) CTAs); the lanes share the re-evaluation's samples and
+// lane 0 writes the record.
 template <int JMAX, int VMAX>
 __global__ void __launch_bounds__(128) finalize_kernel(const SearchArgs a) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (s >= a.n_states) return;
     if (a.skip && a.skip[s]) return;
     const pps_state& st = a.states[s];
@@ -780,8 +801,8 @@ __global__ void __launch_bounds__(128) finalize_kernel(const SearchArgs a) {
         load_opps<JMAX>(st, sk, o);
         PointResult<JMAX, VMAX> r;
         const ItemGrid gr{a.g, a.x0, a.y0, a.V};
-        eval_point<JMAX, VMAX, false>(a.prm, gr, a.speed, a.speed2, st, sk, o,
-                                      b.ix, b.iy, nullptr, r);
+        eval_point<JMAX, VMAX, false, kKUnroll, 32>(a.prm, gr, a.speed, a.speed2, st,
+                                                    sk, o, b.ix, b.iy, nullptr, r);
         float m = 0.f, sc = 0.f;
         bool f = false;
 #pragma unroll
@@ -795,7 +816,7 @@ __global__ void __launch_bounds__(128) finalize_kernel(const SearchArgs a) {
         if (!f || __float_as_uint(sc) != __float_as_uint(b.score))
             b.status |= PPS_STATE_INCONSISTENT;
     }
-    a.best[s] = b;
+    if ((threadIdx.x & 31) == 0) a.best[s] = b;
 }
 
 }  // namespace pps
