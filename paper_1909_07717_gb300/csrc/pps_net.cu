@@ -92,6 +92,18 @@ cudaError_t cast_weights(pps_net* nt) {
 }
 
 // The input map of n states into nt->a0: rasterised from the states, or
+// The rasteriser of n states into nt->a0: a lane a pixel when that fills a
+// wave of the GPU's resident CTAs, else four lanes a pixel (a quarter of
+// the serial chain for the small batches of serving; same results).
+void launch_raster(pps_net* nt, const pps_state* states, int n, cudaStream_t st) {
+    if ((long long)n * raster_ctas<1>() >= 8LL * nt->num_sms)
+        raster_kernel<1><<<(unsigned)(n * raster_ctas<1>()), kRasterTpb, 0, st>>>(
+            states, n, nt->cfg, nt->a0);
+    else
+        raster_kernel<4><<<(unsigned)(n * raster_ctas<4>()), kRasterTpb, 0, st>>>(
+            states, n, nt->cfg, nt->a0);
+}
+
 // (states NULL) copied from a caller's map[n][46][61][8] bf16 into the
 // 16-channel rows the kernels read (channels 8..15 zero).
 cudaError_t load_input(pps_net* nt, const pps_state* states,
@@ -99,8 +111,7 @@ cudaError_t load_input(pps_net* nt, const pps_state* states,
     const long long P = (long long)n * NPIX;
     cudaStream_t st = nt->stream;
     if (states) {
-        raster_kernel<<<(unsigned)(n * kRasterCtas), kRasterTpb, 0, st>>>(states, n, nt->cfg,
-                                                      nt->a0);
+        launch_raster(nt, states, n, st);
         return cudaGetLastError();
     }
     if ((reinterpret_cast<uintptr_t>(map) & 15) != 0)
@@ -541,8 +552,7 @@ extern "C" pps_status pps_net_raster(pps_net* nt, const pps_state* states,
     if (!out) return PPS_EINVAL;
     cudaSetDevice(nt->device);
     const long long P = (long long)n * NPIX;
-    raster_kernel<<<(unsigned)(n * kRasterCtas), kRasterTpb, 0, nt->stream>>>(states, n, nt->cfg,
-                                                          nt->a0);
+    launch_raster(nt, states, n, nt->stream);
     if ((reinterpret_cast<uintptr_t>(out) & 15) != 0)
         return fail(PPS_EINVAL, "pps_net_raster: out must be 16-byte aligned");
     narrow_map_kernel<<<blocks(P, 256), 256, 0, nt->stream>>>(

@@ -70,7 +70,9 @@ constexpr float kScoreFloor = -1.2f;  // below every score of a 12 x 9 m field
 constexpr float kSubOff = 0.05f;      // sub-points: the cell's quadrant centres
 
 // The cell features of the pixel centred at (cx, cy), each the largest over
-// the four sub-points (cx +- 0.05, cy +- 0.05) (clamped into the field):
+// its four sub-points (cx +- 0.05, cy +- 0.05) (clamped into the field);
+// with LANES = 4 this lane takes sub-point sub0 alone and the caller takes
+// the largest across the four lanes that share the pixel:
 // f[0] the coarse score (the value function with the margin of kFeatK
 // samples; kScoreFloor where no speed is feasible), f[1] the margin (best
 // speed, clamped to [-2, 1]), f[2] the open shot angle / pi.
@@ -120,12 +122,12 @@ __device__ __forceinline__ float opp_min_shared(float f, float cbx, float cby,
 // VMAX: speed slots (4 or 8; the slots past cfg.V repeat the last speed
 // and are left out of the margin), the ball terms of two speeds a packed
 // f32x2 instruction.
-template <int J, bool GEN, int VMAX>
+template <int J, bool GEN, int VMAX, int LANES>
 __device__ __forceinline__ void cell_features(const pps_state& st,
                                               const StateK& sk,
                                               const OppRegs<J>& o,
                                               const RasterCfg& cfg, float cx,
-                                              float cy, float (&f)[3]) {
+                                              float cy, int sub0, float (&f)[3]) {
     constexpr int VP = VMAX / 2;
     float2 s2[VP];
 #pragma unroll
@@ -134,7 +136,7 @@ __device__ __forceinline__ void cell_features(const pps_state& st,
     const float hw = 0.5f * st.field_wid;
     float mbest = -CUDART_INF_F, tbest = 0.f, sbest = kScoreFloor;
 #pragma unroll 1
-    for (int sub = 0; sub < 4; ++sub) {
+    for (int sub = sub0; sub < 4; sub += LANES) {
         const float qx =
             fminf(fmaxf(cx + ((sub & 1) ? kSubOff : -kSubOff), -sk.Lh), sk.Lh);
         const float qy =
@@ -212,17 +214,28 @@ __device__ __forceinline__ void cell_features(const pps_state& st,
 // thread derives the state's constants and scales its opponents into
 // shared memory, and the pixels read them from there (broadcasts) instead
 // of each thread deriving them and holding the opponents in registers.
+// LANES lanes a pixel: 1 (each lane the pixel's four sub-points in turn;
+// the most work a CTA, for large batches) or 4 (a lane a sub-point, the
+// features' maxima taken across the four: a quarter of the serial chain,
+// for batches that leave most of the GPU idle).
 constexpr int kRasterTpb = 128;
-constexpr int kRasterCtas = (NPIX + kRasterTpb - 1) / kRasterTpb;
+template <int LANES>
+__host__ __device__ constexpr int raster_ctas() {
+    return (NPIX + kRasterTpb / LANES - 1) / (kRasterTpb / LANES);
+}
 
+template <int LANES>
 __global__ void __launch_bounds__(kRasterTpb, 8)
     raster_kernel(const pps_state* __restrict__ states, int n,
                               const RasterCfg cfg,
                               __nv_bfloat16* __restrict__ out) {
+    constexpr int kPix = kRasterTpb / LANES, kCtas = raster_ctas<LANES>();
     __shared__ StateK s_sk;
     __shared__ __align__(16) unsigned char s_opp[sizeof(OppRegs<PPS_MAX_OPP>)];
-    const int s = (int)(blockIdx.x / kRasterCtas);
-    const int q = (int)(blockIdx.x - (unsigned)s * kRasterCtas) * kRasterTpb + threadIdx.x;
+    const int s = (int)(blockIdx.x / kCtas);
+    const int sub = LANES == 4 ? (int)(threadIdx.x & 3) : 0;
+    const int q = (int)(blockIdx.x - (unsigned)s * kCtas) * kPix +
+                  (int)(threadIdx.x / LANES);
     const pps_state& st = states[s];
     if (threadIdx.x == 0) {
         const StateK d = derive_state(st, cfg.prm, PPS_MAX_OPP, PPS_MAX_K);
@@ -233,37 +246,51 @@ __global__ void __launch_bounds__(kRasterTpb, 8)
             load_opps<PPS_MAX_OPP>(st, d, *reinterpret_cast<OppRegs<PPS_MAX_OPP>*>(s_opp));
     }
     __syncthreads();
-    if (q >= NPIX) return;
-    const long long i = (long long)s * NPIX + q;
-    const int y = q / W, x = q - y * W;
+    // lanes past the map's last pixel still take part in the shuffles below
+    const bool active = q < NPIX;
+    const int qa = active ? q : NPIX - 1;
+    const long long i = (long long)s * NPIX + qa;
+    const int y = qa / W, x = qa - y * W;
     const float cx = __fdiv_rn((float)(x - 30), 5.f);
     const float cy = __fdiv_rn(__fsub_rn((float)y, 22.5f), 5.f);
     const StateK& sk = s_sk;
+
+    float f[3] = {kScoreFloor, -2.f, 0.f};
+    if (sk.valid && active) {
+        const auto& o8 = *reinterpret_cast<const OppRegs<8>*>(s_opp);
+        const auto& o16 = *reinterpret_cast<const OppRegs<PPS_MAX_OPP>*>(s_opp);
+        if (cfg.V <= 4) {
+            if (sk.nopp <= 8)
+                sk.general ? cell_features<8, true, 4, LANES>(st, sk, o8, cfg, cx, cy, sub, f)
+                           : cell_features<8, false, 4, LANES>(st, sk, o8, cfg, cx, cy, sub, f);
+            else
+                sk.general ? cell_features<PPS_MAX_OPP, true, 4, LANES>(st, sk, o16, cfg, cx, cy, sub, f)
+                           : cell_features<PPS_MAX_OPP, false, 4, LANES>(st, sk, o16, cfg, cx, cy, sub, f);
+        } else {
+            if (sk.nopp <= 8)
+                sk.general ? cell_features<8, true, 8, LANES>(st, sk, o8, cfg, cx, cy, sub, f)
+                           : cell_features<8, false, 8, LANES>(st, sk, o8, cfg, cx, cy, sub, f);
+            else
+                sk.general ? cell_features<PPS_MAX_OPP, true, 8, LANES>(st, sk, o16, cfg, cx, cy, sub, f)
+                           : cell_features<PPS_MAX_OPP, false, 8, LANES>(st, sk, o16, cfg, cx, cy, sub, f);
+        }
+    }
+    // the largest over the pixel's four sub-points (maxima are exact; the
+    // margin's clamp is monotone, so the clamp of the largest is the largest
+    // clamp)
+    if (LANES == 4) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int off = 1; off < 4; off <<= 1)
+                f[k] = fmaxf(f[k], __shfl_xor_sync(0xffffffffu, f[k], off));
+    }
+    if (!active || sub != 0) return;
 
     float dens = 0.f;
     for (int j = 0; j < sk.nopp; ++j) {
         const float dx = cx - st.opp_pos[j][0], dy = cy - st.opp_pos[j][1];
         dens += expf(-(dx * dx + dy * dy) / (2.f * kSigOpp * kSigOpp));
-    }
-    float f[3] = {kScoreFloor, -2.f, 0.f};
-    if (sk.valid) {
-        const auto& o8 = *reinterpret_cast<const OppRegs<8>*>(s_opp);
-        const auto& o16 = *reinterpret_cast<const OppRegs<PPS_MAX_OPP>*>(s_opp);
-        if (cfg.V <= 4) {
-            if (sk.nopp <= 8)
-                sk.general ? cell_features<8, true, 4>(st, sk, o8, cfg, cx, cy, f)
-                           : cell_features<8, false, 4>(st, sk, o8, cfg, cx, cy, f);
-            else
-                sk.general ? cell_features<PPS_MAX_OPP, true, 4>(st, sk, o16, cfg, cx, cy, f)
-                           : cell_features<PPS_MAX_OPP, false, 4>(st, sk, o16, cfg, cx, cy, f);
-        } else {
-            if (sk.nopp <= 8)
-                sk.general ? cell_features<8, true, 8>(st, sk, o8, cfg, cx, cy, f)
-                           : cell_features<8, false, 8>(st, sk, o8, cfg, cx, cy, f);
-            else
-                sk.general ? cell_features<PPS_MAX_OPP, true, 8>(st, sk, o16, cfg, cx, cy, f)
-                           : cell_features<PPS_MAX_OPP, false, 8>(st, sk, o16, cfg, cx, cy, f);
-        }
     }
     const float dxm = cx - sk.bx, dym = cy - sk.by;
     const float gx = sk.Lh - cx;

@@ -89,6 +89,26 @@ def _forward_map(torch, net, dmaps, n, layers):
     return out.cpu().numpy().astype(np.float64)
 
 
+def test_raster_lane_mappings_agree(torch):
+    """The rasteriser runs a lane a pixel for batches that fill the GPU and
+    four lanes a pixel (one a sub-point, the maxima taken across them) for
+    small ones: 160 states in one call and the same states 4 at a time give
+    the same bits (with a 16-opponent state, an invalid one and one with no
+    opponents among them)."""
+    batch = synth.ssl_states(509, 160, K=64, n_opp=16)
+    batch["n_opp"][3] = 0
+    batch["n_opp"][77] = 11
+    batch["K"][5] = 0                      # invalid
+    net = pps.Net(max_batch=160)
+    try:
+        _, whole = _gpu_raster(torch, net, batch)
+        parts = [_gpu_raster(torch, net, synth.take(batch, list(range(i, i + 4))))[1]
+                 for i in range(0, 160, 4)]
+    finally:
+        net.close()
+    assert np.array_equal(whole, np.concatenate(parts))
+
+
 def test_forward_exact_on_an_integer_network(torch):
     """Integer input maps and weights: every sum of the network is an
     integer that float32 and bfloat16 hold exactly (net_bounds asserts
