@@ -52,7 +52,7 @@ int pps_occupancy(const void* func, int tpb, size_t smem);
 struct pps_net_scratch {
     int* skip;
     int* list;
-    int* list_n;
+    int* list_n;                // == (int*)(queue + 1)
     unsigned long long* queue;  // the refinement's work-queue counter
 };
 cudaError_t pps_net_predict(pps_net* net, const pps_state* states, int n,

@@ -36,8 +36,10 @@ struct pps_net {
     int* cells = nullptr;  // proposal scratch: max_batch x NPIX
     int* skip = nullptr;   // proposal scratch: max_batch
     int* list = nullptr;   // proposal scratch: max_batch states to re-search
-    int* list_n = nullptr; // proposal scratch: their number
-    unsigned long long* queue = nullptr;  // proposal scratch: work queue
+    // proposal scratch: the work queue's counter, then (in the next 8
+    // bytes, so that one memset clears both) the list's length
+    unsigned long long* queue = nullptr;
+    int* list_n = nullptr;
     float* smax = nullptr; // training scratch: max_batch best labels
     int* err = nullptr;    // set by a kernel whose bounded wait ran out
     float* wpart = nullptr;  // weight-gradient partial sums, one row per CTA
@@ -409,8 +411,8 @@ extern "C" pps_status pps_net_create(int device, void* stream, int max_batch,
     al(&nt->skip, sizeof(int) * (size_t)max_batch);
     al(&nt->smax, sizeof(float) * (size_t)max_batch);
     al(&nt->list, sizeof(int) * (size_t)max_batch);
-    al(&nt->list_n, sizeof(int));
-    al(&nt->queue, sizeof(unsigned long long));
+    al(&nt->queue, 2 * sizeof(unsigned long long));
+    if (nt->queue) nt->list_n = reinterpret_cast<int*>(nt->queue + 1);
     al(&nt->err, sizeof(int));
     al(&nt->wpart, sizeof(float) * (size_t)(nt->num_sms > 0 ? nt->num_sms : 1) *
                        (9 * CH * CH + CH));
@@ -434,8 +436,8 @@ extern "C" void pps_net_destroy(pps_net* nt) {
                     (void*)nt->a2, (void*)nt->a3, (void*)nt->g1, (void*)nt->g2,
                     (void*)nt->g3, (void*)nt->g4, (void*)nt->out,
                     (void*)nt->loss, (void*)nt->cells, (void*)nt->skip,
-                    (void*)nt->smax, (void*)nt->list, (void*)nt->list_n,
-                    (void*)nt->err, (void*)nt->wpart, (void*)nt->queue})
+                    (void*)nt->smax, (void*)nt->list, (void*)nt->err,
+                    (void*)nt->wpart, (void*)nt->queue})
         if (p) cudaFree(p);
     cudaGetLastError();
     delete nt;

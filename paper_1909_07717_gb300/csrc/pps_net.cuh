@@ -230,13 +230,23 @@ __global__ void __launch_bounds__(kRasterTpb, 8)
                               const RasterCfg cfg,
                               __nv_bfloat16* __restrict__ out) {
     constexpr int kPix = kRasterTpb / LANES, kCtas = raster_ctas<LANES>();
+    constexpr int kStateWords = (int)(sizeof(pps_state) / 4);
+    static_assert(sizeof(pps_state) % 4 == 0 && kStateWords <= kRasterTpb,
+                  "the state is copied a 32-bit word a thread");
     __shared__ StateK s_sk;
     __shared__ __align__(16) unsigned char s_opp[sizeof(OppRegs<PPS_MAX_OPP>)];
+    __shared__ __align__(16) pps_state s_st;
     const int s = (int)(blockIdx.x / kCtas);
     const int sub = LANES == 4 ? (int)(threadIdx.x & 3) : 0;
     const int q = (int)(blockIdx.x - (unsigned)s * kCtas) * kPix +
                   (int)(threadIdx.x / LANES);
-    const pps_state& st = states[s];
+    // the state in shared memory, a word a thread (one memory latency, not
+    // the chain of field loads the derivation would wait on)
+    if (threadIdx.x < kStateWords)
+        reinterpret_cast<uint32_t*>(&s_st)[threadIdx.x] =
+            __ldg(reinterpret_cast<const uint32_t*>(states + s) + threadIdx.x);
+    __syncthreads();
+    const pps_state& st = s_st;
     if (threadIdx.x == 0) {
         const StateK d = derive_state(st, cfg.prm, PPS_MAX_OPP, PPS_MAX_K);
         s_sk = d;
@@ -649,10 +659,16 @@ __global__ void cell_label_kernel(const float* __restrict__ point_best,
 
 // Top-k map pixels of every state (one CTA per state), best first; equal
 // scores keep the smaller pixel.  Keys are (order-preserving score bits,
-// ~pixel), all distinct: an 8-pass radix select (8-bit digits, most
-// significant first) finds the k-th largest key T, the k keys >= T are
-// compacted, and only those are sorted (bitonic, next power of two).
-constexpr int kTopkThreads = 256;
+// ~pixel), all distinct: a radix select (8-bit digits, most significant
+// first; it stops at the first digit whose keys are all needed) finds the
+// k-th largest key T, the k keys >= T are compacted, and only those are
+// ordered: up to 512 of them each go straight to its rank (the number of
+// selected keys above it, counted by several threads a key), more are
+// sorted by a bitonic network (next power of two).  1024 threads: a state
+// alone on the GPU (one frame) is latency-bound, and each thread holds at
+// most three pixels.
+constexpr int kTopkThreads = 1024;
+constexpr int kTopkIters = (NPIX + kTopkThreads - 1) / kTopkThreads;
 
 __device__ __forceinline__ unsigned long long topk_key(const float* sc, int i) {
     uint32_t u = __float_as_uint(sc[i]);
@@ -671,72 +687,121 @@ __global__ void __launch_bounds__(kTopkThreads)
     unsigned long long* key = tk;         // NPIX keys
     unsigned long long* sel = tk + NPIX;  // p2 selected keys
     __shared__ int hist[256];
-    __shared__ int warp_sum[kTopkThreads / 32];
+    __shared__ int warp_sum[8];
     __shared__ unsigned long long s_prefix;
-    __shared__ int s_need, s_count;
+    __shared__ int s_need, s_count, s_done;
     const int s = blockIdx.x, t = threadIdx.x;
     const int lane = t & 31, warp = t >> 5;
     const float* sc = scores + (long long)s * NPIX;
+    // the pixels' keys (all loads in flight at once)
     if (jobs) {
         const pps_grid g = jobs[s].grid;
         const CellLattice cl = cell_lattice(g);
-        for (int i = t; i < NPIX; i += blockDim.x) {
-            const int cy = i / W, cx = i - cy * W;
-            key[i] = cl.ok && cell_on_grid(cl, g, cx, cy)
-                         ? topk_key(sc, i)
-                         : (unsigned long long)(~(uint32_t)i);
+#pragma unroll
+        for (int it = 0; it < kTopkIters; ++it) {
+            const int i = it * kTopkThreads + t;
+            if (i < NPIX) {
+                const int cy = i / W, cx = i - cy * W;
+                key[i] = cl.ok && cell_on_grid(cl, g, cx, cy)
+                             ? topk_key(sc, i)
+                             : (unsigned long long)(~(uint32_t)i);
+            }
         }
     } else {
-        for (int i = t; i < NPIX; i += blockDim.x) key[i] = topk_key(sc, i);
+#pragma unroll
+        for (int it = 0; it < kTopkIters; ++it) {
+            const int i = it * kTopkThreads + t;
+            if (i < NPIX) key[i] = topk_key(sc, i);
+        }
     }
     if (t == 0) {
         s_prefix = 0ull;
         s_need = k;
         s_count = 0;
+        s_done = 0;
     }
     __syncthreads();
     unsigned long long mask = 0ull;
     for (int shift = 56; shift >= 0 && k < NPIX; shift -= 8) {
-        hist[t] = 0;
+        if (t < 256) hist[t] = 0;
         __syncthreads();
         const unsigned long long prefix = s_prefix;
-        for (int i = t; i < NPIX; i += blockDim.x) {
-            const unsigned long long v = key[i];
-            if ((v & mask) == prefix) atomicAdd(&hist[(v >> shift) & 255u], 1);
+#pragma unroll
+        for (int it = 0; it < kTopkIters; ++it) {
+            const int i = it * kTopkThreads + t;
+            if (i < NPIX) {
+                const unsigned long long v = key[i];
+                if ((v & mask) == prefix)
+                    atomicAdd(&hist[(v >> shift) & 255u], 1);
+            }
         }
         __syncthreads();
         // counts of digits 255 - t, inclusive scan from the top digit down
-        const int own = hist[255 - t];
-        int incl = own;
+        // (the first 256 threads)
+        int own = 0, incl = 0;
+        if (t < 256) {
+            own = hist[255 - t];
+            incl = own;
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += y;
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += y;
+            }
+            if (lane == 31) warp_sum[warp] = incl;
         }
-        if (lane == 31) warp_sum[warp] = incl;
         __syncthreads();
-        for (int w = 0; w < warp; ++w) incl += warp_sum[w];
         const int need = s_need;
+        if (t < 256) {
+            for (int w = 0; w < warp; ++w) incl += warp_sum[w];
+        }
         __syncthreads();
-        if (incl >= need && incl - own < need) {  // exactly one thread
+        if (t < 256 && incl >= need && incl - own < need) {  // exactly one thread
             s_prefix = prefix | ((unsigned long long)(255 - t) << shift);
             s_need = need - (incl - own);
+            // every key of the new prefix is needed: the prefix (its lower
+            // bits zero) is a threshold that selects exactly k keys
+            s_done = s_need == own;
         }
         mask |= 0xFFull << shift;
         __syncthreads();
+        if (s_done) break;
     }
     // the k-th largest key (or every key when k == NPIX)
     const unsigned long long T = k < NPIX ? s_prefix : 0ull;
-    for (int i = t; i < p2; i += blockDim.x) sel[i] = 0ull;
+    for (int i = t; i < p2; i += kTopkThreads) sel[i] = 0ull;
     __syncthreads();
-    for (int i = t; i < NPIX; i += blockDim.x) {
-        const unsigned long long v = key[i];
-        if (v >= T) sel[atomicAdd(&s_count, 1)] = v;
+#pragma unroll
+    for (int it = 0; it < kTopkIters; ++it) {
+        const int i = it * kTopkThreads + t;
+        const unsigned long long v = i < NPIX ? key[i] : 0ull;
+        const bool take = i < NPIX && v >= T;
+        const unsigned b = __ballot_sync(0xffffffffu, take);
+        int at = 0;
+        if (lane == 0 && b) at = atomicAdd(&s_count, __popc(b));
+        at = __shfl_sync(0xffffffffu, at, 0);
+        if (take) sel[at + __popc(b & ((1u << lane) - 1u))] = v;
     }
     __syncthreads();
+    if (k <= 512) {
+        // exactly k keys (all distinct): Q threads per key (Q a power of
+        // two, k Q <= 1024) each count the keys above it among every Q-th
+        // one, summed across the Q adjacent lanes
+        int Q = 32;
+        while (Q > 1 && Q * k > kTopkThreads) Q >>= 1;
+        const int i = t / Q, part = t & (Q - 1);
+        const unsigned long long v = i < k ? sel[i] : 0ull;
+        int r = 0;
+        if (i < k)
+            for (int j = part; j < k; j += Q) r += sel[j] > v;
+        for (int off = Q >> 1; off > 0; off >>= 1)
+            r += __shfl_xor_sync(0xffffffffu, r, off);
+        if (i < k && part == 0)
+            cells[(long long)s * k + r] = (int)(~(uint32_t)(v & 0xffffffffull));
+        return;
+    }
     for (int size = 2; size <= p2; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = t; i < p2; i += blockDim.x) {
+            for (int i = t; i < p2; i += kTopkThreads) {
                 const int j = i ^ stride;
                 if (j > i) {
                     const bool desc = (i & size) == 0;
@@ -750,7 +815,7 @@ __global__ void __launch_bounds__(kTopkThreads)
             __syncthreads();
         }
     }
-    for (int i = t; i < k; i += blockDim.x)
+    for (int i = t; i < k; i += kTopkThreads)
         cells[(long long)s * k + i] = (int)(~(uint32_t)(sel[i] & 0xffffffffull));
 }
 

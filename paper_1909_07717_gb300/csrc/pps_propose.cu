@@ -134,14 +134,13 @@ cudaError_t run(const pps::SearchArgs& base, const int* cells, int topk,
     constexpr int tpb = pps::search_tpb<J, V>();
     long long grid = (items + tpb / 32 - 1) / (tpb / 32);
     if (grid > cap) grid = cap;
-    e = cudaMemsetAsync(ns.queue, 0, sizeof(unsigned long long), st);
+    // the queue counter and the list's length (the next word) at once
+    e = cudaMemsetAsync(ns.queue, 0, 2 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     refine_kernel<J, V><<<(unsigned)grid, tpb, 0, st>>>(a, cells, topk, prune,
                                                         ns.queue);
     pps::finalize_kernel<J, V><<<pps::finalize_blocks(a.n_states), 128, 0, st>>>(a);
     if (!fallback) return cudaGetLastError();
-    e = cudaMemsetAsync(ns.list_n, 0, sizeof(int), st);
-    if (e != cudaSuccess) return e;
     fallback_list_kernel<<<(a.n_states + 127) / 128, 128, 0, st>>>(
         a.best, a.n_states, ns.skip, ns.list, ns.list_n);
     e = cudaMemsetAsync(a.keys, 0, sizeof(unsigned long long) * a.n_states, st);
@@ -173,9 +172,11 @@ bool finite_pos(float x) { return std::isfinite(x) && x > 0.f; }
 // The proposal for states that each carry a job (grid and speeds), all
 // grids of one spacing 0.2 / m on the map's cell lattice (cell_lattice):
 // fields up to 12 x 9 m.  A state's work is its topk cells' m x m fine
-// points, cut into items of 32 consecutive (cell rank, point) slots, so a
-// cell of 64 points is two items and a cell of 16 points half of one.
-// Items run rank-major: item q of every state before item q + 1 of any.
+// points, cut into items of 32 / G consecutive (cell rank, point) slots, a
+// warp an item: G lanes share a point and split its samples (G = 1 for
+// batches that fill the GPU; for small ones G grows, up to 32, until the
+// items fill it, which cuts the latency of the call by up to G).  Items
+// run rank-major: item q of every state before item q + 1 of any.
 using pps::net::CellLattice;
 using pps::net::cell_lattice;
 
@@ -183,13 +184,14 @@ struct JobsArgs {
     const pps_state* states;
     const pps_job* jobs;
     int n, kmax, m, vmax, topk, items_per_state;
+    int lanes;  // G: lanes per point, a power of two up to 32
     pps_params prm;
     const int* cells;  // n x topk map pixels, best first
     pps_best* best;
     unsigned long long* keys;
     int* counts;
-    const int* list;    // fallback: the states to search on their full grid
-    const int* list_n;
+    int* list;    // fallback: the states to search on their full grid,
+    int* list_n;  //   appended by the finalize
 };
 
 // A job's grid, speeds and cell lattice; valid = the state's grid has the
@@ -223,17 +225,54 @@ __device__ __forceinline__ void load_job_cells(const pps_job& j, int m,
     }
 }
 
+// lead: the lane that counts its point's feasible passes (the first of the
+// lanes that share the point; they all hold the same result).
+// A warp's copy of one state and its job in shared memory (the finalize):
+// every lane loads a few words at once (one memory latency) instead of the
+// chain of field loads the per-state setup would otherwise wait on, and the
+// re-evaluation reads the opponents from shared memory.
+struct WarpStateJob {
+    pps_state st;
+    pps_job job;
+};
+static_assert(sizeof(pps_state) % 4 == 0 && sizeof(pps_job) % 4 == 0,
+              "copied as 32-bit words");
+
+template <int BYTES>
+__device__ __forceinline__ void warp_copy(void* dst, const void* src,
+                                          int lane) {
+    constexpr int kWords = BYTES / 4;
+    const uint32_t* from = static_cast<const uint32_t*>(src);
+    uint32_t* to = static_cast<uint32_t*>(dst);
+    uint32_t w[(kWords + 31) / 32];
+#pragma unroll
+    for (int i = 0; i < (kWords + 31) / 32; ++i)
+        if (i * 32 + lane < kWords) w[i] = __ldg(from + i * 32 + lane);
+#pragma unroll
+    for (int i = 0; i < (kWords + 31) / 32; ++i)
+        if (i * 32 + lane < kWords) to[i * 32 + lane] = w[i];
+}
+
+__device__ __forceinline__ void load_state_job(WarpStateJob& d,
+                                               const JobsArgs& a, int s,
+                                               int lane) {
+    __syncwarp();
+    warp_copy<sizeof(pps_state)>(&d.st, a.states + s, lane);
+    warp_copy<sizeof(pps_job)>(&d.job, a.jobs + s, lane);
+    __syncwarp();
+}
+
 template <int JMAX, int VMAX>
 __device__ __forceinline__ void reduce_item(const JobsArgs& a, int s,
-                                            int lane, bool active, int p,
-                                            int P, int V,
+                                            int lane, bool active, bool lead,
+                                            int p, int P, int V,
                                             const pps::PointResult<JMAX, VMAX>& r) {
     int cnt = 0;
     unsigned long long key = 0ull;
 #pragma unroll
     for (int v = 0; v < VMAX; ++v) {
         const bool f = active && v < V && r.feas[v];
-        cnt += f;
+        cnt += f && lead;
         if (f) {
             const uint32_t idx = (uint32_t)(v * P + p);
             const unsigned long long k2 =
@@ -257,14 +296,15 @@ __global__ void __launch_bounds__(pps::search_tpb<JMAX, VMAX>(), 1)
     const int lane = threadIdx.x & 31;
     const long long n_items = (long long)a.n * a.items_per_state;
     const int m2 = a.m * a.m;
+    const int G = a.lanes, per = 32 / G;
     for (long long item = next_item(queue, lane); item < n_items;
          item = next_item(queue, lane)) {
         const int q = (int)(item / a.n);
         const int s = (int)(item - (long long)q * a.n);
+        const int slot = q * per + lane / G;
+        const int rank = slot / m2, within = slot - rank * m2;
         JobCells jc;
         load_job_cells(a.jobs[s], a.m, a.vmax, jc);
-        const int slot = q * 32 + lane;
-        const int rank = slot / m2, within = slot - rank * m2;
         bool active = jc.ok && rank < a.topk;
         int ix = 0, iy = 0;
         if (active) {
@@ -295,65 +335,35 @@ __global__ void __launch_bounds__(pps::search_tpb<JMAX, VMAX>(), 1)
             }
         }
         pps::PointResult<JMAX, VMAX> res;
-        pps::eval_point<JMAX, VMAX, false>(a.prm, jc.gr, jc.sp, jc.sp2, st, sk,
-                                           o, ix, iy, nullptr, res);
-        reduce_item<JMAX, VMAX>(a, s, lane, active, iy * jc.nx + ix, jc.P,
-                                jc.gr.V, res);
+        pps::eval_point<JMAX, VMAX, false, pps::kKUnroll, 0>(
+            a.prm, jc.gr, jc.sp, jc.sp2, st, sk, o, ix, iy, nullptr, res, G);
+        reduce_item<JMAX, VMAX>(a, s, lane, active, (lane & (G - 1)) == 0,
+                                iy * jc.nx + ix, jc.P, jc.gr.V, res);
     }
 }
 
-// Fallback: the listed states on their full grids.  A CTA takes a listed
-// state at a time and its warps share that state's 32-point items.
+// The finalize of state s by one warp (my: the warp's shared copy):
+// decode the key, re-evaluate the winner for its margin and check that the
+// score reproduces; clears the state's key and count for the next call.  A
+// state whose job does not fit the call (another spacing, off the lattice,
+// bad speeds) is invalid.  With `append`, a valid state without a pass is
+// appended to the fallback list.  The key and count are read from L2 (the
+// refinement's atomics complete there).
 template <int JMAX, int VMAX>
-__global__ void __launch_bounds__(pps::search_tpb<JMAX, VMAX>(), 1)
-    fallback_jobs_kernel(const JobsArgs a) {
-    constexpr int kWarps = pps::search_tpb<JMAX, VMAX>() / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nl = *a.list_n;
-    for (int li = blockIdx.x; li < nl; li += gridDim.x) {
-        const int s = a.list[li];
-        JobCells jc;
-        load_job_cells(a.jobs[s], a.m, a.vmax, jc);
-        if (!jc.ok) continue;
-        const pps_state& st = a.states[s];
-        const pps::StateK sk = pps::derive_state(st, a.prm, JMAX, a.kmax);
-        pps::OppRegs<JMAX> o;
-        pps::load_opps<JMAX>(st, sk, o);
-        const int words = (jc.P + 31) / 32;
-        for (int chunk = warp; chunk < words; chunk += kWarps) {
-            const int p = chunk * 32 + lane;
-            const bool active = p < jc.P;
-            const int pc = active ? p : jc.P - 1;
-            const int iy = pc / jc.nx, ix = pc - iy * jc.nx;
-            pps::PointResult<JMAX, VMAX> res;
-            pps::eval_point<JMAX, VMAX, false>(a.prm, jc.gr, jc.sp, jc.sp2, st,
-                                               sk, o, ix, iy, nullptr, res);
-            reduce_item<JMAX, VMAX>(a, s, lane, active, p, jc.P, jc.gr.V, res);
-        }
-    }
-}
-
-// Per state (or, with a list, per listed state): decode the key,
-// re-evaluate the winner for its margin and check that the score
-// reproduces; clears the state's key and count for the next call.  A state
-// whose job does not fit the call (another spacing, off the lattice, bad
-// speeds) is invalid.
-template <int JMAX, int VMAX>
-__global__ void __launch_bounds__(128) jobs_finalize_kernel(const JobsArgs a,
-                                                            bool listed) {
-    // one warp per state; the lanes share the re-evaluation's samples
-    const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (i >= (listed ? *a.list_n : a.n)) return;
-    const int s = listed ? a.list[i] : i;
-    const pps_state& st = a.states[s];
+__device__ __noinline__ void finalize_state(const JobsArgs& a, int s,
+                                            int lane, WarpStateJob& my,
+                                            bool append) {
+    const unsigned long long key = __ldcg(a.keys + s);
+    const int count = __ldcg(a.counts + s);
+    load_state_job(my, a, s, lane);
+    const pps_state& st = my.st;
     JobCells jc;
-    load_job_cells(a.jobs[s], a.m, a.vmax, jc);
+    load_job_cells(my.job, a.m, a.vmax, jc);
     pps::StateK sk = pps::derive_state(st, a.prm, JMAX, a.kmax);
     sk.valid = sk.valid && jc.ok;
     pps_best b;
-    b.n_feasible = a.counts[s];
+    b.n_feasible = count;
     b.status = sk.valid ? PPS_STATE_OK : PPS_STATE_INVALID;
-    const unsigned long long key = a.keys[s];
     if (!sk.valid || key == 0ull) {
         b.idx = sk.valid ? -1 : -2;
         b.ix = b.iy = b.speed_idx = -1;
@@ -387,10 +397,62 @@ __global__ void __launch_bounds__(128) jobs_finalize_kernel(const JobsArgs a,
         if (!f || __float_as_uint(sc) != __float_as_uint(b.score))
             b.status |= PPS_STATE_INCONSISTENT;
     }
-    if ((threadIdx.x & 31) != 0) return;
+    if (lane != 0) return;
     a.best[s] = b;
     a.keys[s] = 0ull;
     a.counts[s] = 0;
+    if (append && b.idx == -1) a.list[atomicAdd(a.list_n, 1)] = s;
+}
+
+// One warp per state.
+constexpr int kFinalizeTpb = 128;
+
+template <int JMAX, int VMAX>
+__global__ void __launch_bounds__(kFinalizeTpb)
+    jobs_finalize_kernel(const JobsArgs a, bool append) {
+    __shared__ WarpStateJob sh[kFinalizeTpb / 32];
+    const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (i >= a.n) return;
+    finalize_state<JMAX, VMAX>(a, i, threadIdx.x & 31, sh[threadIdx.x >> 5],
+                               append);
+}
+
+// Fallback: the listed states on their full grids.  A CTA takes a listed
+// state at a time and its warps share that state's 32-point items; its
+// first warp then finalizes the state.
+template <int JMAX, int VMAX>
+__global__ void __launch_bounds__(pps::search_tpb<JMAX, VMAX>(), 1)
+    fallback_jobs_kernel(const JobsArgs a) {
+    constexpr int kWarps = pps::search_tpb<JMAX, VMAX>() / 32;
+    __shared__ WarpStateJob sh;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nl = *a.list_n;
+    for (int li = blockIdx.x; li < nl; li += gridDim.x) {
+        const int s = a.list[li];
+        JobCells jc;
+        load_job_cells(a.jobs[s], a.m, a.vmax, jc);
+        if (!jc.ok) continue;
+        const pps_state& st = a.states[s];
+        const pps::StateK sk = pps::derive_state(st, a.prm, JMAX, a.kmax);
+        pps::OppRegs<JMAX> o;
+        pps::load_opps<JMAX>(st, sk, o);
+        const int words = (jc.P + 31) / 32;
+        for (int chunk = warp; chunk < words; chunk += kWarps) {
+            const int p = chunk * 32 + lane;
+            const bool active = p < jc.P;
+            const int pc = active ? p : jc.P - 1;
+            const int iy = pc / jc.nx, ix = pc - iy * jc.nx;
+            pps::PointResult<JMAX, VMAX> res;
+            pps::eval_point<JMAX, VMAX, false>(a.prm, jc.gr, jc.sp, jc.sp2, st,
+                                               sk, o, ix, iy, nullptr, res);
+            reduce_item<JMAX, VMAX>(a, s, lane, active, true, p, jc.P,
+                                    jc.gr.V, res);
+        }
+        // the state is this CTA's alone: its first warp finalizes it once
+        // every warp's atomics are done
+        __syncthreads();
+        if (warp == 0) finalize_state<JMAX, VMAX>(a, s, lane, sh, false);
+    }
 }
 
 template <int J, int V>
@@ -403,24 +465,34 @@ cudaError_t run_jobs(JobsArgs a, bool fallback, bool prune,
     const long long cap =
         (long long)num_sms *
         pps_occupancy((const void*)refine_jobs_kernel<J, V>, tpb, 0);
+    // lanes per point: doubled while the batch's items still fit in the
+    // resident warps
+    const long long slots = (long long)a.topk * a.m * a.m;
+    const long long warps = cap * (tpb / 32);
+    int G = 1;
+    while (G < 32 && (long long)a.n * ((slots * 2 * G + 31) / 32) <= warps)
+        G *= 2;
+    a.lanes = G;
+    a.items_per_state = (int)((slots * G + 31) / 32);
     const long long items = (long long)a.n * a.items_per_state;
     long long grid = (items + tpb / 32 - 1) / (tpb / 32);
     if (grid > cap) grid = cap;
-    e = cudaMemsetAsync(ns.queue, 0, sizeof(unsigned long long), st);
+    // the queue counter and the list's length (the next word) at once
+    e = cudaMemsetAsync(ns.queue, 0, 2 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
+    if (fallback) {
+        a.list = ns.list;
+        a.list_n = ns.list_n;
+    }
     refine_jobs_kernel<J, V><<<(unsigned)grid, tpb, 0, st>>>(a, prune,
                                                              ns.queue);
-    jobs_finalize_kernel<J, V><<<pps::finalize_blocks(a.n), 128, 0, st>>>(a, false);
+    jobs_finalize_kernel<J, V>
+        <<<(unsigned)((a.n + kFinalizeTpb / 32 - 1) / (kFinalizeTpb / 32)),
+           kFinalizeTpb, 0, st>>>(a, fallback);
     if (!fallback) return cudaGetLastError();
-    e = cudaMemsetAsync(ns.list_n, 0, sizeof(int), st);
-    if (e != cudaSuccess) return e;
-    fallback_list_kernel<<<(a.n + 127) / 128, 128, 0, st>>>(
-        a.best, a.n, ns.skip, ns.list, ns.list_n);
-    a.list = ns.list;
-    a.list_n = ns.list_n;
-    // the finalize left every key and count at zero
+    // the finalize left every key and count at zero and listed the states
+    // without a pass
     fallback_jobs_kernel<J, V><<<(unsigned)num_sms, tpb, 0, st>>>(a);
-    jobs_finalize_kernel<J, V><<<pps::finalize_blocks(a.n), 128, 0, st>>>(a, true);
     return cudaGetLastError();
 }
 
@@ -465,7 +537,6 @@ cudaError_t pps_propose_jobs_enqueue(pps_net* net, const PpsProposeJobs& p,
     a.m = p.m;
     a.vmax = p.vslots;
     a.topk = p.topk;
-    a.items_per_state = (p.topk * p.m * p.m + 31) / 32;
     a.prm = p.prm;
     a.cells = cells;
     a.best = p.best;

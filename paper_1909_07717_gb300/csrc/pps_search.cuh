@@ -304,15 +304,18 @@ __device__ __forceinline__ float opp_min(float f, float cbx, float cby,
 
 // A3 + A4 over the K samples of one point.  mv[v] accumulates
 // min_k (a T_k + sqrt(v^2 - 2 a s_k)); Trow (debug) receives T_k.
-// STRIDE 32: the warp's lanes share one point, lane l taking samples
-// l + 1, l + 33, ... (the caller takes the minimum over the lanes).
+// STRIDE G > 1 (a power of two up to 32): G consecutive lanes share one
+// point, lane l of the group taking samples l + 1, l + 1 + G, ... (the
+// caller takes the minimum over the group).  STRIDE 0: G = g, chosen at
+// run time.
 template <int JMAX, int VMAX, bool GEN, bool TDBG, int KU = kKUnroll, int STRIDE = 1>
 __device__ __forceinline__ void sample_loop(const StateK& sk,
                                             const OppRegs<JMAX>& o,
                                             float cbx, float cby,
                                             float twoabD,
                                             const float (&sp2)[PPS_MAX_SPEEDS],
-                                            float (&mv)[VMAX], float* Trow) {
+                                            float (&mv)[VMAX], float* Trow,
+                                            int g = STRIDE) {
     // speeds in pairs for the packed ball-time terms
     constexpr int VP = (VMAX + 1) / 2;
     float2 s2[VP];
@@ -323,9 +326,11 @@ __device__ __forceinline__ void sample_loop(const StateK& sk,
     // Float sample counter: exact for K <= 2^24, and keeps integer-to-float
     // conversions out of the loop.
     const float Kf = (float)sk.K;
-    const float k0 = STRIDE == 1 ? 1.f : (float)(1 + (threadIdx.x & 31));
+    const int G = STRIDE ? STRIDE : g;
+    const float k0 = G == 1 ? 1.f : (float)(1 + (threadIdx.x & (G - 1)));
+    const float step = (float)G;
 #pragma unroll KU
-    for (float kf = k0; kf <= Kf; kf += (float)STRIDE) {
+    for (float kf = k0; kf <= Kf; kf += step) {
         const float f = __fmul_rn(kf, sk.invK);
         const int k = (int)kf;
         const float n = opp_min<JMAX, GEN>(f, cbx, cby, o, sk.reach);
@@ -483,10 +488,12 @@ struct ItemGrid {
 
 // KU: unroll of the sample loop (samples a register block holds); it only
 // replicates the loop body, so every result is the same bit for bit.
-// STRIDE 32 (all 32 lanes of a warp on the same point): the lanes split the
-// samples and the minimum over them is taken across the warp -- the same
-// minimum, so the same results bit for bit, in a 32nd of the serial time
-// (the finalize kernels, which re-evaluate one point per state).
+// STRIDE G > 1 (G consecutive lanes on the same point, G a power of two up
+// to 32; STRIDE 0 takes G = g at run time): the lanes split the samples and
+// the minimum over them is taken across the group -- the same minimum, so
+// the same results bit for bit, in a G-th of the serial time (the finalize
+// kernels, which re-evaluate one point per state with G = 32, and the
+// refinement of small batches).  Every lane of the warp must take part.
 template <int JMAX, int VMAX, bool TDBG, int KU = kKUnroll, int STRIDE = 1>
 __device__ __forceinline__ void eval_point(const pps_params& prm,
                                            const ItemGrid& gr,
@@ -496,7 +503,8 @@ __device__ __forceinline__ void eval_point(const pps_params& prm,
                                            const StateK& sk,
                                            const OppRegs<JMAX>& o, int ix,
                                            int iy, float* Trow,
-                                           PointResult<JMAX, VMAX>& res) {
+                                           PointResult<JMAX, VMAX>& res,
+                                           int g = STRIDE) {
     // A2: the grid point and c - b are exact in FP64 (x0 + ix g and its
     // difference with the FP32 ball fit in 53 bits); the pass vector enters
     // the sample loop in scaled units, kappa (c - b), with one rounding.
@@ -516,15 +524,16 @@ __device__ __forceinline__ void eval_point(const pps_params& prm,
     for (int v = 0; v < VMAX; ++v) mv[v] = CUDART_INF_F;
     if (sk.general)
         sample_loop<JMAX, VMAX, true, TDBG, KU, STRIDE>(sk, o, cbx, cby, twoabD, sp2,
-                                                        mv, Trow);
+                                                        mv, Trow, g);
     else
         sample_loop<JMAX, VMAX, false, TDBG, KU, STRIDE>(sk, o, cbx, cby, twoabD, sp2,
-                                                         mv, Trow);
-    if (STRIDE > 1) {
+                                                         mv, Trow, g);
+    if (STRIDE != 1) {
+        const int G = STRIDE ? STRIDE : g;
 #pragma unroll
         for (int v = 0; v < VMAX; ++v)
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1)
+            for (int off = G >> 1; off > 0; off >>= 1)
                 mv[v] = fminf(mv[v], __shfl_xor_sync(0xffffffffu, mv[v], off));
     }
 

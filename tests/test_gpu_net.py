@@ -314,12 +314,30 @@ def test_tensor_core_waits_are_bounded(torch):
         net.close()
 
 
-def test_topk_order(torch):
+@pytest.mark.parametrize("k", [1, 17, 256, 512, 513, 700])
+def test_topk_order(torch, k):
+    """Both ways of ordering the selected keys (placement by rank up to 512
+    of them, the bitonic network above) give the sorted order."""
     batch = synth.ssl_states(505, 3, K=32)
-    _, cells, pred = _propose(torch, batch, pps.init_weights(12), 256)
+    _, cells, pred = _propose(torch, batch, pps.init_weights(12), k)
     for s in range(3):
         flat = pred[s].reshape(-1)
-        order = np.lexsort((np.arange(flat.size), -flat))[:256]
+        order = np.lexsort((np.arange(flat.size), -flat))[:k]
+        assert np.array_equal(cells[s], order)
+
+
+@pytest.mark.parametrize("k", [5, 300, 900])
+def test_topk_all_ties(torch, k):
+    """A map that is 0 everywhere: the radix select runs all its passes
+    (no digit holds exactly the keys still needed) and equal scores keep
+    the smaller pixel."""
+    batch = synth.ssl_states(509, 2, K=32)
+    _, cells, pred = _propose(torch, batch, _cancel_weights(), k)
+    assert np.all(pred == 0)
+    for s in range(2):
+        # +0 ranks above -0 (the keys order the float bits)
+        flat = pred[s].reshape(-1)
+        order = np.lexsort((np.arange(flat.size), np.signbit(flat)))[:k]
         assert np.array_equal(cells[s], order)
 
 

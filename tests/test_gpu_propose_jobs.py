@@ -149,6 +149,25 @@ def test_all_cells_of_mixed_fields_equal_the_full_search(torch):
     assert _same_best(pruned, ref)
 
 
+def test_small_batches_split_points_across_lanes(torch):
+    """A batch too small to fill the GPU shares each point among several
+    lanes (they split its samples and take the minimum across them): one
+    and two states refined alone give the bytes they get inside a 64-state
+    batch, where every lane holds a point of its own."""
+    batch = synth.serving_states(707, 64)
+    w = pps.load_net_weights(pps.SERVING_WEIGHTS)
+    for flags in (pps.PPS_PROPOSE_NO_PRUNE, 0):
+        big, big_cells = _propose_jobs(torch, batch, 0.05, w, 256, flags)
+        for idx in ([5], [0, 1]):
+            got, cells = _propose_jobs(torch, synth.take(batch, idx), 0.05, w,
+                                       256, flags)
+            assert np.array_equal(cells, big_cells[idx])
+            if flags:
+                assert got.tobytes() == big[idx].tobytes()
+            else:
+                assert _same_best(got, big[idx])
+
+
 def test_off_grid_cells_rank_last(torch):
     """On a 9 x 6 m field only 46 x 31 of the map's cells hold points: the
     top cells are all among them, in the network's order."""
