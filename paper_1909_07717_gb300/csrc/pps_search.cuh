@@ -469,6 +469,82 @@ __device__ __forceinline__ float shot_angle(const pps_state& st,
                                r);
 }
 
+// The same angle formed by the G lanes that share the point (G a power of
+// two, JMAX <= G <= 32; every lane of the warp takes part, each group of G
+// consecutive lanes with one point): lane i of the group forms opponent i's
+// interval, the group sorts the intervals by start across its lanes (a
+// bitonic network of shuffles; equal starts may come in either order, which
+// changes no gap: the second of two equal starts lies at or below the
+// first's end), the running maximum of the ends is a prefix scan, and each
+// lane measures the gap in front of its interval.  Every interval, running
+// maximum and gap is the value the sequential sweep forms (the same
+// operations on the same operands; maxima are exact), so the angle is the
+// same bit for bit.
+template <int JMAX>
+__device__ __forceinline__ float shot_angle_lanes(const float (*opp)[2],
+                                                  int nopp, float hw,
+                                                  bool front, float cx,
+                                                  float cy, float gx, float r,
+                                                  int G) {
+    const int lane = threadIdx.x & 31, i = lane & (G - 1);
+    const float lo = atan2f(__fsub_rn(-hw, cy), gx);
+    const float hi = atan2f(__fsub_rn(hw, cy), gx);
+    const float r2 = __fmul_rn(r, r);
+    const float ax = gx, ay = __fsub_rn(-hw, cy), by = __fsub_rn(hw, cy);
+    const float a2r2 = __fmul_rn(__fmaf_rn(ax, ax, __fmul_rn(ay, ay)), r2);
+    const float b2r2 = __fmul_rn(__fmaf_rn(ax, ax, __fmul_rn(by, by)), r2);
+    float s = 1e30f, e = 1e30f;
+    bool covers = false;
+    if (i < nopp && i < JMAX) {
+        const float dx = __fsub_rn(opp[i][0], cx);
+        const float dy = __fsub_rn(opp[i][1], cy);
+        const float d2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
+        covers = d2 <= r2;
+        const float ca = __fsub_rn(__fmul_rn(ax, dy), __fmul_rn(ay, dx));
+        const float cb = __fsub_rn(__fmul_rn(ax, dy), __fmul_rn(by, dx));
+        const bool inside = ca >= 0.f && cb <= 0.f;
+        const bool near_a = __fmaf_rn(ax, dx, __fmul_rn(ay, dy)) > 0.f &&
+                            __fmul_rn(ca, ca) <= a2r2;
+        const bool near_b = __fmaf_rn(ax, dx, __fmul_rn(by, dy)) > 0.f &&
+                            __fmul_rn(cb, cb) <= b2r2;
+        if (inside || near_a || near_b) {
+            const float d = __fsqrt_rn(d2);
+            const float phi = atan2f(dy, dx);
+            const float half = asinf(fminf(__fdiv_rn(r, d), 1.f));
+            s = __fsub_rn(phi, half);
+            e = __fadd_rn(phi, half);
+        }
+    }
+    const unsigned group =
+        G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (lane & ~(G - 1));
+    const bool all = (__ballot_sync(0xffffffffu, covers) & group) != 0u;
+    for (int k = 2; k <= G; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const float so = __shfl_xor_sync(0xffffffffu, s, j);
+            const float eo = __shfl_xor_sync(0xffffffffu, e, j);
+            const bool up = (i & k) == 0, lower = (i & j) == 0;
+            if (lower == up ? so < s : so > s) {
+                s = so;
+                e = eo;
+            }
+        }
+    // m: the largest end of the group's intervals up to lane i
+    float m = e;
+    for (int off = 1; off < G; off <<= 1) {
+        const float y = __shfl_up_sync(0xffffffffu, m, off, G);
+        if (i >= off) m = fmaxf(m, y);
+    }
+    const float before = __shfl_up_sync(0xffffffffu, m, 1, G);
+    const float cur = i == 0 ? lo : fmaxf(lo, before);
+    float best = 0.f;
+    if (s > cur && cur < hi) best = __fsub_rn(fminf(s, hi), cur);
+    for (int off = G >> 1; off > 0; off >>= 1)
+        best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, off));
+    const float last = fmaxf(lo, __shfl_sync(0xffffffffu, m, G - 1, G));
+    if (last < hi) best = fmaxf(best, __fsub_rn(hi, last));
+    return front && !all ? best : 0.f;
+}
+
 // Everything per grid point (A2..A6): margins, feasibility and scores for
 // all VMAX speed slots.  Shared by the search and the finalize kernels so
 // that the finalize reproduces the search's numbers bit for bit.
@@ -561,8 +637,17 @@ __device__ __forceinline__ void eval_point(const pps_params& prm,
         any_ok |= ok && v < gr.V;
     }
     float theta = 0.f;
-    if (any_ok)
+    if (STRIDE != 1 && (STRIDE ? STRIDE : g) >= JMAX) {
+        // the group's lanes share the angle's opponents
+        if (__any_sync(0xffffffffu, any_ok)) {
+            const float t = shot_angle_lanes<JMAX>(
+                st.opp_pos, sk.nopp, sk.hw, front, cx, cy, gx,
+                prm.robot_radius, STRIDE ? STRIDE : g);
+            theta = any_ok ? t : 0.f;
+        }
+    } else if (any_ok) {
         theta = shot_angle<JMAX>(st, sk, front, cx, cy, gx, prm.robot_radius);
+    }
     const float dg = __fsqrt_rn(__fmaf_rn(gx, gx, __fmul_rn(cy, cy)));
     const float base =
         __fsub_rn(__fmul_rn(prm.w_angle,
