@@ -38,21 +38,26 @@ __device__ __forceinline__ long long next_item(unsigned long long* queue,
     return (long long)__shfl_sync(0xffffffffu, q, 0);
 }
 
-template <int JMAX, int VMAX>
+// SPLIT (small batches): a half cell is G items of 32 / G points, G lanes a
+// point splitting its samples (G a power of two up to 32; the same bits, as
+// in the per-job refinement below).  Without SPLIT, G = 1 at compile time.
+template <int JMAX, int VMAX, bool SPLIT>
 __global__ void __launch_bounds__(pps::search_tpb<JMAX, VMAX>(), 1)
     refine_kernel(const pps::SearchArgs a, const int* __restrict__ cells,
-                  int topk, bool prune, unsigned long long* queue) {
+                  int topk, int g, bool prune, unsigned long long* queue) {
     const int lane = threadIdx.x & 31;
-    const long long n_items = (long long)a.n_states * topk * 2;
+    const int G = SPLIT ? g : 1;
+    const long long n_items = (long long)a.n_states * topk * 2 * G;
     const pps::ItemGrid gr{a.g, a.x0, a.y0, a.V};
     for (long long item = next_item(queue, lane); item < n_items;
          item = next_item(queue, lane)) {
-        const int r = (int)(item / a.n_states);     // rank x 2 + half
-        const int s = (int)(item - (long long)r * a.n_states);
+        const int rg = (int)(item / a.n_states);  // (rank x 2 + half) x G + sub
+        const int s = (int)(item - (long long)rg * a.n_states);
+        const int r = rg / G, pt = (rg - r * G) * (32 / G) + lane / G;
         const int cell = cells[(long long)s * topk + (r >> 1)];
         const int cy = cell / kMapW, cx = cell - cy * kMapW;
-        const int fx = 8 * cx - 4 + (lane & 7);
-        const int fy = 8 * cy - 4 + (lane >> 3) + 4 * (r & 1);
+        const int fx = 8 * cx - 4 + (pt & 7);
+        const int fy = 8 * cy - 4 + (pt >> 3) + 4 * (r & 1);
         const bool active = fx >= 0 && fx < a.nx && fy >= 0 && fy < a.ny;
         const int ix = active ? fx : 0, iy = active ? fy : 0;
         const int p = iy * a.nx + ix;
@@ -77,14 +82,15 @@ __global__ void __launch_bounds__(pps::search_tpb<JMAX, VMAX>(), 1)
             }
         }
         pps::PointResult<JMAX, VMAX> res;
-        pps::eval_point<JMAX, VMAX, false>(a.prm, gr, a.speed, a.speed2, st, sk,
-                                           o, ix, iy, nullptr, res);
+        pps::eval_point<JMAX, VMAX, false, pps::kKUnroll, SPLIT ? 0 : 1>(
+            a.prm, gr, a.speed, a.speed2, st, sk, o, ix, iy, nullptr, res, G);
+        const bool lead = (lane & (G - 1)) == 0;
         int cnt = 0;
         unsigned long long key = 0ull;
 #pragma unroll
         for (int v = 0; v < VMAX; ++v) {
             const bool f = active && v < a.V && res.feas[v];
-            cnt += f;
+            cnt += f && lead;
             if (f) {
                 const uint32_t idx = (uint32_t)(v * a.P + p);
                 const unsigned long long k2 =
@@ -117,7 +123,7 @@ __global__ void fallback_list_kernel(const pps_best* __restrict__ best, int n,
 
 template <int J, int V>
 int occupancy() {
-    return pps_occupancy((const void*)refine_kernel<J, V>,
+    return pps_occupancy((const void*)refine_kernel<J, V, false>,
                          pps::search_tpb<J, V>(), 0);
 }
 
@@ -130,15 +136,24 @@ cudaError_t run(const pps::SearchArgs& base, const int* cells, int topk,
     cudaError_t e = cudaMemsetAsync(a.keys, 0, sizeof(unsigned long long) * a.n_states, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.counts, 0, sizeof(int) * a.n_states, st);
     if (e != cudaSuccess) return e;
-    const long long items = (long long)a.n_states * topk * 2;
     constexpr int tpb = pps::search_tpb<J, V>();
+    // lanes per point: doubled while the batch's items still fit in the
+    // resident warps
+    const long long halves = (long long)a.n_states * topk * 2;
+    int G = 1;
+    while (G < 32 && halves * 2 * G <= cap * (tpb / 32)) G *= 2;
+    const long long items = halves * G;
     long long grid = (items + tpb / 32 - 1) / (tpb / 32);
     if (grid > cap) grid = cap;
     // the queue counter and the list's length (the next word) at once
     e = cudaMemsetAsync(ns.queue, 0, 2 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    refine_kernel<J, V><<<(unsigned)grid, tpb, 0, st>>>(a, cells, topk, prune,
-                                                        ns.queue);
+    if (G > 1)
+        refine_kernel<J, V, true><<<(unsigned)grid, tpb, 0, st>>>(
+            a, cells, topk, G, prune, ns.queue);
+    else
+        refine_kernel<J, V, false><<<(unsigned)grid, tpb, 0, st>>>(
+            a, cells, topk, 1, prune, ns.queue);
     pps::finalize_kernel<J, V><<<pps::finalize_blocks(a.n_states), 128, 0, st>>>(a);
     if (!fallback) return cudaGetLastError();
     fallback_list_kernel<<<(a.n_states + 127) / 128, 128, 0, st>>>(

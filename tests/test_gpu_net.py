@@ -344,6 +344,22 @@ def test_topk_all_ties(torch, k):
 BEST_FIELDS = ("idx", "ix", "iy", "speed_idx", "score", "margin", "status")
 
 
+def test_small_batches_split_points_across_lanes(torch):
+    """One or two states alone leave the GPU idle, and their refinement
+    shares each point among several lanes (they split its samples and take
+    the minimum across them): the records equal, byte for byte, the ones
+    the same states get inside a 40-state batch, where a lane holds a point
+    of its own."""
+    batch = synth.ssl_states(512, 40, K=64)
+    w = pps.load_net_weights()
+    big, big_cells, _ = _propose(torch, batch, w, 256, pps.PPS_PROPOSE_NO_PRUNE)
+    for idx in ([7], [0, 1]):
+        got, cells, _ = _propose(torch, synth.take(batch, idx), w, 256,
+                                 pps.PPS_PROPOSE_NO_PRUNE)
+        assert np.array_equal(cells, big_cells[idx])
+        assert got.tobytes() == big[idx].tobytes()
+
+
 def _same_best(a, b):
     """Equal best records; n_feasible counts only the points a pruned
     refinement evaluated, so it is compared separately."""
