@@ -48,12 +48,16 @@ int pps_ctx_max_opp(const pps_ctx* ctx);
 int pps_occupancy(const void* func, int tpb, size_t smem);
 
 // Network internals for the proposal path (pps_net.cu): the fallback's
-// per-state skip flags, the list of states to re-search and its length.
+// per-state skip flags, the list of states to re-search and its length,
+// and kPpsStateRecBytes a state for the refinement's per-state records
+// (pps_propose.cu).
+constexpr size_t kPpsStateRecBytes = 384;
 struct pps_net_scratch {
     int* skip;
     int* list;
     int* list_n;                // == (int*)(queue + 1)
     unsigned long long* queue;  // the refinement's work-queue counter
+    void* srec;                 // max_batch x kPpsStateRecBytes
 };
 cudaError_t pps_net_predict(pps_net* net, const pps_state* states, int n,
                             cudaStream_t* st, float** scores, int** cells,

@@ -35,6 +35,7 @@ struct pps_net {
     float* loss = nullptr;
     int* cells = nullptr;  // proposal scratch: max_batch x NPIX
     int* skip = nullptr;   // proposal scratch: max_batch
+    void* srec = nullptr;  // proposal scratch: max_batch per-state records
     int* list = nullptr;   // proposal scratch: max_batch states to re-search
     // proposal scratch: the work queue's counter, then (in the next 8
     // bytes, so that one memset clears both) the list's length
@@ -319,6 +320,7 @@ cudaError_t pps_net_predict(pps_net* nt, const pps_state* states, int n,
     scratch->list = nt->list;
     scratch->list_n = nt->list_n;
     scratch->queue = nt->queue;
+    scratch->srec = nt->srec;
     return forward(nt, states, n, false);
 }
 
@@ -409,6 +411,7 @@ extern "C" pps_status pps_net_create(int device, void* stream, int max_batch,
     al(&nt->loss, sizeof(float));
     al(&nt->cells, sizeof(int) * P);
     al(&nt->skip, sizeof(int) * (size_t)max_batch);
+    al(&nt->srec, kPpsStateRecBytes * (size_t)max_batch);
     al(&nt->smax, sizeof(float) * (size_t)max_batch);
     al(&nt->list, sizeof(int) * (size_t)max_batch);
     al(&nt->queue, 2 * sizeof(unsigned long long));
@@ -436,6 +439,7 @@ extern "C" void pps_net_destroy(pps_net* nt) {
                     (void*)nt->a2, (void*)nt->a3, (void*)nt->g1, (void*)nt->g2,
                     (void*)nt->g3, (void*)nt->g4, (void*)nt->out,
                     (void*)nt->loss, (void*)nt->cells, (void*)nt->skip,
+                    nt->srec,
                     (void*)nt->smax, (void*)nt->list, (void*)nt->err,
                     (void*)nt->wpart, (void*)nt->queue})
         if (p) cudaFree(p);

@@ -38,13 +38,40 @@ __device__ __forceinline__ long long next_item(unsigned long long* queue,
     return (long long)__shfl_sync(0xffffffffu, q, 0);
 }
 
+// A state's derived constants and scaled opponents (derive_state and
+// load_opps, the same values), prepared once a call for the large-batch
+// refinement: its items (half cells, rank-major) come from many states in
+// turn, and deriving them per item was a fifth of its instructions.
+template <int JMAX>
+struct __align__(16) StateRec {
+    pps::StateK sk;
+    pps::OppRegs<JMAX> o;
+};
+static_assert(sizeof(StateRec<PPS_MAX_OPP>) <= kPpsStateRecBytes,
+              "the network's per-state scratch holds a record");
+
+template <int JMAX>
+__global__ void __launch_bounds__(128)
+    prepare_states_kernel(const pps::SearchArgs a,
+                          StateRec<JMAX>* __restrict__ recs) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.n_states) return;
+    StateRec<JMAX> r;
+    r.sk = pps::derive_state(a.states[s], a.prm, JMAX, a.kmax);
+    pps::load_opps<JMAX>(a.states[s], r.sk, r.o);
+    recs[s] = r;
+}
+
 // SPLIT (small batches): a half cell is G items of 32 / G points, G lanes a
 // point splitting its samples (G a power of two up to 32; the same bits, as
-// in the per-job refinement below).  Without SPLIT, G = 1 at compile time.
+// in the per-job refinement below), each item deriving its state itself.
+// Without SPLIT, G = 1 at compile time and the states' records come from
+// prepare_states_kernel.
 template <int JMAX, int VMAX, bool SPLIT>
 __global__ void __launch_bounds__(pps::search_tpb<JMAX, VMAX>(), 1)
     refine_kernel(const pps::SearchArgs a, const int* __restrict__ cells,
-                  int topk, int g, bool prune, unsigned long long* queue) {
+                  int topk, int g, bool prune, unsigned long long* queue,
+                  const StateRec<JMAX>* __restrict__ recs) {
     const int lane = threadIdx.x & 31;
     const int G = SPLIT ? g : 1;
     const long long n_items = (long long)a.n_states * topk * 2 * G;
@@ -62,9 +89,15 @@ __global__ void __launch_bounds__(pps::search_tpb<JMAX, VMAX>(), 1)
         const int ix = active ? fx : 0, iy = active ? fy : 0;
         const int p = iy * a.nx + ix;
         const pps_state& st = a.states[s];
-        const pps::StateK sk = pps::derive_state(st, a.prm, JMAX, a.kmax);
+        pps::StateK sk;
         pps::OppRegs<JMAX> o;
-        pps::load_opps<JMAX>(st, sk, o);
+        if constexpr (SPLIT) {
+            sk = pps::derive_state(st, a.prm, JMAX, a.kmax);
+            pps::load_opps<JMAX>(st, sk, o);
+        } else {
+            sk = recs[s].sk;
+            o = recs[s].o;
+        }
         if (prune) {
             // one read of the state's best so far, shared by the warp
             const unsigned long long cur =
@@ -148,12 +181,16 @@ cudaError_t run(const pps::SearchArgs& base, const int* cells, int topk,
     // the queue counter and the list's length (the next word) at once
     e = cudaMemsetAsync(ns.queue, 0, 2 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    if (G > 1)
+    if (G > 1) {
         refine_kernel<J, V, true><<<(unsigned)grid, tpb, 0, st>>>(
-            a, cells, topk, G, prune, ns.queue);
-    else
+            a, cells, topk, G, prune, ns.queue, nullptr);
+    } else {
+        auto* recs = static_cast<StateRec<J>*>(ns.srec);
+        prepare_states_kernel<J><<<(unsigned)((a.n_states + 127) / 128), 128, 0,
+                                   st>>>(a, recs);
         refine_kernel<J, V, false><<<(unsigned)grid, tpb, 0, st>>>(
-            a, cells, topk, 1, prune, ns.queue);
+            a, cells, topk, 1, prune, ns.queue, recs);
+    }
     pps::finalize_kernel<J, V><<<pps::finalize_blocks(a.n_states), 128, 0, st>>>(a);
     if (!fallback) return cudaGetLastError();
     fallback_list_kernel<<<(a.n_states + 127) / 128, 128, 0, st>>>(
