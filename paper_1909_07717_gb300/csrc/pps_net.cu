@@ -36,6 +36,7 @@ struct pps_net {
     int* cells = nullptr;  // proposal scratch: max_batch x NPIX
     int* skip = nullptr;   // proposal scratch: max_batch
     void* srec = nullptr;  // proposal scratch: max_batch per-state records
+    RasterRec* rrec = nullptr;  // the rasteriser's per-state records
     int* list = nullptr;   // proposal scratch: max_batch states to re-search
     // proposal scratch: the work queue's counter, then (in the next 8
     // bytes, so that one memset clears both) the list's length
@@ -99,12 +100,16 @@ cudaError_t cast_weights(pps_net* nt) {
 // wave of the GPU's resident CTAs, else four lanes a pixel (a quarter of
 // the serial chain for the small batches of serving; same results).
 void launch_raster(pps_net* nt, const pps_state* states, int n, cudaStream_t st) {
-    if ((long long)n * raster_ctas<1>() >= 8LL * nt->num_sms)
+    if ((long long)n * raster_ctas<1>() >= 8LL * nt->num_sms) {
+        // large batches: the states' records prepared once a call
+        raster_prepare_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
+            states, n, nt->cfg, nt->rrec);
         raster_kernel<1><<<(unsigned)(n * raster_ctas<1>()), kRasterTpb, 0, st>>>(
-            states, n, nt->cfg, nt->a0);
-    else
+            states, n, nt->cfg, nt->a0, nt->rrec);
+    } else {
         raster_kernel<4><<<(unsigned)(n * raster_ctas<4>()), kRasterTpb, 0, st>>>(
-            states, n, nt->cfg, nt->a0);
+            states, n, nt->cfg, nt->a0, nullptr);
+    }
 }
 
 // (states NULL) copied from a caller's map[n][46][61][8] bf16 into the
@@ -412,6 +417,7 @@ extern "C" pps_status pps_net_create(int device, void* stream, int max_batch,
     al(&nt->cells, sizeof(int) * P);
     al(&nt->skip, sizeof(int) * (size_t)max_batch);
     al(&nt->srec, kPpsStateRecBytes * (size_t)max_batch);
+    al(&nt->rrec, sizeof(RasterRec) * (size_t)max_batch);
     al(&nt->smax, sizeof(float) * (size_t)max_batch);
     al(&nt->list, sizeof(int) * (size_t)max_batch);
     al(&nt->queue, 2 * sizeof(unsigned long long));
@@ -439,7 +445,7 @@ extern "C" void pps_net_destroy(pps_net* nt) {
                     (void*)nt->a2, (void*)nt->a3, (void*)nt->g1, (void*)nt->g2,
                     (void*)nt->g3, (void*)nt->g4, (void*)nt->out,
                     (void*)nt->loss, (void*)nt->cells, (void*)nt->skip,
-                    nt->srec,
+                    nt->srec, (void*)nt->rrec,
                     (void*)nt->smax, (void*)nt->list, (void*)nt->err,
                     (void*)nt->wpart, (void*)nt->queue})
         if (p) cudaFree(p);

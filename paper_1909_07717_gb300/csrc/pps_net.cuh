@@ -224,17 +224,51 @@ __host__ __device__ constexpr int raster_ctas() {
     return (NPIX + kRasterTpb / LANES - 1) / (kRasterTpb / LANES);
 }
 
+// A state's derived constants and scaled opponents as the rasteriser's CTAs
+// hold them (the 8-slot layout when it has at most 8 opponents), prepared
+// once a call by one thread a state for the large-batch instance: its 22
+// CTAs a state otherwise each derived them on one thread while the other
+// warps waited.
+struct __align__(16) RasterRec {
+    StateK sk;
+    __align__(16) unsigned char opp[sizeof(OppRegs<PPS_MAX_OPP>)];
+};
+static_assert(sizeof(RasterRec) % 16 == 0, "copied 16 bytes a thread");
+
+__device__ __forceinline__ void raster_derive(const pps_state& st,
+                                              const RasterCfg& cfg,
+                                              StateK& sk, unsigned char* opp) {
+    sk = derive_state(st, cfg.prm, PPS_MAX_OPP, PPS_MAX_K);
+    if (sk.nopp <= 8)
+        load_opps<8>(st, sk, *reinterpret_cast<OppRegs<8>*>(opp));
+    else
+        load_opps<PPS_MAX_OPP>(st, sk, *reinterpret_cast<OppRegs<PPS_MAX_OPP>*>(opp));
+}
+
+__global__ void __launch_bounds__(128)
+    raster_prepare_kernel(const pps_state* __restrict__ states, int n,
+                          const RasterCfg cfg, RasterRec* __restrict__ recs) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    RasterRec r;
+    raster_derive(states[s], cfg, r.sk, r.opp);
+    recs[s] = r;
+}
+
+// recs (may be null): the states' records from raster_prepare_kernel.
 template <int LANES>
 __global__ void __launch_bounds__(kRasterTpb, 8)
     raster_kernel(const pps_state* __restrict__ states, int n,
                               const RasterCfg cfg,
-                              __nv_bfloat16* __restrict__ out) {
+                              __nv_bfloat16* __restrict__ out,
+                              const RasterRec* __restrict__ recs) {
     constexpr int kPix = kRasterTpb / LANES, kCtas = raster_ctas<LANES>();
     constexpr int kStateWords = (int)(sizeof(pps_state) / 4);
     static_assert(sizeof(pps_state) % 4 == 0 && kStateWords <= kRasterTpb,
                   "the state is copied a 32-bit word a thread");
-    __shared__ StateK s_sk;
-    __shared__ __align__(16) unsigned char s_opp[sizeof(OppRegs<PPS_MAX_OPP>)];
+    __shared__ RasterRec s_rec;
+    StateK& s_sk = s_rec.sk;
+    unsigned char* s_opp = s_rec.opp;
     __shared__ __align__(16) pps_state s_st;
     const int s = (int)(blockIdx.x / kCtas);
     const int sub = LANES == 4 ? (int)(threadIdx.x & 3) : 0;
@@ -242,20 +276,20 @@ __global__ void __launch_bounds__(kRasterTpb, 8)
                   (int)(threadIdx.x / LANES);
     // the state in shared memory, a word a thread (one memory latency, not
     // the chain of field loads the derivation would wait on)
+    constexpr int kRecChunks = (int)(sizeof(RasterRec) / 16);
+    static_assert(kRecChunks <= kRasterTpb, "one 16-byte chunk a thread");
     if (threadIdx.x < kStateWords)
         reinterpret_cast<uint32_t*>(&s_st)[threadIdx.x] =
             __ldg(reinterpret_cast<const uint32_t*>(states + s) + threadIdx.x);
+    if (recs && threadIdx.x < kRecChunks)
+        reinterpret_cast<uint4*>(&s_rec)[threadIdx.x] =
+            __ldg(reinterpret_cast<const uint4*>(recs + s) + threadIdx.x);
     __syncthreads();
     const pps_state& st = s_st;
-    if (threadIdx.x == 0) {
-        const StateK d = derive_state(st, cfg.prm, PPS_MAX_OPP, PPS_MAX_K);
-        s_sk = d;
-        if (d.nopp <= 8)
-            load_opps<8>(st, d, *reinterpret_cast<OppRegs<8>*>(s_opp));
-        else
-            load_opps<PPS_MAX_OPP>(st, d, *reinterpret_cast<OppRegs<PPS_MAX_OPP>*>(s_opp));
+    if (!recs) {
+        if (threadIdx.x == 0) raster_derive(st, cfg, s_rec.sk, s_rec.opp);
+        __syncthreads();
     }
-    __syncthreads();
     // lanes past the map's last pixel still take part in the shuffles below
     const bool active = q < NPIX;
     const int qa = active ? q : NPIX - 1;
