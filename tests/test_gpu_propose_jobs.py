@@ -149,18 +149,22 @@ def test_all_cells_of_mixed_fields_equal_the_full_search(torch):
     assert _same_best(pruned, ref)
 
 
-def test_small_batches_split_points_across_lanes(torch):
+@pytest.mark.parametrize("max_opp", [16, 12])
+def test_small_batches_split_points_across_lanes(torch, max_opp):
     """A batch too small to fill the GPU shares each point among several
-    lanes (they split its samples and take the minimum across them): one
-    and two states refined alone give the bytes they get inside a 64-state
-    batch, where every lane holds a point of its own."""
+    lanes (they split its samples and take the minimum across them; with at
+    least as many lanes a point as opponent slots, the shot angle is formed
+    across them too): one and two states refined alone give the bytes they
+    get inside a 64-state batch, where every lane holds a point of its own.
+    16 and 12 opponent slots (the states have 6 to 11 opponents)."""
     batch = synth.serving_states(707, 64)
     w = pps.load_net_weights(pps.SERVING_WEIGHTS)
     for flags in (pps.PPS_PROPOSE_NO_PRUNE, 0):
-        big, big_cells = _propose_jobs(torch, batch, 0.05, w, 256, flags)
+        big, big_cells = _propose_jobs(torch, batch, 0.05, w, 256, flags,
+                                       max_opp=max_opp)
         for idx in ([5], [0, 1]):
             got, cells = _propose_jobs(torch, synth.take(batch, idx), 0.05, w,
-                                       256, flags)
+                                       256, flags, max_opp=max_opp)
             assert np.array_equal(cells, big_cells[idx])
             if flags:
                 assert got.tobytes() == big[idx].tobytes()
