@@ -14,6 +14,7 @@
 #pragma once
 
 #include "pps_search.cuh"
+#include "pps_warpcopy.cuh"
 
 namespace pps {
 
@@ -155,19 +156,24 @@ __global__ void __launch_bounds__(TPB) batch_search_kernel(const BatchArgs a) {
 // its samples) and check that the score reproduces; lane 0 writes.
 template <int JMAX, int VMAX>
 __global__ void __launch_bounds__(128) batch_finalize_kernel(const BatchArgs a) {
+    __shared__ WarpStateJob sh[128 / 32];  // the warp's state and job
     const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const bool lead = (threadIdx.x & 31) == 0;
+    const int lane = threadIdx.x & 31;
+    const bool lead = lane == 0;
     if (i == 0 && lead) *a.next = 0ull;  // the queue is empty again for the next launch
     if (i >= a.n_bucket) return;
     const int s = a.bucket_states[i];
-    const pps_state& st = a.states[s];
+    const unsigned long long key = a.keys[s];
+    const int count = a.counts[s];
+    WarpStateJob& my = sh[threadIdx.x >> 5];
+    warp_load_state_job(my, a.states + s, a.jobs + s, lane);
+    const pps_state& st = my.st;
     const StateK sk = derive_state(st, a.prm, JMAX, a.kmax);
     JobView jv;
-    load_job(a.jobs[s], jv);
+    load_job(my.job, jv);
     pps_best b;
-    b.n_feasible = a.counts[s];
+    b.n_feasible = count;
     b.status = sk.valid ? PPS_STATE_OK : PPS_STATE_INVALID;
-    const unsigned long long key = a.keys[s];
     if (!sk.valid || key == 0ull) {
         b.idx = sk.valid ? -1 : -2;
         b.ix = b.iy = b.speed_idx = -1;

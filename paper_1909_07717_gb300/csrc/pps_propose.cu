@@ -13,6 +13,7 @@
 #include "pps_internal.h"
 #include "pps_cells.cuh"
 #include "pps_search.cuh"
+#include "pps_warpcopy.cuh"
 
 char* pps_thread_error_buffer();
 
@@ -277,43 +278,16 @@ __device__ __forceinline__ void load_job_cells(const pps_job& j, int m,
     }
 }
 
-// lead: the lane that counts its point's feasible passes (the first of the
-// lanes that share the point; they all hold the same result).
-// A warp's copy of one state and its job in shared memory (the finalize):
-// every lane loads a few words at once (one memory latency) instead of the
-// chain of field loads the per-state setup would otherwise wait on, and the
-// re-evaluation reads the opponents from shared memory.
-struct WarpStateJob {
-    pps_state st;
-    pps_job job;
-};
-static_assert(sizeof(pps_state) % 4 == 0 && sizeof(pps_job) % 4 == 0,
-              "copied as 32-bit words");
-
-template <int BYTES>
-__device__ __forceinline__ void warp_copy(void* dst, const void* src,
-                                          int lane) {
-    constexpr int kWords = BYTES / 4;
-    const uint32_t* from = static_cast<const uint32_t*>(src);
-    uint32_t* to = static_cast<uint32_t*>(dst);
-    uint32_t w[(kWords + 31) / 32];
-#pragma unroll
-    for (int i = 0; i < (kWords + 31) / 32; ++i)
-        if (i * 32 + lane < kWords) w[i] = __ldg(from + i * 32 + lane);
-#pragma unroll
-    for (int i = 0; i < (kWords + 31) / 32; ++i)
-        if (i * 32 + lane < kWords) to[i * 32 + lane] = w[i];
-}
+using pps::WarpStateJob;
 
 __device__ __forceinline__ void load_state_job(WarpStateJob& d,
                                                const JobsArgs& a, int s,
                                                int lane) {
-    __syncwarp();
-    warp_copy<sizeof(pps_state)>(&d.st, a.states + s, lane);
-    warp_copy<sizeof(pps_job)>(&d.job, a.jobs + s, lane);
-    __syncwarp();
+    pps::warp_load_state_job(d, a.states + s, a.jobs + s, lane);
 }
 
+// lead: the lane that counts its point's feasible passes (the first of the
+// lanes that share the point; they all hold the same result).
 template <int JMAX, int VMAX>
 __device__ __forceinline__ void reduce_item(const JobsArgs& a, int s,
                                             int lane, bool active, bool lead,
