@@ -42,7 +42,7 @@ __device__ __forceinline__ long long next_item(unsigned long long* queue,
 // A state's derived constants and scaled opponents (derive_state and
 // load_opps, the same values), prepared once a call for the large-batch
 // refinement: its items (half cells, rank-major) come from many states in
-// turn, and deriving them per item was a fifth of its instructions.
+// turn, and deriving them per item took a fifth of its time.
 template <int JMAX>
 struct __align__(16) StateRec {
     pps::StateK sk;
