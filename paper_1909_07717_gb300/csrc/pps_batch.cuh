@@ -34,7 +34,23 @@ struct BatchArgs {
     int* counts;                  // per state of the plan
     unsigned long long* next;     // the launch's work-queue counter: 0 when
                                   // it starts, left 0 by the finalize kernel
+    unsigned char* recs;          // may be null: kBatchRecStride bytes per
+                                  // state of the plan (BatchRec)
 };
+
+// A state's derived constants and scaled opponents, prepared once a run by
+// batch_prepare_kernel for the plans, whose items (32 points of one state,
+// one at a time) then load them instead of deriving them each; the serving
+// loop's small launches pass none and derive them per item.
+constexpr size_t kBatchRecStride = 336;
+template <int JMAX>
+struct __align__(16) BatchRec {
+    StateK sk;
+    OppRegs<JMAX> o;
+};
+static_assert(sizeof(BatchRec<PPS_MAX_OPP>) <= kBatchRecStride &&
+                  kBatchRecStride % 16 == 0,
+              "a record fits its 16-byte aligned slot");
 
 // Items a warp takes from the work queue at a time.
 constexpr unsigned long long kQueueRun = 4;
@@ -88,9 +104,17 @@ __device__ __forceinline__ void batch_item(const BatchArgs& a, long long item,
         JobView jv;
         load_job(a.jobs[s], jv);
         const pps_state& st = a.states[s];
-        const StateK sk = derive_state(st, a.prm, JMAX, a.kmax);
+        StateK sk;
         OppRegs<JMAX> o;
-        load_opps<JMAX>(st, sk, o);
+        if (a.recs) {
+            const BatchRec<JMAX>& r = *reinterpret_cast<const BatchRec<JMAX>*>(
+                a.recs + (size_t)s * kBatchRecStride);
+            sk = r.sk;
+            o = r.o;
+        } else {
+            sk = derive_state(st, a.prm, JMAX, a.kmax);
+            load_opps<JMAX>(st, sk, o);
+        }
 
         const int p = chunk * 32 + lane;
         const bool active = p < jv.P;
@@ -128,6 +152,18 @@ __device__ __forceinline__ void batch_item(const BatchArgs& a, long long item,
             if (cnt) atomicAdd(a.counts + s, cnt);
         }
     }
+}
+
+// The records of the bucket's states, a thread a state.
+template <int JMAX>
+__global__ void __launch_bounds__(128) batch_prepare_kernel(const BatchArgs a) {
+    const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (i >= a.n_bucket) return;
+    const int s = a.bucket_states[i];
+    BatchRec<JMAX> r;
+    r.sk = derive_state(a.states[s], a.prm, JMAX, a.kmax);
+    load_opps<JMAX>(a.states[s], r.sk, r.o);
+    *reinterpret_cast<BatchRec<JMAX>*>(a.recs + (size_t)s * kBatchRecStride) = r;
 }
 
 template <int JMAX, int VMAX, int TPB, int KU>

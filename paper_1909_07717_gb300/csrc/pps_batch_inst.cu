@@ -18,6 +18,8 @@ static_assert(J == 6 || J == 8 || J == 12 || J == 16, "opponent slots");
 
 template <int V, int T, int KU>
 cudaError_t go(const BatchArgs& a, int grid, cudaStream_t st) {
+    if (a.recs)
+        batch_prepare_kernel<J><<<(a.n_bucket + 127) / 128, 128, 0, st>>>(a);
     batch_search_kernel<J, V, T, KU><<<grid, T, 0, st>>>(a);
     batch_finalize_kernel<J, V><<<finalize_blocks(a.n_bucket), 128, 0, st>>>(a);
     return cudaGetLastError();

@@ -67,8 +67,9 @@ struct pps_plan {
     unsigned long long* d_keys = nullptr;
     int* d_counts = nullptr;
     unsigned long long* d_next = nullptr;  // one work-queue counter per group
+    unsigned char* d_recs = nullptr;       // per-state records (BatchRec)
     size_t b_jobs = 0, b_states = 0, b_start = 0, b_mask = 0, b_keys = 0,
-           b_counts = 0, b_next = 0;
+           b_counts = 0, b_next = 0, b_recs = 0;
     // autotuning and graph replay
     bool tuned = false;
     cudaStream_t cap_stream = nullptr;
@@ -223,7 +224,10 @@ extern "C" pps_status pps_plan_create(pps_ctx* ctx, const pps_job* jobs,
         (s = upload<unsigned long long>(
              pl, &pl->d_next, &pl->b_next,
              std::vector<unsigned long long>(pl->groups.size(), 0ull).data(),
-             pl->groups.size(), "plan queues")) != PPS_OK) {
+             pl->groups.size(), "plan queues")) != PPS_OK ||
+        (s = upload<unsigned char>(pl, &pl->d_recs, &pl->b_recs, nullptr,
+                                   (size_t)n_states * pps::kBatchRecStride,
+                                   "plan state records")) != PPS_OK) {
         pps_plan_destroy(pl);
         return s;
     }
@@ -275,6 +279,7 @@ pps::BatchArgs group_args(const pps_plan* pl, const Group& g,
     a.keys = pl->d_keys;
     a.counts = pl->d_counts;
     a.next = pl->d_next + (&g - pl->groups.data());
+    a.recs = pl->d_recs;
     return a;
 }
 
@@ -446,6 +451,7 @@ extern "C" void pps_plan_destroy(pps_plan* pl) {
     pps_ctx_free(ctx, pl->d_keys, pl->b_keys);
     pps_ctx_free(ctx, pl->d_counts, pl->b_counts);
     pps_ctx_free(ctx, pl->d_next, pl->b_next);
+    pps_ctx_free(ctx, pl->d_recs, pl->b_recs);
     cudaGetLastError();
     delete pl;
 }
