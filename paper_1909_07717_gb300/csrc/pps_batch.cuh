@@ -14,6 +14,7 @@
 #pragma once
 
 #include "pps_search.cuh"
+#include "pps_staterec.cuh"
 #include "pps_warpcopy.cuh"
 
 namespace pps {
@@ -35,20 +36,15 @@ struct BatchArgs {
     unsigned long long* next;     // the launch's work-queue counter: 0 when
                                   // it starts, left 0 by the finalize kernel
     unsigned char* recs;          // may be null: kBatchRecStride bytes per
-                                  // state of the plan (BatchRec)
+                                  // state of the plan (StateRec)
 };
 
-// A state's derived constants and scaled opponents, prepared once a run by
+// The states' records (StateRec), prepared once a run by
 // batch_prepare_kernel for the plans, whose items (32 points of one state,
 // one at a time) then load them instead of deriving them each; the serving
 // loop's small launches pass none and derive them per item.
 constexpr size_t kBatchRecStride = 336;
-template <int JMAX>
-struct __align__(16) BatchRec {
-    StateK sk;
-    OppRegs<JMAX> o;
-};
-static_assert(sizeof(BatchRec<PPS_MAX_OPP>) <= kBatchRecStride &&
+static_assert(sizeof(StateRec<PPS_MAX_OPP>) <= kBatchRecStride &&
                   kBatchRecStride % 16 == 0,
               "a record fits its 16-byte aligned slot");
 
@@ -107,7 +103,7 @@ __device__ __forceinline__ void batch_item(const BatchArgs& a, long long item,
         StateK sk;
         OppRegs<JMAX> o;
         if (a.recs) {
-            const BatchRec<JMAX>& r = *reinterpret_cast<const BatchRec<JMAX>*>(
+            const StateRec<JMAX>& r = *reinterpret_cast<const StateRec<JMAX>*>(
                 a.recs + (size_t)s * kBatchRecStride);
             sk = r.sk;
             o = r.o;
@@ -160,10 +156,9 @@ __global__ void __launch_bounds__(128) batch_prepare_kernel(const BatchArgs a) {
     const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x);
     if (i >= a.n_bucket) return;
     const int s = a.bucket_states[i];
-    BatchRec<JMAX> r;
-    r.sk = derive_state(a.states[s], a.prm, JMAX, a.kmax);
-    load_opps<JMAX>(a.states[s], r.sk, r.o);
-    *reinterpret_cast<BatchRec<JMAX>*>(a.recs + (size_t)s * kBatchRecStride) = r;
+    StateRec<JMAX> r;
+    make_state_rec<JMAX>(a.states[s], a.prm, a.kmax, r);
+    *reinterpret_cast<StateRec<JMAX>*>(a.recs + (size_t)s * kBatchRecStride) = r;
 }
 
 template <int JMAX, int VMAX, int TPB, int KU>

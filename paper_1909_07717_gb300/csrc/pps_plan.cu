@@ -67,7 +67,7 @@ struct pps_plan {
     unsigned long long* d_keys = nullptr;
     int* d_counts = nullptr;
     unsigned long long* d_next = nullptr;  // one work-queue counter per group
-    unsigned char* d_recs = nullptr;       // per-state records (BatchRec)
+    unsigned char* d_recs = nullptr;       // per-state records (StateRec)
     size_t b_jobs = 0, b_states = 0, b_start = 0, b_mask = 0, b_keys = 0,
            b_counts = 0, b_next = 0, b_recs = 0;
     // autotuning and graph replay

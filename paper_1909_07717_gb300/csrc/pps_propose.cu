@@ -13,6 +13,7 @@
 #include "pps_internal.h"
 #include "pps_cells.cuh"
 #include "pps_search.cuh"
+#include "pps_staterec.cuh"
 #include "pps_warpcopy.cuh"
 
 char* pps_thread_error_buffer();
@@ -39,15 +40,10 @@ __device__ __forceinline__ long long next_item(unsigned long long* queue,
     return (long long)__shfl_sync(0xffffffffu, q, 0);
 }
 
-// A state's derived constants and scaled opponents (derive_state and
-// load_opps, the same values), prepared once a call for the large-batch
-// refinement: its items (half cells, rank-major) come from many states in
-// turn, and deriving them per item took a fifth of its time.
-template <int JMAX>
-struct __align__(16) StateRec {
-    pps::StateK sk;
-    pps::OppRegs<JMAX> o;
-};
+// The large-batch refinement's items (half cells, rank-major) come from
+// many states in turn; deriving each state per item took a fifth of its
+// time, so the states' records are prepared once a call.
+using pps::StateRec;
 static_assert(sizeof(StateRec<PPS_MAX_OPP>) <= kPpsStateRecBytes,
               "the network's per-state scratch holds a record");
 
@@ -58,8 +54,7 @@ __global__ void __launch_bounds__(128)
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= a.n_states) return;
     StateRec<JMAX> r;
-    r.sk = pps::derive_state(a.states[s], a.prm, JMAX, a.kmax);
-    pps::load_opps<JMAX>(a.states[s], r.sk, r.o);
+    pps::make_state_rec<JMAX>(a.states[s], a.prm, a.kmax, r);
     recs[s] = r;
 }
 
